@@ -1,0 +1,79 @@
+"""The seeded input generators: determinism, value ranges, the stated recipes."""
+import math
+
+import numpy as np
+import pytest
+
+from gen import grids
+
+
+def test_splitmix64_reference_values():
+    # SplitMix64 output sequence for state 0 (Steele, Lea & Flood 2014;
+    # the generator as published by Vigna): first outputs of next() from seed 0
+    x = np.array([0], dtype=np.uint64)
+    assert int(grids.splitmix64(x)[0]) == 0xE220A8397B1DCDAF
+    x2 = np.array([0x9E3779B97F4A7C15], dtype=np.uint64)
+    assert int(grids.splitmix64(x2)[0]) == 0x6E789E6AA1B965F4
+
+
+def test_deterministic():
+    a, b = grids.config0(3), grids.config0(3)
+    assert grids.instance_digest(a) == grids.instance_digest(b)
+    assert grids.instance_digest(a) != grids.instance_digest(grids.config0(4))
+
+
+def test_config0_recipe():
+    g = grids.config0(0)
+    assert g.dims == (256, 256, 1) and g.conn == 4 and g.nlink.shape == (2, 65536)
+    I = grids.value_noise_2d(256, 256, 0).ravel()
+    assert I.min() == 0 and I.max() == 255
+    np.testing.assert_array_equal(g.cs, np.abs(I - 80))
+    np.testing.assert_array_equal(g.ct, np.abs(I - 170))
+    # n-link = round(100 exp(-dI^2 / 800)) between right neighbours
+    Im = I.reshape(256, 256)
+    d = np.abs(Im[:, 1:] - Im[:, :-1])
+    want = np.floor(100 * np.exp(-d.astype(float) ** 2 / 800.0) + 0.5).astype(np.int32)
+    np.testing.assert_array_equal(g.nlink[0].reshape(256, 256)[:, :-1], want)
+    assert (g.nlink[0].reshape(256, 256)[:, -1] == 0).all()
+    assert (g.nlink[1].reshape(256, 256)[-1, :] == 0).all()
+
+
+def test_config1_hard_seeds_small():
+    g = grids.segmentation_2d(256, 256, 1, conn=8, hard_seed_frac=0.05)
+    hard = (g.cs == 10 ** 6) | (g.ct == 10 ** 6)
+    assert 0.04 < hard.mean() < 0.06
+    assert ((g.cs == 10 ** 6) <= (g.ct == 0)).all()
+    diag = grids.nlink_lut(100, 20, diag=True)
+    assert diag[0] == 71 and round(100 / math.sqrt(2)) == 71
+    # edges to (-1,+1) vanish on the first column and last row
+    nl3 = g.nlink[3].reshape(256, 256)
+    assert (nl3[:, 0] == 0).all() and (nl3[-1, :] == 0).all()
+
+
+def test_volume_luts():
+    bg = grids.neglog_gauss_lut(80.0, 30.0)
+    c = 10 * math.log(30 * math.sqrt(2 * math.pi))
+    assert bg[80] == round(c)
+    assert bg[0] == math.floor(c + 10 * 80 ** 2 / 1800 + 0.5)
+    assert (grids.nlink_lut(50, 15) <= 50).all() and grids.nlink_lut(50, 15)[0] == 50
+
+
+def test_volume_small():
+    g = grids.volume_3d(20, 18, 9, 0)
+    assert g.nlink.shape == (3, 20 * 18 * 9)
+    assert g.cs.min() >= 0 and g.ct.min() >= 0
+    nl = g.nlink.reshape(3, 9, 18, 20)
+    assert (nl[0, :, :, -1] == 0).all() and (nl[1, :, -1, :] == 0).all() and (nl[2, -1] == 0).all()
+
+
+def test_config3_mu_range():
+    for s in range(5):
+        g = grids.config3(s, side=64)
+        assert g.cs.max() <= 200 and g.ct.max() <= 200
+
+
+def test_config4_shapes():
+    sh = grids.config4_shapes(0)
+    assert len(sh) == 512
+    assert all(64 <= s[0] <= 1024 and s[2] == 1 for s in sh[:384])
+    assert all(48 <= s[0] <= 128 and s[0] == s[2] for s in sh[384:])
