@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Benchmark: exact max-flow / min-cut solve of the 2048x2048 8-connected
+segmentation grid (4.19M vertices, 33.5M arcs, 5% hard seeds at 10^6,
+1024 regions of 64x64) by the CUDA P-ARD solver, through the C ABI.
+
+One step = one mf_solve from capacities already resident on the device:
+Init, all sweeps of Algorithm 2 (discharge, fusion, global gap), the cut
+extraction (S_min, S_max) and the flow value, all on the GPU.
+
+Prints one JSON line (rank 0).  Multi-GPU: one process per GPU
+(torchrun), each rank solves its own instance (seed = rank): replicas, weak
+scaling, no data-path collective.  ``--impl reference`` times the CPU
+oracle (Dinic) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact-maxflow solve ms + sweeps per instance, learned/batched vs plain; HBM GB/s"
+UNIT = "ms/instance"
+SIDE = 2048
+TILE = (64, 64, 1)
+CONN = 8
+BYTES_PER_VERTEX = (CONN + 3) * 4 * 2  # read + write of cap[8], tcap, exc, lab (int32)
+L2_FLUSH_BYTES = 256 << 20
+REF_SAMPLE_SIDE = 1024
+
+
+def workload_name(side=SIDE):
+    return (f"seg2d {side}x{side} 8-connected, value-noise intensity, cs=|I-80| ct=|I-170|, "
+            f"n-links round(100exp(-dI^2/800)) (diagonals /sqrt2), 5% hard seeds at 1e6, "
+            f"{TILE[0]}x{TILE[1]} regions")
+
+
+def make_instance(seed, side=SIDE):
+    from gen import grids
+    return grids.config1(seed=seed, side=side)
+
+
+def directed_arcs(dims):
+    from gen.grids import FWD
+    X, Y, _ = dims
+    return 2 * sum((X - abs(dx)) * (Y - abs(dy)) for dx, dy, _ in FWD[CONN])
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id):
+        self.dev_id = dev_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev_id), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                rows.append((float(p[0]), float(p[1]), p[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, f in enumerate(fl) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def committed_traffic():
+    """DRAM bytes per discharged vertex of the discharge kernel from the
+    committed ncu summary, or None if the kernel source changed since."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ard_discharge_seg2d_2048_c8.txt")
+    src = os.path.join(ROOT, "paper_1109_1146_gb300", "csrc", "ard_discharge.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        kv = {}
+        for ln in open(p):
+            if ln.startswith("bench:"):
+                k, v = ln[len("bench:"):].split("=", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_sha256_16") != sha:
+            return None
+        return float(kv["dram_bytes_per_discharged_vertex"])
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1109_1146_gb300 import Grid, default_opts
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    inst = make_instance(seed=rank)
+    stream = torch.cuda.current_stream()
+    cs = torch.from_numpy(inst.cs).to(dev)
+    ct = torch.from_numpy(inst.ct).to(dev)
+    nl = torch.from_numpy(inst.nlink).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    g = Grid(inst.dims, CONN, tile=TILE, stream=stream)
+    g.set_caps(cs, ct, nl)
+    opts = default_opts()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        g.solve(opts)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    with ClockSampler(f"GPU-{uuid}" if uuid else local) as clk:
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between timed iterations (not timed)
+            ev[k][0].record(stream)
+            stats.append(g.solve(opts))
+            ev[k][1].record(stream)
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(total, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(total.item())
+    flow = g.flow_value()
+
+    # end to end through the public API with host buffers (pinned)
+    pc = torch.from_numpy(inst.cs).pin_memory()
+    pt = torch.from_numpy(inst.ct).pin_memory()
+    pn = torch.from_numpy(inst.nlink).pin_memory()
+    cut_host = torch.empty(inst.n, dtype=torch.uint8).pin_memory()
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_caps(pc, pt, pn)
+        g.solve(opts)
+        g.get_cut(0, out=cut_host)
+        f_host = g.flow_value()
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+        assert f_host == flow
+    e2e = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(e2e, op=torch.distributed.ReduceOp.MAX)
+    g.close()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+
+    units = ws * args.steps
+    value = total_ms / units
+    sweeps = statistics.mean(s.sweeps for s in stats)
+    dis_ms = sum(s.ms_discharge for s in stats)
+    dis_launches = sum(s.sweeps for s in stats)
+    dis_vertices = sum(s.discharged_vertices for s in stats)
+    alg_bytes = dis_vertices * BYTES_PER_VERTEX
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (dis_ms * 1e-3) / 1e9 if dis_ms > 0 else 0.0
+    tb = committed_traffic()
+    traffic = None if tb is None else tb * dis_vertices / dis_launches
+    solve_bytes = alg_bytes / args.steps
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": workload_name(), "vertices": inst.n, "directed_arcs": directed_arcs(inst.dims),
+                   "tile": list(TILE), "regions": (SIDE // TILE[0]) ** 2, "seed": "rank",
+                   "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MiB write)",
+                   "flow_value": flow},
+        "sweeps_per_instance": sweeps,
+        "vertices_per_s": inst.n / (value * 1e-3),
+        "hbm_gbs_solve": solve_bytes / (value * 1e-3) / 1e9,
+        "phase_ms": {"discharge": dis_ms / args.steps, "fuse_gap": sum(s.ms_fuse for s in stats) / args.steps,
+                     "cut": sum(s.ms_cut for s in stats) / args.steps,
+                     "init": sum(s.ms_init for s in stats) / args.steps},
+        "roofline": {"kernel": "ard_discharge_kernel<8,64,64,1,1024>", "bound": "hbm",
+                     "achieved": round(achieved, 2), "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "unit": "GB/s", "frac": round(achieved / peak, 5),
+                     "traffic": None if traffic is None else round(traffic),
+                     "alg_bytes_per_launch": round(alg_bytes / dis_launches),
+                     "launch_ms_avg": round(dis_ms / dis_launches, 4)},
+        "e2e": {"value": round(float(e2e.item()) / units, 4), "unit": UNIT,
+                "h2d_bytes_per_step": int(inst.cs.nbytes + inst.ct.nbytes + inst.nlink.nbytes),
+                "d2h_bytes_per_step": int(inst.n + 8)},
+        "gpu_launches": int(sum(s.launches for s in stats)),
+        "clocks": clk.summary(),
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.solve_instance(inst)
+        t1 = time.perf_counter()
+        assert ref["flow"] == flow, (ref["flow"], flow)
+        line["cpu_baseline"] = {"value": round((t1 - t0) * 1e3, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "the full instance (seed 0): Dinic on the explicit s-t network + "
+                                          "S_min/S_max BFS, single thread"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    inst = make_instance(seed=0, side=REF_SAMPLE_SIDE)
+    scale = (SIDE * SIDE) / inst.n
+    for _ in range(args.warmup):
+        oracle.solve_instance(inst)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve_instance(inst)
+    t1 = time.perf_counter()
+    value = (t1 - t0) * 1e3 / args.steps * scale
+    sample = (f"{REF_SAMPLE_SIDE}x{REF_SAMPLE_SIDE} instance of the same recipe per step (1/{scale:g} of the "
+              f"vertices), time scaled x{scale:g} to one {SIDE}x{SIDE} instance")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 2),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": workload_name(), "vertices": SIDE * SIDE,
+                                            "parallelism": "1 host thread"},
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

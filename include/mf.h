@@ -1,0 +1,180 @@
+/*
+ * mf.h — C ABI of the GB300 grid max-flow / min-cut solver.
+ *
+ * The solver computes a maximum preflow and the minimum s-t cuts of a 2D or 3D
+ * grid network by the parallel sweep of Augmented-path Region Discharge
+ * (P-ARD): Algorithm 2 of Shekhovtsov & Hlavac, "A Distributed Mincut/Maxflow
+ * Algorithm Combining Path Augmentation and Push-Relabel", with the region
+ * discharge of Sec. 4.2 (Procedure ARD, Procedure Augment) and the
+ * region-relabel and global-gap heuristics of Sec. 5.1.  Every region (a tile
+ * of the grid) is discharged by one CUDA thread block per sweep; the flow and
+ * label fusion of Algorithm 2 runs in a separate kernel.  Integer arithmetic
+ * only (int32 capacities, int64 flow value); the results are exact.
+ *
+ * The problem (Sec. 2, Eq. 1): minimise over source sets S
+ *     sum_{v not in S} cs(v) + sum_{v in S} ct(v) + sum_{u in S, w not in S} c(u,w)
+ * where cs / ct are the source / sink link capacities of each grid vertex and
+ * c(u,w) = c(w,u) >= 0 the capacity of the neighbour edge {u,w}.
+ *
+ * Conventions shared by every entry point:
+ *   - vertex index v = (z*Y + y)*X + x (x fastest); n = X*Y*Z (Z = 1 in 2D);
+ *   - connectivity 4 or 8 (2D) or 6 (3D) with the forward half-stencil
+ *       4: h0 = (+1,0)   h1 = (0,+1)
+ *       8: h0 = (+1,0)   h1 = (0,+1)   h2 = (+1,+1)   h3 = (-1,+1)
+ *       6: h0 = (+1,0,0) h1 = (0,+1,0) h2 = (0,0,+1)
+ *     and H = connectivity/2;
+ *   - arc directions d = 0..2H-1: D(2h) = +h-th offset, D(2h+1) = -h-th
+ *     offset; the reverse of d is d^1;
+ *   - all arrays are dense int32 (or uint8) and row-major as above;
+ *   - every call returns an mf_status; no C++ exception crosses the ABI;
+ *     mf_last_error() gives a message for the last failing call on a handle;
+ *   - input buffers stay owned by the caller and are copied; the handle owns
+ *     all device memory it allocates; output buffers are caller-allocated;
+ *   - "on_device" pointers are CUDA device pointers on the handle's device
+ *     (e.g. the data_ptr() of a torch.cuda tensor); otherwise host pointers;
+ *   - all work is ordered on the handle's stream; calls that return host data
+ *     synchronise that stream.
+ * The library has no CPU fallback: without a CUDA device mf_create_grid
+ * fails with MF_ECUDA.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mf_grid mf_grid; /* opaque; owns all device memory of one instance */
+
+typedef enum {
+    MF_OK = 0,
+    MF_EINVAL = 1,       /* bad argument (dims, connectivity, tile, null pointer, negative capacity) */
+    MF_ENOMEM = 2,       /* device or host allocation failed */
+    MF_ECUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error string) */
+    MF_EOVERFLOW = 4,    /* capacities could overflow the int32 residual arithmetic */
+    MF_ESWEEPLIMIT = 5,  /* opts.max_sweeps reached with active vertices left (state consistent) */
+    MF_EROUNDLIMIT = 6,  /* a device-side loop hit its iteration cap (state consistent) */
+    MF_ESTATE = 7        /* call out of order, e.g. mf_solve before mf_set_caps */
+} mf_status;
+
+/* Solver options.  mf_default_opts() fills the defaults. */
+typedef struct {
+    int32_t max_sweeps;            /* sweep cap; 0 = 2|B|^2+1 (the P-ARD bound, Sec. 4.4), clamped to 2^30 */
+    int32_t partial_discharge;     /* 1: sweep s runs only ARD stages k <= s (Sec. 6.2); default 0 */
+    int32_t global_gap;            /* 1: global gap heuristic after each sweep (Sec. 5.1); default 1 */
+    int32_t global_relabel_period; /* P > 0: exact region-distance relabel every P sweeps; 0 = off (default) */
+    int32_t max_rounds;            /* cap on Augment rounds per stage inside one discharge; 0 = default 65536 */
+    int32_t reserved[11];
+} mf_opts;
+
+/* Statistics of the last mf_solve (all optional reading). */
+typedef struct {
+    int32_t sweeps;              /* sweeps of Algorithm 2 performed */
+    int32_t boundary_size;       /* |B| of Sec. 4.1; d_inf = max(|B|, 1) */
+    int64_t discharges;          /* region discharges performed (skipped regions not counted) */
+    int64_t discharged_vertices; /* grid vertices inside the discharged regions, summed */
+    int64_t stages;              /* ARD stages run, summed over discharges */
+    int64_t rounds;              /* Augment rounds (BFS + layered push), summed */
+    int64_t flow_value;          /* |f| (same as mf_flow_value) */
+    int64_t launches;            /* CUDA kernels the solve launched */
+    int32_t gaps;                /* sweeps in which the global gap raised labels */
+    int32_t cut_passes;          /* passes of the cut-extraction closure */
+    double ms_init, ms_sweeps, ms_cut, ms_total; /* device time per phase (CUDA events on the stream) */
+    double ms_discharge;         /* device time of the discharge kernels alone, summed */
+    double ms_fuse;              /* device time of fusion + gap + activity kernels, summed */
+    int32_t reserved[8];
+} mf_stats;
+
+/* Fill *opts with the defaults listed in mf_opts. */
+void mf_default_opts(mf_opts *opts);
+
+/*
+ * Create a grid instance on the current CUDA device.
+ *   ndim          2 or 3;
+ *   dims          {X, Y, Z} (Z ignored and taken as 1 when ndim = 2), each >= 1;
+ *   connectivity  4 or 8 for ndim = 2, 6 for ndim = 3;
+ *   tile          region shape {tx, ty, tz}: the fixed partition of V into
+ *                 regions R_k of Sec. 3 is the tiling of the grid by this
+ *                 shape (edge tiles may be ragged).  Supported: 2D 64x64 and
+ *                 32x32, 3D 16x16x16 and 8x8x8; NULL or {0,0,0} picks 64x64
+ *                 (2D) / 16^3 (3D);
+ *   cuda_stream   cudaStream_t to order all work on, or NULL for a stream
+ *                 owned by the handle.
+ * Allocates the device state (about (2H+6)*4 + 1 bytes per vertex plus a
+ * second copy of the inputs).  On failure *out is NULL.
+ */
+mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int connectivity,
+                         const int32_t tile[3], void *cuda_stream);
+
+/*
+ * Set the capacities (Sec. 2: c : E -> N0, cs / ct the terminal links).
+ *   cs, ct  int32[n], >= 0;
+ *   nlink   int32[H][n]: nlink[h*n + v] = c(v, v + h-th forward offset)
+ *           = c(v + offset, v); entries whose neighbour is outside the grid
+ *           must be 0;
+ *   on_device  0: host pointers, 1: device pointers; both are copied.
+ * Errors: MF_EINVAL for negative capacities or nonzero links leaving the
+ * grid; MF_EOVERFLOW if cs(v) plus the capacities of all edges at v could
+ * exceed INT32_MAX, or if 2 c(u,w) could.
+ */
+mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const int32_t *nlink,
+                      int on_device);
+
+/*
+ * Solve: Init (Sec. 2: saturate every s-link; the part min(cs, ct) of each
+ * vertex is sent s -> v -> t at once and counted in the flow value), then
+ * sweeps of Algorithm 2 with Discharge = ARD until no vertex is active, then
+ * the cut extraction.  opts may be NULL (defaults); stats may be NULL.
+ * May be called again (it restarts from the stored capacities).
+ * Errors: MF_ESTATE before mf_set_caps; MF_ESWEEPLIMIT / MF_EROUNDLIMIT when
+ * a cap is hit (the preflow and labels stay valid; results are not final).
+ */
+mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats);
+
+/*
+ * Step-wise form of mf_solve for inspection: mf_begin runs Init; each
+ * mf_sweep runs one sweep of Algorithm 2 (discharge of every active region,
+ * fusion, global gap) and returns the number of regions left active;
+ * mf_finish extracts the cuts and the flow value.  mf_solve = begin, sweeps
+ * until 0 active regions, finish.
+ */
+mf_status mf_begin(mf_grid *g, const mf_opts *opts);
+mf_status mf_sweep(mf_grid *g, int32_t *active_regions);
+mf_status mf_finish(mf_grid *g);
+
+/*
+ * Minimum cut after a successful solve: out[v] = 1 if v is on the source side.
+ *   which = 0: S_min, the closure of {v : e(v) > 0} under residual arcs
+ *              (the minimal minimum-cut source set);
+ *   which = 1: S_max = V minus {v : v -> t in G_f} (the cut (T-bar, T) of Sec. 2).
+ * out is uint8[n] (host, or device when on_device = 1).
+ */
+mf_status mf_get_cut(mf_grid *g, uint8_t *out, int which, int on_device);
+
+/* |f| = sum of min(cs, ct) plus all flow the sweeps sent into t (int64). */
+mf_status mf_flow_value(mf_grid *g, int64_t *out);
+
+/*
+ * Final (or current, after mf_sweep) residual network:
+ *   res  int32[2H][n]: res[d*n + v] = residual capacity of the arc v -> v + D(d);
+ *   tres int32[n]: residual of v -> t;  exc int32[n]: excess e_f(v).
+ * Any of the three may be NULL.  Host or device buffers per on_device.
+ */
+mf_status mf_get_residual(mf_grid *g, int32_t *res, int32_t *tres, int32_t *exc, int on_device);
+
+/* Current labeling d (int32[n], values 0..d_inf) and d_inf. */
+mf_status mf_get_labels(mf_grid *g, int32_t *lab, int32_t *d_inf, int on_device);
+
+/* Free the handle and all its device memory (NULL is a no-op). */
+mf_status mf_destroy(mf_grid *g);
+
+/* Message of the last failing call on g ("" if none; static text if g is NULL). */
+const char *mf_last_error(const mf_grid *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H */

@@ -1,0 +1,659 @@
+// C ABI (include/mf.h) and the non-discharge kernels of the P-ARD sweep:
+//   init      Init of Sec. 2 plus the terminal reduction;
+//   fuse      label and flow fusion of Algorithm 2 on inter-region arcs;
+//   gap_find  global gap of Sec. 5.1 on the histogram of boundary labels;
+//   post      gap application, region activity for the next sweep;
+//   cut       residual closures giving S_min and S_max.
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/mf.h"
+#include "mf_internal.cuh"
+
+using namespace mf;
+
+struct mf_grid {
+    int ndim = 0, conn = 0, H = 0, N = 0;
+    Geom g{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int *cs = nullptr, *ct = nullptr, *nl = nullptr;  // stored inputs
+    DevState st{};
+    unsigned char *smin = nullptr, *tset = nullptr;
+    Counters64 *c64 = nullptr;
+    int *h_ctr = nullptr;                             // pinned mirror of st.ctr
+    long long boundary = 0;
+    bool caps_set = false, begun = false, finished = false;
+    int sweep = 0;
+    mf_opts opts{};
+    mf_stats stats{};
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    long long launches = 0;
+    std::string err;
+};
+
+static thread_local std::string g_static_err;
+
+static mf_status fail(mf_grid *g, mf_status s, const std::string &m) {
+    if (g) g->err = m;
+    else g_static_err = m;
+    return s;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(g, e_ == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device helpers
+__device__ __forceinline__ bool in_grid(const Geom &g, int x, int y, int z) {
+    return x >= 0 && x < g.X && y >= 0 && y < g.Y && z >= 0 && z < g.Z;
+}
+__device__ __forceinline__ int region_of(const Geom &g, int x, int y, int z) {
+    return ((z / g.tz) * g.RY + y / g.ty) * g.RX + x / g.tx;
+}
+
+// Init (Sec. 2): every s-link saturated, f := 0 on the rest, d := 0.  The part
+// min(cs, ct) of a vertex is sent s -> v -> t at once (counted in flow0):
+// exc = cs - min, tcap = ct - min.  cap[d] gets the edge capacity of arc d.
+template <int CONN>
+__global__ void init_kernel(const Geom g, const DevState st, const int *__restrict__ cs,
+                            const int *__restrict__ ct, const int *__restrict__ nl) {
+    const size_t n = (size_t)g.n;
+    long long part = 0;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
+        const int a = cs[v], b = ct[v], m = min(a, b);
+        part += m;
+        st.exc[v] = a - m;
+        st.tcap[v] = b - m;
+        st.lab[v] = 0;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
+            int c = 0;
+            if (in_grid(g, x + dx, y + dy, z + dz)) {
+                const size_t w = ((size_t)(z + dz) * g.Y + (y + dy)) * g.X + (x + dx);
+                c = (d & 1) ? nl[(size_t)(d >> 1) * n + w] : nl[(size_t)(d >> 1) * n + v];
+            }
+            st.cap[(size_t)d * n + v] = c;
+        }
+        if (a - m > 0) st.active[region_of(g, x, y, z)] = 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && part) atomicAdd((unsigned long long *)st.flow0, (unsigned long long)part);
+}
+
+// Input validation for device-resident capacities: bit 0 negative value,
+// bit 1 nonzero link leaving the grid, bit 2 possible int32 overflow.
+template <int CONN>
+__global__ void validate_kernel(const Geom g, const int *cs, const int *ct, const int *nl, int *flags) {
+    const size_t n = (size_t)g.n;
+    int f = 0;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
+        if (cs[v] < 0 || ct[v] < 0) f |= 1;
+        long long sum = cs[v];
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
+            const bool ing = in_grid(g, x + dx, y + dy, z + dz);
+            int c;
+            if (d & 1) {
+                if (!ing) continue;
+                c = nl[(size_t)(d >> 1) * n + ((size_t)(z + dz) * g.Y + (y + dy)) * g.X + (x + dx)];
+            } else {
+                c = nl[(size_t)(d >> 1) * n + v];
+                if (!ing && c != 0) f |= 2;
+            }
+            if (c < 0) f |= 1;
+            if (c > INT_MAX / 2) f |= 4;
+            sum += c;
+        }
+        if (sum > INT_MAX) f |= 4;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+// Flow and label fusion of Algorithm 2, gather form: every boundary vertex u
+// updates only its own arcs and excess.  For an inter-region arc (u,w):
+//   alpha(a,b) = [d'(a) <= d'(b) + 1];
+//   u's push on (u,w) is kept iff alpha(w,u), w's push on (w,u) iff alpha(u,w);
+//   a refused push goes back to its sender (residual and excess restored).
+// Also commits the new boundary labels and counts the gap histogram.
+template <int CONN>
+__global__ void fuse_kernel(const Geom g, const DevState st) {
+    const int r = blockIdx.x;
+    const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+    const int V = g.tx * g.ty * g.tz;
+    const size_t n = (size_t)g.n;
+    const bool discr = st.disc[r];
+    for (int i = threadIdx.x; i < V; i += blockDim.x) {
+        const int x = rx * g.tx + i % g.tx, y = ry * g.ty + (i / g.tx) % g.ty, z = rz * g.tz + i / (g.tx * g.ty);
+        if (!in_grid(g, x, y, z)) continue;
+        const size_t u = ((size_t)z * g.Y + y) * g.X + x;
+        bool boundary = false;
+        int back_total = 0;
+        int du = -1;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d), wz = z + arc_dz(CONN, d);
+            if (!in_grid(g, wx, wy, wz)) continue;
+            const int rw = region_of(g, wx, wy, wz);
+            if (rw == r) continue;
+            if (!boundary) {
+                boundary = true;
+                du = discr ? st.lab_next[u] : st.lab[u];
+            }
+            const size_t w = ((size_t)wz * g.Y + wy) * g.X + wx;
+            const bool discw = st.disc[rw];
+            const int dw = discw ? st.lab_next[w] : st.lab[w];
+            const int pu = discr ? st.bout[(size_t)d * n + u] : 0;
+            const int pw = discw ? st.bout[(size_t)(d ^ 1) * n + w] : 0;
+            const int back = (dw <= du + 1 ? 0 : pu) + (du <= dw + 1 ? pw : 0);
+            if (back) {
+                st.cap[(size_t)d * n + u] += back;
+                back_total += back;
+            }
+        }
+        if (!boundary) continue;
+        if (back_total) st.exc[u] += back_total;
+        if (discr) st.lab[u] = du;
+        if (du < g.dinf) atomicAdd(&st.hist[min(du, kHistBins)], 1);
+    }
+}
+
+// Global gap (Sec. 5.1, with the boundary-label histogram of Sec. 5.3): the
+// smallest g > 0 below the highest boundary label with no boundary vertex
+// labelled g.  Every vertex with g < d < d_inf cannot reach t.
+__global__ void gap_find_kernel(const DevState st) {
+    __shared__ int s_hi, s_g;
+    if (threadIdx.x == 0) { s_hi = 0; s_g = INT_MAX; }
+    __syncthreads();
+    int hi = 0;
+    for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x)
+        if (st.hist[b] > 0) hi = max(hi, b);
+    atomicMax(&s_hi, hi);
+    __syncthreads();
+    const int top = s_hi;  // labels >= kHistBins share the last bin: never a gap there
+    int gmin = INT_MAX;
+    for (int b = 1 + threadIdx.x; b < top && b < kHistBins; b += blockDim.x)
+        if (st.hist[b] == 0) gmin = min(gmin, b);
+    atomicMin(&s_g, gmin);
+    __syncthreads();
+    if (threadIdx.x == 0) st.ctr[kGap] = s_g == INT_MAX ? 0 : s_g;
+}
+
+// Apply the gap, decide which regions discharge next sweep, reset per-sweep flags.
+template <int CONN>
+__global__ void post_kernel(const Geom g, const DevState st) {
+    const int r = blockIdx.x;
+    const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+    const int V = g.tx * g.ty * g.tz;
+    const int gap = st.ctr[kGap];
+    int act = st.left_active[r];
+    for (int i = threadIdx.x; i < V; i += blockDim.x) {
+        const int x = rx * g.tx + i % g.tx, y = ry * g.ty + (i / g.tx) % g.ty, z = rz * g.tz + i / (g.tx * g.ty);
+        if (!in_grid(g, x, y, z)) continue;
+        const size_t u = ((size_t)z * g.Y + y) * g.X + x;
+        int l = st.lab[u];
+        if (gap > 0 && l > gap && l < g.dinf) {
+            l = g.dinf;
+            st.lab[u] = l;
+        }
+        if (!act && l < g.dinf && st.exc[u] > 0) act = 1;
+    }
+    act = __syncthreads_or(act);
+    if (threadIdx.x == 0) {
+        st.active[r] = (unsigned char)act;
+        st.disc[r] = 0;
+        st.left_active[r] = 0;
+        if (act) atomicAdd(&st.ctr[kActiveRegions], 1);
+    }
+}
+
+__global__ void cut_seed_kernel(const Geom g, const DevState st, unsigned char *smin, unsigned char *tset) {
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < (size_t)g.n; v += (size_t)gridDim.x * blockDim.x) {
+        smin[v] = st.exc[v] > 0;
+        tset[v] = st.tcap[v] > 0;
+    }
+}
+
+// One pass of a residual closure, region by region (pull form: a block only
+// writes vertices of its own region).  fwd = 1: w joins if some member u has a
+// residual arc u -> w (S_min, the closure of {e > 0}); fwd = 0: u joins if it
+// has a residual arc u -> w into the set (vertices reaching t).
+template <int CONN>
+__global__ void cut_pass_kernel(const Geom g, const DevState st, unsigned char *set, int fwd) {
+    extern __shared__ unsigned char s_in[];
+    const int r = blockIdx.x;
+    const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+    const int TX = g.tx, TY = g.ty, V = g.tx * g.ty * g.tz;
+    const size_t n = (size_t)g.n;
+    for (int i = threadIdx.x; i < V; i += blockDim.x) {
+        const int x = rx * TX + i % TX, y = ry * TY + (i / TX) % TY, z = rz * g.tz + i / (TX * TY);
+        s_in[i] = in_grid(g, x, y, z) ? set[((size_t)z * g.Y + y) * g.X + x] : 0;
+    }
+    __syncthreads();
+    int grew = 0;
+    for (bool first = true;; first = false) {
+        int ch = 0;
+        for (int i = threadIdx.x; i < V; i += blockDim.x) {
+            if (s_in[i]) continue;
+            const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
+            const int x = rx * TX + lx, y = ry * TY + ly, z = rz * g.tz + lz;
+            if (!in_grid(g, x, y, z)) continue;
+            const size_t u = ((size_t)z * g.Y + y) * g.X + x;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
+                const int wx = x + dx, wy = y + dy, wz = z + dz;
+                if (!in_grid(g, wx, wy, wz)) continue;
+                const size_t w = ((size_t)wz * g.Y + wy) * g.X + wx;
+                const int nlx = lx + dx, nly = ly + dy, nlz = lz + dz;
+                const bool intile = nlx >= 0 && nlx < TX && nly >= 0 && nly < TY && nlz >= 0 && nlz < g.tz;
+                if (!intile && !first) continue;  // other regions: read once per pass
+                const unsigned char member = intile ? s_in[i + dx + dy * TX + dz * TX * TY] : set[w];
+                if (!member) continue;
+                const int res = fwd ? st.cap[(size_t)(d ^ 1) * n + w] : st.cap[(size_t)d * n + u];
+                if (res > 0) {
+                    s_in[i] = 1;
+                    ch = 1;
+                    break;
+                }
+            }
+        }
+        grew |= ch;
+        if (!__syncthreads_or(ch)) break;
+    }
+    if (__syncthreads_or(grew)) {
+        for (int i = threadIdx.x; i < V; i += blockDim.x) {
+            const int x = rx * TX + i % TX, y = ry * TY + (i / TX) % TY, z = rz * g.tz + i / (TX * TY);
+            if (!in_grid(g, x, y, z) || !s_in[i]) continue;
+            const size_t u = ((size_t)z * g.Y + y) * g.X + x;
+            if (!set[u]) set[u] = 1;
+        }
+        if (threadIdx.x == 0) st.ctr[kChanged] = 1;
+    }
+}
+
+__global__ void complement_kernel(unsigned char *a, size_t n) {
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+        a[v] = !a[v];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+static int grid_blocks(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    return (int)std::min<size_t>(std::max<size_t>(b, 1), 152 * 16);
+}
+
+template <int CONN>
+static cudaError_t launch_init(mf_grid *h) {
+    init_kernel<CONN><<<grid_blocks(h->g.n, 256), 256, 0, h->stream>>>(h->g, h->st, h->cs, h->ct, h->nl);
+    return cudaGetLastError();
+}
+template <int CONN>
+static cudaError_t launch_validate(mf_grid *h, int *flags) {
+    validate_kernel<CONN><<<grid_blocks(h->g.n, 256), 256, 0, h->stream>>>(h->g, h->cs, h->ct, h->nl, flags);
+    return cudaGetLastError();
+}
+template <int CONN>
+static cudaError_t launch_fuse_post(mf_grid *h, bool gap_on) {
+    fuse_kernel<CONN><<<h->g.nreg, 256, 0, h->stream>>>(h->g, h->st);
+    if (gap_on) gap_find_kernel<<<1, 1024, 0, h->stream>>>(h->st);
+    post_kernel<CONN><<<h->g.nreg, 256, 0, h->stream>>>(h->g, h->st);
+    return cudaGetLastError();
+}
+template <int CONN>
+static cudaError_t launch_cut_pass(mf_grid *h, unsigned char *set, int fwd) {
+    const int V = h->g.tx * h->g.ty * h->g.tz;
+    cut_pass_kernel<CONN><<<h->g.nreg, 256, V, h->stream>>>(h->g, h->st, set, fwd);
+    return cudaGetLastError();
+}
+
+#define DISPATCH(conn, fn, ...) \
+    ((conn) == 4 ? fn<4>(__VA_ARGS__) : (conn) == 8 ? fn<8>(__VA_ARGS__) : fn<6>(__VA_ARGS__))
+
+// |B| of Sec. 4.1 for a tiling: a vertex is a boundary vertex iff along some
+// axis it is the first cell of a tile (not at 0) or the last (not at the end);
+// the same set for 4- and 8-connectivity (diagonal neighbours in another tile
+// imply a straight one) and for the 6-connected 3D stencil.
+static long long boundary_count(const Geom &g) {
+    auto inner = [](long long D, long long T) {
+        long long b = 0;
+        for (long long c = 0; c < D; ++c)
+            if ((c % T == 0 && c > 0) || (c % T == T - 1 && c < D - 1)) ++b;
+        return D - b;
+    };
+    return (long long)g.n - inner(g.X, g.tx) * inner(g.Y, g.ty) * inner(g.Z, g.tz);
+}
+
+extern "C" {
+
+void mf_default_opts(mf_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->max_sweeps = 0;
+    o->partial_discharge = 0;
+    o->global_gap = 1;
+    o->global_relabel_period = 0;
+    o->max_rounds = 0;
+}
+
+const char *mf_last_error(const mf_grid *g) { return g ? g->err.c_str() : g_static_err.c_str(); }
+
+static void free_all(mf_grid *h) {
+    void *ptrs[] = {h->cs, h->ct, h->nl, h->st.cap, h->st.tcap, h->st.exc, h->st.lab, h->st.lab_next,
+                    h->st.bout, h->st.active, h->st.disc, h->st.left_active, h->st.flow_t, h->st.flow0,
+                    h->st.hist, h->st.ctr, h->smin, h->tset, h->c64};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    for (auto &e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int connectivity,
+                         const int32_t tile[3], void *cuda_stream) {
+    mf_grid *g = nullptr;
+    if (!out) return fail(nullptr, MF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(nullptr, MF_EINVAL, "dims is NULL");
+    if (!((ndim == 2 && (connectivity == 4 || connectivity == 8)) || (ndim == 3 && connectivity == 6)))
+        return fail(nullptr, MF_EINVAL, "connectivity must be 4 or 8 (ndim 2) or 6 (ndim 3)");
+    long long X = dims[0], Y = dims[1], Z = ndim == 3 ? dims[2] : 1;
+    if (X < 1 || Y < 1 || Z < 1 || X > INT_MAX || Y > INT_MAX || Z > INT_MAX)
+        return fail(nullptr, MF_EINVAL, "dims must be >= 1");
+    long long nll = X * Y * Z;
+    if (nll > (1ll << 31) - 1) return fail(nullptr, MF_EINVAL, "more than 2^31-1 vertices");
+    int tx = 64, ty = 64, tz = 1;
+    if (ndim == 3) tx = ty = tz = 16;
+    if (tile && (tile[0] | tile[1] | tile[2])) {
+        tx = tile[0];
+        ty = tile[1];
+        tz = ndim == 3 ? tile[2] : 1;
+    }
+    if (!discharge_supported(connectivity, tx, ty, tz))
+        return fail(nullptr, MF_EINVAL, "unsupported tile shape for this connectivity");
+    g = new (std::nothrow) mf_grid();
+    if (!g) return fail(nullptr, MF_ENOMEM, "host allocation failed");
+    g->ndim = ndim;
+    g->conn = connectivity;
+    g->H = connectivity / 2;
+    g->N = connectivity;
+    Geom &G = g->g;
+    G.X = (int)X; G.Y = (int)Y; G.Z = (int)Z; G.n = nll;
+    G.tx = tx; G.ty = ty; G.tz = tz;
+    G.RX = (int)((X + tx - 1) / tx); G.RY = (int)((Y + ty - 1) / ty); G.RZ = (int)((Z + tz - 1) / tz);
+    G.nreg = G.RX * G.RY * G.RZ;
+    g->boundary = boundary_count(G);
+    G.dinf = (int)std::max<long long>(g->boundary, 1);
+    auto bail = [&](mf_status s) { free_all(g); std::string m = g->err; delete g; g_static_err = m; return s; };
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) { g->err = std::string("no CUDA device: ") + cudaGetErrorString(e); return bail(MF_ECUDA); }
+    if (cuda_stream) {
+        g->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MF_ECUDA); }
+        g->own_stream = true;
+    }
+    const size_t N = (size_t)connectivity;
+    const size_t n = (size_t)nll;
+    struct A { void **p; size_t bytes; } allocs[] = {
+        {(void **)&g->cs, n * 4}, {(void **)&g->ct, n * 4}, {(void **)&g->nl, (N / 2) * n * 4},
+        {(void **)&g->st.cap, N * n * 4}, {(void **)&g->st.tcap, n * 4}, {(void **)&g->st.exc, n * 4},
+        {(void **)&g->st.lab, n * 4}, {(void **)&g->st.lab_next, n * 4}, {(void **)&g->st.bout, N * n * 4},
+        {(void **)&g->st.active, (size_t)G.nreg}, {(void **)&g->st.disc, (size_t)G.nreg},
+        {(void **)&g->st.left_active, (size_t)G.nreg}, {(void **)&g->st.flow_t, 8}, {(void **)&g->st.flow0, 8},
+        {(void **)&g->st.hist, (kHistBins + 1) * 4}, {(void **)&g->st.ctr, kCtrWords * 4},
+        {(void **)&g->smin, (size_t)n}, {(void **)&g->tset, (size_t)n}, {(void **)&g->c64, sizeof(Counters64)}};
+    for (auto &a : allocs) {
+        e = cudaMalloc(a.p, a.bytes);
+        if (e != cudaSuccess) {
+            g->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+            return bail(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA);
+        }
+    }
+    e = cudaMallocHost((void **)&g->h_ctr, kCtrWords * 4);
+    if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MF_ENOMEM); }
+    for (auto &ev : g->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MF_ECUDA); }
+    }
+    e = cudaMemsetAsync(g->st.disc, 0, (size_t)G.nreg, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->st.left_active, 0, (size_t)G.nreg, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->st.bout, 0, N * n * 4, g->stream);
+    if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MF_ECUDA); }
+    mf_default_opts(&g->opts);
+    *out = g;
+    return MF_OK;
+}
+
+mf_status mf_destroy(mf_grid *g) {
+    if (!g) return MF_OK;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    free_all(g);
+    delete g;
+    return MF_OK;
+}
+
+mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const int32_t *nlink, int on_device) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!cs || !ct || !nlink) return fail(g, MF_EINVAL, "cs, ct and nlink must be non-NULL");
+    const size_t n = (size_t)g->g.n, H = (size_t)g->H;
+    g->caps_set = false;
+    g->begun = g->finished = false;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(g->cs, cs, n * 4, kind, g->stream));
+    CK(cudaMemcpyAsync(g->ct, ct, n * 4, kind, g->stream));
+    CK(cudaMemcpyAsync(g->nl, nlink, H * n * 4, kind, g->stream));
+    CK(cudaMemsetAsync(g->st.ctr, 0, kCtrWords * 4, g->stream));
+    CK(DISPATCH(g->conn, launch_validate, g, &g->st.ctr[kError]));
+    CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    const int f = g->h_ctr[kError];
+    if (f & 1) return fail(g, MF_EINVAL, "negative capacity");
+    if (f & 2) return fail(g, MF_EINVAL, "nonzero neighbour capacity leaving the grid");
+    if (f & 4) return fail(g, MF_EOVERFLOW, "capacities could overflow int32");
+    g->caps_set = true;
+    return MF_OK;
+}
+
+mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
+    if (opts) g->opts = *opts;
+    else mf_default_opts(&g->opts);
+    if (g->opts.max_rounds <= 0) g->opts.max_rounds = 1 << 16;
+    const size_t nreg = (size_t)g->g.nreg;
+    CK(cudaMemsetAsync(g->st.active, 0, nreg, g->stream));
+    CK(cudaMemsetAsync(g->st.disc, 0, nreg, g->stream));
+    CK(cudaMemsetAsync(g->st.left_active, 0, nreg, g->stream));
+    CK(cudaMemsetAsync(g->st.flow_t, 0, 8, g->stream));
+    CK(cudaMemsetAsync(g->st.flow0, 0, 8, g->stream));
+    CK(cudaMemsetAsync(g->st.ctr, 0, kCtrWords * 4, g->stream));
+    CK(cudaMemsetAsync(g->c64, 0, sizeof(Counters64), g->stream));
+    CK(DISPATCH(g->conn, launch_init, g));
+    g->launches = 1;
+    g->sweep = 0;
+    g->begun = true;
+    g->finished = false;
+    memset(&g->stats, 0, sizeof(g->stats));
+    g->stats.boundary_size = (int32_t)g->boundary;
+    return MF_OK;
+}
+
+static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
+    SweepArgs sa;
+    sa.sweep = g->sweep;
+    sa.partial = g->opts.partial_discharge;
+    sa.max_rounds = g->opts.max_rounds;
+    sa.c64 = g->c64;
+    CK(cudaMemsetAsync(g->st.hist, 0, (kHistBins + 1) * 4, g->stream));
+    CK(cudaMemsetAsync(g->st.ctr, 0, 4 * (kGap + 1), g->stream));  // active count, error, gap
+    CK(cudaEventRecord(g->ev[4], g->stream));
+    CK(launch_discharge(g->conn, g->g, g->st, sa, g->stream));
+    CK(cudaEventRecord(g->ev[5], g->stream));
+    CK(DISPATCH(g->conn, launch_fuse_post, g, g->opts.global_gap != 0));
+    CK(cudaEventRecord(g->ev[6], g->stream));
+    g->launches += g->opts.global_gap ? 4 : 3;
+    CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    {
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, g->ev[4], g->ev[5]);
+        cudaEventElapsedTime(&b, g->ev[5], g->ev[6]);
+        g->stats.ms_discharge += a;
+        g->stats.ms_fuse += b;
+    }
+    ++g->sweep;
+    g->stats.sweeps = g->sweep;
+    if (g->h_ctr[kGap] > 0) g->stats.gaps++;
+    if (active_out) *active_out = g->h_ctr[kActiveRegions];
+    if (g->h_ctr[kError]) return fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
+    return MF_OK;
+}
+
+mf_status mf_sweep(mf_grid *g, int32_t *active) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!g->begun) return fail(g, MF_ESTATE, "mf_begin has not been called");
+    return run_sweep(g, active);
+}
+
+mf_status mf_finish(mf_grid *g) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!g->begun) return fail(g, MF_ESTATE, "mf_begin has not been called");
+    cut_seed_kernel<<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->g, g->st, g->smin, g->tset);
+    CK(cudaGetLastError());
+    int passes = 0;
+    for (int which = 0; which < 2; ++which) {
+        for (;;) {
+            CK(cudaMemsetAsync(&g->st.ctr[kChanged], 0, 4, g->stream));
+            CK(DISPATCH(g->conn, launch_cut_pass, g, which == 0 ? g->smin : g->tset, which == 0 ? 1 : 0));
+            ++g->launches;
+            CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            ++passes;
+            if (!g->h_ctr[kChanged]) break;
+        }
+    }
+    complement_kernel<<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->tset, (size_t)g->g.n);
+    CK(cudaGetLastError());
+    g->stats.cut_passes = passes;
+    long long f0 = 0;
+    unsigned long long ft = 0;
+    CK(cudaMemcpyAsync(&f0, g->st.flow0, 8, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(&ft, g->st.flow_t, 8, cudaMemcpyDeviceToHost, g->stream));
+    Counters64 c{};
+    CK(cudaMemcpyAsync(&c, g->c64, sizeof(c), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->stats.flow_value = f0 + (long long)ft;
+    g->stats.stages = (int64_t)c.stages;
+    g->stats.rounds = (int64_t)c.rounds;
+    g->stats.discharges = (int64_t)c.discharges;
+    g->stats.discharged_vertices = (int64_t)c.discharged_vertices;
+    g->launches += 2;  // seed + complement
+    g->stats.launches = g->launches;
+    g->finished = true;
+    return MF_OK;
+}
+
+mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    CK(cudaEventRecord(g->ev[0], g->stream));
+    mf_status s = mf_begin(g, opts);
+    if (s != MF_OK) return s;
+    CK(cudaEventRecord(g->ev[1], g->stream));
+    long long cap = g->opts.max_sweeps > 0 ? g->opts.max_sweeps
+                                            : std::min<long long>(2 * g->boundary * g->boundary + 1, 1ll << 30);
+    mf_status rs = MF_OK;
+    for (;;) {
+        int32_t act = 0;
+        rs = run_sweep(g, &act);
+        if (rs != MF_OK) break;
+        if (act == 0) break;
+        if (g->sweep >= cap) {
+            rs = fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left");
+            break;
+        }
+    }
+    CK(cudaEventRecord(g->ev[2], g->stream));
+    if (rs == MF_OK) {
+        s = mf_finish(g);
+        if (s != MF_OK) return s;
+    }
+    CK(cudaEventRecord(g->ev[3], g->stream));
+    CK(cudaEventSynchronize(g->ev[3]));
+    float a = 0, b = 0, c = 0;
+    cudaEventElapsedTime(&a, g->ev[0], g->ev[1]);
+    cudaEventElapsedTime(&b, g->ev[1], g->ev[2]);
+    cudaEventElapsedTime(&c, g->ev[2], g->ev[3]);
+    g->stats.ms_init = a;
+    g->stats.ms_sweeps = b;
+    g->stats.ms_cut = c;
+    g->stats.ms_total = a + b + c;
+    if (stats) *stats = g->stats;
+    return rs;
+}
+
+mf_status mf_get_cut(mf_grid *g, uint8_t *out, int which, int on_device) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!out || (which != 0 && which != 1)) return fail(g, MF_EINVAL, "bad output or which");
+    if (!g->finished) return fail(g, MF_ESTATE, "no finished solve");
+    CK(cudaMemcpyAsync(out, which == 0 ? g->smin : g->tset, (size_t)g->g.n,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+    if (!on_device) CK(cudaStreamSynchronize(g->stream));
+    return MF_OK;
+}
+
+mf_status mf_flow_value(mf_grid *g, int64_t *out) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!out) return fail(g, MF_EINVAL, "out is NULL");
+    if (!g->begun) return fail(g, MF_ESTATE, "no solve");
+    long long f0 = 0;
+    unsigned long long ft = 0;
+    CK(cudaMemcpyAsync(&f0, g->st.flow0, 8, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(&ft, g->st.flow_t, 8, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    *out = f0 + (long long)ft;
+    return MF_OK;
+}
+
+mf_status mf_get_residual(mf_grid *g, int32_t *res, int32_t *tres, int32_t *exc, int on_device) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!g->begun) return fail(g, MF_ESTATE, "no solve");
+    const size_t n = (size_t)g->g.n;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (res) CK(cudaMemcpyAsync(res, g->st.cap, (size_t)g->N * n * 4, k, g->stream));
+    if (tres) CK(cudaMemcpyAsync(tres, g->st.tcap, n * 4, k, g->stream));
+    if (exc) CK(cudaMemcpyAsync(exc, g->st.exc, n * 4, k, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return MF_OK;
+}
+
+mf_status mf_get_labels(mf_grid *g, int32_t *lab, int32_t *d_inf, int on_device) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (d_inf) *d_inf = g->g.dinf;
+    if (lab) {
+        if (!g->begun) return fail(g, MF_ESTATE, "no solve");
+        CK(cudaMemcpyAsync(lab, g->st.lab, (size_t)g->g.n * 4,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+    }
+    return MF_OK;
+}
+
+}  // extern "C"

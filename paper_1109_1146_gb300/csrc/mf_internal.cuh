@@ -1,0 +1,82 @@
+// Internal declarations of the P-ARD grid solver (not part of the C ABI).
+//
+// Device state, all int32 SoA planes over the full grid (plane[d][v], v =
+// (z*Y + y)*X + x):
+//   cap[d]   residual capacity of the arc v -> v + D(d) (Sec. 2, c_f);
+//   tcap     residual capacity of v -> t;
+//   exc      excess e_f(v);
+//   lab      labeling d of Sec. 4.1 (values 0..d_inf);
+//   lab_next new labels of region-boundary vertices written by a discharge and
+//            committed by the fusion kernel (Algorithm 2 fuses labels after
+//            all regions are discharged);
+//   bout[d]  flow a discharge pushed across the region boundary on the arc
+//            v -> v + D(d) (only entries of boundary arcs are used).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mf {
+
+constexpr int kInf = 0x7fffffff;   // "no distance" inside a discharge
+constexpr int kHistBins = 16384;   // exact gap histogram bins; labels >= this share one bin
+
+// forward half-stencil and arc directions (see include/mf.h)
+__host__ __device__ constexpr int fwd_dx(int conn, int h) {
+    return conn == 8 ? (h == 0 ? 1 : h == 1 ? 0 : h == 2 ? 1 : -1) : (h == 0 ? 1 : 0);
+}
+__host__ __device__ constexpr int fwd_dy(int conn, int h) {
+    return conn == 6 ? (h == 1 ? 1 : 0) : (h == 0 ? 0 : 1);
+}
+__host__ __device__ constexpr int fwd_dz(int conn, int h) { return (conn == 6 && h == 2) ? 1 : 0; }
+__host__ __device__ constexpr int arc_dx(int conn, int d) { return (d & 1) ? -fwd_dx(conn, d >> 1) : fwd_dx(conn, d >> 1); }
+__host__ __device__ constexpr int arc_dy(int conn, int d) { return (d & 1) ? -fwd_dy(conn, d >> 1) : fwd_dy(conn, d >> 1); }
+__host__ __device__ constexpr int arc_dz(int conn, int d) { return (d & 1) ? -fwd_dz(conn, d >> 1) : fwd_dz(conn, d >> 1); }
+
+struct Geom {
+    int X, Y, Z;        // grid dims
+    long long n;        // X*Y*Z
+    int tx, ty, tz;     // tile (region) shape
+    int RX, RY, RZ;     // regions per axis
+    int nreg;
+    int dinf;           // d_inf = max(|B|, 1)  (Sec. 4.1)
+};
+
+struct DevState {
+    int *cap, *tcap, *exc, *lab, *lab_next, *bout;
+    unsigned char *active;       // [nreg] region has active vertices -> discharge next sweep
+    unsigned char *disc;         // [nreg] region was discharged in the current sweep
+    unsigned char *left_active;  // [nreg] a discharge left an active vertex (partial discharges)
+    unsigned long long *flow_t;  // flow pushed into t by all discharges
+    long long *flow0;            // sum of min(cs, ct) (terminal reduction)
+    int *hist;                   // [kHistBins + 1] labels of boundary vertices
+    int *ctr;                    // small counters, see Ctr
+};
+
+// indices into DevState::ctr
+enum Ctr : int {
+    kActiveRegions = 0,  // regions active for the next sweep
+    kError = 1,          // nonzero: a device loop hit its cap (MF_EROUNDLIMIT)
+    kGap = 2,            // gap level g found this sweep (0 = none)
+    kChanged = 3,        // cut extraction: a pass changed the set
+    kStages = 4,         // ARD stages (low 32 bits; also kept in 64-bit below)
+    kDischarges = 5,
+    kCtrWords = 16
+};
+struct Counters64 {
+    unsigned long long stages, rounds, discharges, discharged_vertices;
+};
+
+struct SweepArgs {
+    int sweep;          // 0-based sweep index
+    int partial;        // partial discharges (Sec. 6.2)
+    int max_rounds;     // Augment round cap per stage
+    Counters64 *c64;
+};
+
+// launchers (ard_discharge.cu)
+size_t discharge_smem_bytes(int conn, int tx, int ty, int tz);
+bool discharge_supported(int conn, int tx, int ty, int tz);
+cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
+                             cudaStream_t stream);
+
+}  // namespace mf

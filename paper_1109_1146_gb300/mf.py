@@ -1,0 +1,202 @@
+"""Python binding of the C ABI in include/mf.h (argument marshalling only).
+
+Every step of the solver runs in libmf.so (hand-written CUDA for sm_103a).
+This module only converts numpy arrays / torch tensors into pointers and
+sizes, calls the C functions of the same names and raises on a nonzero
+status.  If the library has not been built it raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "_lib", "libmf.so")
+
+MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EOVERFLOW, MF_ESWEEPLIMIT, MF_EROUNDLIMIT, MF_ESTATE = range(8)
+STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "MF_ESWEEPLIMIT",
+                "MF_EROUNDLIMIT", "MF_ESTATE"]
+
+# every symbol include/mf.h declares
+EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
+           "mf_finish", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
+           "mf_last_error"]
+
+
+class mf_opts(ctypes.Structure):
+    _fields_ = [("max_sweeps", ctypes.c_int32), ("partial_discharge", ctypes.c_int32),
+                ("global_gap", ctypes.c_int32), ("global_relabel_period", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+
+
+class mf_stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("boundary_size", ctypes.c_int32),
+                ("discharges", ctypes.c_int64), ("discharged_vertices", ctypes.c_int64),
+                ("stages", ctypes.c_int64), ("rounds", ctypes.c_int64), ("flow_value", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("gaps", ctypes.c_int32), ("cut_passes", ctypes.c_int32),
+                ("ms_init", ctypes.c_double), ("ms_sweeps", ctypes.c_double), ("ms_cut", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_discharge", ctypes.c_double), ("ms_fuse", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 8)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class MFError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+
+
+_lib = None
+
+
+def load(path: str = LIBPATH):
+    """Load libmf.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmf.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "mf_default_opts": (None, [ctypes.POINTER(mf_opts)]),
+        "mf_create_grid": (I, [ctypes.POINTER(P), I, P, I, P, P]),
+        "mf_set_caps": (I, [P, P, P, P, I]),
+        "mf_solve": (I, [P, ctypes.POINTER(mf_opts), ctypes.POINTER(mf_stats)]),
+        "mf_begin": (I, [P, ctypes.POINTER(mf_opts)]),
+        "mf_sweep": (I, [P, ctypes.POINTER(ctypes.c_int32)]),
+        "mf_finish": (I, [P]),
+        "mf_get_cut": (I, [P, P, I, I]),
+        "mf_flow_value": (I, [P, ctypes.POINTER(I64)]),
+        "mf_get_residual": (I, [P, P, P, P, I]),
+        "mf_get_labels": (I, [P, P, ctypes.POINTER(ctypes.c_int32), I]),
+        "mf_destroy": (I, [P]),
+        "mf_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_opts(**kw) -> mf_opts:
+    o = mf_opts()
+    load().mf_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (contiguous int32/uint8)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+class Grid:
+    """One grid instance (owns a mf_grid handle)."""
+
+    def __init__(self, dims, connectivity, tile=None, stream=None):
+        lib = load()
+        dims = tuple(int(d) for d in dims) + (1,) * (3 - len(dims))
+        self.ndim = 3 if connectivity == 6 else 2
+        self.dims = dims
+        self.conn = connectivity
+        self.n = dims[0] * dims[1] * dims[2]
+        self.H = connectivity // 2
+        d = (ctypes.c_int64 * 3)(*dims)
+        t = None if tile is None else (ctypes.c_int32 * 3)(*(tuple(tile) + (1,) * (3 - len(tile))))
+        s = None
+        if stream is not None:
+            s = stream if isinstance(stream, int) else stream.cuda_stream
+        h = ctypes.c_void_p()
+        st = lib.mf_create_grid(ctypes.byref(h), self.ndim, d, connectivity, t, s)
+        if st != MF_OK:
+            raise MFError(st, lib.mf_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+
+    def _check(self, st):
+        if st != MF_OK:
+            raise MFError(st, self._lib.mf_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_caps(self, cs, ct, nlink):
+        pc, dc = _ptr(cs)
+        pt, dt = _ptr(ct)
+        pn, dn = _ptr(nlink)
+        if not (dc == dt == dn):
+            raise ValueError("cs, ct and nlink must all be host or all be device buffers")
+        self._check(self._lib.mf_set_caps(self._h, pc, pt, pn, dc))
+
+    def solve(self, opts: mf_opts | None = None, check=True):
+        stats = mf_stats()
+        st = self._lib.mf_solve(self._h, None if opts is None else ctypes.byref(opts), ctypes.byref(stats))
+        if check:
+            self._check(st)
+        return stats
+
+    def begin(self, opts: mf_opts | None = None):
+        self._check(self._lib.mf_begin(self._h, None if opts is None else ctypes.byref(opts)))
+
+    def sweep(self) -> int:
+        a = ctypes.c_int32()
+        self._check(self._lib.mf_sweep(self._h, ctypes.byref(a)))
+        return a.value
+
+    def finish(self):
+        self._check(self._lib.mf_finish(self._h))
+
+    def get_cut(self, which=0, out=None):
+        if out is None:
+            out = np.empty(self.n, dtype=np.uint8)
+        p, dev = _ptr(out)
+        self._check(self._lib.mf_get_cut(self._h, p, int(which), dev))
+        return out
+
+    def flow_value(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self._lib.mf_flow_value(self._h, ctypes.byref(v)))
+        return v.value
+
+    def get_residual(self):
+        res = np.empty((2 * self.H, self.n), dtype=np.int32)
+        tres = np.empty(self.n, dtype=np.int32)
+        exc = np.empty(self.n, dtype=np.int32)
+        self._check(self._lib.mf_get_residual(self._h, res.ctypes.data, tres.ctypes.data, exc.ctypes.data, 0))
+        return res, tres, exc
+
+    def get_labels(self):
+        lab = np.empty(self.n, dtype=np.int32)
+        dinf = ctypes.c_int32()
+        self._check(self._lib.mf_get_labels(self._h, lab.ctypes.data, ctypes.byref(dinf), 0))
+        return lab, dinf.value

@@ -1,0 +1,145 @@
+"""Parity of the CUDA P-ARD solver with the CPU oracle (called through the C ABI).
+
+Bar: flow value, S_min and S_max bit-identical to Dinic; the final preflow
+accepted by the independent verifier; sweeps within the P-ARD bound 2|B|^2+1
+(Sec. 4.4).  Sizes span several regions and ragged edge tiles."""
+import numpy as np
+import pytest
+
+import oracle
+from gen import grids
+from helpers import assert_parity, gpu_solve, opts
+
+pytestmark = pytest.mark.gpu
+
+
+def _bound_ok(inst, got, tile):
+    b = oracle.boundary_size(inst.dims, inst.conn, tile)
+    assert got["stats"].boundary_size == b
+    assert got["stats"].sweeps <= 2 * b * b + 1
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_config0_workload(seed):
+    inst = grids.config0(seed)
+    got = gpu_solve(inst)
+    assert_parity(inst, got)
+    _bound_ok(inst, got, (64, 64, 1))
+
+
+CASES = [
+    # (dims, conn, tile)
+    ((200, 150, 1), 4, (64, 64, 1)),
+    ((130, 70, 1), 8, (64, 64, 1)),
+    ((97, 61, 1), 4, (32, 32, 1)),
+    ((75, 90, 1), 8, (32, 32, 1)),
+    ((40, 35, 20), 6, (16, 16, 16)),
+    ((21, 19, 13), 6, (8, 8, 8)),
+]
+
+
+@pytest.mark.parametrize("dims,conn,tile", CASES)
+@pytest.mark.parametrize("kind", ["seg", "rand"])
+def test_ragged_multi_region(dims, conn, tile, kind):
+    if kind == "seg":
+        inst = (grids.volume_3d(*dims, seed=3) if conn == 6 else
+                grids.segmentation_2d(dims[0], dims[1], 3, conn=conn, hard_seed_frac=0.03))
+    else:
+        inst = grids.random_grid(dims, conn, 11, cmax=30, tmax=60, p_zero=0.3)
+    got = gpu_solve(inst, tile=tile)
+    assert_parity(inst, got)
+    _bound_ok(inst, got, tile)
+
+
+@pytest.mark.parametrize("dims,conn,tile", [((1, 1, 1), 4, (64, 64, 1)), ((5, 1, 1), 4, (64, 64, 1)),
+                                            ((64, 64, 1), 8, (64, 64, 1)), ((16, 16, 16), 6, (16, 16, 16)),
+                                            ((1, 300, 1), 4, (32, 32, 1)), ((3, 3, 40), 6, (8, 8, 8))])
+def test_degenerate_shapes(dims, conn, tile):
+    inst = grids.random_grid(dims, conn, 5, cmax=25, tmax=40)
+    got = gpu_solve(inst, tile=tile)
+    assert_parity(inst, got)
+
+
+def test_single_region_is_one_sweep():
+    # one region: stage 0 of ARD is a complete augmenting-path max-flow (d_inf = 1)
+    inst = grids.segmentation_2d(64, 64, 2, conn=4)
+    got = gpu_solve(inst, tile=(64, 64, 1))
+    assert_parity(inst, got)
+    assert got["stats"].sweeps == 1
+
+
+@pytest.mark.parametrize("conn", [4, 8, 6])
+def test_zero_neighbour_links(conn):
+    dims = (50, 40, 1) if conn != 6 else (20, 20, 20)
+    inst = grids.random_grid(dims, conn, 1, cmax=0, tmax=50)
+    got = gpu_solve(inst, tile=(32, 32, 1) if conn != 6 else (8, 8, 8))
+    assert_parity(inst, got)
+    assert got["flow"] == int(np.minimum(inst.cs, inst.ct).astype(np.int64).sum())
+
+
+def test_all_zero_capacities():
+    inst = grids.random_grid((70, 70, 1), 4, 1, cmax=0, tmax=0)
+    got = gpu_solve(inst)
+    assert got["flow"] == 0 and got["smin"].sum() == 0 and got["smax"].sum() == inst.n
+
+
+def test_strong_links_carry_everything():
+    inst = grids.random_grid((100, 90, 1), 4, 3, cmax=0, tmax=50)
+    inst.nlink[:] = 10 ** 6
+    inst.nlink[0].reshape(90, 100)[:, -1] = 0
+    inst.nlink[1].reshape(90, 100)[-1, :] = 0
+    got = gpu_solve(inst)
+    assert_parity(inst, got)
+    assert got["flow"] == min(int(inst.cs.sum()), int(inst.ct.sum()))
+
+
+@pytest.mark.parametrize("conn,dims,t1,t2", [(4, (150, 130, 1), (64, 64, 1), (32, 32, 1)),
+                                             (8, (150, 130, 1), (64, 64, 1), (32, 32, 1)),
+                                             (6, (40, 40, 24), (16, 16, 16), (8, 8, 8))])
+def test_result_invariant_under_tile_shape(conn, dims, t1, t2):
+    inst = (grids.volume_3d(*dims, seed=4) if conn == 6 else
+            grids.segmentation_2d(dims[0], dims[1], 4, conn=conn))
+    a = gpu_solve(inst, tile=t1, residual=False)
+    b = gpu_solve(inst, tile=t2, residual=False)
+    assert a["flow"] == b["flow"]
+    np.testing.assert_array_equal(a["smin"], b["smin"])
+    np.testing.assert_array_equal(a["smax"], b["smax"])
+
+
+@pytest.mark.parametrize("kw", [dict(partial_discharge=1), dict(global_gap=0),
+                                dict(partial_discharge=1, global_gap=0)])
+def test_options_keep_exact_results(kw):
+    inst = grids.segmentation_2d(190, 170, 6, conn=8, hard_seed_frac=0.05)
+    got = gpu_solve(inst, opts=opts(**kw))
+    assert_parity(inst, got)
+
+
+def test_repeat_solve_same_handle():
+    from paper_1109_1146_gb300 import Grid
+    inst = grids.config0(5)
+    ref = oracle.solve_instance(inst)
+    with Grid(inst.dims, 4) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        for _ in range(3):
+            g.solve()
+            assert g.flow_value() == ref["flow"]
+            np.testing.assert_array_equal(g.get_cut(0), ref["smin"])
+
+
+def test_device_resident_inputs():
+    torch = pytest.importorskip("torch")
+    from paper_1109_1146_gb300 import Grid
+    inst = grids.segmentation_2d(150, 100, 8, conn=8)
+    ref = oracle.solve_instance(inst)
+    dev = torch.device("cuda:0")
+    cs = torch.from_numpy(inst.cs).to(dev)
+    ct = torch.from_numpy(inst.ct).to(dev)
+    nl = torch.from_numpy(inst.nlink).to(dev)
+    with Grid(inst.dims, 8, stream=torch.cuda.current_stream()) as g:
+        g.set_caps(cs, ct, nl)
+        g.solve()
+        out = torch.empty(inst.n, dtype=torch.uint8, device=dev)
+        g.get_cut(0, out=out)
+        torch.cuda.synchronize()
+        assert g.flow_value() == ref["flow"]
+        np.testing.assert_array_equal(out.cpu().numpy(), ref["smin"])
