@@ -66,7 +66,8 @@ typedef struct {
     int32_t global_gap;            /* 1: global gap heuristic after each sweep (Sec. 5.1); default 1 */
     int32_t global_relabel_period; /* P > 0: exact region-distance relabel every P sweeps; 0 = off (default) */
     int32_t max_rounds;            /* cap on Augment rounds per stage inside one discharge; 0 = default 65536 */
-    int32_t reserved[11];
+    int32_t kernel_variant;        /* 0: bit-parallel 2D discharge where available (default); 1: generic kernel */
+    int32_t reserved[10];
 } mf_opts;
 
 /* Statistics of the last mf_solve (all optional reading). */

@@ -393,6 +393,8 @@ size_t discharge_smem_bytes(int conn, int tx, int ty, int tz) {
 
 cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
                              cudaStream_t stream) {
+    if (sa.variant == 0 && g.tz == 1 && discharge2d_supported(conn, g.tx, g.ty))
+        return launch_discharge2d(conn, g, st, sa, stream);
 #define X(c, a, b, z, t) \
     if (conn == c && g.tx == a && g.ty == b && g.tz == z) return launch_one<c, a, b, z, t>(g, st, sa, stream);
     MF_TILES(X)

@@ -501,6 +501,7 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     sa.sweep = g->sweep;
     sa.partial = g->opts.partial_discharge;
     sa.max_rounds = g->opts.max_rounds;
+    sa.variant = g->opts.kernel_variant;
     sa.c64 = g->c64;
     CK(cudaMemsetAsync(g->st.hist, 0, (kHistBins + 1) * 4, g->stream));
     CK(cudaMemsetAsync(g->st.ctr, 0, 4 * (kGap + 1), g->stream));  // active count, error, gap

@@ -70,6 +70,7 @@ struct SweepArgs {
     int sweep;          // 0-based sweep index
     int partial;        // partial discharges (Sec. 6.2)
     int max_rounds;     // Augment round cap per stage
+    int variant;        // 0: bit-parallel 2D kernel where available, 1: generic kernel
     Counters64 *c64;
 };
 
@@ -78,5 +79,9 @@ size_t discharge_smem_bytes(int conn, int tx, int ty, int tz);
 bool discharge_supported(int conn, int tx, int ty, int tz);
 cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
                              cudaStream_t stream);
+// ard_discharge2d.cu
+bool discharge2d_supported(int conn, int tx, int ty);
+cudaError_t launch_discharge2d(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
+                               cudaStream_t stream);
 
 }  // namespace mf

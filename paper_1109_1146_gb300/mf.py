@@ -28,7 +28,8 @@ EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_b
 class mf_opts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("partial_discharge", ctypes.c_int32),
                 ("global_gap", ctypes.c_int32), ("global_relabel_period", ctypes.c_int32),
-                ("max_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+                ("max_rounds", ctypes.c_int32), ("kernel_variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
 
 
 class mf_stats(ctypes.Structure):

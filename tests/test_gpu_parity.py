@@ -143,3 +143,14 @@ def test_device_resident_inputs():
         torch.cuda.synchronize()
         assert g.flow_value() == ref["flow"]
         np.testing.assert_array_equal(out.cpu().numpy(), ref["smin"])
+
+
+@pytest.mark.parametrize("conn,dims,tile", [(4, (200, 150, 1), (64, 64, 1)), (8, (130, 170, 1), (64, 64, 1)),
+                                            (4, (97, 61, 1), (32, 32, 1)), (8, (75, 90, 1), (32, 32, 1))])
+@pytest.mark.parametrize("kind", ["seg", "rand"])
+def test_generic_kernel_variant(conn, dims, tile, kind):
+    # the generic per-vertex discharge kernel (variant 1) must give the same exact answer
+    inst = (grids.segmentation_2d(dims[0], dims[1], 9, conn=conn, hard_seed_frac=0.05) if kind == "seg"
+            else grids.random_grid(dims, conn, 13, cmax=30, tmax=60, p_zero=0.3))
+    got = gpu_solve(inst, tile=tile, opts=opts(kernel_variant=1))
+    assert_parity(inst, got)
