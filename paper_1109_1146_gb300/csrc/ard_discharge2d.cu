@@ -30,12 +30,15 @@ template <int CONN, int TX, int TY, int NT>
 struct Cfg2D {
     static constexpr int N = CONN;
     static constexpr int V = TX * TY;
+    static constexpr int NW = NT / 32;                  // warps
     static constexpr int VPT = V / NT;
     static constexpr int RPL = TY / 32;                 // rows per lane of the graph warp
     static constexpr int HL = 2 * (TX + 2) + 2 * TY;    // halo cells (B^R plus unused corners)
     static constexpr int PER = 2 * TX + 2 * (TY - 2);   // perimeter positions of the tile
-    static constexpr size_t smem = (size_t)(N + 3) * V * 4 + (size_t)V * 4    // cap, tcap, exc, lab
-                                   + (size_t)(N + 4) * TY * 8                // R[N], T, E, seed, vis
+    static constexpr int LCAP = 64;                     // BFS layers kept as masks
+    static constexpr size_t smem = (size_t)(N + 3) * V * 4                  // cap, tcap, exc, lab
+                                   + (size_t)(N + 5) * TY * 8               // R[N], T, E, seed, inc, vis
+                                   + (size_t)(LCAP + 1) * TY * 8            // BFS layers 1..LCAP
                                    + (size_t)HL * 4 + 64;
     static_assert(TX == 32 || TX == 64, "row width must be 32 or 64");
     static_assert(TY % 32 == 0 && V % NT == 0 && NT % 32 == 0, "tile/threads mismatch");
@@ -50,22 +53,49 @@ __device__ __forceinline__ int halo_idx(int hx, int hy) {
     return 2 * (TX + 2) + TY + hy;
 }
 
+// Kogge-Stone fill inside one row: x joins if x+1 is in g and pl[x] (arc x -> x+1),
+// or x-1 is in g and pr[x] (arc x -> x-1), repeatedly (a whole run at once).
+__device__ __forceinline__ u64 row_fill(u64 g, u64 pl, u64 pr) {
+    u64 a = g, p = pl;
+    a |= p & (a >> 1);  p &= p >> 1;
+    a |= p & (a >> 2);  p &= p >> 2;
+    a |= p & (a >> 4);  p &= p >> 4;
+    a |= p & (a >> 8);  p &= p >> 8;
+    a |= p & (a >> 16); p &= p >> 16;
+    a |= p & (a >> 32);
+    u64 b = g;
+    p = pr;
+    b |= p & (b << 1);  p &= p << 1;
+    b |= p & (b << 2);  p &= p << 2;
+    b |= p & (b << 4);  p &= p << 4;
+    b |= p & (b << 8);  p &= p << 8;
+    b |= p & (b << 16); p &= p << 16;
+    b |= p & (b << 32);
+    return a | b;
+}
+
+// distance tag of a deep BFS layer (negative: never equal to a label >= 0)
+__device__ __forceinline__ int deep_tag(int epoch, int L) { return ~((epoch << 16) | L); }
+
 template <int CONN, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT, 1)
 ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     using C = Cfg2D<CONN, TX, TY, NT>;
-    constexpr int N = C::N, V = C::V, VPT = C::VPT, RPL = C::RPL;
+    constexpr int N = C::N, V = C::V, VPT = C::VPT, RPL = C::RPL, NW = C::NW, LCAP = C::LCAP;
+    constexpr int HW = TX / 32;  // 32-bit halves per row
     extern __shared__ __align__(16) unsigned char smraw[];
-    int *s_cap = (int *)smraw;            // [N][V]
+    int *s_cap = (int *)smraw;            // [N][V] residual of arc i -> i + D(d)
     int *s_tcap = s_cap + N * V;          // [V]
     int *s_exc = s_tcap + V;              // [V]
-    int *s_lab = s_exc + V;               // [V] BFS tag (epoch<<16|layer), then region label
-    u64 *s_R = (u64 *)(s_lab + V);        // [N][TY]
-    u64 *s_T = s_R + N * TY;              // [TY]
-    u64 *s_E = s_T + TY;                  // [TY]
-    u64 *s_seed = s_E + TY;               // [TY]
-    u64 *s_vis = s_seed + TY;             // [TY]
-    int *s_hl = (int *)(s_vis + TY);      // [HL]
+    int *s_lab = s_exc + V;               // [V] region label (deep BFS layers: negative tags)
+    u64 *s_R = (u64 *)(s_lab + V);        // [N][TY] residual masks
+    u64 *s_T = s_R + N * TY;              // [TY] residual arc to t
+    u64 *s_E = s_T + TY;                  // [TY] positive excess
+    u64 *s_seed = s_E + TY;               // [TY] stage seeds (arcs into T_k \ {t})
+    u64 *s_inc = s_seed + TY;             // [TY] vertices that joined the closure
+    u64 *s_vis = s_inc + TY;              // [TY] final closure
+    u64 *s_layer = s_vis + TY;            // [LCAP+1][TY] BFS layers
+    int *s_hl = (int *)(s_layer + (LCAP + 1) * TY);  // [HL] labels of B^R
     __shared__ int s_ctl[4];
     __shared__ unsigned long long s_flow;
 
@@ -158,6 +188,12 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
         }
         __syncwarp();
     };
+    auto load_masks = [&](u64 (&Rm)[N][RPL]) {
+#pragma unroll
+        for (int j = 0; j < RPL; ++j)
+#pragma unroll
+            for (int d = 0; d < N; ++d) Rm[d][j] = s_R[d * TY + lane * RPL + j];
+    };
     // one backward BFS step on the masks: vertices with a residual arc into f
     auto expand = [&](const u64 (&Rm)[N][RPL], const u64 (&f)[RPL], u64 (&out)[RPL]) {
         const u64 up = __shfl_up_sync(0xffffffffu, f[RPL - 1], 1);
@@ -172,6 +208,60 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
             out[j] = a;
         }
     };
+    // closure C := C U {u : u -> seeds of stage k} (reachability, no distances);
+    // the vertices that joined go to s_inc; returns whether C meets the excess
+    u64 Cl[RPL];
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) Cl[j] = 0;
+    auto closure_extend = [&](int k) -> bool {
+        halo_seeds(k);
+        u64 Rm[N][RPL], fr[RPL], inc[RPL];
+        load_masks(Rm);
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            const int y = lane * RPL + j;
+            const u64 sd = (k == 0 ? s_T[y] : s_seed[y]) & ~Cl[j];
+            const u64 f = row_fill(sd, Rm[0][j] & ~Cl[j], Rm[1][j] & ~Cl[j]);
+            Cl[j] |= f;
+            inc[j] = f;
+            fr[j] = f;
+            any |= f != 0ull;
+        }
+        while (__any_sync(0xffffffffu, any)) {
+            u64 nf[RPL];
+            expand(Rm, fr, nf);
+            any = false;
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                const u64 f = row_fill(nf[j] & ~Cl[j], Rm[0][j] & ~Cl[j], Rm[1][j] & ~Cl[j]);
+                Cl[j] |= f;
+                inc[j] |= f;
+                fr[j] = f;
+                any |= f != 0ull;
+            }
+        }
+        bool meets = false;
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            const int y = lane * RPL + j;
+            s_inc[y] = inc[j];
+            meets |= (Cl[j] & s_E[y]) != 0ull;
+        }
+        return __any_sync(0xffffffffu, meets);
+    };
+    // all threads: label the vertices that joined the closure at stage k
+    auto write_labels = [&](int k) {
+        for (int y = warp; y < TY; y += NW) {
+            const u64 m = s_inc[y];
+            if (!m) continue;
+#pragma unroll
+            for (int h = 0; h < HW; ++h) {
+                const int x = lane + 32 * h;
+                if ((m >> x) & 1ull) s_lab[y * TX + x] = k;
+            }
+        }
+    };
 
     const int klimit = sa.partial ? sa.sweep : INT_MAX;
     long long flow_acc = 0;
@@ -180,173 +270,176 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
 
     // ---- ARD stages ------------------------------------------------------------
     for (int k = 0;;) {
-        if (k > klimit) break;
-        ++stages;
-        for (int round = 0;; ++round) {
-            if (round >= sa.max_rounds) { err = true; break; }
-            if (++epoch >= 32767) {  // distance tags wrap: clear them
-                for (int i = tid; i < V; i += NT) s_lab[i] = 0;
-                __syncthreads();
-                epoch = 1;
+        if (warp == 0) {
+            const bool reach = closure_extend(k);
+            const int kn = next_stage(k);
+            if (lane == 0) {
+                s_ctl[0] = reach;
+                s_ctl[1] = kn;
             }
-            const int tag = epoch << 16;
-            if (warp == 0) {
-                halo_seeds(k);
-                u64 Rm[N][RPL], vis[RPL], fr[RPL], ex[RPL];
-                int lmax = 0;
-                bool unreached = false;
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) {
-                    const int y = lane * RPL + j;
-#pragma unroll
-                    for (int d = 0; d < N; ++d) Rm[d][j] = s_R[d * TY + y];
-                    ex[j] = s_E[y];
-                    fr[j] = s_T[y] | s_seed[y];
-                    vis[j] = fr[j];
-                    for (u64 m = fr[j]; m; m &= m - 1) s_lab[y * TX + __ffsll((long long)m) - 1] = tag | 1;
-                    if (fr[j] & ex[j]) lmax = 1;
-                    if (ex[j] & ~vis[j]) unreached = true;
+        }
+        __syncthreads();
+        write_labels(k);
+        const int reach = s_ctl[0], kn = s_ctl[1];
+        // after a round-cap error no more augmentation, but the labels of every
+        // stage are still computed so the labeling stays valid
+        const bool aug = k <= klimit && !err;
+        if (aug) ++stages;
+        if (aug && reach) {
+            // Augment(R, T_k): rounds of exact BFS + layered push
+            for (int round = 0;; ++round) {
+                if (round >= sa.max_rounds) { err = true; break; }
+                if (++epoch >= 32767) {  // deep-layer tags wrap: clear them
+                    __syncthreads();
+                    for (int i = tid; i < V; i += NT) s_lab[i] = 0;
+                    __syncthreads();
+                    epoch = 1;
                 }
-                int L = 1;
-                while (__any_sync(0xffffffffu, unreached)) {
-                    u64 nf[RPL];
-                    expand(Rm, fr, nf);
-                    ++L;
-                    bool any = false;
-                    unreached = false;
+                if (warp == 0) {
+                    halo_seeds(k);
+                    u64 Rm[N][RPL], vis[RPL], fr[RPL], ex[RPL];
+                    load_masks(Rm);
+                    int lmax = 0;
+                    bool unreached = false;
 #pragma unroll
                     for (int j = 0; j < RPL; ++j) {
                         const int y = lane * RPL + j;
-                        nf[j] &= ~vis[j];
-                        vis[j] |= nf[j];
-                        fr[j] = nf[j];
-                        any |= nf[j] != 0ull;
-                        for (u64 m = nf[j]; m; m &= m - 1) s_lab[y * TX + __ffsll((long long)m) - 1] = tag | L;
-                        if (nf[j] & ex[j]) lmax = L;
+                        ex[j] = s_E[y];
+                        fr[j] = s_T[y] | s_seed[y];
+                        vis[j] = fr[j];
+                        s_layer[1 * TY + y] = fr[j];
+                        if (fr[j] & ex[j]) lmax = 1;
                         if (ex[j] & ~vis[j]) unreached = true;
                     }
-                    if (!__any_sync(0xffffffffu, any)) break;
-                }
-                lmax = __reduce_max_sync(0xffffffffu, lmax);
-                if (lane == 0) s_ctl[0] = lmax;
-            }
-            __syncthreads();
-            const int Lmax = s_ctl[0];
-            if (Lmax == 0) break;  // no excess vertex reaches T_k: stage done
-            ++rounds;
-            // layered push: a vertex at layer L pushes only to layer L-1 (or to
-            // T_k from layer 1), so every arc and every excess has one writer
-            for (int L = Lmax; L >= 1; --L) {
-                const int tagL = tag | L, tagL1 = tag | (L - 1);
+                    int L = 1;
+                    while (__any_sync(0xffffffffu, unreached)) {
+                        u64 nf[RPL];
+                        expand(Rm, fr, nf);
+                        bool any = false;
 #pragma unroll
-                for (int q = 0; q < VPT; ++q) {
-                    const int i = tid + q * NT;
-                    const int lx = i % TX, ly = i / TX;
-                    if (!((s_E[ly] >> lx) & 1ull)) continue;
-                    if (s_lab[i] != tagL) continue;
-                    int e = s_exc[i];
-                    if (e <= 0) continue;
-                    if (L == 1) {
-                        const int tc = s_tcap[i];
-                        if (tc > 0) {
-                            const int dl = min(e, tc);
-                            s_tcap[i] = tc - dl;
-                            e -= dl;
-                            flow_acc += dl;
-                            if (tc == dl) atomicAnd(&s_T[ly], ~(1ull << lx));
+                        for (int j = 0; j < RPL; ++j) {
+                            nf[j] &= ~vis[j];
+                            any |= nf[j] != 0ull;
                         }
+                        if (!__any_sync(0xffffffffu, any)) break;
+                        ++L;
+                        unreached = false;
 #pragma unroll
-                        for (int d = 0; d < N; ++d) {
-                            if (e == 0) break;
-                            const int hx = lx + arc_dx(CONN, d), hy = ly + arc_dy(CONN, d);
-                            if (hx >= 0 && hx < TX && hy >= 0 && hy < TY) continue;
-                            const int c = s_cap[d * V + i];
-                            if (c > 0 && s_hl[halo_idx<TX, TY>(hx, hy)] < k) {
-                                const int dl = min(e, c);
-                                s_cap[d * V + i] = c - dl;
-                                e -= dl;
-                                if (c == dl) atomicAnd(&s_R[d * TY + ly], ~(1ull << lx));
+                        for (int j = 0; j < RPL; ++j) {
+                            const int y = lane * RPL + j;
+                            vis[j] |= nf[j];
+                            fr[j] = nf[j];
+                            if (L <= LCAP) {
+                                s_layer[L * TY + y] = nf[j];
+                            } else {
+                                const int tg = deep_tag(epoch, L);
+                                for (u64 m = nf[j]; m; m &= m - 1) s_lab[y * TX + __ffsll((long long)m) - 1] = tg;
                             }
-                        }
-                    } else {
-#pragma unroll
-                        for (int d = 0; d < N; ++d) {
-                            if (e == 0) break;
-                            const int nx = lx + arc_dx(CONN, d), ny = ly + arc_dy(CONN, d);
-                            if (!(nx >= 0 && nx < TX && ny >= 0 && ny < TY)) continue;
-                            const int j = ny * TX + nx;
-                            const int c = s_cap[d * V + i];
-                            if (c > 0 && s_lab[j] == tagL1) {
-                                const int dl = min(e, c);
-                                s_cap[d * V + i] = c - dl;
-                                const int rc = s_cap[(d ^ 1) * V + j];
-                                s_cap[(d ^ 1) * V + j] = rc + dl;
-                                const int old = atomicAdd(&s_exc[j], dl);
-                                e -= dl;
-                                if (c == dl) atomicAnd(&s_R[d * TY + ly], ~(1ull << lx));
-                                if (rc == 0) atomicOr(&s_R[(d ^ 1) * TY + ny], 1ull << nx);
-                                if (old == 0) atomicOr(&s_E[ny], 1ull << nx);
-                            }
+                            if (nf[j] & ex[j]) lmax = L;
+                            if (ex[j] & ~vis[j]) unreached = true;
                         }
                     }
-                    s_exc[i] = e;
-                    if (e == 0) atomicAnd(&s_E[ly], ~(1ull << lx));
+                    lmax = __reduce_max_sync(0xffffffffu, lmax);
+                    if (lane == 0) s_ctl[2] = lmax;
                 }
                 __syncthreads();
-            }
-        }
-        if (err) break;
-        if (warp == 0) {
-            const int kn = next_stage(k);
-            if (lane == 0) s_ctl[1] = kn;
-        }
-        __syncthreads();
-        const int kn = s_ctl[1];
-        if (kn == INT_MAX) break;
-        k = kn;
-    }
-
-    // ---- region-relabel (warp 0): d(u) = min{k : u -> T_k}, else d_inf ------------
-    if (warp == 0) {
-        u64 Rm[N][RPL], vis[RPL], fr[RPL];
+                const int Lmax = s_ctl[2];
+                if (Lmax == 0) break;  // no excess vertex reaches T_k: stage done
+                ++rounds;
+                // layered push, top layer first: a vertex of layer L pushes only to
+                // layer L-1 (to T_k from layer 1), so every arc has one writer per step
+                for (int L = Lmax; L >= 1; --L) {
+                    const int tgL = deep_tag(epoch, L), tgL1 = deep_tag(epoch, L - 1);
+                    for (int y = warp; y < TY; y += NW) {
+                        u64 P = s_E[y];
+                        if (L <= LCAP) P &= s_layer[L * TY + y];
+                        if (!P) continue;
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) {
-            const int y = lane * RPL + j;
+                        for (int h = 0; h < HW; ++h) {
+                            const int lx = lane + 32 * h, ly = y;
+                            if (!((P >> lx) & 1ull)) continue;
+                            const int i = ly * TX + lx;
+                            if (L > LCAP && s_lab[i] != tgL) continue;
+                            int e = s_exc[i];
+                            if (e <= 0) continue;
+                            if (L == 1) {
+                                const int tc = s_tcap[i];
+                                if (tc > 0) {
+                                    const int dl = min(e, tc);
+                                    s_tcap[i] = tc - dl;
+                                    e -= dl;
+                                    flow_acc += dl;
+                                    if (tc == dl) atomicAnd(&s_T[ly], ~(1ull << lx));
+                                }
 #pragma unroll
-            for (int d = 0; d < N; ++d) Rm[d][j] = s_R[d * TY + y];
-            vis[j] = 0;
-        }
-        for (int k = 0;;) {
-            halo_seeds(k);
-            bool any = false;
+                                for (int d = 0; d < N; ++d) {
+                                    if (e == 0) break;
+                                    const int hx = lx + arc_dx(CONN, d), hy = ly + arc_dy(CONN, d);
+                                    if (hx >= 0 && hx < TX && hy >= 0 && hy < TY) continue;
+                                    const int c = s_cap[d * V + i];
+                                    if (c > 0 && s_hl[halo_idx<TX, TY>(hx, hy)] < k) {
+                                        const int dl = min(e, c);
+                                        s_cap[d * V + i] = c - dl;
+                                        e -= dl;
+                                        if (c == dl) atomicAnd(&s_R[d * TY + ly], ~(1ull << lx));
+                                    }
+                                }
+                            } else {
 #pragma unroll
-            for (int j = 0; j < RPL; ++j) {
-                const int y = lane * RPL + j;
-                fr[j] = (k == 0 ? s_T[y] : s_seed[y]) & ~vis[j];
-                vis[j] |= fr[j];
-                any |= fr[j] != 0ull;
-                for (u64 m = fr[j]; m; m &= m - 1) s_lab[y * TX + __ffsll((long long)m) - 1] = k;
-            }
-            while (__any_sync(0xffffffffu, any)) {
-                u64 nf[RPL];
-                expand(Rm, fr, nf);
-                any = false;
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) {
-                    const int y = lane * RPL + j;
-                    nf[j] &= ~vis[j];
-                    vis[j] |= nf[j];
-                    fr[j] = nf[j];
-                    any |= nf[j] != 0ull;
-                    for (u64 m = nf[j]; m; m &= m - 1) s_lab[y * TX + __ffsll((long long)m) - 1] = k;
+                                for (int d = 0; d < N; ++d) {
+                                    if (e == 0) break;
+                                    const int nx = lx + arc_dx(CONN, d), ny = ly + arc_dy(CONN, d);
+                                    if (!(nx >= 0 && nx < TX && ny >= 0 && ny < TY)) continue;
+                                    const int j = ny * TX + nx;
+                                    const int c = s_cap[d * V + i];
+                                    if (c <= 0) continue;
+                                    const bool below = (L - 1 <= LCAP) ? ((s_layer[(L - 1) * TY + ny] >> nx) & 1ull) != 0
+                                                                       : s_lab[j] == tgL1;
+                                    if (!below) continue;
+                                    const int dl = min(e, c);
+                                    s_cap[d * V + i] = c - dl;
+                                    const int rc = s_cap[(d ^ 1) * V + j];
+                                    s_cap[(d ^ 1) * V + j] = rc + dl;
+                                    const int old = atomicAdd(&s_exc[j], dl);
+                                    e -= dl;
+                                    if (c == dl) atomicAnd(&s_R[d * TY + ly], ~(1ull << lx));
+                                    if (rc == 0) atomicOr(&s_R[(d ^ 1) * TY + ny], 1ull << nx);
+                                    if (old == 0) atomicOr(&s_E[ny], 1ull << nx);
+                                }
+                            }
+                            s_exc[i] = e;
+                            if (e == 0) atomicAnd(&s_E[ly], ~(1ull << lx));
+                        }
+                    }
+                    __syncthreads();
                 }
             }
-            const int kn = next_stage(k);
-            if (kn == INT_MAX) break;
-            k = kn;
-        }
+            // the residual graph changed: rebuild the closure and labels of stages <= k
+            if (warp == 0) {
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) s_vis[lane * RPL + j] = vis[j];
+                for (int j = 0; j < RPL; ++j) Cl[j] = 0;
+            }
+            for (int k2 = 0;;) {
+                if (warp == 0) {
+                    closure_extend(k2);
+                    const int n2 = next_stage(k2);
+                    if (lane == 0) s_ctl[3] = n2;
+                }
+                __syncthreads();
+                write_labels(k2);
+                const int n2 = s_ctl[3];
+                __syncthreads();
+                if (n2 == INT_MAX || n2 > k) break;
+                k2 = n2;
+            }
+        }
+        if (kn == INT_MAX) break;
+        k = kn;
+        __syncthreads();
+    }
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) s_vis[lane * RPL + j] = Cl[j];
     }
     __syncthreads();
 

@@ -1,0 +1,103 @@
+"""Per-sweep invariants of P-ARD on the GPU state (Sec. 4.4, Statement on the
+properties of the parallel sweep), checked on the CPU after every sweep:
+
+  * the preflow is feasible (capacity, antisymmetry, e >= 0);
+  * the labeling is valid for the region distance (Sec. 4.1):
+        d(u) <= d(w) + 1 on residual arcs with both ends in B,
+        d(u) <= d(w)     on the other residual arcs,  d(u) = 0 if c_f(u,t) > 0;
+  * labels never decrease (labeling monotony);
+  * after a sweep no vertex outside B is active (optimality), when partial
+    discharges are off;
+  * the sweep count stays within 2|B|^2 + 1.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gen import grids
+from paper_1109_1146_gb300 import Grid, default_opts
+
+pytestmark = pytest.mark.gpu
+
+_FWD = grids.FWD
+
+
+def _arc_targets(dims, conn):
+    """For every arc direction d: target index of each vertex (-1 outside)."""
+    X, Y, Z = dims
+    zz, yy, xx = np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+    out = []
+    for h, (dx, dy, dz) in enumerate(_FWD[conn]):
+        for sg in (1, -1):
+            x2, y2, z2 = xx + sg * dx, yy + sg * dy, zz + sg * dz
+            ok = (x2 >= 0) & (x2 < X) & (y2 >= 0) & (y2 < Y) & (z2 >= 0) & (z2 < Z)
+            t = np.where(ok, (z2 * Y + y2) * X + x2, -1)
+            out.append(t.ravel())
+    return out
+
+
+def check_state(inst, res, tres, exc, lab, dinf, inB, targets):
+    n = inst.n
+    assert (res >= 0).all() and (tres >= 0).all() and (exc >= 0).all()
+    assert (tres <= inst.ct).all()
+    # antisymmetry + excess recomputed from residuals
+    e = inst.cs.astype(np.int64) - (inst.ct.astype(np.int64) - tres)
+    for d, t in enumerate(targets):
+        ok = t >= 0
+        h = d >> 1
+        c = np.where(d & 1, 0, inst.nlink[h]).astype(np.int64)
+        if d & 1:
+            c = np.zeros(n, np.int64)
+            c[ok] = inst.nlink[h][t[ok]]
+        assert (res[d][~ok] == 0).all()
+        back = np.zeros(n, np.int64)
+        back[ok] = res[d ^ 1][t[ok]]
+        assert (res[d][ok].astype(np.int64) + back[ok] == 2 * c[ok]).all()
+        e -= np.where(ok, c - res[d], 0)
+    assert (e == exc).all()
+    # validity of the labeling
+    assert (lab >= 0).all() and (lab <= dinf).all()
+    assert (lab[tres > 0] == 0).all()
+    for d, t in enumerate(targets):
+        ok = (t >= 0) & (res[d] > 0)
+        u = np.flatnonzero(ok)
+        w = t[ok]
+        slack = (inB[u] & inB[w]).astype(np.int64)
+        bad = lab[u] > lab[w].astype(np.int64) + slack
+        assert not bad.any(), f"labeling invalid on {bad.sum()} arcs (dir {d})"
+
+
+@pytest.mark.parametrize("conn,dims,tile,partial", [
+    (4, (192, 160, 1), (64, 64, 1), 0), (8, (150, 130, 1), (64, 64, 1), 0),
+    (8, (100, 90, 1), (32, 32, 1), 0), (4, (120, 96, 1), (32, 32, 1), 1),
+    (6, (40, 36, 30), (16, 16, 16), 0), (6, (24, 20, 18), (8, 8, 8), 1)])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_sweep_invariants(conn, dims, tile, partial, variant):
+    inst = (grids.volume_3d(*dims, seed=2) if conn == 6 else
+            grids.segmentation_2d(dims[0], dims[1], 2, conn=conn, hard_seed_frac=0.04))
+    inB = oracle.boundary_mask(inst.dims, conn, tile)
+    targets = _arc_targets(inst.dims, conn)
+    bound = oracle.sweep_bound(inst.dims, conn, tile)
+    with Grid(inst.dims, conn, tile=tile) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        g.begin(default_opts(partial_discharge=partial, kernel_variant=variant))
+        prev, dinf = g.get_labels()
+        sweeps = 0
+        while True:
+            active = g.sweep()
+            sweeps += 1
+            res, tres, exc = g.get_residual()
+            lab, dinf = g.get_labels()
+            check_state(inst, res, tres, exc, lab, dinf, inB, targets)
+            assert (lab >= prev).all(), "labels decreased"
+            if not partial:
+                act = (exc > 0) & (lab < dinf)
+                assert not (act & ~inB).any(), "active vertex outside B after a sweep"
+            prev = lab
+            if active == 0:
+                break
+            assert sweeps <= bound
+        g.finish()
+        ref = oracle.solve_instance(inst)
+        assert g.flow_value() == ref["flow"]
+        np.testing.assert_array_equal(g.get_cut(0), ref["smin"])
