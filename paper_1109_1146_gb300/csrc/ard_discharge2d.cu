@@ -2,21 +2,24 @@
 //
 // Same computation as ard_discharge.cu (Procedure ARD of Sec. 4.2 with
 // Procedure Augment done in synchronous rounds of "BFS from T_k, then a
-// layered push from the highest BFS layer down", followed by the ARD
-// region-relabel of Sec. 5.1), organised for a 64- or 32-wide tile:
+// layered push from the highest BFS layer down", and the ARD region-relabel
+// of Sec. 5.1), organised for a 64- or 32-wide tile:
 //
-//   * the residual graph of the tile is also kept as bit masks, one machine
-//     word per tile row and arc direction: R_d[y] bit x = [c_f((x,y) -> (x,y)+D(d)) > 0];
-//     T[y] bit x = [c_f(v,t) > 0]; E[y] bit x = [e_f(v) > 0];
-//   * warp 0 (the "graph warp") runs every BFS and every reachability flood on
-//     these masks: lane l holds rows l*RPL .. l*RPL+RPL-1 in registers, a BFS
-//     step is a handful of shifts/ands per row plus two warp shuffles for the
-//     rows above and below, with no block barrier;
-//   * all warps do the per-vertex integer work (tile staging, the layered
-//     push, write-back) and keep the masks current with shared-memory atomics.
+//   * the residual graph of the tile is also kept as bit masks, one 64-bit
+//     word per tile row: R_d[y] bit x = [c_f((x,y) -> (x,y)+D(d)) > 0],
+//     T[y] bit x = [c_f(v,t) > 0], E[y] bit x = [e_f(v) > 0];
+//   * warp 0 (the "graph warp") runs every BFS and reachability flood on these
+//     masks: lane l holds rows l*RPL .. l*RPL+RPL-1 in registers; a BFS step is
+//     a few shifts/ands per row plus two shuffles for the rows above and below,
+//     with no block barrier; floods also close whole row runs at once
+//     (Kogge-Stone fill along the row);
+//   * all warps do the per-vertex integer work: staging, the layered push,
+//     rebuilding the masks from the planes after a push pass, write-back.
 //
-// BFS distances are stored as (epoch << 16 | layer) so no per-round reset of
-// the distance array is needed.
+// Stage checks ("does an excess vertex reach T_k?") use a reachability closure
+// C_k extended stage by stage; its increments are the region labels
+// d(u) = min{k : u -> T_k}.  Augmentation invalidates the closure; it is then
+// rebuilt for the next check, and the labels are recomputed once at the end.
 #include <climits>
 #include <cstdint>
 
@@ -26,22 +29,37 @@ namespace mf {
 
 typedef unsigned long long u64;
 
+#ifdef MF_DIAG
+__device__ unsigned long long mf_diag[32];
+}  // namespace mf
+extern "C" int mf_diag_read(unsigned long long *out, int reset) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+    if (cudaMemcpyFromSymbol(out, mf::mf_diag, sizeof(unsigned long long) * 32) != cudaSuccess) return 2;
+    if (reset) {
+        static const unsigned long long z[32] = {0};
+        if (cudaMemcpyToSymbol(mf::mf_diag, z, sizeof(z)) != cudaSuccess) return 3;
+    }
+    return 0;
+}
+namespace mf {
+#endif
+
 template <int CONN, int TX, int TY, int NT>
 struct Cfg2D {
     static constexpr int N = CONN;
     static constexpr int V = TX * TY;
     static constexpr int NW = NT / 32;                  // warps
-    static constexpr int VPT = V / NT;
     static constexpr int RPL = TY / 32;                 // rows per lane of the graph warp
+    static constexpr int HW = TX / 32;                  // 32-bit halves per row
     static constexpr int HL = 2 * (TX + 2) + 2 * TY;    // halo cells (B^R plus unused corners)
-    static constexpr int PER = 2 * TX + 2 * (TY - 2);   // perimeter positions of the tile
+    static constexpr int PER = 2 * TX + 2 * TY;         // perimeter slots: top, bottom, left, right
     static constexpr int LCAP = 64;                     // BFS layers kept as masks
     static constexpr size_t smem = (size_t)(N + 3) * V * 4                  // cap, tcap, exc, lab
-                                   + (size_t)(N + 5) * TY * 8               // R[N], T, E, seed, inc, vis
+                                   + (size_t)(N + 4) * TY * 8               // R[N], T, E, inc, vis
                                    + (size_t)(LCAP + 1) * TY * 8            // BFS layers 1..LCAP
-                                   + (size_t)HL * 4 + 64;
+                                   + (size_t)(HL + PER) * 4 + 64;           // halo labels, hmin
     static_assert(TX == 32 || TX == 64, "row width must be 32 or 64");
-    static_assert(TY % 32 == 0 && V % NT == 0 && NT % 32 == 0, "tile/threads mismatch");
+    static_assert(TY % 32 == 0 && TY <= 64 && V % NT == 0 && NT % 32 == 0, "tile/threads mismatch");
 };
 
 // halo cell index of (hx, hy), a cell just outside the tile
@@ -81,8 +99,7 @@ template <int CONN, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT, 1)
 ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     using C = Cfg2D<CONN, TX, TY, NT>;
-    constexpr int N = C::N, V = C::V, VPT = C::VPT, RPL = C::RPL, NW = C::NW, LCAP = C::LCAP;
-    constexpr int HW = TX / 32;  // 32-bit halves per row
+    constexpr int N = C::N, V = C::V, RPL = C::RPL, NW = C::NW, HW = C::HW, LCAP = C::LCAP;
     extern __shared__ __align__(16) unsigned char smraw[];
     int *s_cap = (int *)smraw;            // [N][V] residual of arc i -> i + D(d)
     int *s_tcap = s_cap + N * V;          // [V]
@@ -91,55 +108,79 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     u64 *s_R = (u64 *)(s_lab + V);        // [N][TY] residual masks
     u64 *s_T = s_R + N * TY;              // [TY] residual arc to t
     u64 *s_E = s_T + TY;                  // [TY] positive excess
-    u64 *s_seed = s_E + TY;               // [TY] stage seeds (arcs into T_k \ {t})
-    u64 *s_inc = s_seed + TY;             // [TY] vertices that joined the closure
+    u64 *s_inc = s_E + TY;                // [TY] vertices that joined the closure
     u64 *s_vis = s_inc + TY;              // [TY] final closure
     u64 *s_layer = s_vis + TY;            // [LCAP+1][TY] BFS layers
     int *s_hl = (int *)(s_layer + (LCAP + 1) * TY);  // [HL] labels of B^R
+    int *s_hmin = s_hl + C::HL;           // [PER] min label over residual boundary arcs of a perimeter vertex
     __shared__ int s_ctl[4];
     __shared__ unsigned long long s_flow;
 
     const int r = blockIdx.x;
     if (!st.active[r]) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    DIAG_DECL
+    const long long diag_t0 = clock64();
+    (void)diag_t0;
     const int rx = r % g.RX, ry = r / g.RX;
     const int ox = rx * TX, oy = ry * TY;
     const size_t n = (size_t)g.n;
     const int dinf = g.dinf;
     if (tid == 0) s_flow = 0;
 
-    // ---- stage the tile; build the masks with warp ballots ---------------------
+    // rebuild the row masks from the planes (all threads; a warp covers 32
+    // consecutive vertices of one row, so one ballot gives half a row word)
+    auto rebuild_masks = [&]() {
+        for (int i = tid; i < V; i += NT) {
+            const int lx = i % TX, ly = i / TX;
+            const int hw = (ly * 2 + (lx >> 5));
 #pragma unroll
-    for (int q = 0; q < VPT; ++q) {
-        const int i = tid + q * NT;
+            for (int d = 0; d < N; ++d) {
+                const unsigned b = __ballot_sync(0xffffffffu, s_cap[d * V + i] > 0);
+                if (lane == 0) ((unsigned *)s_R)[d * TY * 2 + hw] = b;
+            }
+            const unsigned bt = __ballot_sync(0xffffffffu, s_tcap[i] > 0);
+            const unsigned be = __ballot_sync(0xffffffffu, s_exc[i] > 0);
+            if (lane == 0) {
+                ((unsigned *)s_T)[hw] = bt;
+                ((unsigned *)s_E)[hw] = be;
+            }
+        }
+    };
+    // perimeter slot p -> tile coordinates (top row, bottom row, left column, right column)
+    auto per_xy = [](int p, int &x, int &y) {
+        if (p < TX) { x = p; y = 0; }
+        else if (p < 2 * TX) { x = p - TX; y = TY - 1; }
+        else if (p < 2 * TX + TY) { x = 0; y = p - 2 * TX; }
+        else { x = TX - 1; y = p - 2 * TX - TY; }
+    };
+    // hmin[p] = min{d(w) : residual arc from the perimeter vertex to w in B^R}
+    auto rebuild_hmin = [&]() {
+        for (int p = tid; p < C::PER; p += NT) {
+            int x, y;
+            per_xy(p, x, y);
+            int m = INT_MAX;
+#pragma unroll
+            for (int d = 0; d < N; ++d) {
+                const int hx = x + arc_dx(CONN, d), hy = y + arc_dy(CONN, d);
+                if (hx >= 0 && hx < TX && hy >= 0 && hy < TY) continue;
+                if (s_cap[d * V + y * TX + x] > 0) m = min(m, s_hl[halo_idx<TX, TY>(hx, hy)]);
+            }
+            s_hmin[p] = m;
+        }
+    };
+
+    // ---- stage the tile --------------------------------------------------------
+    for (int i = tid; i < V; i += NT) {
         const int lx = i % TX, ly = i / TX;
         const int x = ox + lx, y = oy + ly;
         const bool in = x < g.X && y < g.Y;
         const size_t v = (size_t)y * g.X + x;
-        int tc = 0, ex = 0;
 #pragma unroll
-        for (int d = 0; d < N; ++d) {
-            const int c = in ? st.cap[d * n + v] : 0;
-            s_cap[d * V + i] = c;
-            const unsigned b = __ballot_sync(0xffffffffu, c > 0);
-            if (lane == 0) ((unsigned *)s_R)[(d * TY + ly) * 2 + (lx >> 5)] = b;
-        }
-        if (in) {
-            tc = st.tcap[v];
-            ex = st.exc[v];
-        }
-        s_tcap[i] = tc;
-        s_exc[i] = ex;
+        for (int d = 0; d < N; ++d) s_cap[d * V + i] = in ? st.cap[d * n + v] : 0;
+        s_tcap[i] = in ? st.tcap[v] : 0;
+        s_exc[i] = in ? st.exc[v] : 0;
         s_lab[i] = 0;
-        const unsigned bt = __ballot_sync(0xffffffffu, tc > 0);
-        const unsigned be = __ballot_sync(0xffffffffu, ex > 0);
-        if (lane == 0) {
-            ((unsigned *)s_T)[ly * 2 + (lx >> 5)] = bt;
-            ((unsigned *)s_E)[ly * 2 + (lx >> 5)] = be;
-        }
-    }
-    if (TX == 32) {  // upper halves of the row words are never written above
-        for (int w = tid; w < (N + 2) * TY; w += NT) ((unsigned *)s_R)[w * 2 + 1] = 0;
     }
     for (int h = tid; h < C::HL; h += NT) {
         int hx, hy;
@@ -152,7 +193,14 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
         const bool ing = x >= 0 && x < g.X && y >= 0 && y < g.Y;
         s_hl[h] = (ing && (CONN == 8 || !corner)) ? st.lab[(size_t)y * g.X + x] : dinf;
     }
+    if (TX == 32) {  // upper halves of the row words are never written by the ballots
+        for (int w = tid; w < (N + 2) * TY; w += NT) ((unsigned *)s_R)[w * 2 + 1] = 0;
+    }
     __syncthreads();
+    rebuild_masks();
+    rebuild_hmin();
+    __syncthreads();
+    DIAG_LAP(0);
 
     // ---- graph-warp helpers (warp 0) ------------------------------------------
     // next stage value above k: min{d(w)+1 > k : w in B^R, d(w) < d_inf}
@@ -164,29 +212,32 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
         }
         return __reduce_min_sync(0xffffffffu, best);
     };
-    // s_seed[y] bit x = vertex (x,y) has a residual arc to a boundary vertex w with d(w) < k
-    auto halo_seeds = [&](int k) {
-        for (int y = lane; y < TY; y += 32) s_seed[y] = 0;
-        __syncwarp();
-        if (k > 0) {
-            for (int p = lane; p < C::PER; p += 32) {
-                int x, y;
-                if (p < TX) { x = p; y = 0; }
-                else if (p < 2 * TX) { x = p - TX; y = TY - 1; }
-                else if (p < 2 * TX + TY - 2) { x = 0; y = p - 2 * TX + 1; }
-                else { x = TX - 1; y = p - (2 * TX + TY - 2) + 1; }
-                bool s = false;
+    // seed rows of T_k: vertices with a residual arc to t, or to w in B^R with d(w) < k
+    auto seed_rows = [&](int k, u64 (&sd)[RPL]) {
+        u64 top = 0, bot = 0;
 #pragma unroll
-                for (int d = 0; d < N; ++d) {
-                    const int hx = x + arc_dx(CONN, d), hy = y + arc_dy(CONN, d);
-                    if (hx >= 0 && hx < TX && hy >= 0 && hy < TY) continue;
-                    if (!((s_R[d * TY + y] >> x) & 1ull)) continue;
-                    if (s_hl[halo_idx<TX, TY>(hx, hy)] < k) s = true;
-                }
-                if (s) atomicOr(&s_seed[y], 1ull << x);
-            }
+        for (int h = 0; h < HW; ++h) {
+            const int x = lane + 32 * h;
+            top |= (u64)__ballot_sync(0xffffffffu, s_hmin[x] < k) << (32 * h);
+            bot |= (u64)__ballot_sync(0xffffffffu, s_hmin[TX + x] < k) << (32 * h);
         }
-        __syncwarp();
+        unsigned lft[RPL], rgt[RPL];
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) {
+            const int y = lane + 32 * h;
+            lft[h] = __ballot_sync(0xffffffffu, s_hmin[2 * TX + y] < k);
+            rgt[h] = __ballot_sync(0xffffffffu, s_hmin[2 * TX + TY + y] < k);
+        }
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            const int y = lane * RPL + j;
+            u64 s = s_T[y];
+            s |= (u64)((lft[y >> 5] >> (y & 31)) & 1u);
+            s |= (u64)((rgt[y >> 5] >> (y & 31)) & 1u) << (TX - 1);
+            if (y == 0) s |= top;
+            if (y == TY - 1) s |= bot;
+            sd[j] = s;
+        }
     };
     auto load_masks = [&](u64 (&Rm)[N][RPL]) {
 #pragma unroll
@@ -208,21 +259,17 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
             out[j] = a;
         }
     };
-    // closure C := C U {u : u -> seeds of stage k} (reachability, no distances);
-    // the vertices that joined go to s_inc; returns whether C meets the excess
+    // closure Cl := Cl U {u : u -> sd} (residual reachability); increments to s_inc
     u64 Cl[RPL];
 #pragma unroll
     for (int j = 0; j < RPL; ++j) Cl[j] = 0;
-    auto closure_extend = [&](int k) -> bool {
-        halo_seeds(k);
+    auto flood = [&](const u64 (&sd)[RPL]) {
         u64 Rm[N][RPL], fr[RPL], inc[RPL];
         load_masks(Rm);
         bool any = false;
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
-            const int y = lane * RPL + j;
-            const u64 sd = (k == 0 ? s_T[y] : s_seed[y]) & ~Cl[j];
-            const u64 f = row_fill(sd, Rm[0][j] & ~Cl[j], Rm[1][j] & ~Cl[j]);
+            const u64 f = row_fill(sd[j] & ~Cl[j], Rm[0][j] & ~Cl[j], Rm[1][j] & ~Cl[j]);
             Cl[j] |= f;
             inc[j] = f;
             fr[j] = f;
@@ -232,6 +279,7 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
             u64 nf[RPL];
             expand(Rm, fr, nf);
             any = false;
+            DIAG_ADD(3, 1);
 #pragma unroll
             for (int j = 0; j < RPL; ++j) {
                 const u64 f = row_fill(nf[j] & ~Cl[j], Rm[0][j] & ~Cl[j], Rm[1][j] & ~Cl[j]);
@@ -241,16 +289,16 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                 any |= f != 0ull;
             }
         }
-        bool meets = false;
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) {
-            const int y = lane * RPL + j;
-            s_inc[y] = inc[j];
-            meets |= (Cl[j] & s_E[y]) != 0ull;
-        }
-        return __any_sync(0xffffffffu, meets);
+        for (int j = 0; j < RPL; ++j) s_inc[lane * RPL + j] = inc[j];
     };
-    // all threads: label the vertices that joined the closure at stage k
+    auto closure_meets_excess = [&]() -> bool {
+        bool m = false;
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) m |= (Cl[j] & s_E[lane * RPL + j]) != 0ull;
+        return __any_sync(0xffffffffu, m);
+    };
+    // all threads: label the vertices of s_inc with k
     auto write_labels = [&](int k) {
         for (int y = warp; y < TY; y += NW) {
             const u64 m = s_inc[y];
@@ -266,12 +314,23 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     const int klimit = sa.partial ? sa.sweep : INT_MAX;
     long long flow_acc = 0;
     int rounds = 0, stages = 0, epoch = 0;
-    bool err = false;
+    bool err = false, any_aug = false;
+    bool cl_valid = true;  // warp 0: Cl is the closure of T_k on the current graph (empty at start)
 
     // ---- ARD stages ------------------------------------------------------------
     for (int k = 0;;) {
+        DIAG_MARK();
         if (warp == 0) {
-            const bool reach = closure_extend(k);
+            DIAG_ADD(2, 1);
+            u64 sd[RPL];
+            seed_rows(k, sd);
+            if (!cl_valid) {
+#pragma unroll
+                for (int j = 0; j < RPL; ++j) Cl[j] = 0;
+                cl_valid = true;
+            }
+            flood(sd);
+            const bool reach = closure_meets_excess();
             const int kn = next_stage(k);
             if (lane == 0) {
                 s_ctl[0] = reach;
@@ -279,13 +338,13 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
             }
         }
         __syncthreads();
-        write_labels(k);
+        DIAG_LAP(1);
         const int reach = s_ctl[0], kn = s_ctl[1];
-        // after a round-cap error no more augmentation, but the labels of every
-        // stage are still computed so the labeling stays valid
+        if (!any_aug) write_labels(k);  // labels stay exact until the first augmentation
         const bool aug = k <= klimit && !err;
         if (aug) ++stages;
         if (aug && reach) {
+            any_aug = true;
             // Augment(R, T_k): rounds of exact BFS + layered push
             for (int round = 0;; ++round) {
                 if (round >= sa.max_rounds) { err = true; break; }
@@ -295,24 +354,27 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                     __syncthreads();
                     epoch = 1;
                 }
+                DIAG_MARK();
                 if (warp == 0) {
-                    halo_seeds(k);
-                    u64 Rm[N][RPL], vis[RPL], fr[RPL], ex[RPL];
+                    DIAG_ADD(5, 1);
+                    u64 Rm[N][RPL], vis[RPL], fr[RPL], want[RPL];
                     load_masks(Rm);
+                    seed_rows(k, fr);
                     int lmax = 0;
-                    bool unreached = false;
+                    bool pending = false;
 #pragma unroll
                     for (int j = 0; j < RPL; ++j) {
                         const int y = lane * RPL + j;
-                        ex[j] = s_E[y];
-                        fr[j] = s_T[y] | s_seed[y];
+                        // excess that can reach T_k lies inside the (older) closure
+                        const u64 ex = s_E[y] & Cl[j];
                         vis[j] = fr[j];
                         s_layer[1 * TY + y] = fr[j];
-                        if (fr[j] & ex[j]) lmax = 1;
-                        if (ex[j] & ~vis[j]) unreached = true;
+                        if (fr[j] & ex) lmax = 1;
+                        want[j] = ex & ~vis[j];
+                        pending |= want[j] != 0ull;
                     }
                     int L = 1;
-                    while (__any_sync(0xffffffffu, unreached)) {
+                    while (__any_sync(0xffffffffu, pending)) {
                         u64 nf[RPL];
                         expand(Rm, fr, nf);
                         bool any = false;
@@ -323,7 +385,7 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                         }
                         if (!__any_sync(0xffffffffu, any)) break;
                         ++L;
-                        unreached = false;
+                        pending = false;
 #pragma unroll
                         for (int j = 0; j < RPL; ++j) {
                             const int y = lane * RPL + j;
@@ -335,14 +397,17 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                                 const int tg = deep_tag(epoch, L);
                                 for (u64 m = nf[j]; m; m &= m - 1) s_lab[y * TX + __ffsll((long long)m) - 1] = tg;
                             }
-                            if (nf[j] & ex[j]) lmax = L;
-                            if (ex[j] & ~vis[j]) unreached = true;
+                            if (nf[j] & want[j]) lmax = L;
+                            want[j] &= ~nf[j];
+                            pending |= want[j] != 0ull;
                         }
                     }
                     lmax = __reduce_max_sync(0xffffffffu, lmax);
                     if (lane == 0) s_ctl[2] = lmax;
+                    DIAG_ADD(6, L);
                 }
                 __syncthreads();
+                DIAG_LAP(4);
                 const int Lmax = s_ctl[2];
                 if (Lmax == 0) break;  // no excess vertex reaches T_k: stage done
                 ++rounds;
@@ -351,8 +416,7 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                 for (int L = Lmax; L >= 1; --L) {
                     const int tgL = deep_tag(epoch, L), tgL1 = deep_tag(epoch, L - 1);
                     for (int y = warp; y < TY; y += NW) {
-                        u64 P = s_E[y];
-                        if (L <= LCAP) P &= s_layer[L * TY + y];
+                        const u64 P = L <= LCAP ? s_layer[L * TY + y] : ~0ull;
                         if (!P) continue;
 #pragma unroll
                         for (int h = 0; h < HW; ++h) {
@@ -369,7 +433,6 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                                     s_tcap[i] = tc - dl;
                                     e -= dl;
                                     flow_acc += dl;
-                                    if (tc == dl) atomicAnd(&s_T[ly], ~(1ull << lx));
                                 }
 #pragma unroll
                                 for (int d = 0; d < N; ++d) {
@@ -381,7 +444,6 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                                         const int dl = min(e, c);
                                         s_cap[d * V + i] = c - dl;
                                         e -= dl;
-                                        if (c == dl) atomicAnd(&s_R[d * TY + ly], ~(1ull << lx));
                                     }
                                 }
                             } else {
@@ -398,56 +460,67 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                                     if (!below) continue;
                                     const int dl = min(e, c);
                                     s_cap[d * V + i] = c - dl;
-                                    const int rc = s_cap[(d ^ 1) * V + j];
-                                    s_cap[(d ^ 1) * V + j] = rc + dl;
-                                    const int old = atomicAdd(&s_exc[j], dl);
+                                    s_cap[(d ^ 1) * V + j] += dl;
+                                    atomicAdd(&s_exc[j], dl);
                                     e -= dl;
-                                    if (c == dl) atomicAnd(&s_R[d * TY + ly], ~(1ull << lx));
-                                    if (rc == 0) atomicOr(&s_R[(d ^ 1) * TY + ny], 1ull << nx);
-                                    if (old == 0) atomicOr(&s_E[ny], 1ull << nx);
                                 }
                             }
                             s_exc[i] = e;
-                            if (e == 0) atomicAnd(&s_E[ly], ~(1ull << lx));
                         }
                     }
                     __syncthreads();
                 }
-            }
-            // the residual graph changed: rebuild the closure and labels of stages <= k
-            if (warp == 0) {
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) Cl[j] = 0;
-            }
-            for (int k2 = 0;;) {
-                if (warp == 0) {
-                    closure_extend(k2);
-                    const int n2 = next_stage(k2);
-                    if (lane == 0) s_ctl[3] = n2;
-                }
+                rebuild_masks();
+                rebuild_hmin();
                 __syncthreads();
-                write_labels(k2);
-                const int n2 = s_ctl[3];
-                __syncthreads();
-                if (n2 == INT_MAX || n2 > k) break;
-                k2 = n2;
+                DIAG_LAP(7);
+                DIAG_ADD(8, Lmax);
             }
+            if (warp == 0) cl_valid = false;  // the residual graph changed
         }
         if (kn == INT_MAX) break;
+        // nothing left to learn: labels are recomputed at the end anyway
+        if (any_aug && (kn > klimit || err)) break;
         k = kn;
         __syncthreads();
+    }
+
+    // ---- region-relabel after augmentation: d(u) = min{k : u -> T_k} -------------
+    if (any_aug) {
+        DIAG_MARK();
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) Cl[j] = 0;
+        }
+        for (int k2 = 0;;) {
+            if (warp == 0) {
+                DIAG_ADD(2, 1);
+                u64 sd[RPL];
+                seed_rows(k2, sd);
+                flood(sd);
+                const int n2 = next_stage(k2);
+                if (lane == 0) s_ctl[3] = n2;
+            }
+            __syncthreads();
+            write_labels(k2);
+            const int n2 = s_ctl[3];
+            __syncthreads();
+            if (n2 == INT_MAX) break;
+            k2 = n2;
+        }
+        DIAG_LAP(9);
     }
     if (warp == 0) {
 #pragma unroll
         for (int j = 0; j < RPL; ++j) s_vis[lane * RPL + j] = Cl[j];
     }
     __syncthreads();
+    DIAG_MARK();
 
     // ---- write back -------------------------------------------------------------
     int left = 0;
-#pragma unroll
-    for (int q = 0; q < VPT; ++q) {
-        const int i = tid + q * NT;
+    for (int i = tid; i < V; i += NT) {
         const int lx = i % TX, ly = i / TX;
         const int x = ox + lx, y = oy + ly;
         if (!(x < g.X && y < g.Y)) continue;
@@ -481,6 +554,10 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     if (lane == 0 && f) atomicAdd(&s_flow, f);
     __syncthreads();
     if (tid == 0) {
+        DIAG_LAP(10);
+        DIAG_ADD(11, clock64() - diag_t0);
+        DIAG_ADD(12, 1);
+        DIAG_FLUSH();
         if (s_flow) atomicAdd(st.flow_t, s_flow);
         st.disc[r] = 1;
         st.left_active[r] = (unsigned char)left;

@@ -339,6 +339,7 @@ static long long boundary_count(const Geom &g) {
     return (long long)g.n - inner(g.X, g.tx) * inner(g.Y, g.ty) * inner(g.Z, g.tz);
 }
 
+
 extern "C" {
 
 void mf_default_opts(mf_opts *o) {

@@ -74,6 +74,22 @@ struct SweepArgs {
     Counters64 *c64;
 };
 
+// Optional phase probes (clock64 deltas and counters per discharge phase),
+// compiled only with -DMF_DIAG; they expand to nothing otherwise.
+#ifdef MF_DIAG
+#define DIAG_DECL unsigned long long dg_[16] = {0}; long long dt_ = clock64();
+#define DIAG_MARK() (dt_ = clock64())
+#define DIAG_LAP(slot) do { const long long t_ = clock64(); dg_[slot] += t_ - dt_; dt_ = t_; } while (0)
+#define DIAG_ADD(slot, v) (dg_[slot] += (unsigned long long)(v))
+#define DIAG_FLUSH() do { for (int s_ = 0; s_ < 16; ++s_) if (dg_[s_]) atomicAdd(&mf_diag[s_], dg_[s_]); } while (0)
+#else
+#define DIAG_DECL
+#define DIAG_MARK() ((void)0)
+#define DIAG_LAP(slot) ((void)0)
+#define DIAG_ADD(slot, v) ((void)0)
+#define DIAG_FLUSH() ((void)0)
+#endif
+
 // launchers (ard_discharge.cu)
 size_t discharge_smem_bytes(int conn, int tx, int ty, int tz);
 bool discharge_supported(int conn, int tx, int ty, int tz);
