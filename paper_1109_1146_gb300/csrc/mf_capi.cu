@@ -25,6 +25,7 @@ struct mf_grid {
     int *cs = nullptr, *ct = nullptr, *nl = nullptr;  // stored inputs
     DevState st{};
     unsigned char *smin = nullptr, *tset = nullptr;
+    void *cut_scratch = nullptr;                      // 2D cut: bit masks and sets
     Counters64 *c64 = nullptr;
     int *h_ctr = nullptr;                             // pinned mirror of st.ctr
     long long boundary = 0;
@@ -124,21 +125,47 @@ __global__ void validate_kernel(const Geom g, const int *cs, const int *ct, cons
     if (f) atomicOr(flags, f);
 }
 
+// A region is "touched" in a sweep when it or one of its neighbour regions
+// (across a stencil arc) was discharged: only those can see their boundary
+// flow, excess or labels change.
+template <int CONN>
+__device__ __forceinline__ bool region_touched(const Geom &g, const DevState &st, int r) {
+    if (st.disc[r]) return true;
+    const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+#pragma unroll
+    for (int d = 0; d < CONN; ++d) {
+        const int qx = rx + arc_dx(CONN, d), qy = ry + arc_dy(CONN, d), qz = rz + arc_dz(CONN, d);
+        if (qx < 0 || qx >= g.RX || qy < 0 || qy >= g.RY || qz < 0 || qz >= g.RZ) continue;
+        if (st.disc[(qz * g.RY + qy) * g.RX + qx]) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int hist_bin(int l) { return l < kHistBins ? l : kHistBins; }
+
 // Flow and label fusion of Algorithm 2, gather form: every boundary vertex u
 // updates only its own arcs and excess.  For an inter-region arc (u,w):
 //   alpha(a,b) = [d'(a) <= d'(b) + 1];
 //   u's push on (u,w) is kept iff alpha(w,u), w's push on (w,u) iff alpha(u,w);
 //   a refused push goes back to its sender (residual and excess restored).
-// Also commits the new boundary labels and counts the gap histogram.
+// Also commits the new boundary labels and keeps the histogram of boundary
+// labels (Sec. 5.3: the global gap needs labels of B only) up to date.
 template <int CONN>
 __global__ void fuse_kernel(const Geom g, const DevState st) {
     const int r = blockIdx.x;
+    __shared__ int s_touch;
+    if (threadIdx.x == 0) s_touch = region_touched<CONN>(g, st, r);
+    __syncthreads();
+    if (!s_touch) return;
     const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
     const int V = g.tx * g.ty * g.tz;
     const size_t n = (size_t)g.n;
     const bool discr = st.disc[r];
     for (int i = threadIdx.x; i < V; i += blockDim.x) {
-        const int x = rx * g.tx + i % g.tx, y = ry * g.ty + (i / g.tx) % g.ty, z = rz * g.tz + i / (g.tx * g.ty);
+        const int lx = i % g.tx, ly = (i / g.tx) % g.ty, lz = i / (g.tx * g.ty);
+        if (lx != 0 && lx != g.tx - 1 && ly != 0 && ly != g.ty - 1 && (CONN != 6 || (lz != 0 && lz != g.tz - 1)))
+            continue;  // interior of the tile
+        const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
         if (!in_grid(g, x, y, z)) continue;
         const size_t u = ((size_t)z * g.Y + y) * g.X + x;
         bool boundary = false;
@@ -167,14 +194,21 @@ __global__ void fuse_kernel(const Geom g, const DevState st) {
         }
         if (!boundary) continue;
         if (back_total) st.exc[u] += back_total;
-        if (discr) st.lab[u] = du;
-        if (du < g.dinf) atomicAdd(&st.hist[min(du, kHistBins)], 1);
+        if (discr) {
+            const int old = st.lab[u];
+            if (old != du) {
+                if (old < g.dinf) atomicSub(&st.hist[hist_bin(old)], 1);
+                if (du < g.dinf) atomicAdd(&st.hist[hist_bin(du)], 1);
+                st.lab[u] = du;
+            }
+        }
     }
 }
 
 // Global gap (Sec. 5.1, with the boundary-label histogram of Sec. 5.3): the
 // smallest g > 0 below the highest boundary label with no boundary vertex
-// labelled g.  Every vertex with g < d < d_inf cannot reach t.
+// labelled g.  Every vertex with g < d < d_inf cannot reach t.  The bins
+// above g are emptied (those labels become d_inf).
 __global__ void gap_find_kernel(const DevState st) {
     __shared__ int s_hi, s_g;
     if (threadIdx.x == 0) { s_hi = 0; s_g = INT_MAX; }
@@ -190,19 +224,33 @@ __global__ void gap_find_kernel(const DevState st) {
         if (st.hist[b] == 0) gmin = min(gmin, b);
     atomicMin(&s_g, gmin);
     __syncthreads();
-    if (threadIdx.x == 0) st.ctr[kGap] = s_g == INT_MAX ? 0 : s_g;
+    const int gap = s_g == INT_MAX ? 0 : s_g;
+    if (threadIdx.x == 0) st.ctr[kGap] = gap;
+    if (gap > 0)
+        for (int b = gap + 1 + threadIdx.x; b <= kHistBins; b += blockDim.x) st.hist[b] = 0;
 }
 
-// Apply the gap, decide which regions discharge next sweep, reset per-sweep flags.
+// Apply the gap (all vertices of every region, only when a gap was found),
+// decide which regions discharge in the next sweep (only touched regions can
+// become active), reset the per-sweep flags.
 template <int CONN>
 __global__ void post_kernel(const Geom g, const DevState st) {
     const int r = blockIdx.x;
+    const int gap = st.ctr[kGap];
+    __shared__ int s_touch;
+    if (threadIdx.x == 0) s_touch = region_touched<CONN>(g, st, r);
+    __syncthreads();
+    const bool touched = s_touch;
+    if (!touched && gap == 0) return;
     const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
     const int V = g.tx * g.ty * g.tz;
-    const int gap = st.ctr[kGap];
-    int act = st.left_active[r];
+    int act = touched ? st.left_active[r] : 0;
     for (int i = threadIdx.x; i < V; i += blockDim.x) {
-        const int x = rx * g.tx + i % g.tx, y = ry * g.ty + (i / g.tx) % g.ty, z = rz * g.tz + i / (g.tx * g.ty);
+        const int lx = i % g.tx, ly = (i / g.tx) % g.ty, lz = i / (g.tx * g.ty);
+        const bool border = lx == 0 || lx == g.tx - 1 || ly == 0 || ly == g.ty - 1 ||
+                            (CONN == 6 && (lz == 0 || lz == g.tz - 1));
+        if (gap == 0 && !border) continue;
+        const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
         if (!in_grid(g, x, y, z)) continue;
         const size_t u = ((size_t)z * g.Y + y) * g.X + x;
         int l = st.lab[u];
@@ -210,15 +258,26 @@ __global__ void post_kernel(const Geom g, const DevState st) {
             l = g.dinf;
             st.lab[u] = l;
         }
-        if (!act && l < g.dinf && st.exc[u] > 0) act = 1;
+        if (touched && border && !act && l < g.dinf && st.exc[u] > 0) act = 1;
     }
     act = __syncthreads_or(act);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && touched) {
         st.active[r] = (unsigned char)act;
-        st.disc[r] = 0;
-        st.left_active[r] = 0;
         if (act) atomicAdd(&st.ctr[kActiveRegions], 1);
     }
+}
+
+// per-sweep flags are cleared after post has read them
+__global__ void clear_flags_kernel(const DevState st, int nreg) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
+        st.disc[r] = 0;
+        st.left_active[r] = 0;
+    }
+}
+
+// histogram at Init: every boundary vertex has label 0
+__global__ void hist_init_kernel(const DevState st, int nb) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) st.hist[0] = nb;
 }
 
 __global__ void cut_seed_kernel(const Geom g, const DevState st, unsigned char *smin, unsigned char *tset) {
@@ -313,6 +372,7 @@ static cudaError_t launch_fuse_post(mf_grid *h, bool gap_on) {
     fuse_kernel<CONN><<<h->g.nreg, 256, 0, h->stream>>>(h->g, h->st);
     if (gap_on) gap_find_kernel<<<1, 1024, 0, h->stream>>>(h->st);
     post_kernel<CONN><<<h->g.nreg, 256, 0, h->stream>>>(h->g, h->st);
+    clear_flags_kernel<<<(h->g.nreg + 255) / 256, 256, 0, h->stream>>>(h->st, h->g.nreg);
     return cudaGetLastError();
 }
 template <int CONN>
@@ -357,7 +417,7 @@ const char *mf_last_error(const mf_grid *g) { return g ? g->err.c_str() : g_stat
 static void free_all(mf_grid *h) {
     void *ptrs[] = {h->cs, h->ct, h->nl, h->st.cap, h->st.tcap, h->st.exc, h->st.lab, h->st.lab_next,
                     h->st.bout, h->st.active, h->st.disc, h->st.left_active, h->st.flow_t, h->st.flow0,
-                    h->st.hist, h->st.ctr, h->smin, h->tset, h->c64};
+                    h->st.hist, h->st.ctr, h->smin, h->tset, h->c64, h->cut_scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
@@ -420,8 +480,10 @@ mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int con
         {(void **)&g->st.active, (size_t)G.nreg}, {(void **)&g->st.disc, (size_t)G.nreg},
         {(void **)&g->st.left_active, (size_t)G.nreg}, {(void **)&g->st.flow_t, 8}, {(void **)&g->st.flow0, 8},
         {(void **)&g->st.hist, (kHistBins + 1) * 4}, {(void **)&g->st.ctr, kCtrWords * 4},
-        {(void **)&g->smin, (size_t)n}, {(void **)&g->tset, (size_t)n}, {(void **)&g->c64, sizeof(Counters64)}};
+        {(void **)&g->smin, (size_t)n}, {(void **)&g->tset, (size_t)n}, {(void **)&g->c64, sizeof(Counters64)},
+        {(void **)&g->cut_scratch, ndim == 2 ? cut2d_scratch_bytes(G, connectivity) : 0}};
     for (auto &a : allocs) {
+        if (a.bytes == 0) continue;
         e = cudaMalloc(a.p, a.bytes);
         if (e != cudaSuccess) {
             g->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -487,8 +549,11 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
     CK(cudaMemsetAsync(g->st.flow0, 0, 8, g->stream));
     CK(cudaMemsetAsync(g->st.ctr, 0, kCtrWords * 4, g->stream));
     CK(cudaMemsetAsync(g->c64, 0, sizeof(Counters64), g->stream));
+    CK(cudaMemsetAsync(g->st.hist, 0, (kHistBins + 1) * 4, g->stream));
     CK(DISPATCH(g->conn, launch_init, g));
-    g->launches = 1;
+    hist_init_kernel<<<1, 32, 0, g->stream>>>(g->st, (int)g->boundary);
+    CK(cudaGetLastError());
+    g->launches = 2;
     g->sweep = 0;
     g->begun = true;
     g->finished = false;
@@ -504,14 +569,13 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     sa.max_rounds = g->opts.max_rounds;
     sa.variant = g->opts.kernel_variant;
     sa.c64 = g->c64;
-    CK(cudaMemsetAsync(g->st.hist, 0, (kHistBins + 1) * 4, g->stream));
     CK(cudaMemsetAsync(g->st.ctr, 0, 4 * (kGap + 1), g->stream));  // active count, error, gap
     CK(cudaEventRecord(g->ev[4], g->stream));
     CK(launch_discharge(g->conn, g->g, g->st, sa, g->stream));
     CK(cudaEventRecord(g->ev[5], g->stream));
     CK(DISPATCH(g->conn, launch_fuse_post, g, g->opts.global_gap != 0));
     CK(cudaEventRecord(g->ev[6], g->stream));
-    g->launches += g->opts.global_gap ? 4 : 3;
+    g->launches += g->opts.global_gap ? 5 : 4;
     CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     {
@@ -538,22 +602,28 @@ mf_status mf_sweep(mf_grid *g, int32_t *active) {
 mf_status mf_finish(mf_grid *g) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!g->begun) return fail(g, MF_ESTATE, "mf_begin has not been called");
-    cut_seed_kernel<<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->g, g->st, g->smin, g->tset);
-    CK(cudaGetLastError());
     int passes = 0;
-    for (int which = 0; which < 2; ++which) {
-        for (;;) {
-            CK(cudaMemsetAsync(&g->st.ctr[kChanged], 0, 4, g->stream));
-            CK(DISPATCH(g->conn, launch_cut_pass, g, which == 0 ? g->smin : g->tset, which == 0 ? 1 : 0));
-            ++g->launches;
-            CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
-            CK(cudaStreamSynchronize(g->stream));
-            ++passes;
-            if (!g->h_ctr[kChanged]) break;
+    if (g->ndim == 2) {
+        CK(cut2d(g->conn, g->g, g->st, g->cut_scratch, g->smin, g->tset, g->h_ctr, &passes, g->stream));
+        g->launches += 2 + passes + 1;
+    } else {
+        cut_seed_kernel<<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->g, g->st, g->smin, g->tset);
+        CK(cudaGetLastError());
+        for (int which = 0; which < 2; ++which) {
+            for (;;) {
+                CK(cudaMemsetAsync(&g->st.ctr[kChanged], 0, 4, g->stream));
+                CK(DISPATCH(g->conn, launch_cut_pass, g, which == 0 ? g->smin : g->tset, which == 0 ? 1 : 0));
+                ++g->launches;
+                CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
+                CK(cudaStreamSynchronize(g->stream));
+                ++passes;
+                if (!g->h_ctr[kChanged]) break;
+            }
         }
+        complement_kernel<<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->tset, (size_t)g->g.n);
+        CK(cudaGetLastError());
+        g->launches += 2;
     }
-    complement_kernel<<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->tset, (size_t)g->g.n);
-    CK(cudaGetLastError());
     g->stats.cut_passes = passes;
     long long f0 = 0;
     unsigned long long ft = 0;
@@ -567,7 +637,6 @@ mf_status mf_finish(mf_grid *g) {
     g->stats.rounds = (int64_t)c.rounds;
     g->stats.discharges = (int64_t)c.discharges;
     g->stats.discharged_vertices = (int64_t)c.discharged_vertices;
-    g->launches += 2;  // seed + complement
     g->stats.launches = g->launches;
     g->finished = true;
     return MF_OK;

@@ -95,6 +95,10 @@ size_t discharge_smem_bytes(int conn, int tx, int ty, int tz);
 bool discharge_supported(int conn, int tx, int ty, int tz);
 cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
                              cudaStream_t stream);
+// cut2d.cu: residual closures S_min / S_max of a 2D grid on bit masks
+size_t cut2d_scratch_bytes(const Geom &g, int conn);
+cudaError_t cut2d(int conn, const Geom &g, const DevState &st, void *scratch, unsigned char *smin,
+                  unsigned char *smax, int *h_changed, int *passes, cudaStream_t s);
 // ard_discharge2d.cu
 bool discharge2d_supported(int conn, int tx, int ty);
 cudaError_t launch_discharge2d(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
