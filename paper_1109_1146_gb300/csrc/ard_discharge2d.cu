@@ -57,7 +57,7 @@ struct Cfg2D {
     static constexpr size_t smem = (size_t)(N + 3) * V * 4                  // cap, tcap, exc, lab
                                    + (size_t)(N + 4) * TY * 8               // R[N], T, E, inc, vis
                                    + (size_t)(LCAP + 1) * TY * 8            // BFS layers 1..LCAP
-                                   + (size_t)(HL + PER) * 4 + 64;           // halo labels, hmin
+                                   + (size_t)(HL + PER) * 4 + TY + 64;      // halo labels, hmin, dirty rows
     static_assert(TX == 32 || TX == 64, "row width must be 32 or 64");
     static_assert(TY % 32 == 0 && TY <= 64 && V % NT == 0 && NT % 32 == 0, "tile/threads mismatch");
 };
@@ -113,6 +113,7 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     u64 *s_layer = s_vis + TY;            // [LCAP+1][TY] BFS layers
     int *s_hl = (int *)(s_layer + (LCAP + 1) * TY);  // [HL] labels of B^R
     int *s_hmin = s_hl + C::HL;           // [PER] min label over residual boundary arcs of a perimeter vertex
+    unsigned char *s_dirty = (unsigned char *)(s_hmin + C::PER);  // [TY] rows whose planes changed
     __shared__ int s_ctl[4];
     __shared__ unsigned long long s_flow;
 
@@ -171,17 +172,33 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     };
 
     // ---- stage the tile --------------------------------------------------------
-    for (int i = tid; i < V; i += NT) {
-        const int lx = i % TX, ly = i / TX;
-        const int x = ox + lx, y = oy + ly;
-        const bool in = x < g.X && y < g.Y;
-        const size_t v = (size_t)y * g.X + x;
+    const bool full = ox + TX <= g.X && oy + TY <= g.Y;
+    const bool vec = full && (g.X % 4) == 0;  // every row starts on a 16-byte boundary
+    if (vec) {
+        for (int i4 = tid; i4 < V / 4; i4 += NT) {
+            const int i = i4 * 4, lx = i % TX, ly = i / TX;
+            const size_t v = (size_t)(oy + ly) * g.X + ox + lx;
 #pragma unroll
-        for (int d = 0; d < N; ++d) s_cap[d * V + i] = in ? st.cap[d * n + v] : 0;
-        s_tcap[i] = in ? st.tcap[v] : 0;
-        s_exc[i] = in ? st.exc[v] : 0;
-        s_lab[i] = 0;
+            for (int d = 0; d < N; ++d)
+                *(int4 *)&s_cap[d * V + i] = __ldcs((const int4 *)&st.cap[d * n + v]);
+            *(int4 *)&s_tcap[i] = __ldcs((const int4 *)&st.tcap[v]);
+            *(int4 *)&s_exc[i] = __ldcs((const int4 *)&st.exc[v]);
+            *(int4 *)&s_lab[i] = make_int4(0, 0, 0, 0);
+        }
+    } else {
+        for (int i = tid; i < V; i += NT) {
+            const int lx = i % TX, ly = i / TX;
+            const int x = ox + lx, y = oy + ly;
+            const bool in = x < g.X && y < g.Y;
+            const size_t v = (size_t)y * g.X + x;
+#pragma unroll
+            for (int d = 0; d < N; ++d) s_cap[d * V + i] = in ? st.cap[d * n + v] : 0;
+            s_tcap[i] = in ? st.tcap[v] : 0;
+            s_exc[i] = in ? st.exc[v] : 0;
+            s_lab[i] = 0;
+        }
     }
+    for (int y = tid; y < TY; y += NT) s_dirty[y] = 0;
     for (int h = tid; h < C::HL; h += NT) {
         int hx, hy;
         if (h < TX + 2) { hx = h - 1; hy = -1; }
@@ -412,12 +429,29 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                 if (Lmax == 0) break;  // no excess vertex reaches T_k: stage done
                 ++rounds;
                 // layered push, top layer first: a vertex of layer L pushes only to
-                // layer L-1 (to T_k from layer 1), so every arc has one writer per step
+                // layer L-1 (to T_k from layer 1), so every arc has one writer per step.
+                // The masks R_d are exact for the arcs from layer L to L-1 until layer L
+                // pushes, so A_d = R_d & (layer L-1 seen through arc d) lists the
+                // admissible arcs of a whole row at once.
                 for (int L = Lmax; L >= 1; --L) {
                     const int tgL = deep_tag(epoch, L), tgL1 = deep_tag(epoch, L - 1);
+                    const bool lo_mask = L - 1 <= LCAP;
                     for (int y = warp; y < TY; y += NW) {
                         const u64 P = L <= LCAP ? s_layer[L * TY + y] : ~0ull;
                         if (!P) continue;
+                        u64 A[N];
+                        if (L > 1 && lo_mask) {
+                            const u64 *lay = s_layer + (L - 1) * TY;
+                            const u64 la = y > 0 ? lay[y - 1] : 0ull, l0 = lay[y], lb = y < TY - 1 ? lay[y + 1] : 0ull;
+#pragma unroll
+                            for (int d = 0; d < N; ++d) {
+                                const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d);
+                                const u64 src = dy < 0 ? la : dy > 0 ? lb : l0;
+                                const u64 sh = dx > 0 ? (src >> 1) : dx < 0 ? (src << 1) : src;
+                                A[d] = s_R[d * TY + y] & sh;
+                            }
+                        }
+                        bool pushed = false;
 #pragma unroll
                         for (int h = 0; h < HW; ++h) {
                             const int lx = lane + 32 * h, ly = y;
@@ -426,6 +460,7 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                             if (L > LCAP && s_lab[i] != tgL) continue;
                             int e = s_exc[i];
                             if (e <= 0) continue;
+                            const int e0 = e;
                             if (L == 1) {
                                 const int tc = s_tcap[i];
                                 if (tc > 0) {
@@ -451,13 +486,16 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                                 for (int d = 0; d < N; ++d) {
                                     if (e == 0) break;
                                     const int nx = lx + arc_dx(CONN, d), ny = ly + arc_dy(CONN, d);
-                                    if (!(nx >= 0 && nx < TX && ny >= 0 && ny < TY)) continue;
+                                    bool adm;
+                                    if (lo_mask) {
+                                        adm = (A[d] >> lx) & 1ull;
+                                    } else {
+                                        adm = nx >= 0 && nx < TX && ny >= 0 && ny < TY &&
+                                              s_lab[ny * TX + nx] == tgL1 && s_cap[d * V + i] > 0;
+                                    }
+                                    if (!adm) continue;
                                     const int j = ny * TX + nx;
                                     const int c = s_cap[d * V + i];
-                                    if (c <= 0) continue;
-                                    const bool below = (L - 1 <= LCAP) ? ((s_layer[(L - 1) * TY + ny] >> nx) & 1ull) != 0
-                                                                       : s_lab[j] == tgL1;
-                                    if (!below) continue;
                                     const int dl = min(e, c);
                                     s_cap[d * V + i] = c - dl;
                                     s_cap[(d ^ 1) * V + j] += dl;
@@ -466,6 +504,11 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
                                 }
                             }
                             s_exc[i] = e;
+                            pushed |= e != e0;
+                        }
+                        if (__any_sync(0xffffffffu, pushed) && lane < 3) {
+                            const int yy = y - 1 + lane;
+                            if (yy >= 0 && yy < TY) s_dirty[yy] = 1;
                         }
                     }
                     __syncthreads();
@@ -518,13 +561,14 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     __syncthreads();
     DIAG_MARK();
 
-    // ---- write back -------------------------------------------------------------
+    // ---- write back: planes of rows that changed; labels and boundary flows always
     int left = 0;
     for (int i = tid; i < V; i += NT) {
         const int lx = i % TX, ly = i / TX;
         const int x = ox + lx, y = oy + ly;
         if (!(x < g.X && y < g.Y)) continue;
         const size_t v = (size_t)y * g.X + x;
+        const bool dirty = s_dirty[ly] != 0;
         bool perim = false;
 #pragma unroll
         for (int d = 0; d < N; ++d) {
@@ -532,17 +576,23 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
             const int gx = x + arc_dx(CONN, d), gy = y + arc_dy(CONN, d);
             const bool intile = nx >= 0 && nx < TX && ny >= 0 && ny < TY;
             const bool ing = gx >= 0 && gx < g.X && gy >= 0 && gy < g.Y;
-            const int c = s_cap[d * V + i];
             if (intile) {
-                st.cap[d * n + v] = c;
+                if (dirty) st.cap[d * n + v] = s_cap[d * V + i];
             } else if (ing) {
                 perim = true;
-                st.bout[d * n + v] = st.cap[d * n + v] - c;  // flow pushed across the boundary
-                st.cap[d * n + v] = c;
+                if (dirty) {
+                    const int c = s_cap[d * V + i];
+                    st.bout[d * n + v] = st.cap[d * n + v] - c;  // flow pushed across the boundary
+                    st.cap[d * n + v] = c;
+                } else {
+                    st.bout[d * n + v] = 0;
+                }
             }
         }
-        st.tcap[v] = s_tcap[i];
-        st.exc[v] = s_exc[i];
+        if (dirty) {
+            st.tcap[v] = s_tcap[i];
+            st.exc[v] = s_exc[i];
+        }
         const int lab = ((s_vis[ly] >> lx) & 1ull) ? s_lab[i] : dinf;
         if (perim) st.lab_next[v] = lab;
         else st.lab[v] = lab;

@@ -60,7 +60,7 @@ __device__ __forceinline__ bool in_grid(const Geom &g, int x, int y, int z) {
     return x >= 0 && x < g.X && y >= 0 && y < g.Y && z >= 0 && z < g.Z;
 }
 __device__ __forceinline__ int region_of(const Geom &g, int x, int y, int z) {
-    return ((z / g.tz) * g.RY + y / g.ty) * g.RX + x / g.tx;
+    return ((z >> g.sz) * g.RY + (y >> g.sy)) * g.RX + (x >> g.sx);
 }
 
 // Init (Sec. 2): every s-link saturated, f := 0 on the rest, d := 0.  The part
@@ -162,7 +162,7 @@ __global__ void fuse_kernel(const Geom g, const DevState st) {
     const size_t n = (size_t)g.n;
     const bool discr = st.disc[r];
     for (int i = threadIdx.x; i < V; i += blockDim.x) {
-        const int lx = i % g.tx, ly = (i / g.tx) % g.ty, lz = i / (g.tx * g.ty);
+        const int lx = i & (g.tx - 1), ly = (i >> g.sx) & (g.ty - 1), lz = i >> (g.sx + g.sy);
         if (lx != 0 && lx != g.tx - 1 && ly != 0 && ly != g.ty - 1 && (CONN != 6 || (lz != 0 && lz != g.tz - 1)))
             continue;  // interior of the tile
         const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
@@ -246,7 +246,7 @@ __global__ void post_kernel(const Geom g, const DevState st) {
     const int V = g.tx * g.ty * g.tz;
     int act = touched ? st.left_active[r] : 0;
     for (int i = threadIdx.x; i < V; i += blockDim.x) {
-        const int lx = i % g.tx, ly = (i / g.tx) % g.ty, lz = i / (g.tx * g.ty);
+        const int lx = i & (g.tx - 1), ly = (i >> g.sx) & (g.ty - 1), lz = i >> (g.sx + g.sy);
         const bool border = lx == 0 || lx == g.tx - 1 || ly == 0 || ly == g.ty - 1 ||
                             (CONN == 6 && (lz == 0 || lz == g.tz - 1));
         if (gap == 0 && !border) continue;
@@ -457,6 +457,7 @@ mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int con
     Geom &G = g->g;
     G.X = (int)X; G.Y = (int)Y; G.Z = (int)Z; G.n = nll;
     G.tx = tx; G.ty = ty; G.tz = tz;
+    G.sx = __builtin_ctz(tx); G.sy = __builtin_ctz(ty); G.sz = __builtin_ctz(tz);
     G.RX = (int)((X + tx - 1) / tx); G.RY = (int)((Y + ty - 1) / ty); G.RZ = (int)((Z + tz - 1) / tz);
     G.nreg = G.RX * G.RY * G.RZ;
     g->boundary = boundary_count(G);

@@ -35,7 +35,8 @@ __host__ __device__ constexpr int arc_dz(int conn, int d) { return (d & 1) ? -fw
 struct Geom {
     int X, Y, Z;        // grid dims
     long long n;        // X*Y*Z
-    int tx, ty, tz;     // tile (region) shape
+    int tx, ty, tz;     // tile (region) shape (powers of two)
+    int sx, sy, sz;     // log2 of the tile shape
     int RX, RY, RZ;     // regions per axis
     int nreg;
     int dinf;           // d_inf = max(|B|, 1)  (Sec. 4.1)
