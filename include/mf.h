@@ -64,7 +64,8 @@ typedef struct {
     int32_t max_sweeps;            /* sweep cap; 0 = 2|B|^2+1 (the P-ARD bound, Sec. 4.4), clamped to 2^30 */
     int32_t partial_discharge;     /* 1: sweep s runs only ARD stages k <= s (Sec. 6.2); default 0 */
     int32_t global_gap;            /* 1: global gap heuristic after each sweep (Sec. 5.1); default 1 */
-    int32_t global_relabel_period; /* P > 0: exact region-distance relabel every P sweeps; 0 = off (default) */
+    int32_t global_relabel_period; /* P > 0: exact region-distance relabel after every P-th sweep (2D grids,
+                                      Sec. 4.1 distance); 0 = off; default 4 */
     int32_t max_rounds;            /* cap on Augment rounds per stage inside one discharge; 0 = default 65536 */
     int32_t kernel_variant;        /* 0: bit-parallel 2D discharge where available (default); 1: generic kernel */
     int32_t reserved[10];
@@ -85,7 +86,9 @@ typedef struct {
     double ms_init, ms_sweeps, ms_cut, ms_total; /* device time per phase (CUDA events on the stream) */
     double ms_discharge;         /* device time of the discharge kernels alone, summed */
     double ms_fuse;              /* device time of fusion + gap + activity kernels, summed */
-    int32_t reserved[8];
+    int32_t global_relabels;     /* exact region-distance relabels run (opts.global_relabel_period) */
+    int32_t relabel_levels;      /* BFS levels of those relabels, summed */
+    int32_t reserved[6];
 } mf_stats;
 
 /* Fill *opts with the defaults listed in mf_opts. */

@@ -17,10 +17,13 @@
 #include <algorithm>
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "mf_internal.cuh"
 
 namespace mf {
 
+namespace cg = cooperative_groups;
 typedef unsigned long long u64;
 
 // Build the masks: M[d][y][w] bit b (x = 64w + b) and the seed words S[y][w].
@@ -156,6 +159,298 @@ __global__ void cut_bytes_kernel(const Geom g, int W64, const u64 *Smin, const u
         smin[v] = (Smin[w] >> (x & 63)) & 1ull;
         smax[v] = !((Tset[w] >> (x & 63)) & 1ull);
     }
+}
+
+// ---- global relabel (exact region distance) on the same bit masks ---------------
+//
+// The region distance of Sec. 4.1 counts the inter-region arcs of a path to
+// t (labels may only drop across them).  Level sets by a 0-1 BFS:
+//   S_0     = vertices that reach t inside their own region;
+//   S_{k}   = intra-region closure of S_{k-1} plus the vertices with a residual
+//             inter-region arc into S_{k-1}.
+// A vertex first found at level k has region distance k; vertices never found
+// cannot reach t (distance d_inf).  The labeling is raised to max(d, level),
+// which keeps it valid (a maximum of two valid labelings is valid, Sec. 6.1)
+// and monotone.  One launch per level; the set is double-buffered so a level
+// reads only the previous level.
+
+// bits of a row word whose arc in direction (dx, dy) stays inside the region tile
+__device__ __forceinline__ u64 intra_bits(const Geom &g, int y, int dx, int dy) {
+    u64 m = ~0ull;
+    if (dx > 0) m &= g.tx == 64 ? 0x7fffffffffffffffull : 0x7fffffff7fffffffull;
+    if (dx < 0) m &= g.tx == 64 ? 0xfffffffffffffffeull : 0xfffffffefffffffeull;
+    if (dy > 0 && ((y + 1) & (g.ty - 1)) == 0) m = 0;
+    if (dy < 0 && (y & (g.ty - 1)) == 0) m = 0;
+    return m;
+}
+
+template <int CONN>
+struct GlrBlock {
+    int bx, by, yy[2];
+    u64 m[CONN][2], mi[CONN][2];  // residual masks of the block rows; intra-region part
+};
+
+template <int CONN>
+__device__ __forceinline__ void glr_load_block(const Geom &g, int W64, int blk, const u64 *__restrict__ M,
+                                               GlrBlock<CONN> &B) {
+    const int lane = threadIdx.x & 31;
+    const size_t plane = (size_t)g.Y * W64;
+    B.bx = blk % W64;
+    B.by = blk / W64;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int y = B.by * 64 + 2 * lane + j;
+        B.yy[j] = y;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            B.m[d][j] = y < g.Y ? M[d * plane + (size_t)y * W64 + B.bx] : 0ull;
+            B.mi[d][j] = B.m[d][j] & intra_bits(g, y, arc_dx(CONN, d), arc_dy(CONN, d));
+        }
+    }
+}
+
+template <int CONN>
+__device__ __forceinline__ bool glr_level_block(const Geom &g, int W64, const GlrBlock<CONN> &B,
+                                                const u64 *__restrict__ Sin, u64 *Sout, int level, int *lab) {
+    const int lane = threadIdx.x & 31;
+    const int bx = B.bx, by = B.by;
+    auto word = [&](const u64 *A, int y, int w) -> u64 {
+        return (y >= 0 && y < g.Y && w >= 0 && w < W64) ? A[(size_t)y * W64 + w] : 0ull;
+    };
+    const auto &m = B.m;
+    const auto &mi = B.mi;
+    const int *yy = B.yy;
+    u64 s[2], s0[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        s[j] = word(Sin, yy[j], bx);
+        s0[j] = s[j];
+    }
+    if (level > 0) {
+        // vertices with a residual inter-region arc into S_{level-1}
+        u64 sl[2], sr[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            sl[j] = word(Sin, yy[j], bx - 1) >> 63;
+            sr[j] = word(Sin, yy[j], bx + 1) & 1ull;
+        }
+        const int ya = by * 64 - 1, yb = by * 64 + 64;
+        const u64 sa = word(Sin, ya, bx), sal = word(Sin, ya, bx - 1) >> 63, sar = word(Sin, ya, bx + 1) & 1ull;
+        const u64 sb = word(Sin, yb, bx), sbl = word(Sin, yb, bx - 1) >> 63, sbr = word(Sin, yb, bx + 1) & 1ull;
+        const u64 up = __shfl_up_sync(0xffffffffu, s[1], 1), upl = __shfl_up_sync(0xffffffffu, sl[1], 1),
+                  upr = __shfl_up_sync(0xffffffffu, sr[1], 1);
+        const u64 dn = __shfl_down_sync(0xffffffffu, s[0], 1), dnl = __shfl_down_sync(0xffffffffu, sl[0], 1),
+                  dnr = __shfl_down_sync(0xffffffffu, sr[0], 1);
+        u64 nf[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const u64 fa = j == 0 ? (lane == 0 ? sa : up) : s[0];
+            const u64 fal = j == 0 ? (lane == 0 ? sal : upl) : sl[0];
+            const u64 far_ = j == 0 ? (lane == 0 ? sar : upr) : sr[0];
+            const u64 fb = j == 1 ? (lane == 31 ? sb : dn) : s[1];
+            const u64 fbl = j == 1 ? (lane == 31 ? sbl : dnl) : sl[1];
+            const u64 fbr = j == 1 ? (lane == 31 ? sbr : dnr) : sr[1];
+            u64 c[8];
+            c[0] = (s[j] >> 1) | (sr[j] << 63);
+            c[1] = (s[j] << 1) | sl[j];
+            c[2] = fb;
+            c[3] = fa;
+            c[4] = (fb >> 1) | (fbr << 63);
+            c[5] = (fa << 1) | fal;
+            c[6] = (fb << 1) | fbl;
+            c[7] = (fa >> 1) | (far_ << 63);
+            u64 a = 0;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) a |= (m[d][j] & ~mi[d][j]) & c[d];
+            nf[j] = a & ~s[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) s[j] |= nf[j];
+    }
+    // closure inside the regions (intra-region arcs only)
+    for (;;) {
+        const u64 up = __shfl_up_sync(0xffffffffu, s[1], 1);
+        const u64 dn = __shfl_down_sync(0xffffffffu, s[0], 1);
+        bool any = false;
+        u64 nf[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const u64 fa = j == 0 ? (lane == 0 ? 0ull : up) : s[0];
+            const u64 fb = j == 1 ? (lane == 31 ? 0ull : dn) : s[1];
+            u64 a = (mi[0][j] & (s[j] >> 1)) | (mi[1][j] & (s[j] << 1)) | (mi[2][j] & fb) | (mi[3][j] & fa);
+            if (CONN == 8)
+                a |= (mi[4][j] & (fb >> 1)) | (mi[5][j] & (fa << 1)) | (mi[6][j] & (fb << 1)) | (mi[7][j] & (fa >> 1));
+            a &= ~s[j];
+            a = fill_row(a, mi[0][j] & ~s[j], mi[1][j] & ~s[j]);
+            nf[j] = a;
+            any |= a != 0ull;
+        }
+        if (!__any_sync(0xffffffffu, any)) break;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) s[j] |= nf[j];
+    }
+    bool grew = false;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (yy[j] >= g.Y) continue;
+        Sout[(size_t)yy[j] * W64 + bx] = s[j];
+        // members found at this level get label max(d, level); level 0 changes nothing
+        u64 nw = level == 0 ? 0ull : (s[j] & ~s0[j]);
+        grew |= nw != 0ull;
+        for (; nw; nw &= nw - 1) {
+            const int x = bx * 64 + __ffsll((long long)nw) - 1;
+            int *p = &lab[(size_t)yy[j] * g.X + x];
+            if (*p < level) *p = level;
+        }
+    }
+    return __any_sync(0xffffffffu, grew);
+}
+
+// All levels in one cooperative launch: every warp takes 64x64 blocks in turn,
+// and the grid synchronises between levels.  flags[3] are "a block grew"
+// words, triple-buffered so that the word read after level L is not reset
+// before every thread has passed the next grid barrier.
+template <int CONN>
+__global__ void glr_levels_kernel(const Geom g, int W64, int BY, const u64 *__restrict__ M, u64 *A, u64 *B,
+                                  int *lab, int *flags, int *levels_out, int max_levels) {
+    cg::grid_group grid = cg::this_grid();
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int nblk = W64 * BY;
+    const bool resident = nblk <= nwarps;  // each warp keeps its block's masks in registers
+    GlrBlock<CONN> blkm;
+    if (resident && wid < nblk) glr_load_block<CONN>(g, W64, wid, M, blkm);
+    for (int b = wid; b < nblk; b += nwarps) {
+        if (!resident) glr_load_block<CONN>(g, W64, b, M, blkm);
+        glr_level_block<CONN>(g, W64, blkm, A, B, 0, lab);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        flags[1] = 0;
+        flags[2] = 0;
+    }
+    grid.sync();
+    int level = 1;
+    for (; level < max_levels; ++level) {
+        const u64 *in = (level & 1) ? B : A;
+        u64 *out = (level & 1) ? A : B;
+        bool grew = false;
+        for (int b = wid; b < nblk; b += nwarps) {
+            if (!resident) glr_load_block<CONN>(g, W64, b, M, blkm);
+            grew |= glr_level_block<CONN>(g, W64, blkm, in, out, level, lab);
+        }
+        if (grew && lane == 0) atomicOr(&flags[level % 3], 1);
+        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(level + 1) % 3] = 0;
+        grid.sync();
+        if (!*(volatile int *)&flags[level % 3]) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *levels_out = level + 1;
+}
+
+// After the last level: unreached vertices get d_inf; rebuild the boundary-label
+// histogram (per-block shared counts for small labels, merged once) and mark
+// the regions that still hold an active vertex.
+template <int CONN>
+__global__ void glr_finish_kernel(const Geom g, const DevState st, int W64, const u64 *S) {
+    constexpr int SB = 2048;  // labels below SB are counted in shared memory first
+    __shared__ int sh[SB];
+    for (int b = threadIdx.x; b < SB; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < (size_t)g.n; v += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(v / g.X), x = (int)(v % g.X);
+        int l = st.lab[v];
+        if (!((S[(size_t)y * W64 + (x >> 6)] >> (x & 63)) & 1ull)) {
+            l = g.dinf;
+            st.lab[v] = l;
+        }
+        if (l >= g.dinf) continue;
+        const int r = ((y >> g.sy) * g.RX) + (x >> g.sx);
+        if (st.exc[v] > 0) st.active[r] = 1;
+        const int lx = x & (g.tx - 1), ly = y & (g.ty - 1);
+        if (lx != 0 && lx != g.tx - 1 && ly != 0 && ly != g.ty - 1) continue;  // tile interior: not in B
+        bool inB = false;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d);
+            if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y) continue;
+            if (((wy >> g.sy) * g.RX + (wx >> g.sx)) != r) inB = true;
+        }
+        if (!inB) continue;
+        if (l < SB) atomicAdd(&sh[l], 1);
+        else atomicAdd(&st.hist[l < kHistBins ? l : kHistBins], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < SB; b += blockDim.x)
+        if (sh[b]) atomicAdd(&st.hist[b], sh[b]);
+}
+
+__global__ void count_active_kernel(const DevState st, int nreg) {
+    int c = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) c += st.active[r] != 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
+}
+
+// Exact region-distance relabel of a 2D grid (tiles 32 or 64 wide).  Uses the
+// cut scratch (masks and two set buffers).  levels: number of BFS levels run.
+template <int CONN>
+static cudaError_t glr2d_impl(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
+                              cudaStream_t s) {
+    const int W64 = (g.X + 63) / 64, BY = (g.Y + 63) / 64;
+    const size_t plane = (size_t)g.Y * W64;
+    u64 *M = (u64 *)scratch;
+    u64 *A = M + CONN * plane;
+    u64 *B = A + plane;
+    const size_t total = (size_t)W64 * 64 * g.Y;
+    const int mb = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
+    cut_masks_kernel<CONN><<<mb, 256, 0, s>>>(g, st, W64, 1, (unsigned *)M, (unsigned *)A);
+    // one cooperative launch for all levels; the grid must be co-resident
+    static int max_blocks = 0;
+    if (!max_blocks) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, glr_levels_kernel<CONN>, 256, 0);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        max_blocks = per_sm * sms;
+        if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    }
+    int nblocks = std::min((W64 * BY + 7) / 8, max_blocks);
+    int *flags = &st.ctr[kGlrFlags];
+    int *lvl = &st.ctr[kGlrLevels];
+    int max_levels = 1 << 20;
+    u64 *pa = A, *pb = B;
+    int *lab = st.lab;
+    Geom gg = g;
+    int w64 = W64, by = BY;
+    void *args[] = {&gg, &w64, &by, (void *)&M, &pa, &pb, &lab, &flags, &lvl, &max_levels};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)glr_levels_kernel<CONN>, dim3(nblocks), dim3(256),
+                                                args, 0, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(h_changed, lvl, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *levels = *h_changed;
+    // the last level written: odd levels write A, even levels write B
+    u64 *in = (*levels - 1) % 2 == 1 ? A : B;
+    if (*levels - 1 == 0) in = B;
+    e = cudaMemsetAsync(st.hist, 0, (kHistBins + 1) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st.active, 0, (size_t)g.nreg, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&st.ctr[kActiveRegions], 0, 4, s);
+    if (e != cudaSuccess) return e;
+    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, 152 * 32);
+    glr_finish_kernel<CONN><<<nb, 256, 0, s>>>(g, st, W64, in);
+    count_active_kernel<<<(g.nreg + 255) / 256, 256, 0, s>>>(st, g.nreg);
+    return cudaGetLastError();
+}
+
+bool glr2d_supported(const Geom &g) { return g.tz == 1 && g.Z == 1 && (g.tx == 64 || g.tx == 32); }
+
+cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
+                  cudaStream_t s) {
+    if (conn == 4) return glr2d_impl<4>(g, st, scratch, h_changed, levels, s);
+    if (conn == 8) return glr2d_impl<8>(g, st, scratch, h_changed, levels, s);
+    return cudaErrorInvalidValue;
 }
 
 size_t cut2d_scratch_bytes(const Geom &g, int conn) {

@@ -408,7 +408,7 @@ void mf_default_opts(mf_opts *o) {
     o->max_sweeps = 0;
     o->partial_discharge = 0;
     o->global_gap = 1;
-    o->global_relabel_period = 0;
+    o->global_relabel_period = 4;
     o->max_rounds = 0;
 }
 
@@ -589,8 +589,25 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     ++g->sweep;
     g->stats.sweeps = g->sweep;
     if (g->h_ctr[kGap] > 0) g->stats.gaps++;
-    if (active_out) *active_out = g->h_ctr[kActiveRegions];
-    if (g->h_ctr[kError]) return fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
+    if (g->h_ctr[kError]) {
+        if (active_out) *active_out = g->h_ctr[kActiveRegions];
+        return fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
+    }
+    int active = g->h_ctr[kActiveRegions];
+    const int P = g->opts.global_relabel_period;
+    if (P > 0 && active > 0 && g->sweep % P == 0 && g->ndim == 2 && glr2d_supported(g->g)) {
+        // exact region-distance relabel (raises labels to max(d, d*)), then the
+        // activity of every region is recomputed from the new labels
+        int levels = 0;
+        CK(glr2d(g->conn, g->g, g->st, g->cut_scratch, g->h_ctr, &levels, g->stream));
+        CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        active = g->h_ctr[kActiveRegions];
+        g->stats.global_relabels++;
+        g->stats.relabel_levels += levels;
+        g->launches += 4 + levels;
+    }
+    if (active_out) *active_out = active;
     return MF_OK;
 }
 

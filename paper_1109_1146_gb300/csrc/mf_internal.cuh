@@ -61,6 +61,8 @@ enum Ctr : int {
     kChanged = 3,        // cut extraction: a pass changed the set
     kStages = 4,         // ARD stages (low 32 bits; also kept in 64-bit below)
     kDischarges = 5,
+    kGlrFlags = 8,       // 3 words: global relabel "grew" flags
+    kGlrLevels = 11,     // global relabel: levels run
     kCtrWords = 16
 };
 struct Counters64 {
@@ -100,6 +102,10 @@ cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const 
 size_t cut2d_scratch_bytes(const Geom &g, int conn);
 cudaError_t cut2d(int conn, const Geom &g, const DevState &st, void *scratch, unsigned char *smin,
                   unsigned char *smax, int *h_changed, int *passes, cudaStream_t s);
+// global relabel: exact region distance on bit masks (2D, tiles 32 or 64 wide)
+bool glr2d_supported(const Geom &g);
+cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
+                  cudaStream_t s);
 // ard_discharge2d.cu
 bool discharge2d_supported(int conn, int tx, int ty);
 cudaError_t launch_discharge2d(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,

@@ -39,7 +39,8 @@ class mf_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("gaps", ctypes.c_int32), ("cut_passes", ctypes.c_int32),
                 ("ms_init", ctypes.c_double), ("ms_sweeps", ctypes.c_double), ("ms_cut", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_discharge", ctypes.c_double), ("ms_fuse", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("global_relabels", ctypes.c_int32), ("relabel_levels", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

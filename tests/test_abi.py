@@ -55,7 +55,7 @@ def test_struct_layout_matches_header(tmp_path):
 
 def test_default_opts(lib):
     o = mf.default_opts()
-    assert (o.max_sweeps, o.partial_discharge, o.global_gap, o.global_relabel_period, o.max_rounds) == (0, 0, 1, 0, 0)
+    assert (o.max_sweeps, o.partial_discharge, o.global_gap, o.global_relabel_period, o.max_rounds) == (0, 0, 1, 4, 0)
 
 
 @pytest.mark.parametrize("ndim,dims,conn,tile,frag", [

@@ -71,8 +71,8 @@ def check_state(inst, res, tres, exc, lab, dinf, inB, targets):
     (4, (192, 160, 1), (64, 64, 1), 0), (8, (150, 130, 1), (64, 64, 1), 0),
     (8, (100, 90, 1), (32, 32, 1), 0), (4, (120, 96, 1), (32, 32, 1), 1),
     (6, (40, 36, 30), (16, 16, 16), 0), (6, (24, 20, 18), (8, 8, 8), 1)])
-@pytest.mark.parametrize("variant", [0, 1])
-def test_sweep_invariants(conn, dims, tile, partial, variant):
+@pytest.mark.parametrize("variant,glr", [(0, 0), (1, 0), (0, 1)])
+def test_sweep_invariants(conn, dims, tile, partial, variant, glr):
     inst = (grids.volume_3d(*dims, seed=2) if conn == 6 else
             grids.segmentation_2d(dims[0], dims[1], 2, conn=conn, hard_seed_frac=0.04))
     inB = oracle.boundary_mask(inst.dims, conn, tile)
@@ -80,7 +80,7 @@ def test_sweep_invariants(conn, dims, tile, partial, variant):
     bound = oracle.sweep_bound(inst.dims, conn, tile)
     with Grid(inst.dims, conn, tile=tile) as g:
         g.set_caps(inst.cs, inst.ct, inst.nlink)
-        g.begin(default_opts(partial_discharge=partial, kernel_variant=variant))
+        g.begin(default_opts(partial_discharge=partial, kernel_variant=variant, global_relabel_period=glr))
         prev, dinf = g.get_labels()
         sweeps = 0
         while True:

@@ -107,11 +107,16 @@ def test_result_invariant_under_tile_shape(conn, dims, t1, t2):
 
 
 @pytest.mark.parametrize("kw", [dict(partial_discharge=1), dict(global_gap=0),
-                                dict(partial_discharge=1, global_gap=0)])
-def test_options_keep_exact_results(kw):
-    inst = grids.segmentation_2d(190, 170, 6, conn=8, hard_seed_frac=0.05)
-    got = gpu_solve(inst, opts=opts(**kw))
+                                dict(partial_discharge=1, global_gap=0), dict(global_relabel_period=1),
+                                dict(global_relabel_period=2, partial_discharge=1),
+                                dict(global_relabel_period=1, global_gap=0)])
+@pytest.mark.parametrize("conn,tile", [(8, (64, 64, 1)), (4, (32, 32, 1))])
+def test_options_keep_exact_results(kw, conn, tile):
+    inst = grids.segmentation_2d(190, 170, 6, conn=conn, hard_seed_frac=0.05)
+    got = gpu_solve(inst, tile=tile, opts=opts(**kw))
     assert_parity(inst, got)
+    if kw.get("global_relabel_period"):
+        assert got["stats"].global_relabels >= 1
 
 
 def test_repeat_solve_same_handle():
