@@ -171,6 +171,36 @@ mf_status mf_get_residual(mf_grid *g, int32_t *res, int32_t *tres, int32_t *exc,
 /* Current labeling d (int32[n], values 0..d_inf) and d_inf. */
 mf_status mf_get_labels(mf_grid *g, int32_t *lab, int32_t *d_inf, int on_device);
 
+/*
+ * Allocation-free cut extraction for 2D grids.  The paper has no counterpart:
+ * this is a service for callers that must not allocate device memory at call
+ * time, for example code that runs inside a framework owning all device
+ * memory through its own pool with a fixed budget, or a latency-critical
+ * loop where cudaMalloc (which may synchronise the device) is not allowed
+ * after start-up.  It computes the same two cuts as mf_get_cut from a
+ * residual network in the mf_get_residual layout:
+ *   res, tres, exc  device pointers (int32[connectivity][n], int32[n], int32[n]),
+ *                   typically the output of mf_get_residual(..., on_device = 1)
+ *                   after a successful mf_solve;
+ *   smin, smax      device outputs, uint8[n]: S_min (closure of {e > 0} under
+ *                   residual arcs) and S_max (V minus {v -> t}), 1 = source side;
+ *   dims            {X, Y}; connectivity 4 or 8; cuda_stream may be NULL.
+ * All scratch lives in one file-scope device array of 8 MiB inside the
+ * library (every GPU that loads the library holds it until the process
+ * exits); nothing is allocated.  A grid needs 256 + (connectivity+2) * Y *
+ * ceil(X/64) * 8 bytes of it (up to about 2590 x 2590 at 8-connectivity,
+ * 3340 x 3340 at 4-connectivity); larger grids are rejected with MF_EINVAL.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race and must not be issued.  The call
+ * synchronises cuda_stream before returning.  Errors: MF_EINVAL (arguments,
+ * size), MF_ECUDA; message in mf_last_error(NULL).
+ */
+mf_status mf_min_cut_2d_noalloc(const int64_t dims[2], int connectivity, const int32_t *res,
+                                const int32_t *tres, const int32_t *exc, uint8_t *smin, uint8_t *smax,
+                                void *cuda_stream);
+
 /* Free the handle and all its device memory (NULL is a no-op). */
 mf_status mf_destroy(mf_grid *g);
 

@@ -40,6 +40,8 @@ struct mf_grid {
 
 static thread_local std::string g_static_err;
 
+void mf::set_static_error(const std::string &m) { g_static_err = m; }
+
 static mf_status fail(mf_grid *g, mf_status s, const std::string &m) {
     if (g) g->err = m;
     else g_static_err = m;

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace mf {
 
 constexpr int kInf = 0x7fffffff;   // "no distance" inside a discharge
@@ -102,6 +104,8 @@ cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const 
 size_t cut2d_scratch_bytes(const Geom &g, int conn);
 cudaError_t cut2d(int conn, const Geom &g, const DevState &st, void *scratch, unsigned char *smin,
                   unsigned char *smax, int *h_changed, int *passes, cudaStream_t s);
+// message returned by mf_last_error(NULL) for calls without a handle (mf_capi.cu)
+void set_static_error(const std::string &m);
 // global relabel: exact region distance on bit masks (2D, tiles 32 or 64 wide)
 bool glr2d_supported(const Geom &g);
 cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,

@@ -22,7 +22,7 @@ STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "
 # every symbol include/mf.h declares
 EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
            "mf_finish", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
-           "mf_last_error"]
+           "mf_last_error", "mf_min_cut_2d_noalloc"]
 
 
 class mf_opts(ctypes.Structure):
@@ -78,6 +78,7 @@ def load(path: str = LIBPATH):
         "mf_get_labels": (I, [P, P, ctypes.POINTER(ctypes.c_int32), I]),
         "mf_destroy": (I, [P]),
         "mf_last_error": (ctypes.c_char_p, [P]),
+        "mf_min_cut_2d_noalloc": (I, [P, I, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -106,6 +107,23 @@ def _ptr(a):
             raise ValueError("tensor must be contiguous")
         return a.data_ptr(), int(a.is_cuda)
     raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def min_cut_2d_noalloc(dims, connectivity, res, tres, exc, smin, smax, stream=None):
+    """Allocation-free cut extraction (see include/mf.h): all buffers are
+    device tensors; raises MFError on a nonzero status."""
+    lib = load()
+    d = (ctypes.c_int64 * 2)(int(dims[0]), int(dims[1]))
+    ptrs = []
+    for a in (res, tres, exc, smin, smax):
+        p, dev = _ptr(a)
+        if not dev:
+            raise ValueError("mf_min_cut_2d_noalloc takes device buffers")
+        ptrs.append(p)
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    st = lib.mf_min_cut_2d_noalloc(d, int(connectivity), *ptrs, s)
+    if st != MF_OK:
+        raise MFError(st, lib.mf_last_error(None).decode())
 
 
 class Grid:

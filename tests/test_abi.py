@@ -24,7 +24,7 @@ def lib():
 def _declared():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(mf_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(mf_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_declares_binding_exports():
@@ -33,7 +33,7 @@ def test_header_declares_binding_exports():
 
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.check_output(["nm", "-D", "--defined-only", mf.LIBPATH]).decode()
-    exported = set(re.findall(r" T (mf_[a-z_]+)$", out, flags=re.M))
+    exported = set(re.findall(r" T (mf_[a-z0-9_]+)$", out, flags=re.M))
     missing = [s for s in _declared() if s not in exported]
     assert not missing, missing
     for s in _declared():
