@@ -149,6 +149,21 @@ mf_status mf_sweep(mf_grid *g, int32_t *active_regions);
 mf_status mf_finish(mf_grid *g);
 
 /*
+ * Batched solve: every grid of the array (each with capacities set, all on
+ * one device) is solved at once.  Each sweep builds one work queue of the
+ * active regions of all unfinished instances per kernel type (connectivity
+ * and tile shape) and runs it with persistent thread blocks that pull
+ * (instance, region) items; fusion, gap and activity run as one launch each
+ * over the regions of the whole batch; an instance leaves the batch when it
+ * has no active region.  All work is ordered on grids[0]'s stream.  Per
+ * instance results are then read as after mf_solve (mf_get_cut,
+ * mf_flow_value); stats (nullable) receives count entries (the ms_* fields
+ * are those of the whole batch).  The global relabel option is not applied
+ * in batched solves.
+ */
+mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, mf_stats *stats);
+
+/*
  * Minimum cut after a successful solve: out[v] = 1 if v is on the source side.
  *   which = 0: S_min, the closure of {v : e(v) > 0} under residual arcs
  *              (the minimal minimum-cut source set);

@@ -56,8 +56,8 @@ __device__ __forceinline__ int block_reduce_max(int v, int *slots, int &ph) {
 }
 
 template <int CONN, int TX, int TY, int TZ, int NT>
-__global__ void __launch_bounds__(NT, 1)
-ard_discharge_kernel(const Geom g, const DevState st, const SweepArgs sa) {
+__device__ __forceinline__ void discharge_region(const Geom &g, const DevState &st, const SweepArgs &sa,
+                                                 const int r) {
     using C = TileCfg<CONN, TX, TY, TZ, NT>;
     constexpr int N = C::N, V = C::V, VPT = C::VPT;
     extern __shared__ __align__(16) int smem[];
@@ -69,8 +69,6 @@ ard_discharge_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     __shared__ int s_red[3];
     __shared__ unsigned long long s_flow;
 
-    const int r = blockIdx.x;
-    if (!st.active[r]) return;      // regions without active vertices are skipped (Sec. 5.3)
     const int tid = threadIdx.x;
     if (tid < 3) s_red[tid] = INT_MIN;
     if (tid == 0) s_flow = 0;
@@ -354,6 +352,48 @@ ard_discharge_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     }
 }
 
+template <int CONN, int TX, int TY, int TZ, int NT>
+__global__ void __launch_bounds__(NT, 1) ard_discharge_kernel(const Geom g, const DevState st, const SweepArgs sa) {
+    const int r = blockIdx.x;
+    if (!st.active[r]) return;  // regions without active vertices are skipped (Sec. 5.3)
+    discharge_region<CONN, TX, TY, TZ, NT>(g, st, sa, r);
+}
+
+// persistent blocks over a work queue of (instance, region) items of a batch
+template <int CONN, int TX, int TY, int TZ, int NT>
+__global__ void __launch_bounds__(NT, 1)
+ard_discharge_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ items, const int *count,
+                           int *head, const SweepArgs sa) {
+    __shared__ int s_it;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_it = atomicAdd(head, 1);
+        __syncthreads();
+        const int it = s_it;
+        if (it >= *count) break;
+        const int2 w = items[it];
+        const Inst &I = insts[w.x];
+        SweepArgs a = sa;
+        a.c64 = I.c64;
+        discharge_region<CONN, TX, TY, TZ, NT>(I.g, I.st, a, w.y);
+    }
+}
+
+template <int CONN, int TX, int TY, int TZ, int NT>
+static cudaError_t launch_batch_one(const Inst *insts, const int2 *items, const int *count, int *head,
+                                    const SweepArgs &sa, int blocks, cudaStream_t s) {
+    using C = TileCfg<CONN, TX, TY, TZ, NT>;
+    static bool attr_set = false;
+    auto k = ard_discharge_batch_kernel<CONN, TX, TY, TZ, NT>;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k<<<blocks, NT, C::smem, s>>>(insts, items, count, head, sa);
+    return cudaGetLastError();
+}
+
 // ---- instantiation table ----------------------------------------------------
 template <int CONN, int TX, int TY, int TZ, int NT>
 static cudaError_t launch_one(const Geom &g, const DevState &st, const SweepArgs &sa, cudaStream_t s) {
@@ -389,6 +429,18 @@ size_t discharge_smem_bytes(int conn, int tx, int ty, int tz) {
     MF_TILES(X)
 #undef X
     return 0;
+}
+
+cudaError_t launch_discharge_batch(int conn, int tx, int ty, int tz, int variant, const Inst *insts,
+                                   const int2 *items, const int *count, int *head, const SweepArgs &sa,
+                                   int blocks, cudaStream_t stream) {
+    if (variant == 0 && tz == 1 && discharge2d_supported(conn, tx, ty))
+        return launch_discharge2d_batch(conn, tx, ty, insts, items, count, head, sa, blocks, stream);
+#define X(c, a, b, z, t) \
+    if (conn == c && tx == a && ty == b && tz == z) return launch_batch_one<c, a, b, z, t>(insts, items, count, head, sa, blocks, stream);
+    MF_TILES(X)
+#undef X
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,

@@ -96,8 +96,8 @@ __device__ __forceinline__ u64 row_fill(u64 g, u64 pl, u64 pr) {
 __device__ __forceinline__ int deep_tag(int epoch, int L) { return ~((epoch << 16) | L); }
 
 template <int CONN, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, 1)
-ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
+__device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState &st, const SweepArgs &sa,
+                                                   const int r) {
     using C = Cfg2D<CONN, TX, TY, NT>;
     constexpr int N = C::N, V = C::V, RPL = C::RPL, NW = C::NW, HW = C::HW, LCAP = C::LCAP;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -117,8 +117,6 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     __shared__ int s_ctl[4];
     __shared__ unsigned long long s_flow;
 
-    const int r = blockIdx.x;
-    if (!st.active[r]) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     DIAG_DECL
     const long long diag_t0 = clock64();
@@ -620,6 +618,49 @@ ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     }
 }
 
+// one block per region of one grid; regions without active vertices are skipped (Sec. 5.3)
+template <int CONN, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT, 1) ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
+    const int r = blockIdx.x;
+    if (!st.active[r]) return;
+    discharge2d_region<CONN, TX, TY, NT>(g, st, sa, r);
+}
+
+// persistent blocks over a work queue of (instance, region) items of a batch
+template <int CONN, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT, 1)
+ard_discharge2d_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ items, const int *count,
+                             int *head, const SweepArgs sa) {
+    __shared__ int s_it;
+    for (;;) {
+        __syncthreads();  // the previous item is done with s_it and the shared planes
+        if (threadIdx.x == 0) s_it = atomicAdd(head, 1);
+        __syncthreads();
+        const int it = s_it;
+        if (it >= *count) break;
+        const int2 w = items[it];
+        const Inst &I = insts[w.x];
+        SweepArgs a = sa;
+        a.c64 = I.c64;
+        discharge2d_region<CONN, TX, TY, NT>(I.g, I.st, a, w.y);
+    }
+}
+
+template <int CONN, int TX, int TY, int NT>
+static cudaError_t launch2d_batch(const Inst *insts, const int2 *items, const int *count, int *head,
+                                  const SweepArgs &sa, int blocks, cudaStream_t s) {
+    using C = Cfg2D<CONN, TX, TY, NT>;
+    static bool attr_set = false;
+    auto k = ard_discharge2d_batch_kernel<CONN, TX, TY, NT>;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k<<<blocks, NT, C::smem, s>>>(insts, items, count, head, sa);
+    return cudaGetLastError();
+}
+
 template <int CONN, int TX, int TY, int NT>
 static cudaError_t launch2d(const Geom &g, const DevState &st, const SweepArgs &sa, cudaStream_t s) {
     using C = Cfg2D<CONN, TX, TY, NT>;
@@ -636,6 +677,16 @@ static cudaError_t launch2d(const Geom &g, const DevState &st, const SweepArgs &
 
 bool discharge2d_supported(int conn, int tx, int ty) {
     return (conn == 4 || conn == 8) && ((tx == 64 && ty == 64) || (tx == 32 && ty == 32));
+}
+
+cudaError_t launch_discharge2d_batch(int conn, int tx, int ty, const Inst *insts, const int2 *items,
+                                     const int *count, int *head, const SweepArgs &sa, int blocks,
+                                     cudaStream_t stream) {
+    if (conn == 4 && tx == 64 && ty == 64) return launch2d_batch<4, 64, 64, 512>(insts, items, count, head, sa, blocks, stream);
+    if (conn == 8 && tx == 64 && ty == 64) return launch2d_batch<8, 64, 64, 512>(insts, items, count, head, sa, blocks, stream);
+    if (conn == 4 && tx == 32 && ty == 32) return launch2d_batch<4, 32, 32, 256>(insts, items, count, head, sa, blocks, stream);
+    if (conn == 8 && tx == 32 && ty == 32) return launch2d_batch<8, 32, 32, 256>(insts, items, count, head, sa, blocks, stream);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_discharge2d(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,

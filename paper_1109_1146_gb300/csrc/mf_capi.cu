@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/mf.h"
 #include "mf_internal.cuh"
@@ -153,8 +154,7 @@ __device__ __forceinline__ int hist_bin(int l) { return l < kHistBins ? l : kHis
 // Also commits the new boundary labels and keeps the histogram of boundary
 // labels (Sec. 5.3: the global gap needs labels of B only) up to date.
 template <int CONN>
-__global__ void fuse_kernel(const Geom g, const DevState st) {
-    const int r = blockIdx.x;
+__device__ __forceinline__ void fuse_region(const Geom &g, const DevState &st, const int r) {
     __shared__ int s_touch;
     if (threadIdx.x == 0) s_touch = region_touched<CONN>(g, st, r);
     __syncthreads();
@@ -207,11 +207,14 @@ __global__ void fuse_kernel(const Geom g, const DevState st) {
     }
 }
 
+template <int CONN>
+__global__ void fuse_kernel(const Geom g, const DevState st) { fuse_region<CONN>(g, st, blockIdx.x); }
+
 // Global gap (Sec. 5.1, with the boundary-label histogram of Sec. 5.3): the
 // smallest g > 0 below the highest boundary label with no boundary vertex
 // labelled g.  Every vertex with g < d < d_inf cannot reach t.  The bins
 // above g are emptied (those labels become d_inf).
-__global__ void gap_find_kernel(const DevState st) {
+__device__ __forceinline__ void gap_find_body(const DevState &st) {
     __shared__ int s_hi, s_g;
     if (threadIdx.x == 0) { s_hi = 0; s_g = INT_MAX; }
     __syncthreads();
@@ -232,12 +235,13 @@ __global__ void gap_find_kernel(const DevState st) {
         for (int b = gap + 1 + threadIdx.x; b <= kHistBins; b += blockDim.x) st.hist[b] = 0;
 }
 
+__global__ void gap_find_kernel(const DevState st) { gap_find_body(st); }
+
 // Apply the gap (all vertices of every region, only when a gap was found),
 // decide which regions discharge in the next sweep (only touched regions can
 // become active), reset the per-sweep flags.
 template <int CONN>
-__global__ void post_kernel(const Geom g, const DevState st) {
-    const int r = blockIdx.x;
+__device__ __forceinline__ void post_region(const Geom &g, const DevState &st, const int r) {
     const int gap = st.ctr[kGap];
     __shared__ int s_touch;
     if (threadIdx.x == 0) s_touch = region_touched<CONN>(g, st, r);
@@ -266,6 +270,70 @@ __global__ void post_kernel(const Geom g, const DevState st) {
     if (threadIdx.x == 0 && touched) {
         st.active[r] = (unsigned char)act;
         if (act) atomicAdd(&st.ctr[kActiveRegions], 1);
+    }
+}
+
+template <int CONN>
+__global__ void post_kernel(const Geom g, const DevState st) { post_region<CONN>(g, st, blockIdx.x); }
+
+// ---- batched sweep kernels: one block per (instance, region) of the batch table
+__global__ void batch_reset_kernel(const Inst *insts, const unsigned char *done, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        if (!done[i]) {
+            int *c = insts[i].st.ctr;
+            c[kActiveRegions] = 0;
+            c[kGap] = 0;
+        }
+}
+
+// work lists of the active regions, one list per kernel type
+__global__ void batch_items_kernel(const Inst *insts, const int2 *regs, int nregs, const unsigned char *done,
+                                   const int *type_of, int cap_per_type, int2 *items, int *cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nregs; i += gridDim.x * blockDim.x) {
+        const int2 w = regs[i];
+        if (done[w.x] || !insts[w.x].st.active[w.y]) continue;
+        const int t = type_of[w.x];
+        const int pos = atomicAdd(&cnt[t], 1);
+        items[(size_t)t * cap_per_type + pos] = w;
+    }
+}
+
+template <int CONN>
+__global__ void fuse_batch_kernel(const Inst *insts, const int2 *regs, const unsigned char *done) {
+    const int2 w = regs[blockIdx.x];
+    if (done[w.x] || insts[w.x].conn != CONN) return;
+    fuse_region<CONN>(insts[w.x].g, insts[w.x].st, w.y);
+}
+
+__global__ void gap_find_batch_kernel(const Inst *insts, const unsigned char *done) {
+    if (done[blockIdx.x]) return;
+    gap_find_body(insts[blockIdx.x].st);
+}
+
+template <int CONN>
+__global__ void post_batch_kernel(const Inst *insts, const int2 *regs, const unsigned char *done) {
+    const int2 w = regs[blockIdx.x];
+    if (done[w.x] || insts[w.x].conn != CONN) return;
+    post_region<CONN>(insts[w.x].g, insts[w.x].st, w.y);
+}
+
+__global__ void clear_batch_kernel(const Inst *insts, const int2 *regs, int nregs, const unsigned char *done) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nregs; i += gridDim.x * blockDim.x) {
+        const int2 w = regs[i];
+        if (done[w.x]) continue;
+        insts[w.x].st.disc[w.y] = 0;
+        insts[w.x].st.left_active[w.y] = 0;
+    }
+}
+
+// per instance: finished when no region is active; an error also ends it
+__global__ void batch_end_kernel(const Inst *insts, unsigned char *done, int *sweeps, int *any, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        if (done[i]) continue;
+        const int *c = insts[i].st.ctr;
+        sweeps[i] += 1;
+        if (c[kActiveRegions] == 0 || c[kError]) done[i] = 1;
+        else atomicAdd(any, 1);
     }
 }
 
@@ -697,6 +765,176 @@ mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats) {
     g->stats.ms_cut = c;
     g->stats.ms_total = a + b + c;
     if (stats) *stats = g->stats;
+    return rs;
+}
+
+// ---- batched solve --------------------------------------------------------------
+struct BatchBufs {
+    Inst *insts = nullptr;
+    int2 *regs = nullptr, *items = nullptr;
+    int *type_of = nullptr, *cnt = nullptr, *head = nullptr, *sweeps = nullptr, *any = nullptr;
+    unsigned char *done = nullptr;
+    ~BatchBufs() {
+        void *p[] = {insts, regs, items, type_of, cnt, head, sweeps, any, done};
+        for (void *q : p)
+            if (q) cudaFree(q);
+    }
+};
+
+mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, mf_stats *stats) {
+    mf_grid *g = nullptr;  // for CK: errors are reported on the first handle
+    if (!grids || count < 1) return fail(nullptr, MF_EINVAL, "grids must be a non-empty array");
+    for (int i = 0; i < count; ++i)
+        if (!grids[i]) return fail(nullptr, MF_EINVAL, "null grid in the batch");
+    g = grids[0];
+    for (int i = 0; i < count; ++i) {
+        if (!grids[i]->caps_set) return fail(g, MF_ESTATE, "a grid of the batch has no capacities");
+        if (grids[i]->device != g->device) return fail(g, MF_EINVAL, "all grids must be on one device");
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == grids[i]) return fail(g, MF_EINVAL, "a grid appears twice in the batch");
+    }
+    cudaStream_t s = g->stream;
+    CK(cudaEventRecord(g->ev[0], s));
+    // Init of every instance on its own stream, then everything on the batch stream
+    long long cap = 0;
+    for (int i = 0; i < count; ++i) {
+        mf_status st = mf_begin(grids[i], opts);
+        if (st != MF_OK) return st;
+        if (grids[i]->stream != s) {
+            cudaError_t e = cudaStreamSynchronize(grids[i]->stream);
+            if (e != cudaSuccess) return fail(g, MF_ECUDA, cudaGetErrorString(e));
+        }
+        const long long b = grids[i]->boundary;
+        cap = std::max(cap, g->opts.max_sweeps > 0 ? (long long)g->opts.max_sweeps
+                                                    : std::min<long long>(2 * b * b + 1, 1ll << 30));
+    }
+    CK(cudaEventRecord(g->ev[1], s));
+    // kernel types (connectivity, tile) and the table of all regions
+    struct Type { int conn, tx, ty, tz; };
+    std::vector<Type> types;
+    std::vector<int> type_of(count);
+    std::vector<Inst> hinst(count);
+    std::vector<int2> hregs;
+    for (int i = 0; i < count; ++i) {
+        const mf_grid *h = grids[i];
+        int t = -1;
+        for (size_t k = 0; k < types.size(); ++k)
+            if (types[k].conn == h->conn && types[k].tx == h->g.tx && types[k].ty == h->g.ty && types[k].tz == h->g.tz)
+                t = (int)k;
+        if (t < 0) {
+            types.push_back({h->conn, h->g.tx, h->g.ty, h->g.tz});
+            t = (int)types.size() - 1;
+        }
+        type_of[i] = t;
+        hinst[i].g = h->g;
+        hinst[i].st = h->st;
+        hinst[i].c64 = h->c64;
+        hinst[i].conn = h->conn;
+        for (int r = 0; r < h->g.nreg; ++r) hregs.push_back(make_int2(i, r));
+    }
+    const int nregs = (int)hregs.size();
+    const int nt = (int)types.size();
+    BatchBufs B;
+    CK(cudaMalloc(&B.insts, sizeof(Inst) * count));
+    CK(cudaMalloc(&B.regs, sizeof(int2) * nregs));
+    CK(cudaMalloc(&B.items, sizeof(int2) * (size_t)nregs * nt));
+    CK(cudaMalloc(&B.type_of, sizeof(int) * count));
+    CK(cudaMalloc(&B.cnt, sizeof(int) * nt));
+    CK(cudaMalloc(&B.head, sizeof(int) * nt));
+    CK(cudaMalloc(&B.sweeps, sizeof(int) * count));
+    CK(cudaMalloc(&B.any, sizeof(int)));
+    CK(cudaMalloc(&B.done, count));
+    CK(cudaMemcpyAsync(B.insts, hinst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.regs, hregs.data(), sizeof(int2) * nregs, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.type_of, type_of.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(B.sweeps, 0, sizeof(int) * count, s));
+    CK(cudaMemsetAsync(B.done, 0, count, s));
+    const mf_opts &o = g->opts;
+    SweepArgs sa{};
+    sa.partial = o.partial_discharge;
+    sa.max_rounds = o.max_rounds;
+    sa.variant = o.kernel_variant;
+    const int eb = (int)std::min<long long>(((long long)nregs + 255) / 256, 152 * 8);
+    mf_status rs = MF_OK;
+    int sweep = 0;
+    long long launches = 0;
+    for (;; ++sweep) {
+        sa.sweep = sweep;
+        CK(cudaMemsetAsync(B.cnt, 0, sizeof(int) * nt, s));
+        CK(cudaMemsetAsync(B.head, 0, sizeof(int) * nt, s));
+        CK(cudaMemsetAsync(B.any, 0, sizeof(int), s));
+        batch_reset_kernel<<<(count + 255) / 256, 256, 0, s>>>(B.insts, B.done, count);
+        batch_items_kernel<<<eb, 256, 0, s>>>(B.insts, B.regs, nregs, B.done, B.type_of, nregs, B.items, B.cnt);
+        CK(cudaGetLastError());
+        for (int t = 0; t < nt; ++t)
+            CK(launch_discharge_batch(types[t].conn, types[t].tx, types[t].ty, types[t].tz, sa.variant, B.insts,
+                                      B.items + (size_t)t * nregs, B.cnt + t, B.head + t, sa, 152 * 4, s));
+        // fusion / gap / activity per connectivity of the instances (one launch per connectivity)
+        for (int conn : {4, 8, 6}) {
+            bool has = false;
+            for (auto &ty : types) has |= ty.conn == conn;
+            if (!has) continue;
+            if (conn == 4) fuse_batch_kernel<4><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
+            if (conn == 8) fuse_batch_kernel<8><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
+            if (conn == 6) fuse_batch_kernel<6><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
+        }
+        if (o.global_gap) gap_find_batch_kernel<<<count, 1024, 0, s>>>(B.insts, B.done);
+        for (int conn : {4, 8, 6}) {
+            bool has = false;
+            for (auto &ty : types) has |= ty.conn == conn;
+            if (!has) continue;
+            if (conn == 4) post_batch_kernel<4><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
+            if (conn == 8) post_batch_kernel<8><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
+            if (conn == 6) post_batch_kernel<6><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
+        }
+        clear_batch_kernel<<<eb, 256, 0, s>>>(B.insts, B.regs, nregs, B.done);
+        batch_end_kernel<<<(count + 255) / 256, 256, 0, s>>>(B.insts, B.done, B.sweeps, B.any, count);
+        CK(cudaGetLastError());
+        launches += 6 + nt + (o.global_gap ? 1 : 0);
+        int any = 0;
+        CK(cudaMemcpyAsync(g->h_ctr, B.any, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        any = g->h_ctr[0];
+        if (!any) break;
+        if (sweep + 1 >= cap) {
+            rs = fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left in the batch");
+            break;
+        }
+    }
+    CK(cudaEventRecord(g->ev[2], s));
+    std::vector<int> hsweeps(count);
+    CK(cudaMemcpyAsync(hsweeps.data(), B.sweeps, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // errors, cuts and flow values per instance
+    for (int i = 0; i < count; ++i) {
+        mf_grid *h = grids[i];
+        CK(cudaMemcpyAsync(h->h_ctr, h->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        h->sweep = hsweeps[i];
+        h->stats.sweeps = hsweeps[i];
+        if (h->h_ctr[kError] && rs == MF_OK) rs = fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
+    }
+    if (rs == MF_OK) {
+        for (int i = 0; i < count; ++i) {
+            mf_status st = mf_finish(grids[i]);
+            if (st != MF_OK) return st;
+        }
+    }
+    CK(cudaEventRecord(g->ev[3], s));
+    CK(cudaEventSynchronize(g->ev[3]));
+    float a = 0, b = 0, c = 0;
+    cudaEventElapsedTime(&a, g->ev[0], g->ev[1]);
+    cudaEventElapsedTime(&b, g->ev[1], g->ev[2]);
+    cudaEventElapsedTime(&c, g->ev[2], g->ev[3]);
+    for (int i = 0; i < count; ++i) {
+        mf_grid *h = grids[i];
+        h->stats.ms_init = a;
+        h->stats.ms_sweeps = b;
+        h->stats.ms_cut = c;
+        h->stats.ms_total = a + b + c;
+        h->stats.launches += launches;
+        if (stats) stats[i] = h->stats;
+    }
     return rs;
 }
 

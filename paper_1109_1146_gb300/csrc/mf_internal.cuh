@@ -95,6 +95,14 @@ struct SweepArgs {
 #define DIAG_FLUSH() ((void)0)
 #endif
 
+// one instance of a batch: its geometry, device state and statistics counters
+struct Inst {
+    Geom g;
+    DevState st;
+    Counters64 *c64;
+    int conn;   // stencil of the instance (batched fusion kernels are per connectivity)
+};
+
 // launchers (ard_discharge.cu)
 size_t discharge_smem_bytes(int conn, int tx, int ty, int tz);
 bool discharge_supported(int conn, int tx, int ty, int tz);
@@ -110,8 +118,16 @@ void set_static_error(const std::string &m);
 bool glr2d_supported(const Geom &g);
 cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
                   cudaStream_t s);
+// persistent discharge over a work queue of (instance, region) items of one
+// kernel type (connectivity, tile); blocks pull items until *count is reached
+cudaError_t launch_discharge_batch(int conn, int tx, int ty, int tz, int variant, const Inst *insts,
+                                   const int2 *items, const int *count, int *head, const SweepArgs &sa,
+                                   int blocks, cudaStream_t stream);
 // ard_discharge2d.cu
 bool discharge2d_supported(int conn, int tx, int ty);
+cudaError_t launch_discharge2d_batch(int conn, int tx, int ty, const Inst *insts, const int2 *items,
+                                     const int *count, int *head, const SweepArgs &sa, int blocks,
+                                     cudaStream_t stream);
 cudaError_t launch_discharge2d(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
                                cudaStream_t stream);
 

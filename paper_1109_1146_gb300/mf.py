@@ -22,7 +22,7 @@ STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "
 # every symbol include/mf.h declares
 EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
            "mf_finish", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
-           "mf_last_error", "mf_min_cut_2d_noalloc"]
+           "mf_last_error", "mf_min_cut_2d_noalloc", "mf_solve_batch"]
 
 
 class mf_opts(ctypes.Structure):
@@ -79,6 +79,7 @@ def load(path: str = LIBPATH):
         "mf_destroy": (I, [P]),
         "mf_last_error": (ctypes.c_char_p, [P]),
         "mf_min_cut_2d_noalloc": (I, [P, I, P, P, P, P, P, P]),
+        "mf_solve_batch": (I, [P, I, ctypes.POINTER(mf_opts), ctypes.POINTER(mf_stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -124,6 +125,18 @@ def min_cut_2d_noalloc(dims, connectivity, res, tres, exc, smin, smax, stream=No
     st = lib.mf_min_cut_2d_noalloc(d, int(connectivity), *ptrs, s)
     if st != MF_OK:
         raise MFError(st, lib.mf_last_error(None).decode())
+
+
+def solve_batch(grids, opts: mf_opts | None = None):
+    """mf_solve_batch over a list of Grid objects; returns their mf_stats."""
+    lib = load()
+    n = len(grids)
+    arr = (ctypes.c_void_p * n)(*[g._h.value for g in grids])
+    stats = (mf_stats * n)()
+    st = lib.mf_solve_batch(arr, n, None if opts is None else ctypes.byref(opts), stats)
+    if st != MF_OK:
+        raise MFError(st, lib.mf_last_error(grids[0]._h).decode())
+    return list(stats)
 
 
 class Grid:

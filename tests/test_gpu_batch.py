@@ -1,0 +1,74 @@
+"""Batched persistent solve (mf_solve_batch): many grids of uneven sizes,
+mixed connectivities and tile shapes in one sweep loop.  Every instance must
+match the oracle bit-exactly and agree with its own single solve (same
+sweeps: the batch runs the same per-instance sequence of operations)."""
+import numpy as np
+import pytest
+
+import oracle
+from gen import grids
+from helpers import assert_parity
+from paper_1109_1146_gb300 import Grid, default_opts, mf
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch_instances():
+    out = []
+    out.append((grids.segmentation_2d(100, 90, 1, conn=4), (64, 64, 1)))
+    out.append((grids.segmentation_2d(64, 64, 2, conn=4), (64, 64, 1)))
+    out.append((grids.segmentation_2d(213, 150, 3, conn=4, hard_seed_frac=0.05), (64, 64, 1)))
+    out.append((grids.segmentation_2d(97, 61, 4, conn=4), (32, 32, 1)))
+    out.append((grids.segmentation_2d(130, 170, 5, conn=8, hard_seed_frac=0.05), (64, 64, 1)))
+    out.append((grids.random_grid((77, 55, 1), 8, 6, cmax=30, tmax=60, p_zero=0.3), (32, 32, 1)))
+    out.append((grids.volume_3d(30, 28, 26, 7), (16, 16, 16)))
+    out.append((grids.volume_3d(20, 20, 20, 8), (8, 8, 8)))
+    out.append((grids.random_grid((5, 1, 1), 4, 9, cmax=10, tmax=20), (64, 64, 1)))
+    return out
+
+
+@pytest.mark.parametrize("kw", [dict(global_relabel_period=0), dict(partial_discharge=1, global_relabel_period=0)])
+def test_batch_matches_oracle_and_single_solves(kw):
+    insts = _batch_instances()
+    opts = default_opts(**kw)
+    handles = []
+    for inst, tile in insts:
+        g = Grid(inst.dims, inst.conn, tile=tile)
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        handles.append(g)
+    stats = mf.solve_batch(handles, opts)
+    for (inst, tile), g, st in zip(insts, handles, stats):
+        got = {"flow": g.flow_value(), "smin": g.get_cut(0), "smax": g.get_cut(1)}
+        got["res"], got["tres"], got["exc"] = g.get_residual()
+        assert_parity(inst, got)
+        assert st.flow_value == got["flow"]
+        # the same instance alone
+        with Grid(inst.dims, inst.conn, tile=tile) as h:
+            h.set_caps(inst.cs, inst.ct, inst.nlink)
+            s1 = h.solve(opts)
+            assert s1.sweeps == st.sweeps
+            assert s1.discharges == st.discharges
+    for g in handles:
+        g.close()
+
+
+def test_batch_of_one_and_repeat():
+    inst = grids.config0(3)
+    ref = oracle.solve_instance(inst)
+    with Grid(inst.dims, 4) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        for _ in range(2):
+            mf.solve_batch([g])
+            assert g.flow_value() == ref["flow"]
+            np.testing.assert_array_equal(g.get_cut(0), ref["smin"])
+
+
+def test_batch_rejects_bad_input():
+    inst = grids.config0(0)
+    a = Grid(inst.dims, 4)
+    with pytest.raises(mf.MFError):
+        mf.solve_batch([a])  # no capacities yet
+    a.set_caps(inst.cs, inst.ct, inst.nlink)
+    with pytest.raises(mf.MFError):
+        mf.solve_batch([a, a])  # the same grid twice
+    a.close()
