@@ -272,6 +272,77 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """Batched persistent solve of the uneven batch (384 2D 4-connected grids,
+    side U{64..1024}, and 128 3D 6-connected grids, side U{48..128}) against
+    the same instances solved one by one with the default settings."""
+    import tempfile
+
+    import torch
+
+    from gen import grids
+    from paper_1109_1146_gb300 import Grid, autotune, default_opts, mf
+
+    torch.cuda.set_device(0)
+    shapes = grids.config4_shapes(0)[: args.batch_count] if args.batch_count else grids.config4_shapes(0)
+    insts = []
+    for i, (X, Y, Z) in enumerate(shapes):
+        if Z == 1:
+            insts.append(grids.segmentation_2d(X, Y, 5000 + i, conn=4))
+        else:
+            insts.append(grids.volume_3d(X, Y, Z, 5000 + i))
+    nv = sum(x.n for x in insts)
+    stream = torch.cuda.current_stream()
+    # plain: one solve per instance, default tile and options
+    plain_ms, plain_sweeps, flows = 0.0, 0, []
+    for x in insts:
+        with Grid(x.dims, x.conn, stream=stream) as g:
+            g.set_caps(x.cs, x.ct, x.nlink)
+            g.solve()
+            st = g.solve()
+            plain_ms += st.ms_total
+            plain_sweeps += st.sweeps
+            flows.append(g.flow_value())
+    table = autotune.tune(insts, cache_path=os.path.join(tempfile.gettempdir(), "mf_autotune.json"))
+    sched = autotune.batch_schedule(insts, table)
+    handles = []
+    for x in insts:
+        tile, _ = autotune.choose(x, table)
+        g = Grid(x.dims, x.conn, tile=tile, stream=stream)
+        g.set_caps(x.cs, x.ct, x.nlink)
+        handles.append(g)
+    opts = default_opts(**sched)
+    for _ in range(args.warmup):
+        mf.solve_batch(handles, opts)
+    times = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        stats = mf.solve_batch(handles, opts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    bflows = [h.flow_value() for h in handles]
+    assert bflows == flows, "batched and single solves disagree"
+    bms = statistics.median(times)
+    line = {"metric": METRIC, "workload": "batch", "value": round(bms / len(insts), 4), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "uneven batch: 384 2D 4-conn grids side U{64..1024} + 128 3D 6-conn side "
+                                   "U{48..128} (first %d), segmentation / volume generators" % len(insts),
+                       "instances": len(insts), "vertices": nv, "autotune": table, "schedule": sched},
+            "batch_ms": round(bms, 3), "plain_sequential_ms": round(plain_ms, 3),
+            "plain_ms_per_instance": round(plain_ms / len(insts), 4),
+            "speedup_vs_plain": round(plain_ms / bms, 3),
+            "sweeps_per_instance_batch": sum(s.sweeps for s in stats) / len(insts),
+            "sweeps_per_instance_plain": plain_sweeps / len(insts),
+            "vertices_per_s_batch": nv / (bms * 1e-3)}
+    for h in handles:
+        h.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -305,11 +376,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="seg2048", choices=["seg2048", "batch"])
+    ap.add_argument("--batch-count", type=int, default=0, help="first N instances of the batch (0 = all 512)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 
