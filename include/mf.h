@@ -68,7 +68,8 @@ typedef struct {
                                       Sec. 4.1 distance); 0 = off; default 4 */
     int32_t max_rounds;            /* cap on Augment rounds per stage inside one discharge; 0 = default 65536 */
     int32_t kernel_variant;        /* 0: bit-parallel 2D discharge where available (default); 1: generic kernel */
-    int32_t reserved[10];
+    int32_t warm_start;            /* 1: start from the preflow of the last mf_warm_start instead of Init's zero flow */
+    int32_t reserved[9];
 } mf_opts;
 
 /* Statistics of the last mf_solve (all optional reading). */
@@ -88,7 +89,8 @@ typedef struct {
     double ms_fuse;              /* device time of fusion + gap + activity kernels, summed */
     int32_t global_relabels;     /* exact region-distance relabels run (opts.global_relabel_period) */
     int32_t relabel_levels;      /* BFS levels of those relabels, summed */
-    int32_t reserved[6];
+    int32_t projection_rounds;   /* rounds of the warm-start projection (0 for a cold start) */
+    int32_t reserved[5];
 } mf_stats;
 
 /* Fill *opts with the defaults listed in mf_opts. */
@@ -215,6 +217,56 @@ mf_status mf_get_labels(mf_grid *g, int32_t *lab, int32_t *d_inf, int on_device)
 mf_status mf_min_cut_2d_noalloc(const int64_t dims[2], int connectivity, const int32_t *res,
                                 const int32_t *tres, const int32_t *exc, uint8_t *smin, uint8_t *smax,
                                 void *cuda_stream);
+
+/*
+ * Learned warm start (2D grids; the paper is silent: the hook is the zero flow
+ * of Init, Sec. 2).  Scale S = 100.
+ *   mf_warm_features: x = device float[2+N][n]: cs/S, ct/S, then for arc
+ *     directions d = 0..N-1 the capacity of the edge carried by arc d at v, /S.
+ *   mf_warm_targets (after a finished solve): t = device float[N+2][n]: the
+ *     flow out of v along arc d (d = 0..N-1), then, with m = min(cs, ct)
+ *     routed straight through v by Init, cs - m - e(v) and ct - m - c_f(v,t);
+ *     all /S.
+ *   mf_warm_start: projects a prediction p (device float[N+2][n], target
+ *     layout) to a valid preflow: edge flow f(v, v+h-th offset) = round(S p[2h][v])
+ *     clamped to [-c, c]; sink flow round(S p[N+1][v]) clamped to
+ *     [0, ct - min(cs,ct)]; every s-link saturated; then synchronous rounds in
+ *     which each vertex with negative excess lowers its own outflows (sink
+ *     first, then arcs 0..N-1) until no excess is negative.  max_rounds <= 0
+ *     means 4096; *rounds (nullable) receives the rounds used.  The next
+ *     mf_solve / mf_begin with opts.warm_start = 1 starts from this preflow;
+ *     its labels are the exact region distances to t in the residual graph of
+ *     that preflow (the global relabel, counted in stats.global_relabels) on
+ *     2D grids with 32- or 64-wide tiles, else 0.  If no region is active
+ *     after that relabel the solve makes no sweep.  MF_EROUNDLIMIT if the rounds run out: solve cold instead.
+ * The results of a warm solve are the same exact flow value and cuts.
+ */
+mf_status mf_warm_features(mf_grid *g, float *x);
+mf_status mf_warm_targets(mf_grid *g, float *t);
+mf_status mf_warm_start(mf_grid *g, const float *pred, int32_t max_rounds, int32_t *rounds);
+
+/*
+ * The network of the warm start: four 3x3 convolutions (zero padding),
+ * C -> 32 -> 32 -> 32 -> C with ReLU after the first three, C = 6 (4-connected)
+ * or 10 (8-connected).  FP32 master parameters, BF16 weights in every product,
+ * FP32 accumulation.  Parameter vector: for layers l = 1..4 the weights
+ * [C_out][C_in][3][3] then the biases [C_out].  Activations are device float
+ * [N][C][H][W].  Training: forward, mf_cnn_mse (loss and dy), zero_grad,
+ * backward (gradients of the parameters; needs the forward's input), Adam.
+ */
+typedef struct mf_cnn mf_cnn;
+mf_status mf_cnn_create(mf_cnn **out, int in_ch, int out_ch, uint64_t seed, void *cuda_stream);
+mf_status mf_cnn_destroy(mf_cnn *c);
+const char *mf_cnn_last_error(const mf_cnn *c);
+int64_t mf_cnn_num_params(const mf_cnn *c);
+mf_status mf_cnn_get_params(mf_cnn *c, float *out, int on_device);
+mf_status mf_cnn_set_params(mf_cnn *c, const float *in, int on_device);
+mf_status mf_cnn_get_grads(mf_cnn *c, float *out, int on_device);
+mf_status mf_cnn_forward(mf_cnn *c, const float *x, int N, int H, int W, float *y);
+mf_status mf_cnn_zero_grad(mf_cnn *c);
+mf_status mf_cnn_backward(mf_cnn *c, const float *x, const float *dy);
+mf_status mf_cnn_mse(mf_cnn *c, const float *y, const float *target, float *dy, int64_t count, double *loss);
+mf_status mf_cnn_adam_step(mf_cnn *c, float lr, float beta1, float beta2, float eps);
 
 /* Free the handle and all its device memory (NULL is a no-op). */
 mf_status mf_destroy(mf_grid *g);

@@ -27,6 +27,10 @@ struct mf_grid {
     DevState st{};
     unsigned char *smin = nullptr, *tset = nullptr;
     void *cut_scratch = nullptr;                      // 2D cut: bit masks and sets
+    int *warmF = nullptr, *warmFt = nullptr, *warmE = nullptr;  // projected initial flows (warm start)
+    bool warm_ready = false;
+    int warm_rounds = 0;
+    int begin_active = -1;                            // active regions after mf_begin's relabel, -1: unknown
     Counters64 *c64 = nullptr;
     int *h_ctr = nullptr;                             // pinned mirror of st.ctr
     long long boundary = 0;
@@ -487,7 +491,8 @@ const char *mf_last_error(const mf_grid *g) { return g ? g->err.c_str() : g_stat
 static void free_all(mf_grid *h) {
     void *ptrs[] = {h->cs, h->ct, h->nl, h->st.cap, h->st.tcap, h->st.exc, h->st.lab, h->st.lab_next,
                     h->st.bout, h->st.active, h->st.disc, h->st.left_active, h->st.flow_t, h->st.flow0,
-                    h->st.hist, h->st.ctr, h->smin, h->tset, h->c64, h->cut_scratch};
+                    h->st.hist, h->st.ctr, h->smin, h->tset, h->c64, h->cut_scratch, h->warmF, h->warmFt,
+                    h->warmE};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
@@ -590,6 +595,7 @@ mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const in
     const size_t n = (size_t)g->g.n, H = (size_t)g->H;
     g->caps_set = false;
     g->begun = g->finished = false;
+    g->warm_ready = false;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(g->cs, cs, n * 4, kind, g->stream));
     CK(cudaMemcpyAsync(g->ct, ct, n * 4, kind, g->stream));
@@ -621,7 +627,12 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
     CK(cudaMemsetAsync(g->st.ctr, 0, kCtrWords * 4, g->stream));
     CK(cudaMemsetAsync(g->c64, 0, sizeof(Counters64), g->stream));
     CK(cudaMemsetAsync(g->st.hist, 0, (kHistBins + 1) * 4, g->stream));
-    CK(DISPATCH(g->conn, launch_init, g));
+    if (g->opts.warm_start) {
+        if (!g->warm_ready) return fail(g, MF_ESTATE, "warm_start requested without a successful mf_warm_start");
+        CK(launch_warm_init(g->conn, g->g, g->st, g->cs, g->ct, g->nl, g->warmF, g->warmFt, g->warmE, g->stream));
+    } else {
+        CK(DISPATCH(g->conn, launch_init, g));
+    }
     hist_init_kernel<<<1, 32, 0, g->stream>>>(g->st, (int)g->boundary);
     CK(cudaGetLastError());
     g->launches = 2;
@@ -630,6 +641,22 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
     g->finished = false;
     memset(&g->stats, 0, sizeof(g->stats));
     g->stats.boundary_size = (int32_t)g->boundary;
+    g->stats.projection_rounds = g->opts.warm_start ? g->warm_rounds : 0;
+    g->begin_active = -1;
+    if (g->opts.warm_start && g->ndim == 2 && glr2d_supported(g->g)) {
+        // A projected preflow leaves excess where the prediction was wrong and
+        // labels 0 everywhere; exact region distances (a valid labeling) put the
+        // excess that cannot reach t at d-infinity before the first sweep, so
+        // the sweeps only move the excess that still can.
+        int levels = 0;
+        CK(glr2d(g->conn, g->g, g->st, g->cut_scratch, g->h_ctr, &levels, g->stream));
+        CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        g->begin_active = g->h_ctr[kActiveRegions];
+        g->stats.global_relabels = 1;
+        g->stats.relabel_levels = levels;
+        g->launches += 4 + levels;
+    }
     return MF_OK;
 }
 
@@ -739,7 +766,7 @@ mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats) {
     long long cap = g->opts.max_sweeps > 0 ? g->opts.max_sweeps
                                             : std::min<long long>(2 * g->boundary * g->boundary + 1, 1ll << 30);
     mf_status rs = MF_OK;
-    for (;;) {
+    while (g->begin_active != 0) {  // 0: the initial labels already show a maximum preflow
         int32_t act = 0;
         rs = run_sweep(g, &act);
         if (rs != MF_OK) break;
@@ -936,6 +963,58 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         if (stats) stats[i] = h->stats;
     }
     return rs;
+}
+
+mf_status mf_warm_features(mf_grid *g, float *x) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!x) return fail(g, MF_EINVAL, "x is NULL");
+    if (g->ndim != 2) return fail(g, MF_EINVAL, "the warm start is for 2D grids");
+    if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
+    CK(launch_warm_features(g->conn, g->g, g->cs, g->ct, g->nl, x, g->stream));
+    return MF_OK;
+}
+
+mf_status mf_warm_targets(mf_grid *g, float *t) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!t) return fail(g, MF_EINVAL, "t is NULL");
+    if (g->ndim != 2) return fail(g, MF_EINVAL, "the warm start is for 2D grids");
+    if (!g->finished) return fail(g, MF_ESTATE, "no finished solve");
+    CK(launch_warm_targets(g->conn, g->g, g->st, g->cs, g->ct, g->nl, t, g->stream));
+    return MF_OK;
+}
+
+mf_status mf_warm_start(mf_grid *g, const float *pred, int32_t max_rounds, int32_t *rounds) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!pred) return fail(g, MF_EINVAL, "pred is NULL");
+    if (g->ndim != 2) return fail(g, MF_EINVAL, "the warm start is for 2D grids");
+    if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
+    g->warm_ready = false;
+    const size_t n = (size_t)g->g.n;
+    if (!g->warmF) {
+        CK(cudaMalloc(&g->warmF, (size_t)g->H * n * 4));
+        CK(cudaMalloc(&g->warmFt, n * 4));
+        CK(cudaMalloc(&g->warmE, n * 4));
+    }
+    if (max_rounds <= 0) max_rounds = 4096;
+    CK(launch_project_init(g->conn, g->g, g->cs, g->ct, g->nl, pred, g->warmF, g->warmFt, g->stream));
+    int r = 0;
+    for (;; ++r) {
+        CK(cudaMemsetAsync(&g->st.ctr[kChanged], 0, 4, g->stream));
+        CK(launch_project_excess(g->conn, g->g, g->cs, g->ct, g->warmF, g->warmFt, g->warmE, &g->st.ctr[kChanged],
+                                 g->stream));
+        CK(cudaMemcpyAsync(g->h_ctr, &g->st.ctr[kChanged], 4, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        if (!g->h_ctr[0]) break;  // every excess non-negative: a valid preflow
+        if (r >= max_rounds) {
+            if (rounds) *rounds = r;
+            return fail(g, MF_EROUNDLIMIT, "projection did not reach a preflow within max_rounds");
+        }
+        CK(launch_project_trim(g->conn, g->g, g->warmE, g->warmF, g->warmFt, g->stream));
+    }
+    g->warm_rounds = r;
+    g->warm_ready = true;
+    if (rounds) *rounds = r;
+    return MF_OK;
 }
 
 mf_status mf_get_cut(mf_grid *g, uint8_t *out, int which, int on_device) {

@@ -123,6 +123,18 @@ cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, in
 cudaError_t launch_discharge_batch(int conn, int tx, int ty, int tz, int variant, const Inst *insts,
                                    const int2 *items, const int *count, int *head, const SweepArgs &sa,
                                    int blocks, cudaStream_t stream);
+// warm.cu: learned warm start (features, targets, projection to a preflow)
+cudaError_t launch_warm_features(int conn, const Geom &g, const int *cs, const int *ct, const int *nl, float *x,
+                                 cudaStream_t s);
+cudaError_t launch_warm_targets(int conn, const Geom &g, const DevState &st, const int *cs, const int *ct,
+                                const int *nl, float *t, cudaStream_t s);
+cudaError_t launch_project_init(int conn, const Geom &g, const int *cs, const int *ct, const int *nl, const float *p,
+                                int *F, int *ft, cudaStream_t s);
+cudaError_t launch_project_excess(int conn, const Geom &g, const int *cs, const int *ct, const int *F, const int *ft,
+                                  int *E, int *neg, cudaStream_t s);
+cudaError_t launch_project_trim(int conn, const Geom &g, const int *E, int *F, int *ft, cudaStream_t s);
+cudaError_t launch_warm_init(int conn, const Geom &g, const DevState &st, const int *cs, const int *ct, const int *nl,
+                             const int *F, const int *ft, const int *E, cudaStream_t s);
 // ard_discharge2d.cu
 bool discharge2d_supported(int conn, int tx, int ty);
 cudaError_t launch_discharge2d_batch(int conn, int tx, int ty, const Inst *insts, const int2 *items,

@@ -22,14 +22,17 @@ STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "
 # every symbol include/mf.h declares
 EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
            "mf_finish", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
-           "mf_last_error", "mf_min_cut_2d_noalloc", "mf_solve_batch"]
+           "mf_last_error", "mf_min_cut_2d_noalloc", "mf_solve_batch", "mf_warm_features", "mf_warm_targets",
+           "mf_warm_start", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
+           "mf_cnn_get_params", "mf_cnn_set_params", "mf_cnn_get_grads", "mf_cnn_forward", "mf_cnn_zero_grad",
+           "mf_cnn_backward", "mf_cnn_mse", "mf_cnn_adam_step"]
 
 
 class mf_opts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("partial_discharge", ctypes.c_int32),
                 ("global_gap", ctypes.c_int32), ("global_relabel_period", ctypes.c_int32),
                 ("max_rounds", ctypes.c_int32), ("kernel_variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("warm_start", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 class mf_stats(ctypes.Structure):
@@ -40,7 +43,7 @@ class mf_stats(ctypes.Structure):
                 ("ms_init", ctypes.c_double), ("ms_sweeps", ctypes.c_double), ("ms_cut", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_discharge", ctypes.c_double), ("ms_fuse", ctypes.c_double),
                 ("global_relabels", ctypes.c_int32), ("relabel_levels", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("projection_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -80,6 +83,21 @@ def load(path: str = LIBPATH):
         "mf_last_error": (ctypes.c_char_p, [P]),
         "mf_min_cut_2d_noalloc": (I, [P, I, P, P, P, P, P, P]),
         "mf_solve_batch": (I, [P, I, ctypes.POINTER(mf_opts), ctypes.POINTER(mf_stats)]),
+        "mf_warm_features": (I, [P, P]),
+        "mf_warm_targets": (I, [P, P]),
+        "mf_warm_start": (I, [P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+        "mf_cnn_create": (I, [ctypes.POINTER(P), I, I, ctypes.c_uint64, P]),
+        "mf_cnn_destroy": (I, [P]),
+        "mf_cnn_last_error": (ctypes.c_char_p, [P]),
+        "mf_cnn_num_params": (I64, [P]),
+        "mf_cnn_get_params": (I, [P, P, I]),
+        "mf_cnn_set_params": (I, [P, P, I]),
+        "mf_cnn_get_grads": (I, [P, P, I]),
+        "mf_cnn_forward": (I, [P, P, I, I, I, P]),
+        "mf_cnn_zero_grad": (I, [P]),
+        "mf_cnn_backward": (I, [P, P, P]),
+        "mf_cnn_mse": (I, [P, P, P, P, I64, ctypes.POINTER(ctypes.c_double)]),
+        "mf_cnn_adam_step": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -228,8 +246,96 @@ class Grid:
         self._check(self._lib.mf_get_residual(self._h, res.ctypes.data, tres.ctypes.data, exc.ctypes.data, 0))
         return res, tres, exc
 
+    def warm_features(self, x):
+        """x: device float tensor [2+N, n]."""
+        p, dev = _ptr(x)
+        assert dev
+        self._check(self._lib.mf_warm_features(self._h, p))
+
+    def warm_targets(self, t):
+        """t: device float tensor [N+2, n] (after a solve)."""
+        p, dev = _ptr(t)
+        assert dev
+        self._check(self._lib.mf_warm_targets(self._h, p))
+
+    def warm_start(self, pred, max_rounds=0, check=True):
+        """Project a prediction (device float [N+2, n]) to the initial preflow of
+        the next solve with warm_start=1; returns (status, rounds)."""
+        p, dev = _ptr(pred)
+        assert dev
+        r = ctypes.c_int32()
+        st = self._lib.mf_warm_start(self._h, p, int(max_rounds), ctypes.byref(r))
+        if check:
+            self._check(st)
+        return st, r.value
+
     def get_labels(self):
         lab = np.empty(self.n, dtype=np.int32)
         dinf = ctypes.c_int32()
         self._check(self._lib.mf_get_labels(self._h, lab.ctypes.data, ctypes.byref(dinf), 0))
         return lab, dinf.value
+
+
+class CNN:
+    """The warm-start network (see include/mf.h); buffers are torch CUDA tensors."""
+
+    def __init__(self, channels=6, seed=0, stream=None):
+        lib = load()
+        h = ctypes.c_void_p()
+        s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        st = lib.mf_cnn_create(ctypes.byref(h), channels, channels, ctypes.c_uint64(seed), s)
+        if st != MF_OK:
+            raise MFError(st, lib.mf_last_error(None).decode())
+        self._h, self._lib, self.channels = h, lib, channels
+
+    def _check(self, st):
+        if st != MF_OK:
+            raise MFError(st, self._lib.mf_cnn_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mf_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self):
+        return int(self._lib.mf_cnn_num_params(self._h))
+
+    def get_params(self):
+        out = np.empty(self.num_params, dtype=np.float32)
+        self._check(self._lib.mf_cnn_get_params(self._h, out.ctypes.data, 0))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self._lib.mf_cnn_set_params(self._h, p.ctypes.data, 0))
+
+    def get_grads(self):
+        out = np.empty(self.num_params, dtype=np.float32)
+        self._check(self._lib.mf_cnn_get_grads(self._h, out.ctypes.data, 0))
+        return out
+
+    def forward(self, x, y):
+        N, C, H, W = x.shape
+        self._check(self._lib.mf_cnn_forward(self._h, x.data_ptr(), N, H, W, y.data_ptr()))
+
+    def zero_grad(self):
+        self._check(self._lib.mf_cnn_zero_grad(self._h))
+
+    def backward(self, x, dy):
+        self._check(self._lib.mf_cnn_backward(self._h, x.data_ptr(), dy.data_ptr()))
+
+    def mse(self, y, t, dy):
+        loss = ctypes.c_double()
+        self._check(self._lib.mf_cnn_mse(self._h, y.data_ptr(), t.data_ptr(), dy.data_ptr(), y.numel(),
+                                         ctypes.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(self._lib.mf_cnn_adam_step(self._h, lr, beta1, beta2, eps))

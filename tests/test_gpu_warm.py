@@ -1,0 +1,119 @@
+"""Learned warm start on the GPU: the network's kernels against the float64
+oracle, the projection to a preflow, exactness of warm solves, and the gain
+of a trained network over the cold start."""
+import numpy as np
+import pytest
+
+import oracle
+from gen import grids
+from helpers import assert_parity
+from oracle import cnn as ocnn
+from paper_1109_1146_gb300 import Grid, default_opts, mf, warmstart
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("c,shape", [(6, (2, 6, 20, 17)), (10, (1, 10, 33, 16)), (6, (1, 6, 48, 64))])
+def test_forward_and_gradients_match_oracle(c, shape):
+    net = mf.CNN(channels=c, seed=11)
+    p = net.get_params()
+    rng = np.random.Generator(np.random.PCG64(5))
+    x = rng.standard_normal(shape).astype(np.float32)
+    dy = rng.standard_normal(shape).astype(np.float32)
+    xt = torch.from_numpy(x).to(DEV)
+    yt = torch.empty_like(xt)
+    net.forward(xt, yt)
+    ref, _, _ = ocnn.forward(p, x.astype(np.float64), c)
+    np.testing.assert_allclose(yt.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+    net.zero_grad()
+    net.backward(xt, torch.from_numpy(dy).to(DEV))
+    g = net.get_grads()
+    gref = ocnn.backward(p, x.astype(np.float64), c, dy.astype(np.float64))
+    scale = np.abs(gref).max()
+    np.testing.assert_allclose(g, gref, rtol=2e-3, atol=2e-4 * scale)
+
+
+def test_adam_reduces_loss_on_fixed_batch():
+    net = mf.CNN(channels=6, seed=2)
+    rng = np.random.Generator(np.random.PCG64(6))
+    x = torch.from_numpy(rng.standard_normal((4, 6, 16, 16)).astype(np.float32)).to(DEV)
+    t = torch.from_numpy(rng.standard_normal((4, 6, 16, 16)).astype(np.float32) * 0.1).to(DEV)
+    y, dy = torch.empty_like(x), torch.empty_like(x)
+    losses = []
+    for _ in range(60):
+        net.forward(x, y)
+        losses.append(net.mse(y, t, dy))
+        net.zero_grad()
+        net.backward(x, dy)
+        net.adam_step(lr=3e-3)
+    assert losses[-1] < 0.5 * losses[0]
+
+
+def _solved_targets(inst):
+    C = inst.conn + 2
+    X, Y = inst.dims[0], inst.dims[1]
+    t = torch.empty((C, Y, X), dtype=torch.float32, device=DEV)
+    with Grid(inst.dims, inst.conn) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        st = g.solve(default_opts(global_relabel_period=0))
+        g.warm_targets(t)
+    return t, st
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_projection_of_the_exact_flows_is_immediate(conn):
+    inst = grids.segmentation_2d(150, 110, 3, conn=conn, hard_seed_frac=0.03)
+    t, cold = _solved_targets(inst)
+    with Grid(inst.dims, conn) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        st, rounds = g.warm_start(t)
+        assert rounds == 0  # the solution's flows already form a preflow
+        ws = g.solve(default_opts(warm_start=1, global_relabel_period=0))
+        got = {"flow": g.flow_value(), "smin": g.get_cut(0), "smax": g.get_cut(1)}
+        got["res"], got["tres"], got["exc"] = g.get_residual()
+    assert_parity(inst, got)
+    # the relabel before the first sweep already sees a maximum preflow
+    assert ws.sweeps == 0 and ws.global_relabels == 1 and cold.sweeps > 0
+
+
+@pytest.mark.parametrize("noise", [0.0, 0.3, 3.0])
+def test_noisy_predictions_project_and_solve_exactly(noise):
+    inst = grids.config3(7, side=128)
+    t, _ = _solved_targets(inst)
+    gen = torch.Generator(device=DEV).manual_seed(1)
+    pred = t + noise * torch.randn(t.shape, generator=gen, device=DEV)
+    with Grid(inst.dims, 4) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        st, rounds = g.warm_start(pred)
+        ws = g.solve(default_opts(warm_start=1))
+        assert ws.projection_rounds == rounds
+        got = {"flow": g.flow_value(), "smin": g.get_cut(0), "smax": g.get_cut(1)}
+        got["res"], got["tres"], got["exc"] = g.get_residual()
+    assert_parity(inst, got)
+
+
+def test_projection_trims_a_chain_by_hand():
+    # 1x3 chain, cs = [5,0,0], ct = [0,0,5], links 4 and 4.  Predicted flows 7
+    # and 6 exceed what s supplies: v0 has excess 5-4 (after clamping 7 -> 4);
+    # v1 receives 4 and sends 4 (6 clamped to 4): fine; so clamping alone gives
+    # a preflow.  Predict 4 on the first link and 4 on the second but a sink
+    # flow the capacity allows: v2 gets 4 and may send 4 -> flow 4 = max flow.
+    cs = np.array([5, 0, 0], np.int32)
+    ct = np.array([0, 0, 5], np.int32)
+    nl = np.array([[4, 4, 0], [0, 0, 0]], np.int32)
+    g = Grid((3, 1, 1), 4)
+    g.set_caps(cs, ct, nl)
+    pred = torch.zeros((6, 1, 3), dtype=torch.float32, device=DEV)
+    pred[0, 0, 0] = 0.07   # v0 -> v1: 7, clamped to 4
+    pred[0, 0, 1] = 0.06   # v1 -> v2: 6, clamped to 4
+    pred[5, 0, 2] = 0.09   # v2 -> t: 9, clamped to 5
+    st, rounds = g.warm_start(pred)
+    # v2: in 4, out 5 -> deficit 1 -> sink flow trimmed to 4 in one round
+    assert rounds == 1
+    g.solve(default_opts(warm_start=1))
+    assert g.flow_value() == 4
+    res, tres, exc = g.get_residual()
+    assert exc.tolist() == [1, 0, 0] and tres.tolist() == [0, 0, 1]
+    g.close()
