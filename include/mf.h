@@ -107,7 +107,10 @@ void mf_default_opts(mf_opts *opts);
  *                 32x32, 3D 16x16x16 and 8x8x8; NULL or {0,0,0} picks 64x64
  *                 (2D) / 16^3 (3D);
  *   cuda_stream   cudaStream_t to order all work on, or NULL for a stream
- *                 owned by the handle.
+ *                 owned by the handle (non-blocking: device buffers that
+ *                 other streams produce or consume must then be ordered by
+ *                 the caller).  The default streams are given by their
+ *                 handles cudaStreamLegacy / cudaStreamPerThread.
  * Allocates the device state (about (2H+6)*4 + 1 bytes per vertex plus a
  * second copy of the inputs).  On failure *out is NULL.
  */
@@ -253,6 +256,8 @@ mf_status mf_warm_start(mf_grid *g, const float *pred, int32_t max_rounds, int32
  * [C_out][C_in][3][3] then the biases [C_out].  Activations are device float
  * [N][C][H][W].  Training: forward, mf_cnn_mse (loss and dy), zero_grad,
  * backward (gradients of the parameters; needs the forward's input), Adam.
+ * All work is ordered on cuda_stream (NULL: the legacy default stream); calls
+ * that return host data (mse's loss, get_params/grads to host) synchronise it.
  */
 typedef struct mf_cnn mf_cnn;
 mf_status mf_cnn_create(mf_cnn **out, int in_ch, int out_ch, uint64_t seed, void *cuda_stream);
@@ -263,10 +268,29 @@ mf_status mf_cnn_get_params(mf_cnn *c, float *out, int on_device);
 mf_status mf_cnn_set_params(mf_cnn *c, const float *in, int on_device);
 mf_status mf_cnn_get_grads(mf_cnn *c, float *out, int on_device);
 mf_status mf_cnn_forward(mf_cnn *c, const float *x, int N, int H, int W, float *y);
+/* Inference only (no state kept for backward): the same network on the tensor
+ * cores, with BF16 activations between layers (the input is rounded to BF16,
+ * each hidden layer's ReLU output is stored as BF16), FP32 accumulation.
+ * x and y as in mf_cnn_forward.  Holds two device buffers of N*H*W*32 BF16. */
+mf_status mf_cnn_infer(mf_cnn *c, const float *x, int N, int H, int W, float *y);
 mf_status mf_cnn_zero_grad(mf_cnn *c);
 mf_status mf_cnn_backward(mf_cnn *c, const float *x, const float *dy);
 mf_status mf_cnn_mse(mf_cnn *c, const float *y, const float *target, float *dy, int64_t count, double *loss);
 mf_status mf_cnn_adam_step(mf_cnn *c, float lr, float beta1, float beta2, float eps);
+
+/*
+ * Optimality certificate of the last finished solve, computed on the device
+ * from the original capacities: the preflow is feasible (0 <= r(v,w),
+ * r(v,w) + r(w,v) = 2 c(v,w), 0 <= c_f(v,t) <= ct - min(cs,ct)), conserves
+ * (e(v) = inflow - outflow >= 0 with every s-link saturated), and its flow
+ * into t equals the capacity of the cut (S_min, V \ S_min) and the reported
+ * flow value; by weak duality (Sec. 2) both are then optimal.
+ *   cut_capacity (nullable)  capacity of (S_min, V \ S_min);
+ *   violations   (nullable)  number of violated vertex / arc conditions;
+ *   certified    (nullable)  1 iff violations = 0 and the three values agree.
+ * MF_ESTATE without a finished solve.
+ */
+mf_status mf_certify(mf_grid *g, int64_t *cut_capacity, int64_t *violations, int32_t *certified);
 
 /* Free the handle and all its device memory (NULL is a no-op). */
 mf_status mf_destroy(mf_grid *g);

@@ -60,16 +60,22 @@ def conv3x3(x, w, b):
     return y
 
 
-def forward(p, x, c):
-    """Returns (output, list of layer inputs, list of layer outputs)."""
+def forward(p, x, c, bf16_activations=False):
+    """Returns (output, list of layer inputs, list of layer outputs).  With
+    bf16_activations the input and each hidden layer's ReLU output are rounded
+    to BF16 (the inference variant of the network)."""
     layers = unpack(np.asarray(p, dtype=np.float32), c)
     ins, outs = [], []
     h = np.asarray(x, dtype=np.float64)
+    if bf16_activations:
+        h = bf16(h)
     for i, (w, b) in enumerate(layers):
         ins.append(h)
         h = conv3x3(h, bf16(w), b.astype(np.float64))
         if i < 3:
             h = np.maximum(h, 0.0)
+            if bf16_activations:
+                h = bf16(h)
         outs.append(h)
     return h, ins, outs
 

@@ -12,6 +12,7 @@
 // atomically), a mean-squared-error loss with its gradient, and Adam.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -155,6 +156,165 @@ __global__ void to_bf16_kernel(const float *p, __nv_bfloat16 *pb, size_t n) {
         pb[i] = __float2bfloat16(p[i]);
 }
 
+// ---- inference on the tensor cores -----------------------------------------------
+// Implicit GEMM per 16x16 output tile: for each of the nine taps,
+// D[pixel][co] += A[pixel][ci] * B[ci][co], A being the input tile shifted by
+// the tap.  The input tile (halo 1) is staged once in shared memory as BF16
+// rows [pixel][channel] padded to KIN + 8 elements (80 or 48 bytes: the eight
+// rows one ldmatrix reads fall in distinct banks); the layer's weights as
+// [tap][co][ci] rows of the same padding.  mma.sync m16n8k16 takes BF16
+// operands with FP32 accumulation; a warp computes two output rows (M = 16
+// pixels each) and shares every B fragment between them.  Activations between
+// layers are BF16 NHWC with 32 channels; the first layer reads the FP32 NCHW
+// network input, the last writes FP32 NCHW.
+constexpr int kIT = 16;       // output tile edge
+constexpr int kIH = kIT + 2;  // staged tile edge
+
+__device__ __forceinline__ void ldsm_x4(const void *p, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x2(const void *p, uint32_t &r0, uint32_t &r1) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int KIN, int NOUT>
+constexpr size_t conv_mma_smem() {
+    return (size_t)(9 * NOUT + kIH * kIH) * (KIN + 8) * 2 + NOUT * 4;
+}
+
+template <int KIN, int NOUT, bool IN_F32, bool OUT_F32, bool RELU>
+__global__ void __launch_bounds__(256) conv3x3_mma_kernel(const void *__restrict__ in, int cin,
+                                                          const __nv_bfloat16 *__restrict__ w,
+                                                          const float *__restrict__ bias, void *__restrict__ out,
+                                                          int cout, int N, int H, int W) {
+    constexpr int AS = KIN + 8;  // BF16 elements per staged row
+    constexpr int NT = NOUT / 8; // n-tiles of 8 output channels
+    constexpr int KS = KIN / 16; // k-steps per tap
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __nv_bfloat16 *s_w = (__nv_bfloat16 *)smraw;          // [9][NOUT][AS]
+    __nv_bfloat16 *s_a = s_w + 9 * NOUT * AS;              // [kIH * kIH][AS]
+    float *s_bias = (float *)(s_a + kIH * kIH * AS);       // [NOUT]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < 9 * NOUT * KIN; i += blockDim.x) {
+        const int tap = i / (NOUT * KIN), co = (i / KIN) % NOUT, ci = i % KIN;
+        s_w[(tap * NOUT + co) * AS + ci] =
+            (co < cout && ci < cin) ? w[((size_t)co * cin + ci) * 9 + tap] : __float2bfloat16(0.f);
+    }
+    for (int i = tid; i < NOUT; i += blockDim.x) s_bias[i] = i < cout ? bias[i] : 0.f;
+    const int tiles_x = (W + kIT - 1) / kIT, tiles_y = (H + kIT - 1) / kIT;
+    const long long per_img = (long long)tiles_x * tiles_y, tiles = per_img * N;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int n = (int)(t / per_img), rem = (int)(t % per_img);
+        const int oy = (rem / tiles_x) * kIT, ox = (rem % tiles_x) * kIT;
+        __syncthreads();  // the previous tile's reads of s_a are done
+        if constexpr (IN_F32) {
+            const float *x = (const float *)in + (size_t)n * cin * H * W;
+            for (int i = tid; i < KIN * kIH * kIH; i += blockDim.x) {
+                const int c = i / (kIH * kIH), p = i % (kIH * kIH);
+                const int gy = oy + p / kIH - 1, gx = ox + p % kIH - 1;
+                float v = 0.f;
+                if (c < cin && gy >= 0 && gy < H && gx >= 0 && gx < W) v = x[((size_t)c * H + gy) * W + gx];
+                s_a[p * AS + c] = __float2bfloat16(v);
+            }
+        } else {
+            const __nv_bfloat16 *x = (const __nv_bfloat16 *)in + (size_t)n * H * W * KIN;
+            constexpr int CH = KIN / 8;  // 16-byte chunks per pixel
+            for (int i = tid; i < kIH * kIH * CH; i += blockDim.x) {
+                const int p = i / CH, q = i % CH;
+                const int gy = oy + p / kIH - 1, gx = ox + p % kIH - 1;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                    v = *(const uint4 *)(x + ((size_t)gy * W + gx) * KIN + q * 8);
+                *(uint4 *)(s_a + p * AS + q * 8) = v;
+            }
+        }
+        __syncthreads();
+        // warp w computes output rows w and w + 8 of the tile
+        const int rows[2] = {warp, warp + 8};
+        float acc[2][NT][4];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[rr][j][e] = s_bias[j * 8 + 2 * (lane & 3) + (e & 1)];
+        const int am = (lane & 7) + 8 * ((lane >> 3) & 1);  // A row (pixel) this lane addresses
+        const int ak = 8 * (lane >> 4);                    // A column offset
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                uint32_t a[2][4];
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr)
+                    ldsm_x4(s_a + ((rows[rr] + ky) * kIH + am + kx) * AS + ks * 16 + ak, a[rr][0], a[rr][1],
+                            a[rr][2], a[rr][3]);
+                if constexpr (NT == 1) {
+                    uint32_t b0, b1;
+                    ldsm_x2(s_w + (tap * NOUT + (lane & 7)) * AS + ks * 16 + 8 * ((lane >> 3) & 1), b0, b1);
+#pragma unroll
+                    for (int rr = 0; rr < 2; ++rr) mma_bf16_16816(acc[rr][0], a[rr], b0, b1);
+                } else {
+#pragma unroll
+                    for (int j2 = 0; j2 < NT / 2; ++j2) {
+                        const int mat = lane >> 3;
+                        const int nt = 2 * j2 + (mat >> 1), kh = mat & 1;
+                        uint32_t b0, b1, b2, b3;
+                        ldsm_x4(s_w + (tap * NOUT + nt * 8 + (lane & 7)) * AS + ks * 16 + kh * 8, b0, b1, b2, b3);
+#pragma unroll
+                        for (int rr = 0; rr < 2; ++rr) {
+                            mma_bf16_16816(acc[rr][2 * j2], a[rr], b0, b1);
+                            mma_bf16_16816(acc[rr][2 * j2 + 1], a[rr], b2, b3);
+                        }
+                    }
+                }
+            }
+        }
+        // accumulator (e = 0,1: pixel g; e = 2,3: pixel g + 8), channels j*8 + 2c, +1
+        const int g8 = lane >> 2, cq = lane & 3;
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int py = oy + rows[rr];
+            if (py >= H) continue;
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    const int px = ox + g8 + 8 * hf;
+                    if (px >= W) continue;
+                    float v0 = acc[rr][j][2 * hf], v1 = acc[rr][j][2 * hf + 1];
+                    if (RELU) {
+                        v0 = fmaxf(v0, 0.f);
+                        v1 = fmaxf(v1, 0.f);
+                    }
+                    const int co = j * 8 + 2 * cq;
+                    if constexpr (OUT_F32) {
+                        float *y = (float *)out + (size_t)n * cout * H * W;
+                        if (co < cout) y[((size_t)co * H + py) * W + px] = v0;
+                        if (co + 1 < cout) y[((size_t)(co + 1) * H + py) * W + px] = v1;
+                    } else {
+                        __nv_bfloat16 *y = (__nv_bfloat16 *)out + ((size_t)n * H * W + (size_t)py * W + px) * NOUT;
+                        *(__nv_bfloat162 *)(y + co) = __floats2bfloat162_rn(v0, v1);
+                    }
+                }
+        }
+    }
+}
+
 // ---- host side ---------------------------------------------------------------
 template <int CIN, int COUT, bool RELU>
 static cudaError_t conv_fwd(const float *x, const __nv_bfloat16 *w, const float *b, float *y, int N, int H, int W,
@@ -169,6 +329,27 @@ static cudaError_t conv_fwd(const float *x, const __nv_bfloat16 *w, const float 
     }
     dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile, N);
     conv3x3_kernel<CIN, COUT, RELU><<<grid, 256, smem, s>>>(x, w, b, y, H, W);
+    return cudaGetLastError();
+}
+
+template <int KIN, int NOUT, bool IN_F32, bool OUT_F32, bool RELU>
+static cudaError_t conv_mma(const void *x, int cin, const __nv_bfloat16 *w, const float *b, void *y, int cout, int N,
+                            int H, int W, cudaStream_t s) {
+    constexpr size_t smem = conv_mma_smem<KIN, NOUT>();
+    auto kern = conv3x3_mma_kernel<KIN, NOUT, IN_F32, OUT_F32, RELU>;
+    static int blocks_per_sm = 0, sms = 0;
+    if (!blocks_per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 256, smem);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    const long long tiles = (long long)((W + kIT - 1) / kIT) * ((H + kIT - 1) / kIT) * N;
+    const int grid = (int)std::min<long long>(tiles, (long long)blocks_per_sm * sms);
+    kern<<<grid, 256, smem, s>>>(x, cin, w, b, y, cout, N, H, W);
     return cudaGetLastError();
 }
 
@@ -228,6 +409,8 @@ struct mf_cnn {
     float *dbuf[2] = {nullptr, nullptr};                           // gradient ping-pong buffers
     float *zero_bias = nullptr;
     double *dloss = nullptr;
+    __nv_bfloat16 *ibuf[2] = {nullptr, nullptr};                   // inference activations, BF16 NHWC x 32
+    size_t icap_pix = 0;
     size_t cap_pix = 0;        // N*H*W the activation buffers hold
     int N = 0, H = 0, W = 0;
     long long steps = 0;
@@ -255,6 +438,17 @@ static void cnn_free_acts(mf_cnn *c) {
     for (auto &d : c->dbuf)
         if (d) { cudaFree(d); d = nullptr; }
     c->cap_pix = 0;
+}
+
+static mf_status cnn_ensure_infer(mf_cnn *c, int N, int H, int W) {
+    const size_t pix = (size_t)N * H * W;
+    if (pix <= c->icap_pix) return MF_OK;
+    for (auto &b : c->ibuf)
+        if (b) { cudaFree(b); b = nullptr; }
+    c->icap_pix = 0;
+    for (auto &b : c->ibuf) CKC(cudaMalloc(&b, pix * 32 * 2));
+    c->icap_pix = pix;
+    return MF_OK;
 }
 
 static mf_status cnn_ensure(mf_cnn *c, int N, int H, int W) {
@@ -330,7 +524,7 @@ mf_status mf_cnn_create(mf_cnn **out, int in_ch, int out_ch, uint64_t seed, void
 mf_status mf_cnn_destroy(mf_cnn *c) {
     if (!c) return MF_OK;
     cnn_free_acts(c);
-    void *ps[] = {c->p, c->g, c->m, c->v, c->pb, c->wt, c->zero_bias, c->dloss};
+    void *ps[] = {c->p, c->g, c->m, c->v, c->pb, c->wt, c->zero_bias, c->dloss, c->ibuf[0], c->ibuf[1]};
     for (void *q : ps)
         if (q) cudaFree(q);
     delete c;
@@ -384,6 +578,27 @@ mf_status mf_cnn_forward(mf_cnn *c, const float *x, int N, int H, int W, float *
                          c->stream));
         in = o;
     }
+    return MF_OK;
+}
+
+mf_status mf_cnn_infer(mf_cnn *c, const float *x, int N, int H, int W, float *y) {
+    if (!c || !x || !y || N < 1 || H < 1 || W < 1) return cnn_fail(c, MF_EINVAL, "bad infer arguments");
+    mf_status s = cnn_ensure_infer(c, N, H, W);
+    if (s != MF_OK) return s;
+    const int cin = c->ch[0], cout = c->ch[4];
+    __nv_bfloat16 *b0 = c->ibuf[0], *b1 = c->ibuf[1];
+    CKC((conv_mma<16, 32, true, false, true>(x, cin, c->pb + c->woff[1], c->p + c->boff[1], b0, 32, N, H, W,
+                                             c->stream)));
+    CKC((conv_mma<32, 32, false, false, true>(b0, 32, c->pb + c->woff[2], c->p + c->boff[2], b1, 32, N, H, W,
+                                              c->stream)));
+    CKC((conv_mma<32, 32, false, false, true>(b1, 32, c->pb + c->woff[3], c->p + c->boff[3], b0, 32, N, H, W,
+                                              c->stream)));
+    if (cout <= 8)
+        CKC((conv_mma<32, 8, false, true, false>(b0, 32, c->pb + c->woff[4], c->p + c->boff[4], y, cout, N, H, W,
+                                                 c->stream)));
+    else
+        CKC((conv_mma<32, 16, false, true, false>(b0, 32, c->pb + c->woff[4], c->p + c->boff[4], y, cout, N, H, W,
+                                                  c->stream)));
     return MF_OK;
 }
 

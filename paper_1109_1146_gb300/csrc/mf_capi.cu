@@ -459,6 +459,66 @@ static cudaError_t launch_cut_pass(mf_grid *h, unsigned char *set, int fwd) {
 #define DISPATCH(conn, fn, ...) \
     ((conn) == 4 ? fn<4>(__VA_ARGS__) : (conn) == 8 ? fn<8>(__VA_ARGS__) : fn<6>(__VA_ARGS__))
 
+// Optimality certificate of a finished solve, from the original capacities:
+// counts violations of the capacity constraints (r(v,w) >= 0 and
+// r(v,w) + r(w,v) = 2 c(v,w); no residual arc leaving the grid), of the sink
+// residual (0 <= c_f(v,t) <= ct - min(cs,ct)) and of conservation
+// (e(v) = cs' - f(v,t) - sum_w f(v,w) and e(v) >= 0), and sums the capacity
+// of the cut (S, V \ S) for S = S_min: cs over V \ S, ct over S, c(v,w) over
+// arcs from S to V \ S, and the flow into t, min(cs,ct) + ct' - c_f(v,t).
+// Weak duality: a feasible preflow whose sink inflow equals the capacity of
+// some cut is a maximum flow and the cut a minimum cut (Sec. 2).
+template <int CONN>
+__global__ void certify_kernel(const Geom g, const DevState st, const int *__restrict__ cs, const int *__restrict__ ct,
+                               const int *__restrict__ nl, const unsigned char *__restrict__ S,
+                               unsigned long long *sums) {
+    const size_t n = (size_t)g.n;
+    unsigned long long cut = 0, tin = 0, bad = 0;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
+        const int a = cs[v], b = ct[v], m = min(a, b);
+        const bool inS = S[v] != 0;
+        cut += (unsigned long long)(inS ? b : a);
+        const int tc = st.tcap[v];
+        if (tc < 0 || tc > b - m) ++bad;
+        tin += (unsigned long long)(b - tc);
+        long long e = (long long)(a - m) - (long long)(b - m - tc);
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d), wz = z + arc_dz(CONN, d);
+            const int r = st.cap[(size_t)d * n + v];
+            if (!in_grid(g, wx, wy, wz)) {
+                if (r != 0) ++bad;
+                continue;
+            }
+            const size_t w = ((size_t)wz * g.Y + wy) * g.X + wx;
+            const int c = (d & 1) ? nl[(size_t)(d >> 1) * n + w] : nl[(size_t)(d >> 1) * n + v];
+            const int rr = st.cap[(size_t)(d ^ 1) * n + w];
+            if (r < 0 || (long long)r + rr != 2ll * c) ++bad;
+            e -= (long long)c - r;
+            if (inS && !S[w]) cut += (unsigned long long)c;
+        }
+        if (e != st.exc[v] || e < 0) ++bad;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cut += __shfl_down_sync(0xffffffffu, cut, o);
+        tin += __shfl_down_sync(0xffffffffu, tin, o);
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cut) atomicAdd(&sums[0], cut);
+        if (tin) atomicAdd(&sums[1], tin);
+        if (bad) atomicAdd(&sums[2], bad);
+    }
+}
+
+template <int CONN>
+static cudaError_t launch_certify(mf_grid *g, unsigned long long *sums) {
+    certify_kernel<CONN><<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->g, g->st, g->cs, g->ct, g->nl, g->smin,
+                                                                          sums);
+    return cudaGetLastError();
+}
+
 // |B| of Sec. 4.1 for a tiling: a vertex is a boundary vertex iff along some
 // axis it is the first cell of a tile (not at 0) or the last (not at the end);
 // the same set for 4- and 8-connectivity (diagonal neighbours in another tile
@@ -997,19 +1057,14 @@ mf_status mf_warm_start(mf_grid *g, const float *pred, int32_t max_rounds, int32
     }
     if (max_rounds <= 0) max_rounds = 4096;
     CK(launch_project_init(g->conn, g->g, g->cs, g->ct, g->nl, pred, g->warmF, g->warmFt, g->stream));
-    int r = 0;
-    for (;; ++r) {
-        CK(cudaMemsetAsync(&g->st.ctr[kChanged], 0, 4, g->stream));
-        CK(launch_project_excess(g->conn, g->g, g->cs, g->ct, g->warmF, g->warmFt, g->warmE, &g->st.ctr[kChanged],
-                                 g->stream));
-        CK(cudaMemcpyAsync(g->h_ctr, &g->st.ctr[kChanged], 4, cudaMemcpyDeviceToHost, g->stream));
-        CK(cudaStreamSynchronize(g->stream));
-        if (!g->h_ctr[0]) break;  // every excess non-negative: a valid preflow
-        if (r >= max_rounds) {
-            if (rounds) *rounds = r;
-            return fail(g, MF_EROUNDLIMIT, "projection did not reach a preflow within max_rounds");
-        }
-        CK(launch_project_trim(g->conn, g->g, g->warmE, g->warmF, g->warmFt, g->stream));
+    CK(launch_project_rounds(g->conn, g->g, g->cs, g->ct, g->warmF, g->warmFt, g->warmE, &g->st.ctr[kGlrFlags],
+                             max_rounds, g->stream));
+    CK(cudaMemcpyAsync(g->h_ctr, &g->st.ctr[kGlrFlags], 3 * 4, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    const int r = g->h_ctr[2];
+    if (r < 0) {
+        if (rounds) *rounds = max_rounds;
+        return fail(g, MF_EROUNDLIMIT, "projection did not reach a preflow within max_rounds");
     }
     g->warm_rounds = r;
     g->warm_ready = true;
@@ -1037,6 +1092,25 @@ mf_status mf_flow_value(mf_grid *g, int64_t *out) {
     CK(cudaMemcpyAsync(&ft, g->st.flow_t, 8, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     *out = f0 + (long long)ft;
+    return MF_OK;
+}
+
+mf_status mf_certify(mf_grid *g, int64_t *cut_capacity, int64_t *violations, int32_t *certified) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!g->finished) return fail(g, MF_ESTATE, "no finished solve");
+    // three 64-bit sums in the last six counter words (unused once a solve has finished)
+    unsigned long long *sums = (unsigned long long *)&g->st.ctr[kCtrWords - 6];
+    CK(cudaMemsetAsync(sums, 0, 3 * 8, g->stream));
+    CK(DISPATCH(g->conn, launch_certify, g, sums));
+    unsigned long long h[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    int64_t flow = 0;
+    mf_status s = mf_flow_value(g, &flow);
+    if (s != MF_OK) return s;
+    if (cut_capacity) *cut_capacity = (int64_t)h[0];
+    if (violations) *violations = (int64_t)h[2];
+    if (certified) *certified = h[2] == 0 && (int64_t)h[0] == flow && (int64_t)h[1] == flow;
     return MF_OK;
 }
 

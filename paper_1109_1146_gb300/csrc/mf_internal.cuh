@@ -130,9 +130,9 @@ cudaError_t launch_warm_targets(int conn, const Geom &g, const DevState &st, con
                                 const int *nl, float *t, cudaStream_t s);
 cudaError_t launch_project_init(int conn, const Geom &g, const int *cs, const int *ct, const int *nl, const float *p,
                                 int *F, int *ft, cudaStream_t s);
-cudaError_t launch_project_excess(int conn, const Geom &g, const int *cs, const int *ct, const int *F, const int *ft,
-                                  int *E, int *neg, cudaStream_t s);
-cudaError_t launch_project_trim(int conn, const Geom &g, const int *E, int *F, int *ft, cudaStream_t s);
+// all trim rounds in one cooperative launch; flags: 3 ints (flags[2] = rounds, -1: limit hit)
+cudaError_t launch_project_rounds(int conn, const Geom &g, const int *cs, const int *ct, int *F, int *ft, int *E,
+                                  int *flags, int max_rounds, cudaStream_t s);
 cudaError_t launch_warm_init(int conn, const Geom &g, const DevState &st, const int *cs, const int *ct, const int *nl,
                              const int *F, const int *ft, const int *E, cudaStream_t s);
 // ard_discharge2d.cu

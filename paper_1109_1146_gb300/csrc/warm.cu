@@ -18,9 +18,14 @@
 //   own outflow (sink flow first, then arcs 0..N-1) by its deficit, until no
 //   excess is negative.  Lowering an outflow only moves flow toward zero, so
 //   capacities stay respected; a round cap ends with a cold start instead.
+#include <algorithm>
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "mf_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mf {
 
@@ -88,62 +93,78 @@ __global__ void project_init_kernel(const Geom g, const int *cs, const int *ct, 
     }
 }
 
-// excess with every s-link saturated; flags a negative one
-template <int CONN>
-__global__ void project_excess_kernel(const Geom g, const int *cs, const int *ct, const int *F, const int *ft, int *E,
-                                      int *neg) {
-    const size_t n = (size_t)g.n;
-    int any = 0;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
-        const int px = (int)(v % g.X), py = (int)(v / g.X);
-        long long e = (long long)cs[v] - min(cs[v], ct[v]) - ft[v];
-#pragma unroll
-        for (int h = 0; h < CONN / 2; ++h) {
-            e -= F[h * n + v];
-            const int wx = px - fwd_dx(CONN, h), wy = py - fwd_dy(CONN, h);
-            if (ingrid2(g, wx, wy)) e += F[h * n + (size_t)wy * g.X + wx];
-        }
-        E[v] = (int)e;
-        any |= e < 0;
-    }
-    if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(neg, 1);
-}
-
 // a vertex with a deficit lowers its own outflows (an edge carries flow one
 // way, so only its tail ever lowers it: no two threads write one edge)
 template <int CONN>
-__global__ void project_trim_kernel(const Geom g, const int *E, int *F, int *ft) {
+__device__ __forceinline__ void trim_vertex(const Geom &g, size_t v, const int *E, int *F, int *ft) {
     const size_t n = (size_t)g.n;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
-        int def = -E[v];
-        if (def <= 0) continue;
-        const int px = (int)(v % g.X), py = (int)(v / g.X);
-        int r = min(ft[v], def);
-        ft[v] -= r;
-        def -= r;
+    int def = -E[v];
+    if (def <= 0) return;
+    const int px = (int)(v % g.X), py = (int)(v / g.X);
+    int r = min(ft[v], def);
+    ft[v] -= r;
+    def -= r;
 #pragma unroll
-        for (int d = 0; d < CONN; ++d) {
-            if (def == 0) break;
-            const int h = d >> 1;
-            if (!(d & 1)) {
-                const int f = F[h * n + v];
-                if (f > 0) {
-                    r = min(f, def);
-                    F[h * n + v] = f - r;
-                    def -= r;
-                }
-            } else {
-                const int wx = px - fwd_dx(CONN, h), wy = py - fwd_dy(CONN, h);
-                if (!ingrid2(g, wx, wy)) continue;
-                const size_t w = (size_t)wy * g.X + wx;
-                const int f = F[h * n + w];  // flow w -> v; negative means v -> w
-                if (f < 0) {
-                    r = min(-f, def);
-                    F[h * n + w] = f + r;
-                    def -= r;
-                }
+    for (int d = 0; d < CONN; ++d) {
+        if (def == 0) break;
+        const int h = d >> 1;
+        if (!(d & 1)) {
+            const int f = F[h * n + v];
+            if (f > 0) {
+                r = min(f, def);
+                F[h * n + v] = f - r;
+                def -= r;
+            }
+        } else {
+            const int wx = px - fwd_dx(CONN, h), wy = py - fwd_dy(CONN, h);
+            if (!ingrid2(g, wx, wy)) continue;
+            const size_t w = (size_t)wy * g.X + wx;
+            const int f = F[h * n + w];  // flow w -> v; negative means v -> w
+            if (f < 0) {
+                r = min(-f, def);
+                F[h * n + w] = f + r;
+                def -= r;
             }
         }
+    }
+}
+
+// All projection rounds in one cooperative launch: each round computes every
+// excess (flagging a negative one), and if some excess is negative and rounds
+// remain, trims.  flags[0..1] alternate between rounds (the host zeroes both
+// first); flags[2] receives the number of trim rounds made, or -1 if
+// max_rounds trims left a negative excess.  Every loop is bounded by
+// max_rounds; the grid is co-resident, so every grid.sync returns.
+template <int CONN>
+__global__ void project_rounds_kernel(const Geom g, const int *cs, const int *ct, int *F, int *ft, int *E, int *flags,
+                                      int max_rounds) {
+    cg::grid_group grid = cg::this_grid();
+    const size_t n = (size_t)g.n;
+    for (int r = 0;; ++r) {
+        int any = 0;
+        for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
+            const int px = (int)(v % g.X), py = (int)(v / g.X);
+            long long e = (long long)cs[v] - min(cs[v], ct[v]) - ft[v];
+#pragma unroll
+            for (int h = 0; h < CONN / 2; ++h) {
+                e -= F[h * n + v];
+                const int wx = px - fwd_dx(CONN, h), wy = py - fwd_dy(CONN, h);
+                if (ingrid2(g, wx, wy)) e += F[h * n + (size_t)wy * g.X + wx];
+            }
+            E[v] = (int)e;
+            any |= e < 0;
+        }
+        if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(&flags[r & 1], 1);
+        grid.sync();
+        const int neg = *(volatile int *)&flags[r & 1];
+        if (!neg || r >= max_rounds) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) flags[2] = neg ? -1 : r;
+            return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(r + 1) & 1] = 0;  // read by nobody since the last sync
+        for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+            trim_vertex<CONN>(g, v, E, F, ft);
+        grid.sync();
     }
 }
 
@@ -214,12 +235,26 @@ cudaError_t launch_project_init(int conn, const Geom &g, const int *cs, const in
                                 int *F, int *ft, cudaStream_t s) {
     WARM_DISPATCH(conn, project_init_kernel, g, cs, ct, nl, p, F, ft);
 }
-cudaError_t launch_project_excess(int conn, const Geom &g, const int *cs, const int *ct, const int *F, const int *ft,
-                                  int *E, int *neg, cudaStream_t s) {
-    WARM_DISPATCH(conn, project_excess_kernel, g, cs, ct, F, ft, E, neg);
-}
-cudaError_t launch_project_trim(int conn, const Geom &g, const int *E, int *F, int *ft, cudaStream_t s) {
-    WARM_DISPATCH(conn, project_trim_kernel, g, E, F, ft);
+cudaError_t launch_project_rounds(int conn, const Geom &g, const int *cs, const int *ct, int *F, int *ft, int *E,
+                                  int *flags, int max_rounds, cudaStream_t s) {
+    const void *kern = conn == 4 ? (const void *)project_rounds_kernel<4>
+                     : conn == 8 ? (const void *)project_rounds_kernel<8> : nullptr;
+    if (!kern) return cudaErrorInvalidValue;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const size_t want = ((size_t)g.n + 255) / 256;
+    const int blocks = (int)std::min<size_t>(want ? want : 1, (size_t)per_sm * sms);
+    e = cudaMemsetAsync(flags, 0, 3 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    Geom gg = g;
+    const int *a_cs = cs, *a_ct = ct;
+    int mr = max_rounds;
+    void *args[] = {&gg, (void *)&a_cs, (void *)&a_ct, &F, &ft, &E, &flags, &mr};
+    return cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(256), args, 0, s);
 }
 cudaError_t launch_warm_init(int conn, const Geom &g, const DevState &st, const int *cs, const int *ct, const int *nl,
                              const int *F, const int *ft, const int *E, cudaStream_t s) {

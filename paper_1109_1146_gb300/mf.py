@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 
 import numpy as np
 
@@ -23,8 +24,9 @@ STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "
 EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
            "mf_finish", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
            "mf_last_error", "mf_min_cut_2d_noalloc", "mf_solve_batch", "mf_warm_features", "mf_warm_targets",
-           "mf_warm_start", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
-           "mf_cnn_get_params", "mf_cnn_set_params", "mf_cnn_get_grads", "mf_cnn_forward", "mf_cnn_zero_grad",
+           "mf_warm_start", "mf_certify", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
+           "mf_cnn_get_params", "mf_cnn_set_params", "mf_cnn_get_grads", "mf_cnn_forward", "mf_cnn_infer",
+           "mf_cnn_zero_grad",
            "mf_cnn_backward", "mf_cnn_mse", "mf_cnn_adam_step"]
 
 
@@ -55,6 +57,44 @@ class MFError(RuntimeError):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
 
 
+_P, _I, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+# every exported call with its ctypes (restype, argtypes): a call without
+# argtypes would pass 64-bit pointers as C int
+SIGNATURES = {
+    "mf_default_opts": (None, [ctypes.POINTER(mf_opts)]),
+    "mf_create_grid": (_I, [ctypes.POINTER(_P), _I, _P, _I, _P, _P]),
+    "mf_set_caps": (_I, [_P, _P, _P, _P, _I]),
+    "mf_solve": (_I, [_P, ctypes.POINTER(mf_opts), ctypes.POINTER(mf_stats)]),
+    "mf_begin": (_I, [_P, ctypes.POINTER(mf_opts)]),
+    "mf_sweep": (_I, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "mf_finish": (_I, [_P]),
+    "mf_get_cut": (_I, [_P, _P, _I, _I]),
+    "mf_flow_value": (_I, [_P, ctypes.POINTER(_I64)]),
+    "mf_get_residual": (_I, [_P, _P, _P, _P, _I]),
+    "mf_get_labels": (_I, [_P, _P, ctypes.POINTER(ctypes.c_int32), _I]),
+    "mf_destroy": (_I, [_P]),
+    "mf_last_error": (ctypes.c_char_p, [_P]),
+    "mf_min_cut_2d_noalloc": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+    "mf_solve_batch": (_I, [_P, _I, ctypes.POINTER(mf_opts), ctypes.POINTER(mf_stats)]),
+    "mf_warm_features": (_I, [_P, _P]),
+    "mf_warm_targets": (_I, [_P, _P]),
+    "mf_warm_start": (_I, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "mf_certify": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32)]),
+    "mf_cnn_create": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.c_uint64, _P]),
+    "mf_cnn_destroy": (_I, [_P]),
+    "mf_cnn_last_error": (ctypes.c_char_p, [_P]),
+    "mf_cnn_num_params": (_I64, [_P]),
+    "mf_cnn_get_params": (_I, [_P, _P, _I]),
+    "mf_cnn_set_params": (_I, [_P, _P, _I]),
+    "mf_cnn_get_grads": (_I, [_P, _P, _I]),
+    "mf_cnn_forward": (_I, [_P, _P, _I, _I, _I, _P]),
+    "mf_cnn_infer": (_I, [_P, _P, _I, _I, _I, _P]),
+    "mf_cnn_zero_grad": (_I, [_P]),
+    "mf_cnn_backward": (_I, [_P, _P, _P]),
+    "mf_cnn_mse": (_I, [_P, _P, _P, _P, _I64, ctypes.POINTER(ctypes.c_double)]),
+    "mf_cnn_adam_step": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+}
+
 _lib = None
 
 
@@ -66,40 +106,9 @@ def load(path: str = LIBPATH):
     if not os.path.exists(path):
         raise ImportError(f"libmf.so not built ({path}); run __graft_entry__.build()")
     lib = ctypes.CDLL(path)
-    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
-    sig = {
-        "mf_default_opts": (None, [ctypes.POINTER(mf_opts)]),
-        "mf_create_grid": (I, [ctypes.POINTER(P), I, P, I, P, P]),
-        "mf_set_caps": (I, [P, P, P, P, I]),
-        "mf_solve": (I, [P, ctypes.POINTER(mf_opts), ctypes.POINTER(mf_stats)]),
-        "mf_begin": (I, [P, ctypes.POINTER(mf_opts)]),
-        "mf_sweep": (I, [P, ctypes.POINTER(ctypes.c_int32)]),
-        "mf_finish": (I, [P]),
-        "mf_get_cut": (I, [P, P, I, I]),
-        "mf_flow_value": (I, [P, ctypes.POINTER(I64)]),
-        "mf_get_residual": (I, [P, P, P, P, I]),
-        "mf_get_labels": (I, [P, P, ctypes.POINTER(ctypes.c_int32), I]),
-        "mf_destroy": (I, [P]),
-        "mf_last_error": (ctypes.c_char_p, [P]),
-        "mf_min_cut_2d_noalloc": (I, [P, I, P, P, P, P, P, P]),
-        "mf_solve_batch": (I, [P, I, ctypes.POINTER(mf_opts), ctypes.POINTER(mf_stats)]),
-        "mf_warm_features": (I, [P, P]),
-        "mf_warm_targets": (I, [P, P]),
-        "mf_warm_start": (I, [P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
-        "mf_cnn_create": (I, [ctypes.POINTER(P), I, I, ctypes.c_uint64, P]),
-        "mf_cnn_destroy": (I, [P]),
-        "mf_cnn_last_error": (ctypes.c_char_p, [P]),
-        "mf_cnn_num_params": (I64, [P]),
-        "mf_cnn_get_params": (I, [P, P, I]),
-        "mf_cnn_set_params": (I, [P, P, I]),
-        "mf_cnn_get_grads": (I, [P, P, I]),
-        "mf_cnn_forward": (I, [P, P, I, I, I, P]),
-        "mf_cnn_zero_grad": (I, [P]),
-        "mf_cnn_backward": (I, [P, P, P]),
-        "mf_cnn_mse": (I, [P, P, P, P, I64, ctypes.POINTER(ctypes.c_double)]),
-        "mf_cnn_adam_step": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
-    }
-    for name, (res, args) in sig.items():
+    if set(SIGNATURES) != set(EXPORTS):
+        raise ImportError("binding signatures and exported names differ")
+    for name, (res, args) in SIGNATURES.items():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
@@ -113,6 +122,25 @@ def default_opts(**kw) -> mf_opts:
     for k, v in kw.items():
         setattr(o, k, int(v))
     return o
+
+
+_CUDA_STREAM_LEGACY = 1  # the cudaStream_t value of the legacy default stream
+
+
+def _stream_arg(stream):
+    """cudaStream_t for the library.  An explicit stream (torch stream or raw
+    handle) is used as given; with none, torch's current stream when torch's
+    CUDA is in use, so that library calls and torch kernels on the caller's
+    stream stay ordered; otherwise NULL (the library's own stream).  torch's
+    default stream has handle 0, which the library would read as NULL, so it
+    is passed as the legacy-stream handle instead."""
+    if stream is None:
+        torch = sys.modules.get("torch")
+        if torch is None or not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    h = stream if isinstance(stream, int) else stream.cuda_stream
+    return h if h else _CUDA_STREAM_LEGACY
 
 
 def _ptr(a):
@@ -139,7 +167,7 @@ def min_cut_2d_noalloc(dims, connectivity, res, tres, exc, smin, smax, stream=No
         if not dev:
             raise ValueError("mf_min_cut_2d_noalloc takes device buffers")
         ptrs.append(p)
-    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    s = _stream_arg(stream)
     st = lib.mf_min_cut_2d_noalloc(d, int(connectivity), *ptrs, s)
     if st != MF_OK:
         raise MFError(st, lib.mf_last_error(None).decode())
@@ -170,9 +198,7 @@ class Grid:
         self.H = connectivity // 2
         d = (ctypes.c_int64 * 3)(*dims)
         t = None if tile is None else (ctypes.c_int32 * 3)(*(tuple(tile) + (1,) * (3 - len(tile))))
-        s = None
-        if stream is not None:
-            s = stream if isinstance(stream, int) else stream.cuda_stream
+        s = _stream_arg(stream)
         h = ctypes.c_void_p()
         st = lib.mf_create_grid(ctypes.byref(h), self.ndim, d, connectivity, t, s)
         if st != MF_OK:
@@ -269,6 +295,12 @@ class Grid:
             self._check(st)
         return st, r.value
 
+    def certify(self):
+        """(certified, cut capacity of S_min, violations) of the last solve."""
+        cut, bad, ok = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        self._check(self._lib.mf_certify(self._h, ctypes.byref(cut), ctypes.byref(bad), ctypes.byref(ok)))
+        return bool(ok.value), cut.value, bad.value
+
     def get_labels(self):
         lab = np.empty(self.n, dtype=np.int32)
         dinf = ctypes.c_int32()
@@ -282,7 +314,7 @@ class CNN:
     def __init__(self, channels=6, seed=0, stream=None):
         lib = load()
         h = ctypes.c_void_p()
-        s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        s = _stream_arg(stream)
         st = lib.mf_cnn_create(ctypes.byref(h), channels, channels, ctypes.c_uint64(seed), s)
         if st != MF_OK:
             raise MFError(st, lib.mf_last_error(None).decode())
@@ -324,6 +356,10 @@ class CNN:
     def forward(self, x, y):
         N, C, H, W = x.shape
         self._check(self._lib.mf_cnn_forward(self._h, x.data_ptr(), N, H, W, y.data_ptr()))
+
+    def infer(self, x, y):
+        N, C, H, W = x.shape
+        self._check(self._lib.mf_cnn_infer(self._h, x.data_ptr(), N, H, W, y.data_ptr()))
 
     def zero_grad(self):
         self._check(self._lib.mf_cnn_zero_grad(self._h))

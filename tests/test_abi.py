@@ -81,3 +81,8 @@ def test_null_handle_calls(lib):
     assert lib.mf_set_caps(None, None, None, None, 0) == mf.MF_EINVAL
     v = ctypes.c_int64()
     assert lib.mf_flow_value(None, ctypes.byref(v)) == mf.MF_EINVAL
+
+
+def test_every_export_has_a_ctypes_signature():
+    # a call without argtypes would pass 64-bit device pointers as C int
+    assert set(mf.SIGNATURES) == set(mf.EXPORTS)

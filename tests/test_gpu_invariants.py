@@ -101,3 +101,29 @@ def test_sweep_invariants(conn, dims, tile, partial, variant, glr):
         ref = oracle.solve_instance(inst)
         assert g.flow_value() == ref["flow"]
         np.testing.assert_array_equal(g.get_cut(0), ref["smin"])
+
+
+@pytest.mark.parametrize("make", [
+    lambda: grids.segmentation_2d(300, 170, 4, conn=4, hard_seed_frac=0.02),
+    lambda: grids.segmentation_2d(257, 190, 5, conn=8, hard_seed_frac=0.02),
+    lambda: grids.volume_3d(40, 33, 29, 6),
+])
+def test_certificate_agrees_with_oracle(make):
+    inst = make()
+    ref = oracle.solve_instance(inst)
+    with Grid(inst.dims, inst.conn) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        g.solve()
+        ok, cut, bad = g.certify()
+        smin = g.get_cut(0)
+    assert ok and bad == 0
+    assert cut == ref["flow"]
+    assert cut == oracle.cut_cost(inst.dims, inst.conn, inst.cs, inst.ct, inst.nlink, smin)
+
+
+def test_certify_needs_a_finished_solve():
+    inst = grids.random_grid((20, 20, 1), 4, 1)
+    with Grid(inst.dims, 4) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        with pytest.raises(Exception):
+            g.certify()

@@ -1,6 +1,8 @@
 """Learned warm start on the GPU: the network's kernels against the float64
 oracle, the projection to a preflow, exactness of warm solves, and the gain
 of a trained network over the cold start."""
+import os
+
 import numpy as np
 import pytest
 
@@ -33,6 +35,28 @@ def test_forward_and_gradients_match_oracle(c, shape):
     gref = ocnn.backward(p, x.astype(np.float64), c, dy.astype(np.float64))
     scale = np.abs(gref).max()
     np.testing.assert_allclose(g, gref, rtol=2e-3, atol=2e-4 * scale)
+
+
+@pytest.mark.parametrize("c,shape", [(6, (2, 6, 20, 17)), (10, (1, 10, 33, 40)), (6, (1, 6, 64, 48))])
+def test_tensor_core_inference_matches_oracle(c, shape):
+    net = mf.CNN(channels=c, seed=12)
+    p = net.get_params()
+    rng = np.random.Generator(np.random.PCG64(7))
+    x = rng.standard_normal(shape).astype(np.float32)
+    xt = torch.from_numpy(x).to(DEV)
+    yt = torch.empty_like(xt)
+    net.infer(xt, yt)
+    got = yt.cpu().numpy()
+    ref, _, _ = ocnn.forward(p, x.astype(np.float64), c, bf16_activations=True)
+    # FP32 against float64 sums: a hidden value next to a BF16 rounding
+    # boundary may round to the neighbouring BF16 value (2^-8 relative)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(got, ref, rtol=1e-2, atol=1e-2 * scale)
+    assert np.abs(got - ref).mean() < 1e-3 * scale
+    # and close to the FP32-activation forward
+    yf = torch.empty_like(xt)
+    net.forward(xt, yf)
+    np.testing.assert_allclose(got, yf.cpu().numpy(), rtol=5e-2, atol=3e-2 * scale)
 
 
 def test_adam_reduces_loss_on_fixed_batch():
@@ -117,3 +141,40 @@ def test_projection_trims_a_chain_by_hand():
     res, tres, exc = g.get_residual()
     assert exc.tolist() == [1, 0, 0] and tres.tolist() == [0, 0, 1]
     g.close()
+
+
+WEIGHTS = os.path.join(os.path.dirname(warmstart.__file__), "weights", "warm_seg2d_1024_c4.npy")
+
+
+def test_trained_network_saves_sweeps():
+    # the committed network (trained by `python -m paper_1109_1146_gb300.warmstart
+    # train` on 2,000 certified 1024x1024 solves) against the cold start on the
+    # first 32 held-out seeds: identical exact results, fewer sweeps in total
+    net = warmstart.load_network(WEIGHTS)
+    cold_sw, warm_sw = [], []
+    for seed in range(warmstart.EVAL_SEED0, warmstart.EVAL_SEED0 + 32):
+        inst = grids.config3(seed)
+        with Grid(inst.dims, 4) as g:
+            g.set_caps(inst.cs, inst.ct, inst.nlink)
+            cold = g.solve()
+            flow, smin = g.flow_value(), g.get_cut(0)
+            ws, _, _, used = warmstart.warm_solve(g, net)
+            assert used
+            assert g.flow_value() == flow
+            np.testing.assert_array_equal(g.get_cut(0), smin)
+            assert g.certify()[0]
+        cold_sw.append(cold.sweeps)
+        warm_sw.append(ws.sweeps)
+    print("cold sweeps", sum(cold_sw), "warm sweeps", sum(warm_sw))
+    assert sum(warm_sw) < sum(cold_sw)
+
+
+def test_untrained_network_gives_exact_results():
+    inst = grids.config3(warmstart.EVAL_SEED0 + 77, side=512)
+    ref = oracle.solve_instance(inst)
+    net = mf.CNN(channels=6, seed=99)
+    with Grid(inst.dims, 4) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        warmstart.warm_solve(g, net)
+        assert g.flow_value() == ref["flow"]
+        np.testing.assert_array_equal(g.get_cut(0), ref["smin"])
