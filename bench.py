@@ -74,7 +74,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev_id), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -127,7 +127,7 @@ def committed_traffic():
     committed ncu summary, or None if the kernel source changed since."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "ard_discharge_seg2d_2048_c8.txt")
-    src = os.path.join(ROOT, "paper_1109_1146_gb300", "csrc", "ard_discharge.cu")
+    src = os.path.join(ROOT, "paper_1109_1146_gb300", "csrc", "ard_discharge2d.cu")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         kv = {}
@@ -245,7 +245,7 @@ def run_ours(args):
         "phase_ms": {"discharge": dis_ms / args.steps, "fuse_gap": sum(s.ms_fuse for s in stats) / args.steps,
                      "cut": sum(s.ms_cut for s in stats) / args.steps,
                      "init": sum(s.ms_init for s in stats) / args.steps},
-        "roofline": {"kernel": "ard_discharge_kernel<8,64,64,1,1024>", "bound": "hbm",
+        "roofline": {"kernel": "ard_discharge2d_kernel<8,64,64,512>", "bound": "hbm",
                      "achieved": round(achieved, 2), "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "unit": "GB/s", "frac": round(achieved / peak, 5),
                      "traffic": None if traffic is None else round(traffic),
@@ -372,7 +372,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
