@@ -29,7 +29,6 @@ sys.path.insert(0, ROOT)
 METRIC = "exact-maxflow solve ms + sweeps per instance, learned/batched vs plain; HBM GB/s"
 UNIT = "ms/instance"
 SIDE = 2048
-TILE = (64, 64, 1)
 CONN = 8
 BYTES_PER_VERTEX = (CONN + 3) * 4 * 2  # read + write of cap[8], tcap, exc, lab (int32)
 L2_FLUSH_BYTES = 256 << 20
@@ -38,8 +37,11 @@ REF_SAMPLE_SIDE = 1024
 
 def workload_name(side=SIDE):
     return (f"seg2d {side}x{side} 8-connected, value-noise intensity, cs=|I-80| ct=|I-170|, "
-            f"n-links round(100exp(-dI^2/800)) (diagonals /sqrt2), 5% hard seeds at 1e6, "
-            f"{TILE[0]}x{TILE[1]} regions")
+            f"n-links round(100exp(-dI^2/800)) (diagonals /sqrt2), 5% hard seeds at 1e6")
+
+
+def kernel_name(tile):
+    return f"ard_discharge2d_kernel<{CONN},{tile[0]},{tile[1]},{256 if tile[0] == 32 else 512}>"
 
 
 def make_instance(seed, side=SIDE):
@@ -122,9 +124,10 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def committed_traffic():
+def committed_traffic(tile):
     """DRAM bytes per discharged vertex of the discharge kernel from the
-    committed ncu summary, or None if the kernel source changed since."""
+    committed ncu summary, or None if the kernel source or the tile differs
+    from the ones measured there."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "ard_discharge_seg2d_2048_c8.txt")
     src = os.path.join(ROOT, "paper_1109_1146_gb300", "csrc", "ard_discharge2d.cu")
@@ -135,7 +138,7 @@ def committed_traffic():
             if ln.startswith("bench:"):
                 k, v = ln[len("bench:"):].split("=", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel_sha256_16") != sha:
+        if kv.get("kernel_sha256_16") != sha or kv.get("tile") != "x".join(str(t) for t in tile):
             return None
         return float(kv["dram_bytes_per_discharged_vertex"])
     except Exception:
@@ -146,7 +149,7 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    from paper_1109_1146_gb300 import Grid, default_opts
+    from paper_1109_1146_gb300 import Grid, autotune, default_opts
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -160,9 +163,12 @@ def run_ours(args):
     ct = torch.from_numpy(inst.ct).to(dev)
     nl = torch.from_numpy(inst.nlink).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    g = Grid(inst.dims, CONN, tile=TILE, stream=stream)
+    # tile and schedule from the autotuner (measured solves of this instance, untimed)
+    table = autotune.tune([inst], single=True)
+    tile, sched = autotune.choose(inst, table, single=True)
+    g = Grid(inst.dims, CONN, tile=tile, stream=stream)
     g.set_caps(cs, ct, nl)
-    opts = default_opts()
+    opts = default_opts(**sched)
 
     def barrier():
         if ws > 1:
@@ -228,7 +234,7 @@ def run_ours(args):
     alg_bytes = dis_vertices * BYTES_PER_VERTEX
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (dis_ms * 1e-3) / 1e9 if dis_ms > 0 else 0.0
-    tb = committed_traffic()
+    tb = committed_traffic(tile)
     traffic = None if tb is None else tb * dis_vertices / dis_launches
     solve_bytes = alg_bytes / args.steps
     line = {
@@ -236,7 +242,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": workload_name(), "vertices": inst.n, "directed_arcs": directed_arcs(inst.dims),
-                   "tile": list(TILE), "regions": (SIDE // TILE[0]) ** 2, "seed": "rank",
+                   "tile": list(tile), "schedule": sched, "autotuned": True,
+                   "regions": (SIDE // tile[0]) * (SIDE // tile[1]), "seed": "rank",
                    "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MiB write)",
                    "flow_value": flow},
         "sweeps_per_instance": sweeps,
@@ -245,7 +252,7 @@ def run_ours(args):
         "phase_ms": {"discharge": dis_ms / args.steps, "fuse_gap": sum(s.ms_fuse for s in stats) / args.steps,
                      "cut": sum(s.ms_cut for s in stats) / args.steps,
                      "init": sum(s.ms_init for s in stats) / args.steps},
-        "roofline": {"kernel": "ard_discharge2d_kernel<8,64,64,512>", "bound": "hbm",
+        "roofline": {"kernel": kernel_name(tile), "bound": "hbm",
                      "achieved": round(achieved, 2), "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "unit": "GB/s", "frac": round(achieved / peak, 5),
                      "traffic": None if traffic is None else round(traffic),

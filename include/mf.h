@@ -104,7 +104,7 @@ void mf_default_opts(mf_opts *opts);
  *   tile          region shape {tx, ty, tz}: the fixed partition of V into
  *                 regions R_k of Sec. 3 is the tiling of the grid by this
  *                 shape (edge tiles may be ragged).  Supported: 2D 64x64 and
- *                 32x32, 3D 16x16x16 and 8x8x8; NULL or {0,0,0} picks 64x64
+ *                 32x32, 3D 16x16x16 and 8x8x8; NULL or {0,0,0} picks 32x32
  *                 (2D) / 16^3 (3D);
  *   cuda_stream   cudaStream_t to order all work on, or NULL for a stream
  *                 owned by the handle (non-blocking: device buffers that

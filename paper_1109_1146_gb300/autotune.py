@@ -1,10 +1,12 @@
-"""Autotuner for the batched solve: region tile shape and sweep schedule per
-(connectivity, size class).
+"""Autotuner: region tile shape and sweep schedule per (connectivity, size
+class), for batched solves and for single solves.
 
 For every class present in a list of instances it solves one representative
 instance (real data from the list) with each candidate configuration through
 the C ABI, keeps the fastest by the library's own device timing, and caches
-the choice in a JSON file so later batches reuse it.
+the choice in a JSON file so later runs reuse it.  Batched solves run no
+global relabel, so their candidates vary the tile and partial discharges;
+single solves also vary the global-relabel period (2D).
 """
 from __future__ import annotations
 
@@ -25,6 +27,18 @@ CANDIDATES = {
 }
 
 
+# global-relabel periods tried for single 2D solves (0 = never)
+GLR_PERIODS = (0, 4, 8)
+
+
+def candidates(conn: int, single: bool):
+    """(tile, opts kwargs) candidates of one connectivity."""
+    base = CANDIDATES[conn]
+    if not single or conn == 6:
+        return [(t, dict(kw, global_relabel_period=0)) for t, kw in base]
+    return [(t, dict(kw, global_relabel_period=p)) for t, kw in base for p in GLR_PERIODS]
+
+
 def size_class(dims) -> int:
     """Half-octave bucket of the number of vertices."""
     n = 1
@@ -33,37 +47,38 @@ def size_class(dims) -> int:
     return int(round(2 * math.log2(n)))
 
 
-def key_of(inst) -> str:
-    return f"c{inst.conn}_s{size_class(inst.dims)}"
+def key_of(inst, single: bool = False) -> str:
+    return f"{'single_' if single else ''}c{inst.conn}_s{size_class(inst.dims)}"
 
 
 def _time_config(inst, tile, kw, reps):
     best = float("inf")
     with Grid(inst.dims, inst.conn, tile=tile) as g:
         g.set_caps(inst.cs, inst.ct, inst.nlink)
-        opts = default_opts(global_relabel_period=0, **kw)
+        opts = default_opts(**kw)
         for _ in range(reps + 1):
             st = g.solve(opts)
             best = min(best, st.ms_total)
     return best
 
 
-def tune(instances, cache_path: str | None = None, reps: int = 2):
+def tune(instances, cache_path: str | None = None, reps: int = 2, single: bool = False):
     """Return {class key: {"tile": [...], "opts": {...}, "ms": t}} for the
-    classes of `instances` (objects with dims, conn, cs, ct, nlink)."""
+    classes of `instances` (objects with dims, conn, cs, ct, nlink); with
+    `single`, for single solves (keys prefixed "single_")."""
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
             cache = json.load(f)
     reps_by_key = {}
     for inst in instances:
-        reps_by_key.setdefault(key_of(inst), inst)
+        reps_by_key.setdefault(key_of(inst, single), inst)
     changed = False
     for k, inst in reps_by_key.items():
         if k in cache:
             continue
         trials = []
-        for tile, kw in CANDIDATES[inst.conn]:
+        for tile, kw in candidates(inst.conn, single):
             trials.append((_time_config(inst, tile, kw, reps), tile, kw))
         t, tile, kw = min(trials, key=lambda x: x[0])
         cache[k] = {"tile": list(tile), "opts": kw, "ms": t}
@@ -75,9 +90,9 @@ def tune(instances, cache_path: str | None = None, reps: int = 2):
     return cache
 
 
-def choose(inst, table):
+def choose(inst, table, single: bool = False):
     """(tile, opts kwargs) chosen for one instance."""
-    e = table[key_of(inst)]
+    e = table[key_of(inst, single)]
     return tuple(e["tile"]), dict(e["opts"])
 
 

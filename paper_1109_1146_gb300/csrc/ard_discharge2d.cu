@@ -53,7 +53,11 @@ struct Cfg2D {
     static constexpr int HW = TX / 32;                  // 32-bit halves per row
     static constexpr int HL = 2 * (TX + 2) + 2 * TY;    // halo cells (B^R plus unused corners)
     static constexpr int PER = 2 * TX + 2 * TY;         // perimeter slots: top, bottom, left, right
-    static constexpr int LCAP = 64;                     // BFS layers kept as masks
+    // 8-connected 32x32 tiles: four blocks per SM (64 registers, 24 layers kept
+    // as masks so that four fit in shared memory; deeper layers use label tags)
+    static constexpr bool DENSE = CONN == 8 && TX == 32;
+    static constexpr int LCAP = DENSE ? 24 : 64;       // BFS layers kept as masks
+    static constexpr int MINB = DENSE ? 4 : 1;         // resident blocks per SM the registers must allow
     static constexpr size_t smem = (size_t)(N + 3) * V * 4                  // cap, tcap, exc, lab
                                    + (size_t)(N + 4) * TY * 8               // R[N], T, E, inc, vis
                                    + (size_t)(LCAP + 1) * TY * 8            // BFS layers 1..LCAP
@@ -620,7 +624,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
 
 // one block per region of one grid; regions without active vertices are skipped (Sec. 5.3)
 template <int CONN, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, 1) ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
+__global__ void __launch_bounds__(NT, (Cfg2D<CONN, TX, TY, NT>::MINB)) ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     const int r = blockIdx.x;
     if (!st.active[r]) return;
     discharge2d_region<CONN, TX, TY, NT>(g, st, sa, r);
@@ -628,7 +632,7 @@ __global__ void __launch_bounds__(NT, 1) ard_discharge2d_kernel(const Geom g, co
 
 // persistent blocks over a work queue of (instance, region) items of a batch
 template <int CONN, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, (Cfg2D<CONN, TX, TY, NT>::MINB))
 ard_discharge2d_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ items, const int *count,
                              int *head, const SweepArgs sa) {
     __shared__ int s_it;

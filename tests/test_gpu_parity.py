@@ -22,7 +22,7 @@ def _bound_ok(inst, got, tile):
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_config0_workload(seed):
     inst = grids.config0(seed)
-    got = gpu_solve(inst)
+    got = gpu_solve(inst, tile=(64, 64, 1))
     assert_parity(inst, got)
     _bound_ok(inst, got, (64, 64, 1))
 
