@@ -280,6 +280,121 @@ __device__ __forceinline__ void post_region(const Geom &g, const DevState &st, c
 template <int CONN>
 __global__ void post_kernel(const Geom g, const DevState st) { post_region<CONN>(g, st, blockIdx.x); }
 
+// ---- 2D fusion and activity over perimeter items -----------------------------
+// One thread per (region, perimeter slot): only tile perimeters hold boundary
+// vertices, so the 2D sweep kernels walk 2 tx + 2 (ty - 2) slots per region
+// instead of whole tiles (a warp covers one region's perimeter, and its lanes
+// share the region-touched test through the cache).
+__device__ __forceinline__ void perimeter_xy(int p, int tx, int ty, int &lx, int &ly) {
+    if (p < tx) { lx = p; ly = 0; }
+    else if (p < 2 * tx) { lx = p - tx; ly = ty - 1; }
+    else if (p < 2 * tx + ty - 2) { lx = 0; ly = 1 + p - 2 * tx; }
+    else { lx = tx - 1; ly = 1 + p - 2 * tx - (ty - 2); }
+}
+
+__device__ __forceinline__ int perimeter_slots(const Geom &g) { return 2 * g.tx + 2 * (g.ty - 2); }
+
+// Algorithm 2's fusion for one boundary vertex u of region r (gather form;
+// see fuse_region); also restarts the activity of a touched region from the
+// excess its discharge left inside the tile.
+template <int CONN>
+__global__ void fuse2d_kernel(const Geom g, const DevState st) {
+    const int P = perimeter_slots(g);
+    const long long items = (long long)g.nreg * P;
+    const size_t n = (size_t)g.n;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < items; k += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(k / P), p = (int)(k % P);
+        if (!region_touched<CONN>(g, st, r)) continue;
+        if (p == 0) st.active[r] = st.left_active[r];
+        int lx, ly;
+        perimeter_xy(p, g.tx, g.ty, lx, ly);
+        const int x = (r % g.RX) * g.tx + lx, y = (r / g.RX) * g.ty + ly;
+        if (x >= g.X || y >= g.Y) continue;
+        const size_t u = (size_t)y * g.X + x;
+        const bool discr = st.disc[r];
+        bool boundary = false;
+        int back_total = 0, du = -1;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d);
+            if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y) continue;
+            const int rw = (wy >> g.sy) * g.RX + (wx >> g.sx);
+            if (rw == r) continue;
+            if (!boundary) {
+                boundary = true;
+                du = discr ? st.lab_next[u] : st.lab[u];
+            }
+            const size_t w = (size_t)wy * g.X + wx;
+            const bool discw = st.disc[rw];
+            const int dw = discw ? st.lab_next[w] : st.lab[w];
+            const int pu = discr ? st.bout[(size_t)d * n + u] : 0;
+            const int pw = discw ? st.bout[(size_t)(d ^ 1) * n + w] : 0;
+            const int back = (dw <= du + 1 ? 0 : pu) + (du <= dw + 1 ? pw : 0);
+            if (back) {
+                st.cap[(size_t)d * n + u] += back;
+                back_total += back;
+            }
+        }
+        if (!boundary) continue;
+        if (back_total) st.exc[u] += back_total;
+        if (discr) {
+            const int old = st.lab[u];
+            if (old != du) {
+                if (old < g.dinf) atomicSub(&st.hist[hist_bin(old)], 1);
+                if (du < g.dinf) atomicAdd(&st.hist[hist_bin(du)], 1);
+                st.lab[u] = du;
+            }
+        }
+    }
+}
+
+// Activity after the fusion: a touched region is active if its discharge left
+// interior excess or a perimeter vertex has excess below d_inf.  With a gap,
+// first every label g < d < d_inf in the grid becomes d_inf (all vertices).
+template <int CONN>
+__global__ void post2d_kernel(const Geom g, const DevState st) {
+    const int gap = st.ctr[kGap];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (gap == 0) {
+        const int P = perimeter_slots(g);
+        const long long items = (long long)g.nreg * P;
+        for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < items; k += stride) {
+            const int r = (int)(k / P), p = (int)(k % P);
+            int lx, ly;
+            perimeter_xy(p, g.tx, g.ty, lx, ly);
+            const int x = (r % g.RX) * g.tx + lx, y = (r / g.RX) * g.ty + ly;
+            if (x >= g.X || y >= g.Y) continue;
+            const size_t u = (size_t)y * g.X + x;
+            if (st.exc[u] > 0 && st.lab[u] < g.dinf && region_touched<CONN>(g, st, r)) st.active[r] = 1;
+        }
+    } else {
+        for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < (long long)g.n; v += stride) {
+            const int x = (int)(v % g.X), y = (int)(v / g.X);
+            int l = st.lab[v];
+            if (l > gap && l < g.dinf) {
+                l = g.dinf;
+                st.lab[v] = l;
+            }
+            const int lx = x & (g.tx - 1), ly = y & (g.ty - 1);
+            if (lx != 0 && lx != g.tx - 1 && ly != 0 && ly != g.ty - 1) continue;
+            const int r = (y >> g.sy) * g.RX + (x >> g.sx);
+            if (l < g.dinf && st.exc[v] > 0 && region_touched<CONN>(g, st, r)) st.active[r] = 1;
+        }
+    }
+}
+
+// count the active regions for the host, reset the per-sweep flags
+__global__ void finish_flags_kernel(const DevState st, int nreg) {
+    int c = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) {
+        c += st.active[r] != 0;
+        st.disc[r] = 0;
+        st.left_active[r] = 0;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
+}
+
 // ---- batched sweep kernels: one block per (instance, region) of the batch table
 __global__ void batch_reset_kernel(const Inst *insts, const unsigned char *done, int count) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
@@ -443,6 +558,15 @@ static cudaError_t launch_validate(mf_grid *h, int *flags) {
 }
 template <int CONN>
 static cudaError_t launch_fuse_post(mf_grid *h, bool gap_on) {
+    if (CONN != 6) {
+        const long long items = (long long)h->g.nreg * (2 * h->g.tx + 2 * (h->g.ty - 2));
+        const int fb = (int)std::min<long long>((items + 255) / 256, 152 * 8);
+        fuse2d_kernel<CONN><<<fb, 256, 0, h->stream>>>(h->g, h->st);
+        if (gap_on) gap_find_kernel<<<1, 1024, 0, h->stream>>>(h->st);
+        post2d_kernel<CONN><<<152 * 8, 256, 0, h->stream>>>(h->g, h->st);
+        finish_flags_kernel<<<(h->g.nreg + 255) / 256, 256, 0, h->stream>>>(h->st, h->g.nreg);
+        return cudaGetLastError();
+    }
     fuse_kernel<CONN><<<h->g.nreg, 256, 0, h->stream>>>(h->g, h->st);
     if (gap_on) gap_find_kernel<<<1, 1024, 0, h->stream>>>(h->st);
     post_kernel<CONN><<<h->g.nreg, 256, 0, h->stream>>>(h->g, h->st);
