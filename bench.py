@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -164,7 +165,8 @@ def run_ours(args):
     nl = torch.from_numpy(inst.nlink).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     # tile and schedule from the autotuner (measured solves of this instance, untimed)
-    table = autotune.tune([inst], single=True)
+    table = autotune.tune([inst], single=True,
+                          cache_path=os.path.join(tempfile.gettempdir(), f"mf_autotune_single_{rank}.json"))
     tile, sched = autotune.choose(inst, table, single=True)
     g = Grid(inst.dims, CONN, tile=tile, stream=stream)
     g.set_caps(cs, ct, nl)
