@@ -69,7 +69,9 @@ typedef struct {
     int32_t max_rounds;            /* cap on Augment rounds per stage inside one discharge; 0 = default 65536 */
     int32_t kernel_variant;        /* 0: bit-parallel 2D discharge where available (default); 1: generic kernel */
     int32_t warm_start;            /* 1: start from the preflow of the last mf_warm_start instead of Init's zero flow */
-    int32_t reserved[9];
+    int32_t graph_loop;            /* 1: mf_solve runs the sweeps as one CUDA graph with a device-side while loop
+                                      (per-phase times ms_discharge / ms_fuse are then not measured); default 0 */
+    int32_t reserved[8];
 } mf_opts;
 
 /* Statistics of the last mf_solve (all optional reading). */

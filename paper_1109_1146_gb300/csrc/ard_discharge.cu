@@ -145,7 +145,7 @@ __device__ __forceinline__ void discharge_region(const Geom &g, const DevState &
         return -block_reduce_max(-best, s_red, ph);  // best <= INT_MAX, so -best > INT_MIN
     };
 
-    const int klimit = sa.partial ? sa.sweep : INT_MAX;
+    const int klimit = sa.partial ? (sa.sweep_dev ? *sa.sweep_dev : sa.sweep) : INT_MAX;
     long long flow_acc = 0;
     int rounds = 0, stages = 0;
     bool err = false;

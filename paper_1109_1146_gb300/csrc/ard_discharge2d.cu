@@ -330,7 +330,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
         }
     };
 
-    const int klimit = sa.partial ? sa.sweep : INT_MAX;
+    const int klimit = sa.partial ? (sa.sweep_dev ? *sa.sweep_dev : sa.sweep) : INT_MAX;
     long long flow_acc = 0;
     int rounds = 0, stages = 0, epoch = 0;
     bool err = false, any_aug = false;

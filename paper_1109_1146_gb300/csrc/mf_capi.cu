@@ -31,6 +31,13 @@ struct mf_grid {
     bool warm_ready = false;
     int warm_rounds = 0;
     int begin_active = -1;                            // active regions after mf_begin's relabel, -1: unknown
+    // CUDA graph of the sweep loop (opts.graph_loop)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;                // private stream the loop body is captured on
+    int *loopctl = nullptr;                           // device loop state, see loop_ctl_kernel
+    int *h_loop = nullptr;                            // pinned mirror
+    int graph_key[5] = {-1, -1, -1, -1, -1};          // options baked into the graph
     Counters64 *c64 = nullptr;
     int *h_ctr = nullptr;                             // pinned mirror of st.ctr
     long long boundary = 0;
@@ -395,6 +402,28 @@ __global__ void finish_flags_kernel(const DevState st, int nreg) {
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
 }
 
+// ---- device-side sweep loop (CUDA graph with a conditional while node) ------
+// loopctl: [0] sweeps done (the next sweep's index), [1] sweeps that found a
+// gap, [2] sweep cap, [3] global-relabel period P (0: none), [4] active regions
+// after the last sweep, [5] error flag of the last sweep.  The loop continues
+// while no error was raised, some region is active, the cap is not reached
+// and the sweep count is not a multiple of P (the host then runs the global
+// relabel and relaunches the graph).
+enum { kLoopSweep = 0, kLoopGaps, kLoopCap, kLoopPeriod, kLoopActive, kLoopError, kLoopWords = 8 };
+
+__global__ void loop_ctl_kernel(const int *ctr, int *lc, cudaGraphConditionalHandle handle) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int active = ctr[kActiveRegions], err = ctr[kError], gap = ctr[kGap];
+    const int s = lc[kLoopSweep] + 1;
+    lc[kLoopSweep] = s;
+    if (gap > 0) lc[kLoopGaps] += 1;
+    lc[kLoopActive] = active;
+    lc[kLoopError] = err;
+    const int P = lc[kLoopPeriod];
+    const bool cont = !err && active > 0 && s < lc[kLoopCap] && !(P > 0 && s % P == 0);
+    cudaGraphSetConditional(handle, cont ? 1u : 0u);
+}
+
 // ---- batched sweep kernels: one block per (instance, region) of the batch table
 __global__ void batch_reset_kernel(const Inst *insts, const unsigned char *done, int count) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
@@ -557,20 +586,20 @@ static cudaError_t launch_validate(mf_grid *h, int *flags) {
     return cudaGetLastError();
 }
 template <int CONN>
-static cudaError_t launch_fuse_post(mf_grid *h, bool gap_on) {
+static cudaError_t launch_fuse_post(mf_grid *h, bool gap_on, cudaStream_t st) {
     if (CONN != 6) {
         const long long items = (long long)h->g.nreg * (2 * h->g.tx + 2 * (h->g.ty - 2));
         const int fb = (int)std::min<long long>((items + 255) / 256, 152 * 8);
-        fuse2d_kernel<CONN><<<fb, 256, 0, h->stream>>>(h->g, h->st);
-        if (gap_on) gap_find_kernel<<<1, 1024, 0, h->stream>>>(h->st);
-        post2d_kernel<CONN><<<152 * 8, 256, 0, h->stream>>>(h->g, h->st);
-        finish_flags_kernel<<<(h->g.nreg + 255) / 256, 256, 0, h->stream>>>(h->st, h->g.nreg);
+        fuse2d_kernel<CONN><<<fb, 256, 0, st>>>(h->g, h->st);
+        if (gap_on) gap_find_kernel<<<1, 1024, 0, st>>>(h->st);
+        post2d_kernel<CONN><<<152 * 8, 256, 0, st>>>(h->g, h->st);
+        finish_flags_kernel<<<(h->g.nreg + 255) / 256, 256, 0, st>>>(h->st, h->g.nreg);
         return cudaGetLastError();
     }
-    fuse_kernel<CONN><<<h->g.nreg, 256, 0, h->stream>>>(h->g, h->st);
-    if (gap_on) gap_find_kernel<<<1, 1024, 0, h->stream>>>(h->st);
-    post_kernel<CONN><<<h->g.nreg, 256, 0, h->stream>>>(h->g, h->st);
-    clear_flags_kernel<<<(h->g.nreg + 255) / 256, 256, 0, h->stream>>>(h->st, h->g.nreg);
+    fuse_kernel<CONN><<<h->g.nreg, 256, 0, st>>>(h->g, h->st);
+    if (gap_on) gap_find_kernel<<<1, 1024, 0, st>>>(h->st);
+    post_kernel<CONN><<<h->g.nreg, 256, 0, st>>>(h->g, h->st);
+    clear_flags_kernel<<<(h->g.nreg + 255) / 256, 256, 0, st>>>(h->st, h->g.nreg);
     return cudaGetLastError();
 }
 template <int CONN>
@@ -672,7 +701,21 @@ void mf_default_opts(mf_opts *o) {
 
 const char *mf_last_error(const mf_grid *g) { return g ? g->err.c_str() : g_static_err.c_str(); }
 
+static void free_graph(mf_grid *h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+}
+
 static void free_all(mf_grid *h) {
+    free_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->loopctl) cudaFree(h->loopctl);
+    if (h->h_loop) cudaFreeHost(h->h_loop);
+    h->cap_stream = nullptr;
+    h->loopctl = nullptr;
+    h->h_loop = nullptr;
     void *ptrs[] = {h->cs, h->ct, h->nl, h->st.cap, h->st.tcap, h->st.exc, h->st.lab, h->st.lab_next,
                     h->st.bout, h->st.active, h->st.disc, h->st.left_active, h->st.flow_t, h->st.flow0,
                     h->st.hist, h->st.ctr, h->smin, h->tset, h->c64, h->cut_scratch, h->warmF, h->warmFt,
@@ -845,7 +888,7 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
 }
 
 static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
-    SweepArgs sa;
+    SweepArgs sa{};
     sa.sweep = g->sweep;
     sa.partial = g->opts.partial_discharge;
     sa.max_rounds = g->opts.max_rounds;
@@ -855,7 +898,7 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     CK(cudaEventRecord(g->ev[4], g->stream));
     CK(launch_discharge(g->conn, g->g, g->st, sa, g->stream));
     CK(cudaEventRecord(g->ev[5], g->stream));
-    CK(DISPATCH(g->conn, launch_fuse_post, g, g->opts.global_gap != 0));
+    CK(DISPATCH(g->conn, launch_fuse_post, g, g->opts.global_gap != 0, g->stream));
     CK(cudaEventRecord(g->ev[6], g->stream));
     g->launches += g->opts.global_gap ? 5 : 4;
     CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
@@ -941,6 +984,99 @@ mf_status mf_finish(mf_grid *g) {
     return MF_OK;
 }
 
+// Capture one sweep (counter reset, discharge, fusion, gap, activity, loop
+// control) as the body of a while node, on a private stream (the caller's
+// may be the legacy default stream, which cannot be captured).  Rebuilt when
+// an option baked into the kernels' arguments changes.
+static mf_status build_graph(mf_grid *g) {
+    const int key[5] = {g->opts.partial_discharge, g->opts.max_rounds, g->opts.kernel_variant,
+                        g->opts.global_gap != 0, 1};
+    if (g->graph_exec && memcmp(key, g->graph_key, sizeof(key)) == 0) return MF_OK;
+    free_graph(g);
+    if (!g->cap_stream) CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    if (!g->loopctl) {
+        CK(cudaMalloc(&g->loopctl, kLoopWords * 4));
+        CK(cudaMallocHost((void **)&g->h_loop, kLoopWords * 4));
+    }
+    CK(cudaGraphCreate(&g->graph, 0));
+    cudaGraphConditionalHandle handle;
+    CK(cudaGraphConditionalHandleCreate(&handle, g->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = handle;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    SweepArgs sa{};
+    sa.sweep_dev = &g->loopctl[kLoopSweep];
+    sa.partial = g->opts.partial_discharge;
+    sa.max_rounds = g->opts.max_rounds;
+    sa.variant = g->opts.kernel_variant;
+    sa.c64 = g->c64;
+    cudaStream_t cs = g->cap_stream;
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = cudaMemsetAsync(g->st.ctr, 0, 4 * (kGap + 1), cs);
+    if (e == cudaSuccess) e = launch_discharge(g->conn, g->g, g->st, sa, cs);
+    if (e == cudaSuccess) e = DISPATCH(g->conn, launch_fuse_post, g, g->opts.global_gap != 0, cs);
+    if (e == cudaSuccess) {
+        loop_ctl_kernel<<<1, 32, 0, cs>>>(g->st.ctr, g->loopctl, handle);
+        e = cudaGetLastError();
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        free_graph(g);
+        return fail(g, MF_ECUDA, std::string("sweep graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    CK(cudaGraphInstantiate(&g->graph_exec, g->graph, 0));
+    memcpy(g->graph_key, key, sizeof(key));
+    return MF_OK;
+}
+
+// The sweep loop on the device: the graph runs sweeps until no region is
+// active, an error, the cap, or a multiple of the global-relabel period (the
+// host then relabels and relaunches).  One host synchronisation per launch.
+static mf_status run_graph_loop(mf_grid *g, long long cap) {
+    mf_status s = build_graph(g);
+    if (s != MF_OK) return s;
+    const int P = (g->opts.global_relabel_period > 0 && g->ndim == 2 && glr2d_supported(g->g))
+                      ? g->opts.global_relabel_period : 0;
+    int init[kLoopWords] = {0};
+    init[kLoopSweep] = g->sweep;
+    init[kLoopCap] = (int)std::min<long long>(cap, INT_MAX);
+    init[kLoopPeriod] = P;
+    memcpy(g->h_loop, init, sizeof(init));
+    CK(cudaMemcpyAsync(g->loopctl, g->h_loop, kLoopWords * 4, cudaMemcpyHostToDevice, g->stream));
+    const int per_sweep = g->opts.global_gap ? 6 : 5;
+    for (;;) {
+        const int before = g->sweep;
+        CK(cudaGraphLaunch(g->graph_exec, g->stream));
+        CK(cudaMemcpyAsync(g->h_loop, g->loopctl, kLoopWords * 4, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        g->sweep = g->h_loop[kLoopSweep];
+        g->launches += (g->sweep - before) * per_sweep;
+        g->stats.sweeps = g->sweep;
+        g->stats.gaps = g->h_loop[kLoopGaps];
+        if (g->h_loop[kLoopError]) return fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
+        int active = g->h_loop[kLoopActive];
+        if (active == 0) return MF_OK;
+        if (g->sweep >= cap) return fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left");
+        if (P > 0 && g->sweep % P == 0) {
+            int levels = 0;
+            CK(glr2d(g->conn, g->g, g->st, g->cut_scratch, g->h_ctr, &levels, g->stream));
+            CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            active = g->h_ctr[kActiveRegions];
+            g->stats.global_relabels++;
+            g->stats.relabel_levels += levels;
+            g->launches += 4 + levels;
+            if (active == 0) return MF_OK;
+        }
+    }
+}
+
 mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     CK(cudaEventRecord(g->ev[0], g->stream));
@@ -950,7 +1086,8 @@ mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats) {
     long long cap = g->opts.max_sweeps > 0 ? g->opts.max_sweeps
                                             : std::min<long long>(2 * g->boundary * g->boundary + 1, 1ll << 30);
     mf_status rs = MF_OK;
-    while (g->begin_active != 0) {  // 0: the initial labels already show a maximum preflow
+    if (g->opts.graph_loop && g->begin_active != 0) rs = run_graph_loop(g, cap);
+    else while (g->begin_active != 0) {  // 0: the initial labels already show a maximum preflow
         int32_t act = 0;
         rs = run_sweep(g, &act);
         if (rs != MF_OK) break;

@@ -73,6 +73,7 @@ struct Counters64 {
 
 struct SweepArgs {
     int sweep;          // 0-based sweep index
+    const int *sweep_dev;  // if set, the sweep index is read here (sweeps inside a CUDA graph)
     int partial;        // partial discharges (Sec. 6.2)
     int max_rounds;     // Augment round cap per stage
     int variant;        // 0: bit-parallel 2D kernel where available, 1: generic kernel

@@ -34,7 +34,7 @@ class mf_opts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("partial_discharge", ctypes.c_int32),
                 ("global_gap", ctypes.c_int32), ("global_relabel_period", ctypes.c_int32),
                 ("max_rounds", ctypes.c_int32), ("kernel_variant", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("warm_start", ctypes.c_int32), ("graph_loop", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 class mf_stats(ctypes.Structure):
