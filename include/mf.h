@@ -67,7 +67,7 @@ typedef struct {
     int32_t global_relabel_period; /* P > 0: exact region-distance relabel after every P-th sweep (2D grids,
                                       Sec. 4.1 distance); 0 = off; default 4 */
     int32_t max_rounds;            /* cap on Augment rounds per stage inside one discharge; 0 = default 65536 */
-    int32_t kernel_variant;        /* 0: bit-parallel 2D discharge where available (default); 1: generic kernel */
+    int32_t kernel_variant;        /* 0: bit-parallel 2D / 3D discharge where the tile allows (default); 1: generic kernel */
     int32_t warm_start;            /* 1: start from the preflow of the last mf_warm_start instead of Init's zero flow */
     int32_t graph_loop;            /* 1: mf_solve runs the sweeps as one CUDA graph with a device-side while loop
                                       (per-phase times ms_discharge / ms_fuse are then not measured); default 0 */
@@ -106,8 +106,9 @@ void mf_default_opts(mf_opts *opts);
  *   tile          region shape {tx, ty, tz}: the fixed partition of V into
  *                 regions R_k of Sec. 3 is the tiling of the grid by this
  *                 shape (edge tiles may be ragged).  Supported: 2D 64x64 and
- *                 32x32, 3D 16x16x16 and 8x8x8; NULL or {0,0,0} picks 32x32
- *                 (2D) / 16^3 (3D);
+ *                 32x32, 3D 32x16x8, 32x8x8 (bit-parallel discharge),
+ *                 16x16x16 and 8x8x8; NULL or {0,0,0} picks 32x32 (2D) /
+ *                 32x8x8 (3D);
  *   cuda_stream   cudaStream_t to order all work on, or NULL for a stream
  *                 owned by the handle (non-blocking: device buffers that
  *                 other streams produce or consume must then be ordered by

@@ -415,7 +415,9 @@ static cudaError_t launch_one(const Geom &g, const DevState &st, const SweepArgs
     X(4, 32, 32, 1, 256)            \
     X(8, 32, 32, 1, 256)            \
     X(6, 16, 16, 16, 1024)          \
-    X(6, 8, 8, 8, 256)
+    X(6, 8, 8, 8, 256)              \
+    X(6, 32, 16, 8, 1024)           \
+    X(6, 32, 8, 8, 256)
 
 bool discharge_supported(int conn, int tx, int ty, int tz) {
 #define X(c, a, b, z, t) if (conn == c && tx == a && ty == b && tz == z) return true;
@@ -436,6 +438,8 @@ cudaError_t launch_discharge_batch(int conn, int tx, int ty, int tz, int variant
                                    int blocks, cudaStream_t stream) {
     if (variant == 0 && tz == 1 && discharge2d_supported(conn, tx, ty))
         return launch_discharge2d_batch(conn, tx, ty, insts, items, count, head, sa, blocks, stream);
+    if (variant == 0 && conn == 6 && discharge3d_supported(tx, ty, tz))
+        return launch_discharge3d_batch(tx, ty, tz, insts, items, count, head, sa, blocks, stream);
 #define X(c, a, b, z, t) \
     if (conn == c && tx == a && ty == b && tz == z) return launch_batch_one<c, a, b, z, t>(insts, items, count, head, sa, blocks, stream);
     MF_TILES(X)
@@ -447,6 +451,8 @@ cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const 
                              cudaStream_t stream) {
     if (sa.variant == 0 && g.tz == 1 && discharge2d_supported(conn, g.tx, g.ty))
         return launch_discharge2d(conn, g, st, sa, stream);
+    if (sa.variant == 0 && conn == 6 && discharge3d_supported(g.tx, g.ty, g.tz))
+        return launch_discharge3d(g, st, sa, stream);
 #define X(c, a, b, z, t) \
     if (conn == c && g.tx == a && g.ty == b && g.tz == z) return launch_one<c, a, b, z, t>(g, st, sa, stream);
     MF_TILES(X)

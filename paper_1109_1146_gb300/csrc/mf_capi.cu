@@ -742,7 +742,7 @@ mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int con
     long long nll = X * Y * Z;
     if (nll > (1ll << 31) - 1) return fail(nullptr, MF_EINVAL, "more than 2^31-1 vertices");
     int tx = 32, ty = 32, tz = 1;
-    if (ndim == 3) tx = ty = tz = 16;
+    if (ndim == 3) { tx = 32; ty = 8; tz = 8; }
     if (tile && (tile[0] | tile[1] | tile[2])) {
         tx = tile[0];
         ty = tile[1];

@@ -143,5 +143,10 @@ cudaError_t launch_discharge2d_batch(int conn, int tx, int ty, const Inst *insts
                                      cudaStream_t stream);
 cudaError_t launch_discharge2d(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
                                cudaStream_t stream);
+// ard_discharge3d.cu (6-connected, tiles 32x16x8 and 32x8x8)
+bool discharge3d_supported(int tx, int ty, int tz);
+cudaError_t launch_discharge3d(const Geom &g, const DevState &st, const SweepArgs &sa, cudaStream_t stream);
+cudaError_t launch_discharge3d_batch(int tx, int ty, int tz, const Inst *insts, const int2 *items, const int *count,
+                                     int *head, const SweepArgs &sa, int blocks, cudaStream_t stream);
 
 }  // namespace mf

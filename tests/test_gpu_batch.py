@@ -23,6 +23,8 @@ def _batch_instances():
     out.append((grids.random_grid((77, 55, 1), 8, 6, cmax=30, tmax=60, p_zero=0.3), (32, 32, 1)))
     out.append((grids.volume_3d(30, 28, 26, 7), (16, 16, 16)))
     out.append((grids.volume_3d(20, 20, 20, 8), (8, 8, 8)))
+    out.append((grids.volume_3d(50, 30, 17, 9), (32, 16, 8)))
+    out.append((grids.volume_3d(40, 25, 20, 10), (32, 8, 8)))
     out.append((grids.random_grid((5, 1, 1), 4, 9, cmax=10, tmax=20), (64, 64, 1)))
     return out
 

@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
     (lambda: grids.segmentation_2d(230, 190, 3, conn=8, hard_seed_frac=0.05), (32, 32, 1)),
     (lambda: grids.segmentation_2d(300, 170, 4, conn=4, hard_seed_frac=0.02), (64, 64, 1)),
     (lambda: grids.volume_3d(41, 37, 30, 2), (8, 8, 8)),
+    (lambda: grids.volume_3d(70, 37, 30, 2), (32, 16, 8)),
 ])
 @pytest.mark.parametrize("kw", [dict(), dict(partial_discharge=1), dict(global_relabel_period=2),
                                 dict(global_relabel_period=3, partial_discharge=1, global_gap=0)])

@@ -35,6 +35,9 @@ CASES = [
     ((75, 90, 1), 8, (32, 32, 1)),
     ((40, 35, 20), 6, (16, 16, 16)),
     ((21, 19, 13), 6, (8, 8, 8)),
+    ((70, 37, 21), 6, (32, 16, 8)),
+    ((45, 30, 19), 6, (32, 8, 8)),
+    ((96, 48, 24), 6, (32, 16, 8)),
 ]
 
 
@@ -53,7 +56,9 @@ def test_ragged_multi_region(dims, conn, tile, kind):
 
 @pytest.mark.parametrize("dims,conn,tile", [((1, 1, 1), 4, (64, 64, 1)), ((5, 1, 1), 4, (64, 64, 1)),
                                             ((64, 64, 1), 8, (64, 64, 1)), ((16, 16, 16), 6, (16, 16, 16)),
-                                            ((1, 300, 1), 4, (32, 32, 1)), ((3, 3, 40), 6, (8, 8, 8))])
+                                            ((1, 300, 1), 4, (32, 32, 1)), ((3, 3, 40), 6, (8, 8, 8)),
+                                            ((1, 1, 1), 6, (32, 16, 8)), ((33, 1, 9), 6, (32, 8, 8)),
+                                            ((32, 16, 8), 6, (32, 16, 8))])
 def test_degenerate_shapes(dims, conn, tile):
     inst = grids.random_grid(dims, conn, 5, cmax=25, tmax=40)
     got = gpu_solve(inst, tile=tile)
@@ -95,7 +100,9 @@ def test_strong_links_carry_everything():
 
 @pytest.mark.parametrize("conn,dims,t1,t2", [(4, (150, 130, 1), (64, 64, 1), (32, 32, 1)),
                                              (8, (150, 130, 1), (64, 64, 1), (32, 32, 1)),
-                                             (6, (40, 40, 24), (16, 16, 16), (8, 8, 8))])
+                                             (6, (40, 40, 24), (16, 16, 16), (8, 8, 8)),
+                                             (6, (70, 40, 24), (32, 16, 8), (16, 16, 16)),
+                                             (6, (64, 40, 24), (32, 8, 8), (8, 8, 8))])
 def test_result_invariant_under_tile_shape(conn, dims, t1, t2):
     inst = (grids.volume_3d(*dims, seed=4) if conn == 6 else
             grids.segmentation_2d(dims[0], dims[1], 4, conn=conn))
