@@ -101,7 +101,7 @@ __device__ __forceinline__ int deep_tag(int epoch, int L) { return ~((epoch << 1
 
 template <int CONN, int TX, int TY, int NT>
 __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState &st, const SweepArgs &sa,
-                                                   const int r) {
+                                                   const int r, unsigned long long *mbar, unsigned &mphase) {
     using C = Cfg2D<CONN, TX, TY, NT>;
     constexpr int N = C::N, V = C::V, RPL = C::RPL, NW = C::NW, HW = C::HW, LCAP = C::LCAP;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -177,16 +177,18 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
     const bool full = ox + TX <= g.X && oy + TY <= g.Y;
     const bool vec = full && (g.X % 4) == 0;  // every row starts on a 16-byte boundary
     if (vec) {
-        for (int i4 = tid; i4 < V / 4; i4 += NT) {
-            const int i = i4 * 4, lx = i % TX, ly = i / TX;
-            const size_t v = (size_t)(oy + ly) * g.X + ox + lx;
-#pragma unroll
-            for (int d = 0; d < N; ++d)
-                *(int4 *)&s_cap[d * V + i] = __ldcs((const int4 *)&st.cap[d * n + v]);
-            *(int4 *)&s_tcap[i] = __ldcs((const int4 *)&st.tcap[v]);
-            *(int4 *)&s_exc[i] = __ldcs((const int4 *)&st.exc[v]);
-            *(int4 *)&s_lab[i] = make_int4(0, 0, 0, 0);
+        // one bulk copy per row of every plane (cap[N], tcap, exc are adjacent in
+        // shared memory) against the block's transaction barrier, spread over
+        // all threads; the labels start at 0 and the halo is gathered meanwhile
+        fence_proxy_async_smem();
+        if (tid == 0) mbar_arrive_expect_tx(mbar, (unsigned)((N + 2) * V * 4));
+        __syncthreads();  // earlier accesses of the planes and the byte count precede the copies
+        for (int c = tid; c < (N + 2) * TY; c += NT) {
+            const int p = c / TY, ly = c % TY;
+            const int *plane = p < N ? st.cap + (size_t)p * n : p == N ? st.tcap : st.exc;
+            bulk_g2s(s_cap + p * V + ly * TX, plane + (size_t)(oy + ly) * g.X + ox, TX * 4, mbar);
         }
+        for (int i4 = tid; i4 < V / 4; i4 += NT) *(int4 *)&s_lab[i4 * 4] = make_int4(0, 0, 0, 0);
     } else {
         for (int i = tid; i < V; i += NT) {
             const int lx = i % TX, ly = i / TX;
@@ -214,6 +216,15 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
     }
     if (TX == 32) {  // upper halves of the row words are never written by the ballots
         for (int w = tid; w < (N + 2) * TY; w += NT) ((unsigned *)s_R)[w * 2 + 1] = 0;
+    }
+    if (vec) {
+        bool landed = mbar_wait(mbar, mphase);
+        if (!landed) landed = mbar_wait(mbar, mphase);  // once more (bounded) before giving up
+        mphase ^= 1u;
+        if (__syncthreads_or(!landed)) {  // never expected: report and leave the region untouched
+            if (tid == 0) atomicExch(&st.ctr[kError], 2);
+            return;
+        }
     }
     __syncthreads();
     rebuild_masks();
@@ -627,7 +638,11 @@ template <int CONN, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT, (Cfg2D<CONN, TX, TY, NT>::MINB)) ard_discharge2d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     const int r = blockIdx.x;
     if (!st.active[r]) return;
-    discharge2d_region<CONN, TX, TY, NT>(g, st, sa, r);
+    __shared__ __align__(8) unsigned long long s_mbar;
+    if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
+    __syncthreads();
+    unsigned phase = 0;
+    discharge2d_region<CONN, TX, TY, NT>(g, st, sa, r, &s_mbar, phase);
 }
 
 // persistent blocks over a work queue of (instance, region) items of a batch
@@ -636,6 +651,9 @@ __global__ void __launch_bounds__(NT, (Cfg2D<CONN, TX, TY, NT>::MINB))
 ard_discharge2d_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ items, const int *count,
                              int *head, const SweepArgs sa) {
     __shared__ int s_it;
+    __shared__ __align__(8) unsigned long long s_mbar;
+    if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
+    unsigned phase = 0;
     for (;;) {
         __syncthreads();  // the previous item is done with s_it and the shared planes
         if (threadIdx.x == 0) s_it = atomicAdd(head, 1);
@@ -646,7 +664,7 @@ ard_discharge2d_batch_kernel(const Inst *__restrict__ insts, const int2 *__restr
         const Inst &I = insts[w.x];
         SweepArgs a = sa;
         a.c64 = I.c64;
-        discharge2d_region<CONN, TX, TY, NT>(I.g, I.st, a, w.y);
+        discharge2d_region<CONN, TX, TY, NT>(I.g, I.st, a, w.y, &s_mbar, phase);
     }
 }
 

@@ -105,7 +105,7 @@ __device__ __forceinline__ void halo3_src(int h, int &lx, int &ly, int &lz, int 
 
 template <int TY, int TZ, int NT>
 __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState &st, const SweepArgs &sa,
-                                                   const int r) {
+                                                   const int r, unsigned long long *mbar, unsigned &mphase) {
     using C = Cfg3D<TY, TZ, NT>;
     constexpr int TX = 32, N = 6, V = C::V, NR = C::NR, RPL = C::RPL, NW = C::NW, LCAP = C::LCAP, LZ = C::LZ;
     constexpr unsigned FULL = 0xffffffffu;
@@ -171,15 +171,19 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
     const bool full = ox + TX <= g.X && oy + TY <= g.Y && oz + TZ <= g.Z;
     const bool vec = full && (g.X % 4) == 0;  // every row starts on a 16-byte boundary
     if (vec) {
-        for (int i4 = tid; i4 < V / 4; i4 += NT) {
-            const int i = i4 * 4, lx = i % TX, rho = i / TX;
-            const size_t v = ((size_t)(oz + rho / TY) * g.Y + (oy + rho % TY)) * g.X + ox + lx;
-#pragma unroll
-            for (int d = 0; d < N; ++d) *(int4 *)&s_cap[d * V + i] = __ldcs((const int4 *)&st.cap[d * n + v]);
-            *(int4 *)&s_tcap[i] = __ldcs((const int4 *)&st.tcap[v]);
-            *(int4 *)&s_exc[i] = __ldcs((const int4 *)&st.exc[v]);
-            *(int4 *)&s_lab[i] = make_int4(0, 0, 0, 0);
+        // one bulk copy per row of every plane (cap[N], tcap, exc are adjacent in
+        // shared memory) against the block's transaction barrier, spread over
+        // all threads; the labels start at 0 and the halo is gathered meanwhile
+        fence_proxy_async_smem();
+        if (tid == 0) mbar_arrive_expect_tx(mbar, (unsigned)((N + 2) * V * 4));
+        __syncthreads();  // earlier accesses of the planes and the byte count precede the copies
+        for (int c = tid; c < (N + 2) * NR; c += NT) {
+            const int p = c / NR, rho = c % NR;
+            const int *plane = p < N ? st.cap + (size_t)p * n : p == N ? st.tcap : st.exc;
+            const size_t v0 = ((size_t)(oz + rho / TY) * g.Y + (oy + rho % TY)) * g.X + ox;
+            bulk_g2s(s_cap + p * V + rho * TX, plane + v0, TX * 4, mbar);
         }
+        for (int i4 = tid; i4 < V / 4; i4 += NT) *(int4 *)&s_lab[i4 * 4] = make_int4(0, 0, 0, 0);
     } else {
         for (int i = tid; i < V; i += NT) {
             const int lx = i % TX, rho = i / TX;
@@ -200,6 +204,15 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
         const int x = ox + lx + arc_dx(6, d), y = oy + ly + arc_dy(6, d), z = oz + lz + arc_dz(6, d);
         const bool ing = x >= 0 && x < g.X && y >= 0 && y < g.Y && z >= 0 && z < g.Z;
         s_hl[h] = ing ? st.lab[((size_t)z * g.Y + y) * g.X + x] : dinf;
+    }
+    if (vec) {
+        bool landed = mbar_wait(mbar, mphase);
+        if (!landed) landed = mbar_wait(mbar, mphase);  // once more (bounded) before giving up
+        mphase ^= 1u;
+        if (__syncthreads_or(!landed)) {  // never expected: report and leave the region untouched
+            if (tid == 0) atomicExch(&st.ctr[kError], 2);
+            return;
+        }
     }
     __syncthreads();
     rebuild_masks();
@@ -586,7 +599,11 @@ template <int TY, int TZ, int NT>
 __global__ void __launch_bounds__(NT, 1) ard_discharge3d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     const int r = blockIdx.x;
     if (!st.active[r]) return;
-    discharge3d_region<TY, TZ, NT>(g, st, sa, r);
+    __shared__ __align__(8) unsigned long long s_mbar;
+    if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
+    __syncthreads();
+    unsigned phase = 0;
+    discharge3d_region<TY, TZ, NT>(g, st, sa, r, &s_mbar, phase);
 }
 
 template <int TY, int TZ, int NT>
@@ -594,6 +611,9 @@ __global__ void __launch_bounds__(NT, 1)
 ard_discharge3d_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ items, const int *count,
                              int *head, const SweepArgs sa) {
     __shared__ int s_it;
+    __shared__ __align__(8) unsigned long long s_mbar;
+    if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
+    unsigned phase = 0;
     for (;;) {
         __syncthreads();  // the previous item is done with s_it and the shared planes
         if (threadIdx.x == 0) s_it = atomicAdd(head, 1);
@@ -604,7 +624,7 @@ ard_discharge3d_batch_kernel(const Inst *__restrict__ insts, const int2 *__restr
         const Inst &I = insts[w.x];
         SweepArgs a = sa;
         a.c64 = I.c64;
-        discharge3d_region<TY, TZ, NT>(I.g, I.st, a, w.y);
+        discharge3d_region<TY, TZ, NT>(I.g, I.st, a, w.y, &s_mbar, phase);
     }
 }
 

@@ -915,6 +915,7 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     if (g->h_ctr[kGap] > 0) g->stats.gaps++;
     if (g->h_ctr[kError]) {
         if (active_out) *active_out = g->h_ctr[kActiveRegions];
+        if (g->h_ctr[kError] == 2) return fail(g, MF_ECUDA, "a bulk copy into shared memory did not complete");
         return fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
     }
     int active = g->h_ctr[kActiveRegions];
@@ -1059,6 +1060,7 @@ static mf_status run_graph_loop(mf_grid *g, long long cap) {
         g->launches += (g->sweep - before) * per_sweep;
         g->stats.sweeps = g->sweep;
         g->stats.gaps = g->h_loop[kLoopGaps];
+        if (g->h_loop[kLoopError] == 2) return fail(g, MF_ECUDA, "a bulk copy into shared memory did not complete");
         if (g->h_loop[kLoopError]) return fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
         int active = g->h_loop[kLoopActive];
         if (active == 0) return MF_OK;

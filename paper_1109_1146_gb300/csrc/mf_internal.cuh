@@ -80,6 +80,53 @@ struct SweepArgs {
     Counters64 *c64;
 };
 
+// ---- bulk asynchronous copies (TMA engine, no tensor map) into shared memory
+// A transaction barrier (mbarrier) in shared memory counts the bytes of the
+// copies issued against it; the phase completes when they have all landed.
+// Addresses and sizes must be multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// one arrival that also announces the bytes the phase waits for
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for a phase: false if it did not complete within the limit
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phase) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+// global -> shared bulk copy of `bytes` completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// order this thread's earlier generic-proxy accesses of shared memory before
+// later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
 // Optional phase probes (clock64 deltas and counters per discharge phase),
 // compiled only with -DMF_DIAG; they expand to nothing otherwise.
 #ifdef MF_DIAG
