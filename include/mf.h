@@ -64,8 +64,8 @@ typedef struct {
     int32_t max_sweeps;            /* sweep cap; 0 = 2|B|^2+1 (the P-ARD bound, Sec. 4.4), clamped to 2^30 */
     int32_t partial_discharge;     /* 1: sweep s runs only ARD stages k <= s (Sec. 6.2); default 0 */
     int32_t global_gap;            /* 1: global gap heuristic after each sweep (Sec. 5.1); default 1 */
-    int32_t global_relabel_period; /* P > 0: exact region-distance relabel after every P-th sweep (2D grids,
-                                      Sec. 4.1 distance); 0 = off; default 4 */
+    int32_t global_relabel_period; /* P > 0: exact region-distance relabel after every P-th sweep (2D grids and
+                                      3D grids with 32-wide tiles; Sec. 4.1 distance); 0 = off; default 4 */
     int32_t max_rounds;            /* cap on Augment rounds per stage inside one discharge; 0 = default 65536 */
     int32_t kernel_variant;        /* 0: bit-parallel 2D / 3D discharge where the tile allows (default); 1: generic kernel */
     int32_t warm_start;            /* 1: start from the preflow of the last mf_warm_start instead of Init's zero flow */

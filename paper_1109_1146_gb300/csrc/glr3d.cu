@@ -1,0 +1,292 @@
+// Exact region-distance relabel (the global relabel heuristic) for 3D
+// 6-connected grids tiled by 32-voxel-wide regions (32x16x8, 32x8x8).
+//
+// d*(u) = the least number of inter-region arcs on a residual path from u to
+// t (the region distance of Sec. 4.1, eq. 3).  Level sets S_0 ⊆ S_1 ⊆ ...:
+// S_0 = vertices that reach t through arcs inside their own region; S_l adds
+// every vertex with a residual inter-region arc into S_{l-1}, then closes each
+// region under its inner arcs.  A vertex first reached at level l gets
+// d := max(d, l); vertices never reached get d_inf.  Raising labels to a
+// valid lower bound of the distance keeps the labeling valid and monotone
+// (the argument of Sec. 6.1).
+//
+// Layout: one 32-bit word per x-run of 32 voxels, word (z, y, xw) at
+// (z * Y + y) * W32 + xw, so a region's rows are the words with xw = its
+// region column.  One warp handles one region per level (lane l holds rows
+// l*RPL .. l*RPL+RPL-1, row rho = z_local * TY + y_local); all levels run in
+// one cooperative launch with a grid barrier per level.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include <cooperative_groups.h>
+
+#include "mf_internal.cuh"
+
+namespace mf {
+
+namespace cg = cooperative_groups;
+typedef unsigned int u32;
+
+// masks M[d][word] bit b = [c_f(v -> v + D(d)) > 0] and T[word] bit b = [c_f(v,t) > 0]
+__global__ void glr3d_masks_kernel(const Geom g, const DevState st, int W32, u32 *M, u32 *T) {
+    const size_t n = (size_t)g.n;
+    const size_t words = (size_t)g.Z * g.Y * W32;
+    const size_t nw = words;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < words * 32; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t w = t >> 5;
+        const int xw = (int)(w % W32), y = (int)((w / W32) % g.Y), z = (int)(w / ((size_t)W32 * g.Y));
+        const int x = xw * 32 + (int)(t & 31);
+        const bool in = x < g.X;
+        const size_t v = ((size_t)z * g.Y + y) * g.X + x;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            const unsigned m = __ballot_sync(0xffffffffu, in && st.cap[d * n + v] > 0);
+            if ((threadIdx.x & 31) == 0) M[d * nw + w] = m;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in && st.tcap[v] > 0);
+        if ((threadIdx.x & 31) == 0) T[w] = m;
+    }
+}
+
+template <int TY, int TZ>
+struct Glr3 {
+    static constexpr int NR = TY * TZ, RPL = NR / 32, LZ = TY / RPL;
+};
+
+// One level for one region (a warp).  level 0 seeds from T; level l > 0 from
+// S_{l-1} and the inter-region arcs into it.  Writes S_l; raises the labels
+// of the vertices it adds.  Returns whether the region's set grew.
+template <int TY, int TZ>
+__device__ bool glr3d_region(const Geom &g, int W32, int r, const u32 *__restrict__ M, const u32 *__restrict__ T,
+                             const u32 *Sin, u32 *Sout, int level, int *lab) {
+    using C = Glr3<TY, TZ>;
+    constexpr int RPL = C::RPL, LZ = C::LZ;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const size_t nw = (size_t)g.Z * g.Y * W32;
+    const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+    u32 m[6][RPL], s[RPL], s0[RPL];
+    size_t wi[RPL];
+    bool rowin[RPL];
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int rho = lane * RPL + j, yl = rho % TY, zl = rho / TY;
+        const int y = ry * TY + yl, z = rz * TZ + zl;
+        rowin[j] = y < g.Y && z < g.Z;
+        wi[j] = ((size_t)z * g.Y + y) * W32 + rx;
+        if (rowin[j]) {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) m[d][j] = M[d * nw + wi[j]];
+            s0[j] = level == 0 ? 0u : Sin[wi[j]];
+            u32 sd = level == 0 ? T[wi[j]] : s0[j];
+            if (level > 0) {
+                // residual inter-region arcs into S_{l-1}
+                if (rx > 0 && ((m[1][j] & 1u) && (Sin[wi[j] - 1] >> 31))) sd |= 1u;
+                if (rx + 1 < g.RX && ((m[0][j] >> 31) && (Sin[wi[j] + 1] & 1u))) sd |= 1u << 31;
+                if (yl == 0 && y > 0) sd |= m[3][j] & Sin[wi[j] - W32];
+                if (yl == TY - 1 && y + 1 < g.Y) sd |= m[2][j] & Sin[wi[j] + W32];
+                if (zl == 0 && z > 0) sd |= m[5][j] & Sin[wi[j] - (size_t)g.Y * W32];
+                if (zl == TZ - 1 && z + 1 < g.Z) sd |= m[4][j] & Sin[wi[j] + (size_t)g.Y * W32];
+            }
+            s[j] = sd;
+        } else {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) m[d][j] = 0u;
+            s0[j] = 0u;
+            s[j] = 0u;
+        }
+    }
+    // closure inside the region (arcs between rows of the tile, and along x within the word)
+    for (;;) {
+        const u32 up = __shfl_up_sync(FULL, s[RPL - 1], 1);
+        const u32 dn = __shfl_down_sync(FULL, s[0], 1);
+        bool any = false;
+        u32 nf[RPL];
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            const int rho = lane * RPL + j, yl = rho % TY, zl = rho / TY;
+            const u32 zm = __shfl_up_sync(FULL, s[j], LZ);
+            const u32 zp = __shfl_down_sync(FULL, s[j], LZ);
+            const u32 fa = j == 0 ? up : s[j - 1];
+            const u32 fb = j == RPL - 1 ? dn : s[j + 1];
+            u32 a = (m[0][j] & (s[j] >> 1)) | (m[1][j] & (s[j] << 1));
+            if (yl < TY - 1) a |= m[2][j] & fb;
+            if (yl > 0) a |= m[3][j] & fa;
+            if (zl < TZ - 1) a |= m[4][j] & zp;
+            if (zl > 0) a |= m[5][j] & zm;
+            a &= ~s[j];
+            // close whole x-runs at once (Kogge-Stone along the word)
+            u32 pl = m[0][j] & ~s[j], pr = m[1][j] & ~s[j], f = a;
+            {
+                u32 q = f, p = pl;
+                q |= p & (q >> 1);  p &= p >> 1;
+                q |= p & (q >> 2);  p &= p >> 2;
+                q |= p & (q >> 4);  p &= p >> 4;
+                q |= p & (q >> 8);  p &= p >> 8;
+                q |= p & (q >> 16);
+                u32 b2 = f;
+                p = pr;
+                b2 |= p & (b2 << 1);  p &= p << 1;
+                b2 |= p & (b2 << 2);  p &= p << 2;
+                b2 |= p & (b2 << 4);  p &= p << 4;
+                b2 |= p & (b2 << 8);  p &= p << 8;
+                b2 |= p & (b2 << 16);
+                f = q | b2;
+            }
+            nf[j] = f;
+            any |= f != 0u;
+        }
+        if (!__any_sync(FULL, any)) break;
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) s[j] |= nf[j];
+    }
+    bool grew = false;
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        if (!rowin[j]) continue;
+        Sout[wi[j]] = s[j];
+        u32 nwb = level == 0 ? 0u : (s[j] & ~s0[j]);
+        grew |= nwb != 0u;
+        const int rho = lane * RPL + j;
+        const size_t row0 = ((size_t)(rz * TZ + rho / TY) * g.Y + (ry * TY + rho % TY)) * g.X + (size_t)rx * 32;
+        for (; nwb; nwb &= nwb - 1) {
+            int *p = &lab[row0 + __ffs((int)nwb) - 1];
+            if (*p < level) *p = level;
+        }
+    }
+    return __any_sync(FULL, grew);
+}
+
+// all levels in one cooperative launch; flags[3] triple-buffered "grew" words
+template <int TY, int TZ>
+__global__ void glr3d_levels_kernel(const Geom g, int W32, const u32 *__restrict__ M, const u32 *__restrict__ T,
+                                    u32 *A, u32 *B, int *lab, int *flags, int *levels_out, int max_levels) {
+    cg::grid_group grid = cg::this_grid();
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (int r = wid; r < g.nreg; r += nwarps) glr3d_region<TY, TZ>(g, W32, r, M, T, nullptr, B, 0, lab);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        flags[1] = 0;
+        flags[2] = 0;
+    }
+    grid.sync();
+    int level = 1;
+    for (; level < max_levels; ++level) {
+        const u32 *in = (level & 1) ? B : A;
+        u32 *out = (level & 1) ? A : B;
+        bool grew = false;
+        for (int r = wid; r < g.nreg; r += nwarps) grew |= glr3d_region<TY, TZ>(g, W32, r, M, T, in, out, level, lab);
+        if (grew && lane == 0) atomicOr(&flags[level % 3], 1);
+        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(level + 1) % 3] = 0;
+        grid.sync();
+        if (!*(volatile int *)&flags[level % 3]) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *levels_out = level + 1;
+}
+
+// unreached vertices get d_inf; boundary-label histogram and region activity
+__global__ void glr3d_finish_kernel(const Geom g, const DevState st, int W32, const u32 *S) {
+    constexpr int SB = 2048;
+    __shared__ int sh[SB];
+    for (int b = threadIdx.x; b < SB; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < (size_t)g.n; v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
+        int l = st.lab[v];
+        if (!((S[((size_t)z * g.Y + y) * W32 + (x >> 5)] >> (x & 31)) & 1u)) {
+            l = g.dinf;
+            st.lab[v] = l;
+        }
+        if (l >= g.dinf) continue;
+        const int r = ((z >> g.sz) * g.RY + (y >> g.sy)) * g.RX + (x >> g.sx);
+        if (st.exc[v] > 0) st.active[r] = 1;
+        bool inB = false;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            const int wx = x + arc_dx(6, d), wy = y + arc_dy(6, d), wz = z + arc_dz(6, d);
+            if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y || wz < 0 || wz >= g.Z) continue;
+            if (((wz >> g.sz) * g.RY + (wy >> g.sy)) * g.RX + (wx >> g.sx) != r) inB = true;
+        }
+        if (!inB) continue;
+        if (l < SB) atomicAdd(&sh[l], 1);
+        else atomicAdd(&st.hist[l < kHistBins ? l : kHistBins], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < SB; b += blockDim.x)
+        if (sh[b]) atomicAdd(&st.hist[b], sh[b]);
+}
+
+__global__ void glr3d_count_kernel(const DevState st, int nreg) {
+    int c = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) c += st.active[r] != 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
+}
+
+bool glr3d_supported(const Geom &g) { return g.tx == 32 && g.tz > 1 && ((g.ty == 16 && g.tz == 8) || (g.ty == 8 && g.tz == 8)); }
+
+size_t glr3d_scratch_bytes(const Geom &g) {
+    const size_t words = (size_t)g.Z * g.Y * ((g.X + 31) / 32);
+    return words * 4 * (6 + 1 + 2);  // masks, T, two level sets
+}
+
+template <int TY, int TZ>
+static cudaError_t glr3d_impl(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
+                              cudaStream_t s) {
+    const int W32 = (g.X + 31) / 32;
+    const size_t words = (size_t)g.Z * g.Y * W32;
+    u32 *M = (u32 *)scratch;
+    u32 *T = M + 6 * words;
+    u32 *A = T + words;
+    u32 *B = A + words;
+    const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, 152 * 32);
+    glr3d_masks_kernel<<<mb, 256, 0, s>>>(g, st, W32, M, T);
+    static int max_blocks = 0;
+    if (!max_blocks) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, glr3d_levels_kernel<TY, TZ>, 256, 0);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        max_blocks = per_sm * sms;
+        if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    }
+    const int nblocks = std::min((g.nreg + 7) / 8, max_blocks);
+    int *flags = &st.ctr[kGlrFlags];
+    int *lvl = &st.ctr[kGlrLevels];
+    int max_levels = 1 << 20;
+    Geom gg = g;
+    int w32 = W32;
+    const u32 *pm = M, *pt = T;
+    u32 *pa = A, *pb = B;
+    int *lab = st.lab;
+    void *args[] = {&gg, &w32, (void *)&pm, (void *)&pt, &pa, &pb, &lab, &flags, &lvl, &max_levels};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)glr3d_levels_kernel<TY, TZ>, dim3(nblocks), dim3(256),
+                                                args, 0, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(h_changed, lvl, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *levels = *h_changed;
+    // level 0 writes B, odd levels A, even levels B; the last level run is levels - 1
+    const int last = *levels - 1;
+    const u32 *fin = (last % 2 == 1) ? A : B;
+    e = cudaMemsetAsync(st.hist, 0, (kHistBins + 1) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st.active, 0, (size_t)g.nreg, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&st.ctr[kActiveRegions], 0, 4, s);
+    if (e != cudaSuccess) return e;
+    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, 152 * 32);
+    glr3d_finish_kernel<<<nb, 256, 0, s>>>(g, st, W32, fin);
+    glr3d_count_kernel<<<(g.nreg + 255) / 256, 256, 0, s>>>(st, g.nreg);
+    return cudaGetLastError();
+}
+
+cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels, cudaStream_t s) {
+    if (g.ty == 16 && g.tz == 8) return glr3d_impl<16, 8>(g, st, scratch, h_changed, levels, s);
+    if (g.ty == 8 && g.tz == 8) return glr3d_impl<8, 8>(g, st, scratch, h_changed, levels, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace mf

@@ -784,7 +784,8 @@ mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int con
         {(void **)&g->st.left_active, (size_t)G.nreg}, {(void **)&g->st.flow_t, 8}, {(void **)&g->st.flow0, 8},
         {(void **)&g->st.hist, (kHistBins + 1) * 4}, {(void **)&g->st.ctr, kCtrWords * 4},
         {(void **)&g->smin, (size_t)n}, {(void **)&g->tset, (size_t)n}, {(void **)&g->c64, sizeof(Counters64)},
-        {(void **)&g->cut_scratch, ndim == 2 ? cut2d_scratch_bytes(G, connectivity) : 0}};
+        {(void **)&g->cut_scratch, ndim == 2 ? cut2d_scratch_bytes(G, connectivity)
+                                             : (glr3d_supported(G) ? glr3d_scratch_bytes(G) : 0)}};
     for (auto &a : allocs) {
         if (a.bytes == 0) continue;
         e = cudaMalloc(a.p, a.bytes);
@@ -887,6 +888,15 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
     return MF_OK;
 }
 
+// the global relabel (exact region distance), 2D or 3D
+static bool glr_supported(const mf_grid *g) {
+    return g->ndim == 2 ? glr2d_supported(g->g) : glr3d_supported(g->g);
+}
+static cudaError_t glr_run(mf_grid *g, int *levels) {
+    return g->ndim == 2 ? glr2d(g->conn, g->g, g->st, g->cut_scratch, g->h_ctr, levels, g->stream)
+                        : glr3d(g->g, g->st, g->cut_scratch, g->h_ctr, levels, g->stream);
+}
+
 static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     SweepArgs sa{};
     sa.sweep = g->sweep;
@@ -920,11 +930,11 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     }
     int active = g->h_ctr[kActiveRegions];
     const int P = g->opts.global_relabel_period;
-    if (P > 0 && active > 0 && g->sweep % P == 0 && g->ndim == 2 && glr2d_supported(g->g)) {
+    if (P > 0 && active > 0 && g->sweep % P == 0 && glr_supported(g)) {
         // exact region-distance relabel (raises labels to max(d, d*)), then the
         // activity of every region is recomputed from the new labels
         int levels = 0;
-        CK(glr2d(g->conn, g->g, g->st, g->cut_scratch, g->h_ctr, &levels, g->stream));
+        CK(glr_run(g, &levels));
         CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
         CK(cudaStreamSynchronize(g->stream));
         active = g->h_ctr[kActiveRegions];
@@ -1042,8 +1052,7 @@ static mf_status build_graph(mf_grid *g) {
 static mf_status run_graph_loop(mf_grid *g, long long cap) {
     mf_status s = build_graph(g);
     if (s != MF_OK) return s;
-    const int P = (g->opts.global_relabel_period > 0 && g->ndim == 2 && glr2d_supported(g->g))
-                      ? g->opts.global_relabel_period : 0;
+    const int P = (g->opts.global_relabel_period > 0 && glr_supported(g)) ? g->opts.global_relabel_period : 0;
     int init[kLoopWords] = {0};
     init[kLoopSweep] = g->sweep;
     init[kLoopCap] = (int)std::min<long long>(cap, INT_MAX);
@@ -1067,7 +1076,7 @@ static mf_status run_graph_loop(mf_grid *g, long long cap) {
         if (g->sweep >= cap) return fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left");
         if (P > 0 && g->sweep % P == 0) {
             int levels = 0;
-            CK(glr2d(g->conn, g->g, g->st, g->cut_scratch, g->h_ctr, &levels, g->stream));
+            CK(glr_run(g, &levels));
             CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
             CK(cudaStreamSynchronize(g->stream));
             active = g->h_ctr[kActiveRegions];

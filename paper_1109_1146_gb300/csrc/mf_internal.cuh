@@ -164,6 +164,10 @@ cudaError_t cut2d(int conn, const Geom &g, const DevState &st, void *scratch, un
 void set_static_error(const std::string &m);
 // global relabel: exact region distance on bit masks (2D, tiles 32 or 64 wide)
 bool glr2d_supported(const Geom &g);
+// glr3d.cu: the same relabel for 3D 6-connected grids with 32-wide tiles
+bool glr3d_supported(const Geom &g);
+size_t glr3d_scratch_bytes(const Geom &g);
+cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels, cudaStream_t s);
 cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
                   cudaStream_t s);
 // persistent discharge over a work queue of (instance, region) items of one

@@ -166,3 +166,13 @@ def test_generic_kernel_variant(conn, dims, tile, kind):
             else grids.random_grid(dims, conn, 13, cmax=30, tmax=60, p_zero=0.3))
     got = gpu_solve(inst, tile=tile, opts=opts(kernel_variant=1))
     assert_parity(inst, got)
+
+
+@pytest.mark.parametrize("tile", [(32, 8, 8, ), (32, 16, 8)])
+@pytest.mark.parametrize("kw", [dict(global_relabel_period=1), dict(global_relabel_period=2, partial_discharge=1),
+                                dict(global_relabel_period=3, global_gap=0)])
+def test_3d_global_relabel_keeps_exact_results(tile, kw):
+    inst = grids.volume_3d(75, 43, 37, 12)
+    got = gpu_solve(inst, tile=tile, opts=opts(**kw))
+    assert_parity(inst, got)
+    assert got["stats"].global_relabels >= 1
