@@ -1,5 +1,6 @@
-// Exact region-distance relabel (the global relabel heuristic) for 3D
-// 6-connected grids tiled by 32-voxel-wide regions (32x16x8, 32x8x8).
+// Exact region-distance relabel (the global relabel heuristic) and the cut
+// closures for 3D 6-connected grids tiled by 32-voxel-wide regions (32x16x8,
+// 32x8x8).
 //
 // d*(u) = the least number of inter-region arcs on a residual path from u to
 // t (the region distance of Sec. 4.1, eq. 3).  Level sets S_0 ⊆ S_1 ⊆ ...:
@@ -148,6 +149,7 @@ __device__ bool glr3d_region(const Geom &g, int W32, int r, const u32 *__restric
         Sout[wi[j]] = s[j];
         u32 nwb = level == 0 ? 0u : (s[j] & ~s0[j]);
         grew |= nwb != 0u;
+        if (!lab) continue;  // a plain closure: no labels
         const int rho = lane * RPL + j;
         const size_t row0 = ((size_t)(rz * TZ + rho / TY) * g.Y + (ry * TY + rho % TY)) * g.X + (size_t)rx * 32;
         for (; nwb; nwb &= nwb - 1) {
@@ -223,6 +225,127 @@ __global__ void glr3d_count_kernel(const DevState st, int nreg) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) c += st.active[r] != 0;
     c = __reduce_add_sync(0xffffffffu, c);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
+}
+
+// ---- cut extraction (Sec. 2) on the same masks --------------------------------
+// S_min = closure of {e > 0} under residual arcs, S_max = V minus {v -> t}.
+// Both as pull closures: v joins when its masked arc of some direction d
+// leads to a member.  which = 0 (S_min): the bit of d at v is [c_f(v + D(d)
+// -> v) > 0] (the arc into v), seeds e > 0; which = 1 ({v -> t}): the bit is
+// [c_f(v -> v + D(d)) > 0], seeds c_f(v,t) > 0.
+__global__ void cut3d_masks_kernel(const Geom g, const DevState st, int W32, int which, u32 *M, u32 *S) {
+    const size_t n = (size_t)g.n;
+    const size_t words = (size_t)g.Z * g.Y * W32;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < words * 32; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t w = t >> 5;
+        const int xw = (int)(w % W32), y = (int)((w / W32) % g.Y), z = (int)(w / ((size_t)W32 * g.Y));
+        const int x = xw * 32 + (int)(t & 31);
+        const bool in = x < g.X;
+        const size_t v = ((size_t)z * g.Y + y) * g.X + x;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            bool b = false;
+            if (in) {
+                if (which == 1) {
+                    b = st.cap[d * n + v] > 0;
+                } else {
+                    const int wx = x + arc_dx(6, d), wy = y + arc_dy(6, d), wz = z + arc_dz(6, d);
+                    if (wx >= 0 && wx < g.X && wy >= 0 && wy < g.Y && wz >= 0 && wz < g.Z)
+                        b = st.cap[(d ^ 1) * n + ((size_t)wz * g.Y + wy) * g.X + wx] > 0;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, b);
+            if ((threadIdx.x & 31) == 0) M[d * words + w] = m;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in && (which == 1 ? st.tcap[v] > 0 : st.exc[v] > 0));
+        if ((threadIdx.x & 31) == 0) S[w] = m;
+    }
+}
+
+// passes over all regions (a warp each: seeds across the faces from the
+// current set, closure inside) until a pass adds nothing; the set grows in
+// place, which only speeds up the fixed point
+template <int TY, int TZ>
+__global__ void closure3d_kernel(const Geom g, int W32, const u32 *__restrict__ M, u32 *S, int *flags,
+                                 int *passes_out, int max_passes) {
+    cg::grid_group grid = cg::this_grid();
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        flags[1] = 0;
+        flags[2] = 0;
+    }
+    grid.sync();
+    int pass = 0;
+    for (; pass < max_passes; ++pass) {
+        bool grew = false;
+        for (int r = wid; r < g.nreg; r += nwarps)
+            grew |= glr3d_region<TY, TZ>(g, W32, r, M, nullptr, S, S, 1, nullptr);
+        if (grew && lane == 0) atomicOr(&flags[pass % 3], 1);
+        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(pass + 1) % 3] = 0;
+        grid.sync();
+        if (!*(volatile int *)&flags[pass % 3]) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *passes_out = pass + 1;
+}
+
+__global__ void cut3d_bytes_kernel(const Geom g, int W32, const u32 *Smin, const u32 *Tset, unsigned char *smin,
+                                   unsigned char *smax) {
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < (size_t)g.n; v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
+        const size_t w = ((size_t)z * g.Y + y) * W32 + (x >> 5);
+        smin[v] = (unsigned char)((Smin[w] >> (x & 31)) & 1u);
+        smax[v] = (unsigned char)(1u - ((Tset[w] >> (x & 31)) & 1u));
+    }
+}
+
+template <int TY, int TZ>
+static cudaError_t cut3d_impl(const Geom &g, const DevState &st, void *scratch, unsigned char *smin,
+                              unsigned char *smax, int *h_changed, int *passes, cudaStream_t s) {
+    const int W32 = (g.X + 31) / 32;
+    const size_t words = (size_t)g.Z * g.Y * W32;
+    u32 *M = (u32 *)scratch;
+    u32 *Smin = M + 6 * words;
+    u32 *Tset = Smin + words;
+    const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, 152 * 32);
+    static int max_blocks = 0;
+    if (!max_blocks) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, closure3d_kernel<TY, TZ>, 256, 0);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        max_blocks = per_sm * sms;
+        if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    }
+    const int nblocks = std::min((g.nreg + 7) / 8, max_blocks);
+    for (int which = 0; which < 2; ++which) {
+        u32 *S = which == 0 ? Smin : Tset;
+        cut3d_masks_kernel<<<mb, 256, 0, s>>>(g, st, W32, which, M, S);
+        Geom gg = g;
+        int w32 = W32, max_passes = 1 << 20;
+        const u32 *pm = M;
+        u32 *ps = S;
+        int *flags = &st.ctr[kGlrFlags], *cnt = &st.ctr[kGlrLevels];
+        void *args[] = {&gg, &w32, (void *)&pm, &ps, &flags, &cnt, &max_passes};
+        cudaError_t e = cudaLaunchCooperativeKernel((const void *)closure3d_kernel<TY, TZ>, dim3(nblocks), dim3(256),
+                                                    args, 0, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_changed, cnt, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        *passes += *h_changed;
+    }
+    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, 152 * 32);
+    cut3d_bytes_kernel<<<nb, 256, 0, s>>>(g, W32, Smin, Tset, smin, smax);
+    return cudaGetLastError();
+}
+
+cudaError_t cut3d(const Geom &g, const DevState &st, void *scratch, unsigned char *smin, unsigned char *smax,
+                  int *h_changed, int *passes, cudaStream_t s) {
+    if (g.ty == 16 && g.tz == 8) return cut3d_impl<16, 8>(g, st, scratch, smin, smax, h_changed, passes, s);
+    if (g.ty == 8 && g.tz == 8) return cut3d_impl<8, 8>(g, st, scratch, smin, smax, h_changed, passes, s);
+    return cudaErrorInvalidValue;
 }
 
 bool glr3d_supported(const Geom &g) { return g.tx == 32 && g.tz > 1 && ((g.ty == 16 && g.tz == 8) || (g.ty == 8 && g.tz == 8)); }

@@ -959,6 +959,9 @@ mf_status mf_finish(mf_grid *g) {
     if (g->ndim == 2) {
         CK(cut2d(g->conn, g->g, g->st, g->cut_scratch, g->smin, g->tset, g->h_ctr, &passes, g->stream));
         g->launches += 2 + passes + 1;
+    } else if (glr3d_supported(g->g)) {
+        CK(cut3d(g->g, g->st, g->cut_scratch, g->smin, g->tset, g->h_ctr, &passes, g->stream));
+        g->launches += 5;
     } else {
         cut_seed_kernel<<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->g, g->st, g->smin, g->tset);
         CK(cudaGetLastError());

@@ -168,6 +168,9 @@ bool glr2d_supported(const Geom &g);
 bool glr3d_supported(const Geom &g);
 size_t glr3d_scratch_bytes(const Geom &g);
 cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels, cudaStream_t s);
+// both cut closures on bit masks (scratch: glr3d_scratch_bytes); passes += passes made
+cudaError_t cut3d(const Geom &g, const DevState &st, void *scratch, unsigned char *smin, unsigned char *smax,
+                  int *h_changed, int *passes, cudaStream_t s);
 cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
                   cudaStream_t s);
 // persistent discharge over a work queue of (instance, region) items of one
