@@ -424,6 +424,15 @@ __global__ void loop_ctl_kernel(const int *ctr, int *lc, cudaGraphConditionalHan
     cudaGraphSetConditional(handle, cont ? 1u : 0u);
 }
 
+// the batch's loop control: any = some instance still has an active region
+__global__ void batch_loop_ctl_kernel(const int *any, int *lc, cudaGraphConditionalHandle handle) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int s = lc[kLoopSweep] + 1;
+    lc[kLoopSweep] = s;
+    lc[kLoopActive] = *any;
+    cudaGraphSetConditional(handle, (*any && s < lc[kLoopCap]) ? 1u : 0u);
+}
+
 // ---- batched sweep kernels: one block per (instance, region) of the batch table
 __global__ void batch_reset_kernel(const Inst *insts, const unsigned char *done, int count) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
@@ -1132,12 +1141,19 @@ mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats) {
 
 // ---- batched solve --------------------------------------------------------------
 struct BatchBufs {
+    int *loop = nullptr;                   // graph loop state (kLoop* words)
+    cudaStream_t cap_stream = nullptr;     // private capture stream of the graph loop
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     Inst *insts = nullptr;
     int2 *regs = nullptr, *items = nullptr;
     int *type_of = nullptr, *cnt = nullptr, *head = nullptr, *sweeps = nullptr, *any = nullptr;
     unsigned char *done = nullptr;
     ~BatchBufs() {
-        void *p[] = {insts, regs, items, type_of, cnt, head, sweeps, any, done};
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        void *p[] = {insts, regs, items, type_of, cnt, head, sweeps, any, done, loop};
         for (void *q : p)
             if (q) cudaFree(q);
     }
@@ -1218,49 +1234,97 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     sa.variant = o.kernel_variant;
     const int eb = (int)std::min<long long>(((long long)nregs + 255) / 256, 152 * 8);
     mf_status rs = MF_OK;
-    int sweep = 0;
     long long launches = 0;
-    for (;; ++sweep) {
-        sa.sweep = sweep;
-        CK(cudaMemsetAsync(B.cnt, 0, sizeof(int) * nt, s));
-        CK(cudaMemsetAsync(B.head, 0, sizeof(int) * nt, s));
-        CK(cudaMemsetAsync(B.any, 0, sizeof(int), s));
-        batch_reset_kernel<<<(count + 255) / 256, 256, 0, s>>>(B.insts, B.done, count);
-        batch_items_kernel<<<eb, 256, 0, s>>>(B.insts, B.regs, nregs, B.done, B.type_of, nregs, B.items, B.cnt);
-        CK(cudaGetLastError());
-        for (int t = 0; t < nt; ++t)
-            CK(launch_discharge_batch(types[t].conn, types[t].tx, types[t].ty, types[t].tz, sa.variant, B.insts,
-                                      B.items + (size_t)t * nregs, B.cnt + t, B.head + t, sa, 152 * 4, s));
+    const int per_sweep = 6 + nt + (o.global_gap ? 1 : 0);
+    // one sweep of the whole batch on stream st (sweep index from the host, or
+    // from sweep_dev inside a graph)
+    auto enqueue_sweep = [&](cudaStream_t st, int sweep_host, const int *sweep_dev) -> cudaError_t {
+        SweepArgs a = sa;
+        a.sweep = sweep_host;
+        a.sweep_dev = sweep_dev;
+        cudaError_t e = cudaMemsetAsync(B.cnt, 0, sizeof(int) * nt, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.head, 0, sizeof(int) * nt, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B.any, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        batch_reset_kernel<<<(count + 255) / 256, 256, 0, st>>>(B.insts, B.done, count);
+        batch_items_kernel<<<eb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done, B.type_of, nregs, B.items, B.cnt);
+        e = cudaGetLastError();
+        for (int t = 0; t < nt && e == cudaSuccess; ++t)
+            e = launch_discharge_batch(types[t].conn, types[t].tx, types[t].ty, types[t].tz, a.variant, B.insts,
+                                       B.items + (size_t)t * nregs, B.cnt + t, B.head + t, a, 152 * 4, st);
+        if (e != cudaSuccess) return e;
         // fusion / gap / activity per connectivity of the instances (one launch per connectivity)
         for (int conn : {4, 8, 6}) {
             bool has = false;
             for (auto &ty : types) has |= ty.conn == conn;
             if (!has) continue;
-            if (conn == 4) fuse_batch_kernel<4><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
-            if (conn == 8) fuse_batch_kernel<8><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
-            if (conn == 6) fuse_batch_kernel<6><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
+            if (conn == 4) fuse_batch_kernel<4><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
+            if (conn == 8) fuse_batch_kernel<8><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
+            if (conn == 6) fuse_batch_kernel<6><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
         }
-        if (o.global_gap) gap_find_batch_kernel<<<count, 1024, 0, s>>>(B.insts, B.done);
+        if (o.global_gap) gap_find_batch_kernel<<<count, 1024, 0, st>>>(B.insts, B.done);
         for (int conn : {4, 8, 6}) {
             bool has = false;
             for (auto &ty : types) has |= ty.conn == conn;
             if (!has) continue;
-            if (conn == 4) post_batch_kernel<4><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
-            if (conn == 8) post_batch_kernel<8><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
-            if (conn == 6) post_batch_kernel<6><<<nregs, 256, 0, s>>>(B.insts, B.regs, B.done);
+            if (conn == 4) post_batch_kernel<4><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
+            if (conn == 8) post_batch_kernel<8><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
+            if (conn == 6) post_batch_kernel<6><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
         }
-        clear_batch_kernel<<<eb, 256, 0, s>>>(B.insts, B.regs, nregs, B.done);
-        batch_end_kernel<<<(count + 255) / 256, 256, 0, s>>>(B.insts, B.done, B.sweeps, B.any, count);
-        CK(cudaGetLastError());
-        launches += 6 + nt + (o.global_gap ? 1 : 0);
-        int any = 0;
-        CK(cudaMemcpyAsync(g->h_ctr, B.any, sizeof(int), cudaMemcpyDeviceToHost, s));
+        clear_batch_kernel<<<eb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done);
+        batch_end_kernel<<<(count + 255) / 256, 256, 0, st>>>(B.insts, B.done, B.sweeps, B.any, count);
+        return cudaGetLastError();
+    };
+    if (o.graph_loop) {
+        // all sweeps as one CUDA graph: a while node whose body is one sweep of
+        // the batch plus a loop-control kernel (continue while an instance is
+        // active and the cap allows); captured on a private stream
+        CK(cudaMalloc(&B.loop, sizeof(int) * kLoopWords));
+        int init[kLoopWords] = {0};
+        init[kLoopCap] = (int)std::min<long long>(cap, INT_MAX);
+        memcpy(g->h_ctr, init, sizeof(init));
+        CK(cudaMemcpyAsync(B.loop, g->h_ctr, sizeof(init), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
-        any = g->h_ctr[0];
-        if (!any) break;
-        if (sweep + 1 >= cap) {
+        CK(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
+        CK(cudaGraphCreate(&B.graph, 0));
+        cudaGraphConditionalHandle handle;
+        CK(cudaGraphConditionalHandleCreate(&handle, B.graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = handle;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, B.graph, nullptr, nullptr, 0, &np));
+        CK(cudaStreamBeginCaptureToGraph(B.cap_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+        cudaError_t e = enqueue_sweep(B.cap_stream, 0, &B.loop[kLoopSweep]);
+        if (e == cudaSuccess) {
+            batch_loop_ctl_kernel<<<1, 32, 0, B.cap_stream>>>(B.any, B.loop, handle);
+            e = cudaGetLastError();
+        }
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(B.cap_stream, &captured);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(g, MF_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        CK(cudaGraphInstantiate(&B.exec, B.graph, 0));
+        CK(cudaGraphLaunch(B.exec, s));
+        CK(cudaMemcpyAsync(g->h_ctr, B.loop, sizeof(init), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        launches += (long long)g->h_ctr[kLoopSweep] * (per_sweep + 1);
+        if (g->h_ctr[kLoopActive] && g->h_ctr[kLoopSweep] >= cap)
             rs = fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left in the batch");
-            break;
+    } else {
+        for (int sweep = 0;; ++sweep) {
+            CK(enqueue_sweep(s, sweep, nullptr));
+            launches += per_sweep;
+            CK(cudaMemcpyAsync(g->h_ctr, B.any, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (!g->h_ctr[0]) break;
+            if (sweep + 1 >= cap) {
+                rs = fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left in the batch");
+                break;
+            }
         }
     }
     CK(cudaEventRecord(g->ev[2], s));
