@@ -375,6 +375,79 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch_warm(args):
+    """Learned warm start with the batched solve: held-out 1024x1024 4-connected
+    segmentation grids (mu_fg, mu_bg per seed) solved one by one cold, batched
+    cold, and batched warm (features, network inference and projection of every
+    instance inside the timed region)."""
+    import torch
+
+    from gen import grids
+    from paper_1109_1146_gb300 import Grid, default_opts, mf, warmstart
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    count = args.batch_count or 64
+    insts = [grids.config3(warmstart.EVAL_SEED0 + i) for i in range(count)]
+    stream = torch.cuda.current_stream()
+    weights = os.path.join(ROOT, "paper_1109_1146_gb300", "weights", "warm_seg2d_1024_c4.npy")
+    net = warmstart.load_network(weights)
+    plain_ms, plain_sweeps, flows = 0.0, 0, []
+    for x in insts:
+        with Grid(x.dims, x.conn, stream=stream) as g:
+            g.set_caps(x.cs, x.ct, x.nlink)
+            g.solve()
+            st = g.solve()
+            plain_ms += st.ms_total
+            plain_sweeps += st.sweeps
+            flows.append(g.flow_value())
+    handles = []
+    for x in insts:
+        g = Grid(x.dims, x.conn, stream=stream)
+        g.set_caps(x.cs, x.ct, x.nlink)
+        handles.append(g)
+    C, X, Y = 6, insts[0].dims[0], insts[0].dims[1]
+    xf = torch.empty((1, C, Y, X), dtype=torch.float32, device=dev)
+    yp = torch.empty_like(xf)
+
+    def one_step(warm):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        if warm:
+            for g in handles:
+                g.warm_features(xf)
+                net.infer(xf, yp)
+                g.warm_start(yp, check=False)
+        stats = mf.solve_batch(handles, default_opts(warm_start=1 if warm else 0, graph_loop=1))
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), stats
+
+    res = {}
+    for warm in (False, True):
+        for _ in range(args.warmup):
+            one_step(warm)
+        runs = [one_step(warm) for _ in range(args.steps)]
+        assert [h.flow_value() for h in handles] == flows, "batched and single solves disagree"
+        res[warm] = (statistics.median(r[0] for r in runs), sum(s.sweeps for s in runs[-1][1]) / count)
+    line = {"metric": METRIC, "workload": "batch_warm", "value": round(res[True][0] / count, 4), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "%d held-out seg2d 1024x1024 4-connected grids, mu_fg and mu_bg ~ U[60,200] per "
+                                   "seed; committed warm-start network" % count, "instances": count},
+            "plain_cold_ms_per_instance": round(plain_ms / count, 4),
+            "batch_cold_ms_per_instance": round(res[False][0] / count, 4),
+            "batch_warm_ms_per_instance": round(res[True][0] / count, 4),
+            "sweeps_per_instance_plain_cold": plain_sweeps / count,
+            "sweeps_per_instance_batch_cold": res[False][1],
+            "sweeps_per_instance_batch_warm": res[True][1],
+            "speedup_batch_warm_vs_plain": round(plain_ms / res[True][0], 3)}
+    for h in handles:
+        h.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -408,7 +481,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="seg2048", choices=["seg2048", "batch"])
+    ap.add_argument("--workload", default="seg2048", choices=["seg2048", "batch", "batch_warm"])
     ap.add_argument("--batch-count", type=int, default=0, help="first N instances of the batch (0 = all 512)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -417,6 +490,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "batch_warm":
+        run_batch_warm(args)
     else:
         run_ours(args)
 

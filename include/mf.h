@@ -167,7 +167,10 @@ mf_status mf_finish(mf_grid *g);
  * instance results are then read as after mf_solve (mf_get_cut,
  * mf_flow_value); stats (nullable) receives count entries (the ms_* fields
  * are those of the whole batch).  The global relabel option is not applied
- * in batched solves.
+ * in batched solves.  With opts->warm_start = 1 each grid starts from its
+ * projected preflow if mf_warm_start succeeded on it, and from Init
+ * otherwise.  With opts->graph_loop = 1 the sweep loop of the batch is one
+ * CUDA graph.
  */
 mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, mf_stats *stats);
 

@@ -1176,7 +1176,13 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     // Init of every instance on its own stream, then everything on the batch stream
     long long cap = 0;
     for (int i = 0; i < count; ++i) {
-        mf_status st = mf_begin(grids[i], opts);
+        // with opts.warm_start, each grid starts from its projected preflow if
+        // mf_warm_start succeeded on it, and cold otherwise
+        mf_opts oi;
+        if (opts) oi = *opts;
+        else mf_default_opts(&oi);
+        if (oi.warm_start && !grids[i]->warm_ready) oi.warm_start = 0;
+        mf_status st = mf_begin(grids[i], &oi);
         if (st != MF_OK) return st;
         if (grids[i]->stream != s) {
             cudaError_t e = cudaStreamSynchronize(grids[i]->stream);

@@ -178,3 +178,27 @@ def test_untrained_network_gives_exact_results():
         warmstart.warm_solve(g, net)
         assert g.flow_value() == ref["flow"]
         np.testing.assert_array_equal(g.get_cut(0), ref["smin"])
+
+
+def test_batched_warm_start_is_exact():
+    # a batch of 2D 4-connected grids, half of them warm-started from noisy
+    # solution flows, plus one 3D grid that stays cold: exact results for all
+    from paper_1109_1146_gb300 import mf as mfmod
+    insts = [grids.config3(30 + i, side=96 + 32 * i) for i in range(4)] + [grids.volume_3d(40, 30, 20, 3)]
+    handles = []
+    for k, inst in enumerate(insts):
+        g = Grid(inst.dims, inst.conn)
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        if k % 2 == 0 and inst.conn == 4:
+            t, _ = _solved_targets(inst)
+            gen = torch.Generator(device=DEV).manual_seed(k)
+            g.warm_start(t + 0.2 * torch.randn(t.shape, generator=gen, device=DEV))
+        handles.append(g)
+    for graph in (0, 1):
+        mfmod.solve_batch(handles, default_opts(warm_start=1, global_relabel_period=0, graph_loop=graph))
+        for inst, g in zip(insts, handles):
+            got = {"flow": g.flow_value(), "smin": g.get_cut(0), "smax": g.get_cut(1)}
+            got["res"], got["tres"], got["exc"] = g.get_residual()
+            assert_parity(inst, got)
+    for g in handles:
+        g.close()
