@@ -63,6 +63,22 @@ def dist_env():
     return ws, rank, local
 
 
+def job_time_ms(local_ms, ws, device=None):
+    """Timed total of the whole job: the maximum over ranks of each rank's
+    timed total (every rank solves its own instance; the slowest bounds it)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(total_ms, ws, steps):
+    """ms per instance over the whole job: ws ranks each solved `steps` instances."""
+    return total_ms / (ws * steps)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -206,10 +222,7 @@ def run_ours(args):
         gev[k][1].record(stream)
     barrier()
     graph_ms = sum(a.elapsed_time(b) for a, b in gev)
-    total = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(total, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(total.item())
+    total_ms = job_time_ms(sum(step_ms), ws, dev)
     flow = g.flow_value()
 
     # end to end through the public API with host buffers (pinned)
@@ -230,9 +243,8 @@ def run_ours(args):
         if k >= args.warmup:
             e2e_ms.append((t1 - t0) * 1e3)
         assert f_host == flow
-    e2e = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(e2e, op=torch.distributed.ReduceOp.MAX)
+    e2e_total = job_time_ms(sum(e2e_ms), ws, dev)
+    graph_total = job_time_ms(graph_ms, ws, dev)
     g.close()
 
     if rank != 0:
@@ -242,7 +254,7 @@ def run_ours(args):
         return
 
     units = ws * args.steps
-    value = total_ms / units
+    value = job_value(total_ms, ws, args.steps)
     sweeps = statistics.mean(s.sweeps for s in stats)
     dis_ms = sum(s.ms_discharge for s in stats)
     dis_launches = sum(s.sweeps for s in stats)
@@ -274,11 +286,11 @@ def run_ours(args):
                      "traffic": None if traffic is None else round(traffic),
                      "alg_bytes_per_launch": round(alg_bytes / dis_launches),
                      "launch_ms_avg": round(dis_ms / dis_launches, 4)},
-        "e2e": {"value": round(float(e2e.item()) / units, 4), "unit": UNIT,
+        "e2e": {"value": round(job_value(e2e_total, ws, args.steps), 4), "unit": UNIT,
                 "h2d_bytes_per_step": int(inst.cs.nbytes + inst.ct.nbytes + inst.nlink.nbytes),
                 "d2h_bytes_per_step": int(inst.n + 8)},
         "gpu_launches": int(sum(s.launches for s in stats)),
-        "graph_loop": {"value": round(graph_ms / args.steps, 4), "unit": UNIT,
+        "graph_loop": {"value": round(job_value(graph_total, ws, args.steps), 4), "unit": UNIT,
                        "note": "same steps, sweep loop as one CUDA graph with a device-side while node"},
         "clocks": clk.summary(),
     }
