@@ -194,6 +194,11 @@ mf_status mf_flow_value(mf_grid *g, int64_t *out);
  */
 mf_status mf_get_residual(mf_grid *g, int32_t *res, int32_t *tres, int32_t *exc, int on_device);
 
+/* The residual network of the last solve (or of the current sweep): the
+ * same as mf_get_residual(g, residual_out, NULL, NULL, 0): host int32[2H][n],
+ * residual_out[d*n + v] = c_f(v -> v + D(d)).  NULL is a no-op. */
+mf_status mf_get_flow(mf_grid *g, int32_t *residual_out);
+
 /* Current labeling d (int32[n], values 0..d_inf) and d_inf. */
 mf_status mf_get_labels(mf_grid *g, int32_t *lab, int32_t *d_inf, int on_device);
 
@@ -273,6 +278,11 @@ int64_t mf_cnn_num_params(const mf_cnn *c);
 mf_status mf_cnn_get_params(mf_cnn *c, float *out, int on_device);
 mf_status mf_cnn_set_params(mf_cnn *c, const float *in, int on_device);
 mf_status mf_cnn_get_grads(mf_cnn *c, float *out, int on_device);
+/* Load the parameters from a NumPy .npy file (little-endian float32 vector of
+ * exactly mf_cnn_num_params entries, as written by the trainer); resets the
+ * optimiser state.  MF_EINVAL with the reason in mf_cnn_last_error on a
+ * missing file, another dtype or shape, or a truncated file. */
+mf_status mf_load_model(mf_cnn *c, const char *path);
 mf_status mf_cnn_forward(mf_cnn *c, const float *x, int N, int H, int W, float *y);
 /* Inference only (no state kept for backward): the same network on the tensor
  * cores, with BF16 activations between layers (the input is rounded to BF16,

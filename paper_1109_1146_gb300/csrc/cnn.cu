@@ -14,6 +14,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -554,6 +556,46 @@ mf_status mf_cnn_set_params(mf_cnn *c, const float *in, int on_device) {
     c->steps = 0;
     CKC(cudaStreamSynchronize(c->stream));
     return MF_OK;
+}
+
+// Parameters from a NumPy .npy file holding a little-endian float32 vector
+// of exactly num_params entries (format versions 1-3).
+mf_status mf_load_model(mf_cnn *c, const char *path) {
+    if (!c || !path) return cnn_fail(c, MF_EINVAL, "null argument");
+    FILE *f = fopen(path, "rb");
+    if (!f) return cnn_fail(c, MF_EINVAL, std::string("cannot open ") + path);
+    auto bad = [&](const std::string &m) {
+        fclose(f);
+        return cnn_fail(c, MF_EINVAL, std::string(path) + ": " + m);
+    };
+    unsigned char pre[8];
+    if (fread(pre, 1, 8, f) != 8 || memcmp(pre, "\x93NUMPY", 6) != 0) return bad("not a .npy file");
+    size_t hlen = 0;
+    if (pre[6] == 1) {
+        unsigned char b[2];
+        if (fread(b, 1, 2, f) != 2) return bad("truncated header");
+        hlen = (size_t)b[0] | ((size_t)b[1] << 8);
+    } else if (pre[6] == 2 || pre[6] == 3) {
+        unsigned char b[4];
+        if (fread(b, 1, 4, f) != 4) return bad("truncated header");
+        hlen = (size_t)b[0] | ((size_t)b[1] << 8) | ((size_t)b[2] << 16) | ((size_t)b[3] << 24);
+    } else {
+        return bad("unsupported .npy version");
+    }
+    if (hlen > (1u << 20)) return bad("header too long");
+    std::string h(hlen, '\0');
+    if (fread(&h[0], 1, hlen, f) != hlen) return bad("truncated header");
+    if (h.find("'descr': '<f4'") == std::string::npos) return bad("dtype is not little-endian float32");
+    if (h.find("'fortran_order': False") == std::string::npos) return bad("Fortran order");
+    const size_t sp = h.find("'shape': (");
+    if (sp == std::string::npos) return bad("no shape");
+    const long long cnt = strtoll(h.c_str() + sp + 10, nullptr, 10);
+    if (cnt != (long long)c->nparam || h.find(",)", sp) == std::string::npos)
+        return bad("shape does not match the network's " + std::to_string(c->nparam) + " parameters");
+    std::vector<float> buf(c->nparam);
+    if (fread(buf.data(), 4, c->nparam, f) != c->nparam) return bad("truncated data");
+    fclose(f);
+    return mf_cnn_set_params(c, buf.data(), 0);
 }
 
 mf_status mf_cnn_get_grads(mf_cnn *c, float *out, int on_device) {

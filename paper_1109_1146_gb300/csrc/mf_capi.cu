@@ -1471,6 +1471,12 @@ mf_status mf_get_residual(mf_grid *g, int32_t *res, int32_t *tres, int32_t *exc,
     return MF_OK;
 }
 
+mf_status mf_get_flow(mf_grid *g, int32_t *residual_out) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!residual_out) return MF_OK;
+    return mf_get_residual(g, residual_out, nullptr, nullptr, 0);
+}
+
 mf_status mf_get_labels(mf_grid *g, int32_t *lab, int32_t *d_inf, int on_device) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (d_inf) *d_inf = g->g.dinf;

@@ -24,7 +24,7 @@ STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "
 EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
            "mf_finish", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
            "mf_last_error", "mf_min_cut_2d_noalloc", "mf_solve_batch", "mf_warm_features", "mf_warm_targets",
-           "mf_warm_start", "mf_certify", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
+           "mf_warm_start", "mf_certify", "mf_get_flow", "mf_load_model", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
            "mf_cnn_get_params", "mf_cnn_set_params", "mf_cnn_get_grads", "mf_cnn_forward", "mf_cnn_infer",
            "mf_cnn_zero_grad",
            "mf_cnn_backward", "mf_cnn_mse", "mf_cnn_adam_step"]
@@ -79,6 +79,8 @@ SIGNATURES = {
     "mf_warm_features": (_I, [_P, _P]),
     "mf_warm_targets": (_I, [_P, _P]),
     "mf_warm_start": (_I, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "mf_get_flow": (_I, [_P, _P]),
+    "mf_load_model": (_I, [_P, ctypes.c_char_p]),
     "mf_certify": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32)]),
     "mf_cnn_create": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.c_uint64, _P]),
     "mf_cnn_destroy": (_I, [_P]),
@@ -301,6 +303,12 @@ class Grid:
         self._check(self._lib.mf_certify(self._h, ctypes.byref(cut), ctypes.byref(bad), ctypes.byref(ok)))
         return bool(ok.value), cut.value, bad.value
 
+    def get_flow(self):
+        """Residual capacities int32[2H, n] (mf_get_flow)."""
+        res = np.empty((self.H * 2, self.n), dtype=np.int32)
+        self._check(self._lib.mf_get_flow(self._h, res.ctypes.data))
+        return res
+
     def get_labels(self):
         lab = np.empty(self.n, dtype=np.int32)
         dinf = ctypes.c_int32()
@@ -360,6 +368,10 @@ class CNN:
     def infer(self, x, y):
         N, C, H, W = x.shape
         self._check(self._lib.mf_cnn_infer(self._h, x.data_ptr(), N, H, W, y.data_ptr()))
+
+    def load(self, path):
+        """Parameters from a .npy file (mf_load_model)."""
+        self._check(self._lib.mf_load_model(self._h, os.fsencode(path)))
 
     def zero_grad(self):
         self._check(self._lib.mf_cnn_zero_grad(self._h))

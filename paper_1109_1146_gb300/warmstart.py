@@ -123,7 +123,7 @@ def save_weights(cnn: CNN, path: str, meta: dict):
 
 def load_network(path: str, conn: int = 4) -> CNN:
     net = CNN(channels=channels(conn), seed=0)
-    net.set_params(np.load(path))
+    net.load(path)
     return net
 
 

@@ -176,3 +176,22 @@ def test_3d_global_relabel_keeps_exact_results(tile, kw):
     got = gpu_solve(inst, tile=tile, opts=opts(**kw))
     assert_parity(inst, got)
     assert got["stats"].global_relabels >= 1
+
+
+def test_resume_after_sweep_cap_and_get_flow():
+    # a sweep cap leaves a consistent state: the caller can keep sweeping and
+    # finish, with exact results; mf_get_flow is the residual of mf_get_residual
+    from paper_1109_1146_gb300 import Grid, MFError
+    inst = grids.segmentation_2d(230, 170, 8, conn=8, hard_seed_frac=0.03)
+    with Grid(inst.dims, 8) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        with pytest.raises(MFError, match="SWEEPLIMIT"):
+            g.solve(opts(max_sweeps=1))
+        for _ in range(10000):
+            if g.sweep() == 0:
+                break
+        g.finish()
+        got = {"flow": g.flow_value(), "smin": g.get_cut(0), "smax": g.get_cut(1)}
+        got["res"], got["tres"], got["exc"] = g.get_residual()
+        np.testing.assert_array_equal(g.get_flow(), got["res"])
+    assert_parity(inst, got)

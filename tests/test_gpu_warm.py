@@ -202,3 +202,19 @@ def test_batched_warm_start_is_exact():
             assert_parity(inst, got)
     for g in handles:
         g.close()
+
+
+def test_load_model_reads_the_trainers_file(tmp_path):
+    net = mf.CNN(channels=6, seed=5)
+    net.load(WEIGHTS)
+    np.testing.assert_array_equal(net.get_params(), np.load(WEIGHTS))
+    bad = tmp_path / "short.npy"
+    np.save(bad, np.zeros(10, dtype=np.float32))
+    with pytest.raises(mf.MFError, match="shape"):
+        net.load(str(bad))
+    f64 = tmp_path / "f64.npy"
+    np.save(f64, np.zeros(net.num_params, dtype=np.float64))
+    with pytest.raises(mf.MFError, match="float32"):
+        net.load(str(f64))
+    with pytest.raises(mf.MFError, match="cannot open"):
+        net.load(str(tmp_path / "missing.npy"))
