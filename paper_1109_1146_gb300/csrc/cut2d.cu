@@ -81,13 +81,11 @@ __device__ __forceinline__ u64 fill_row(u64 g, u64 pl, u64 pr) {
     return a | b;
 }
 
-// One pass: every 64x64 block closes its part of the set (one warp per block).
+// One 64x64 block closes its part of the set (one warp, in place); returns
+// whether it grew.
 template <int CONN>
-__global__ void cut_pass2d_kernel(const Geom g, int W64, int BY, const u64 *__restrict__ M, u64 *S,
-                                  int *changed) {
+__device__ bool cut_block2d(const Geom &g, int W64, int blk, const u64 *__restrict__ M, u64 *S) {
     const int lane = threadIdx.x & 31;
-    const int blk = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (blk >= W64 * BY) return;
     const int bx = blk % W64, by = blk / W64;
     const size_t plane = (size_t)g.Y * W64;
     auto word = [&](const u64 *A, int y, int w) -> u64 {
@@ -146,8 +144,34 @@ __global__ void cut_pass2d_kernel(const Geom g, int W64, int BY, const u64 *__re
             const int y = by * 64 + 2 * lane + j;
             if (y < g.Y && s[j] != s0[j]) S[(size_t)y * W64 + bx] = s[j];
         }
-        if (lane == 0) *changed = 1;
     }
+    return grew;
+}
+
+// Passes over all blocks (a warp each) until a pass adds nothing, in one
+// cooperative launch; flags[3] triple-buffered "grew" words as in the relabel.
+template <int CONN>
+__global__ void cut_closure2d_kernel(const Geom g, int W64, int BY, const u64 *__restrict__ M, u64 *S, int *flags,
+                                     int *passes_out, int max_passes) {
+    cg::grid_group grid = cg::this_grid();
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        flags[1] = 0;
+        flags[2] = 0;
+    }
+    grid.sync();
+    int pass = 1;  // the words of passes 1 and 2 were cleared above; pass p clears those of p + 1
+    for (; pass <= max_passes; ++pass) {
+        bool grew = false;
+        for (int b = wid; b < W64 * BY; b += nwarps) grew |= cut_block2d<CONN>(g, W64, b, M, S);
+        if (grew && lane == 0) atomicOr(&flags[pass % 3], 1);
+        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(pass + 1) % 3] = 0;
+        grid.sync();
+        if (!*(volatile int *)&flags[pass % 3]) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *passes_out = pass;
 }
 
 // S_min / S_max bytes from the two closures
@@ -469,20 +493,32 @@ static cudaError_t cut2d_impl(const Geom &g, const DevState &st, void *scratch, 
     u64 *Tset = Smin + plane;
     const size_t total = (size_t)W64 * 64 * g.Y;
     const int mb = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
-    const int blocks = (W64 * BY + 7) / 8;
+    static int max_blocks = 0;
+    if (!max_blocks) {
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cut_closure2d_kernel<CONN>, 256, 0);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        max_blocks = per_sm * sms;
+        if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    }
+    const int blocks = std::min((W64 * BY + 7) / 8, max_blocks);
     for (int which = 0; which < 2; ++which) {
         u64 *Sset = which == 0 ? Smin : Tset;
         cut_masks_kernel<CONN><<<mb, 256, 0, s>>>(g, st, W64, which, (unsigned *)M, (unsigned *)Sset);
-        for (;;) {
-            cudaError_t e = cudaMemsetAsync(&st.ctr[kChanged], 0, 4, s);
-            if (e != cudaSuccess) return e;
-            cut_pass2d_kernel<CONN><<<blocks, 256, 0, s>>>(g, W64, BY, M, Sset, &st.ctr[kChanged]);
-            e = cudaMemcpyAsync(h_changed, &st.ctr[kChanged], 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return e;
-            ++*passes;
-            if (!*h_changed) break;
-        }
+        Geom gg = g;
+        int w64 = W64, by = BY, max_passes = 1 << 20;
+        const u64 *pm = M;
+        u64 *ps = Sset;
+        int *flags = &st.ctr[kGlrFlags], *cnt = &st.ctr[kGlrLevels];
+        void *args[] = {&gg, &w64, &by, (void *)&pm, &ps, &flags, &cnt, &max_passes};
+        cudaError_t e = cudaLaunchCooperativeKernel((const void *)cut_closure2d_kernel<CONN>, dim3(blocks), dim3(256),
+                                                    args, 0, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_changed, cnt, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        *passes += *h_changed;
     }
     const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, 152 * 32);
     cut_bytes_kernel<<<nb, 256, 0, s>>>(g, W64, Smin, Tset, smin, smax);

@@ -277,8 +277,8 @@ __global__ void closure3d_kernel(const Geom g, int W32, const u32 *__restrict__ 
         flags[2] = 0;
     }
     grid.sync();
-    int pass = 0;
-    for (; pass < max_passes; ++pass) {
+    int pass = 1;  // the words of passes 1 and 2 were cleared above; pass p clears those of p + 1
+    for (; pass <= max_passes; ++pass) {
         bool grew = false;
         for (int r = wid; r < g.nreg; r += nwarps)
             grew |= glr3d_region<TY, TZ>(g, W32, r, M, nullptr, S, S, 1, nullptr);
@@ -287,7 +287,7 @@ __global__ void closure3d_kernel(const Geom g, int W32, const u32 *__restrict__ 
         grid.sync();
         if (!*(volatile int *)&flags[pass % 3]) break;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *passes_out = pass + 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *passes_out = pass;
 }
 
 __global__ void cut3d_bytes_kernel(const Geom g, int W32, const u32 *Smin, const u32 *Tset, unsigned char *smin,

@@ -1,8 +1,9 @@
 // Allocation-free cut extraction for 2D grids (mf_min_cut_2d_noalloc).
 //
 // Same kernels as the cut extraction at the end of mf_solve (cut2d.cu: residual
-// bit masks, block-wise closure passes), but every scratch byte they need
-// lives in one file-scope device array instead of memory from cudaMalloc.
+// bit masks, block-wise closure passes in one cooperative launch), but every
+// scratch byte they need lives in one file-scope device array instead of
+// memory from cudaMalloc.
 // The array is part of the library image: each GPU that loads the library
 // holds it until the process exits.
 #include <cstdint>
@@ -14,7 +15,7 @@
 
 namespace {
 
-constexpr size_t kCtrBytes = 256;                   // counter words (changed flag)
+constexpr size_t kCtrBytes = 256;                   // counter words (closure flags, pass count)
 constexpr size_t kStaticScratchBytes = 8u << 20;    // 8 MiB in total
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kStaticScratchBytes];
@@ -89,7 +90,7 @@ extern "C" mf_status mf_min_cut_2d_noalloc(const int64_t dims[2], int connectivi
     st.cap = const_cast<int *>(res);
     st.tcap = const_cast<int *>(tres);
     st.exc = const_cast<int *>(exc);
-    st.ctr = (int *)base;  // the pass loop clears the words it uses before each pass
+    st.ctr = (int *)base;  // the closure kernel clears the flag words it uses
     int h_changed = 0, passes = 0;
     e = cut2d(connectivity, g, st, (unsigned char *)base + kCtrBytes, smin, smax, &h_changed, &passes,
               (cudaStream_t)cuda_stream);
