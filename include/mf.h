@@ -105,8 +105,8 @@ void mf_default_opts(mf_opts *opts);
  *   connectivity  4 or 8 for ndim = 2, 6 for ndim = 3;
  *   tile          region shape {tx, ty, tz}: the fixed partition of V into
  *                 regions R_k of Sec. 3 is the tiling of the grid by this
- *                 shape (edge tiles may be ragged).  Supported: 2D 64x64 and
- *                 32x32, 3D 32x16x8, 32x8x8 (bit-parallel discharge),
+ *                 shape (edge tiles may be ragged).  Supported: 2D 64x64,
+ *                 64x32 and 32x32, 3D 32x16x8, 32x8x8 (bit-parallel discharge),
  *                 16x16x16 and 8x8x8; NULL or {0,0,0} picks 32x32 (2D) /
  *                 32x8x8 (3D);
  *   cuda_stream   cudaStream_t to order all work on, or NULL for a stream

@@ -18,9 +18,9 @@ from .mf import Grid, default_opts
 
 # (tile, schedule) candidates per connectivity
 CANDIDATES = {
-    4: [((64, 64, 1), {}), ((32, 32, 1), {}), ((64, 64, 1), {"partial_discharge": 1}),
+    4: [((64, 64, 1), {}), ((32, 32, 1), {}), ((64, 32, 1), {}), ((64, 64, 1), {"partial_discharge": 1}),
         ((32, 32, 1), {"partial_discharge": 1})],
-    8: [((64, 64, 1), {}), ((32, 32, 1), {}), ((64, 64, 1), {"partial_discharge": 1}),
+    8: [((64, 64, 1), {}), ((32, 32, 1), {}), ((64, 32, 1), {}), ((64, 64, 1), {"partial_discharge": 1}),
         ((32, 32, 1), {"partial_discharge": 1})],
     6: [((32, 8, 8), {}), ((32, 16, 8), {}), ((16, 16, 16), {}), ((32, 8, 8), {"partial_discharge": 1})],
 }

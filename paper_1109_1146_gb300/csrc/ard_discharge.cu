@@ -414,6 +414,8 @@ static cudaError_t launch_one(const Geom &g, const DevState &st, const SweepArgs
     X(8, 64, 64, 1, 1024)           \
     X(4, 32, 32, 1, 256)            \
     X(8, 32, 32, 1, 256)            \
+    X(4, 64, 32, 1, 256)            \
+    X(8, 64, 32, 1, 256)            \
     X(6, 16, 16, 16, 1024)          \
     X(6, 8, 8, 8, 256)              \
     X(6, 32, 16, 8, 1024)           \

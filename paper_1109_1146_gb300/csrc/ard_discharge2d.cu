@@ -698,7 +698,7 @@ static cudaError_t launch2d(const Geom &g, const DevState &st, const SweepArgs &
 }
 
 bool discharge2d_supported(int conn, int tx, int ty) {
-    return (conn == 4 || conn == 8) && ((tx == 64 && ty == 64) || (tx == 32 && ty == 32));
+    return (conn == 4 || conn == 8) && ((tx == 64 && ty == 64) || (tx == 32 && ty == 32) || (tx == 64 && ty == 32));
 }
 
 cudaError_t launch_discharge2d_batch(int conn, int tx, int ty, const Inst *insts, const int2 *items,
@@ -708,6 +708,8 @@ cudaError_t launch_discharge2d_batch(int conn, int tx, int ty, const Inst *insts
     if (conn == 8 && tx == 64 && ty == 64) return launch2d_batch<8, 64, 64, 512>(insts, items, count, head, sa, blocks, stream);
     if (conn == 4 && tx == 32 && ty == 32) return launch2d_batch<4, 32, 32, 256>(insts, items, count, head, sa, blocks, stream);
     if (conn == 8 && tx == 32 && ty == 32) return launch2d_batch<8, 32, 32, 256>(insts, items, count, head, sa, blocks, stream);
+    if (conn == 4 && tx == 64 && ty == 32) return launch2d_batch<4, 64, 32, 256>(insts, items, count, head, sa, blocks, stream);
+    if (conn == 8 && tx == 64 && ty == 32) return launch2d_batch<8, 64, 32, 256>(insts, items, count, head, sa, blocks, stream);
     return cudaErrorInvalidValue;
 }
 
@@ -717,6 +719,8 @@ cudaError_t launch_discharge2d(int conn, const Geom &g, const DevState &st, cons
     if (conn == 8 && g.tx == 64 && g.ty == 64) return launch2d<8, 64, 64, 512>(g, st, sa, stream);
     if (conn == 4 && g.tx == 32 && g.ty == 32) return launch2d<4, 32, 32, 256>(g, st, sa, stream);
     if (conn == 8 && g.tx == 32 && g.ty == 32) return launch2d<8, 32, 32, 256>(g, st, sa, stream);
+    if (conn == 4 && g.tx == 64 && g.ty == 32) return launch2d<4, 64, 32, 256>(g, st, sa, stream);
+    if (conn == 8 && g.tx == 64 && g.ty == 32) return launch2d<8, 64, 32, 256>(g, st, sa, stream);
     return cudaErrorInvalidValue;
 }
 

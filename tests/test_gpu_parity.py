@@ -33,6 +33,8 @@ CASES = [
     ((130, 70, 1), 8, (64, 64, 1)),
     ((97, 61, 1), 4, (32, 32, 1)),
     ((75, 90, 1), 8, (32, 32, 1)),
+    ((150, 77, 1), 8, (64, 32, 1)),
+    ((131, 100, 1), 4, (64, 32, 1)),
     ((40, 35, 20), 6, (16, 16, 16)),
     ((21, 19, 13), 6, (8, 8, 8)),
     ((70, 37, 21), 6, (32, 16, 8)),
