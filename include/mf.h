@@ -106,9 +106,9 @@ void mf_default_opts(mf_opts *opts);
  *   tile          region shape {tx, ty, tz}: the fixed partition of V into
  *                 regions R_k of Sec. 3 is the tiling of the grid by this
  *                 shape (edge tiles may be ragged).  Supported: 2D 64x64,
- *                 64x32 and 32x32, 3D 32x16x8, 32x8x8 (bit-parallel discharge),
- *                 16x16x16 and 8x8x8; NULL or {0,0,0} picks 32x32 (2D) /
- *                 32x8x8 (3D);
+ *                 64x32 and 32x32, 3D 32x16x8, 32x8x8, 32x8x4 (bit-parallel
+ *                 discharge), 16x16x16 and 8x8x8; NULL or {0,0,0} picks 32x32
+ *                 (2D) / 32x8x4 (3D);
  *   cuda_stream   cudaStream_t to order all work on, or NULL for a stream
  *                 owned by the handle (non-blocking: device buffers that
  *                 other streams produce or consume must then be ordered by

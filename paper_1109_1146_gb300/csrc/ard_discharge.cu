@@ -419,7 +419,8 @@ static cudaError_t launch_one(const Geom &g, const DevState &st, const SweepArgs
     X(6, 16, 16, 16, 1024)          \
     X(6, 8, 8, 8, 256)              \
     X(6, 32, 16, 8, 1024)           \
-    X(6, 32, 8, 8, 256)
+    X(6, 32, 8, 8, 256)             \
+    X(6, 32, 8, 4, 256)
 
 bool discharge_supported(int conn, int tx, int ty, int tz) {
 #define X(c, a, b, z, t) if (conn == c && tx == a && ty == b && tz == z) return true;

@@ -658,12 +658,13 @@ static cudaError_t launch3d_batch(const Inst *insts, const int2 *items, const in
 }
 
 bool discharge3d_supported(int tx, int ty, int tz) {
-    return tx == 32 && ((ty == 16 && tz == 8) || (ty == 8 && tz == 8));
+    return tx == 32 && ((ty == 16 && tz == 8) || (ty == 8 && tz == 8) || (ty == 8 && tz == 4));
 }
 
 cudaError_t launch_discharge3d(const Geom &g, const DevState &st, const SweepArgs &sa, cudaStream_t stream) {
     if (g.tx == 32 && g.ty == 16 && g.tz == 8) return launch3d<16, 8, 512>(g, st, sa, stream);
     if (g.tx == 32 && g.ty == 8 && g.tz == 8) return launch3d<8, 8, 256>(g, st, sa, stream);
+    if (g.tx == 32 && g.ty == 8 && g.tz == 4) return launch3d<8, 4, 256>(g, st, sa, stream);
     return cudaErrorInvalidValue;
 }
 
@@ -671,6 +672,7 @@ cudaError_t launch_discharge3d_batch(int tx, int ty, int tz, const Inst *insts, 
                                      int *head, const SweepArgs &sa, int blocks, cudaStream_t stream) {
     if (tx == 32 && ty == 16 && tz == 8) return launch3d_batch<16, 8, 512>(insts, items, count, head, sa, blocks, stream);
     if (tx == 32 && ty == 8 && tz == 8) return launch3d_batch<8, 8, 256>(insts, items, count, head, sa, blocks, stream);
+    if (tx == 32 && ty == 8 && tz == 4) return launch3d_batch<8, 4, 256>(insts, items, count, head, sa, blocks, stream);
     return cudaErrorInvalidValue;
 }
 

@@ -345,10 +345,13 @@ cudaError_t cut3d(const Geom &g, const DevState &st, void *scratch, unsigned cha
                   int *h_changed, int *passes, cudaStream_t s) {
     if (g.ty == 16 && g.tz == 8) return cut3d_impl<16, 8>(g, st, scratch, smin, smax, h_changed, passes, s);
     if (g.ty == 8 && g.tz == 8) return cut3d_impl<8, 8>(g, st, scratch, smin, smax, h_changed, passes, s);
+    if (g.ty == 8 && g.tz == 4) return cut3d_impl<8, 4>(g, st, scratch, smin, smax, h_changed, passes, s);
     return cudaErrorInvalidValue;
 }
 
-bool glr3d_supported(const Geom &g) { return g.tx == 32 && g.tz > 1 && ((g.ty == 16 && g.tz == 8) || (g.ty == 8 && g.tz == 8)); }
+bool glr3d_supported(const Geom &g) {
+    return g.tx == 32 && g.tz > 1 && ((g.ty == 16 && g.tz == 8) || (g.ty == 8 && g.tz == 8) || (g.ty == 8 && g.tz == 4));
+}
 
 size_t glr3d_scratch_bytes(const Geom &g) {
     const size_t words = (size_t)g.Z * g.Y * ((g.X + 31) / 32);
@@ -409,6 +412,7 @@ static cudaError_t glr3d_impl(const Geom &g, const DevState &st, void *scratch, 
 cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels, cudaStream_t s) {
     if (g.ty == 16 && g.tz == 8) return glr3d_impl<16, 8>(g, st, scratch, h_changed, levels, s);
     if (g.ty == 8 && g.tz == 8) return glr3d_impl<8, 8>(g, st, scratch, h_changed, levels, s);
+    if (g.ty == 8 && g.tz == 4) return glr3d_impl<8, 4>(g, st, scratch, h_changed, levels, s);
     return cudaErrorInvalidValue;
 }
 

@@ -196,9 +196,10 @@ __device__ __forceinline__ void fuse_region(const Geom &g, const DevState &st, c
             }
             const size_t w = ((size_t)wz * g.Y + wy) * g.X + wx;
             const bool discw = st.disc[rw];
-            const int dw = discw ? st.lab_next[w] : st.lab[w];
             const int pu = discr ? st.bout[(size_t)d * n + u] : 0;
             const int pw = discw ? st.bout[(size_t)(d ^ 1) * n + w] : 0;
+            if (!(pu | pw)) continue;  // no flow crossed this arc: nothing to accept or return
+            const int dw = discw ? st.lab_next[w] : st.lab[w];
             const int back = (dw <= du + 1 ? 0 : pu) + (du <= dw + 1 ? pw : 0);
             if (back) {
                 st.cap[(size_t)d * n + u] += back;
@@ -333,9 +334,10 @@ __global__ void fuse2d_kernel(const Geom g, const DevState st) {
             }
             const size_t w = (size_t)wy * g.X + wx;
             const bool discw = st.disc[rw];
-            const int dw = discw ? st.lab_next[w] : st.lab[w];
             const int pu = discr ? st.bout[(size_t)d * n + u] : 0;
             const int pw = discw ? st.bout[(size_t)(d ^ 1) * n + w] : 0;
+            if (!(pu | pw)) continue;  // no flow crossed this arc: nothing to accept or return
+            const int dw = discw ? st.lab_next[w] : st.lab[w];
             const int back = (dw <= du + 1 ? 0 : pu) + (du <= dw + 1 ? pw : 0);
             if (back) {
                 st.cap[(size_t)d * n + u] += back;
@@ -751,7 +753,7 @@ mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int con
     long long nll = X * Y * Z;
     if (nll > (1ll << 31) - 1) return fail(nullptr, MF_EINVAL, "more than 2^31-1 vertices");
     int tx = 32, ty = 32, tz = 1;
-    if (ndim == 3) { tx = 32; ty = 8; tz = 8; }
+    if (ndim == 3) { tx = 32; ty = 8; tz = 4; }
     if (tile && (tile[0] | tile[1] | tile[2])) {
         tx = tile[0];
         ty = tile[1];

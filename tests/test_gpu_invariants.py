@@ -71,7 +71,7 @@ def check_state(inst, res, tres, exc, lab, dinf, inB, targets):
     (4, (192, 160, 1), (64, 64, 1), 0), (8, (150, 130, 1), (64, 64, 1), 0),
     (8, (100, 90, 1), (32, 32, 1), 0), (4, (120, 96, 1), (32, 32, 1), 1), (8, (140, 70, 1), (64, 32, 1), 0),
     (6, (40, 36, 30), (16, 16, 16), 0), (6, (24, 20, 18), (8, 8, 8), 1),
-    (6, (70, 36, 20), (32, 16, 8), 0), (6, (40, 20, 18), (32, 8, 8), 1)])
+    (6, (70, 36, 20), (32, 16, 8), 0), (6, (40, 20, 18), (32, 8, 8), 1), (6, (50, 20, 14), (32, 8, 4), 0)])
 @pytest.mark.parametrize("variant,glr", [(0, 0), (1, 0), (0, 1)])
 def test_sweep_invariants(conn, dims, tile, partial, variant, glr):
     inst = (grids.volume_3d(*dims, seed=2) if conn == 6 else

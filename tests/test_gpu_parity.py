@@ -40,6 +40,7 @@ CASES = [
     ((70, 37, 21), 6, (32, 16, 8)),
     ((45, 30, 19), 6, (32, 8, 8)),
     ((96, 48, 24), 6, (32, 16, 8)),
+    ((70, 30, 22), 6, (32, 8, 4)),
 ]
 
 
