@@ -166,8 +166,10 @@ mf_status mf_finish(mf_grid *g);
  * has no active region.  All work is ordered on grids[0]'s stream.  Per
  * instance results are then read as after mf_solve (mf_get_cut,
  * mf_flow_value); stats (nullable) receives count entries (the ms_* fields
- * are those of the whole batch).  The global relabel option is not applied
- * in batched solves.  With opts->warm_start = 1 each grid starts from its
+ * are those of the whole batch).  The global relabel (opts->
+ * global_relabel_period) runs for every unfinished instance that supports it
+ * after the same sweeps as in a single solve, so each instance takes the same
+ * sweeps as alone.  With opts->warm_start = 1 each grid starts from its
  * projected preflow if mf_warm_start succeeded on it, and from Init
  * otherwise.  With opts->graph_loop = 1 the sweep loop of the batch is one
  * CUDA graph.

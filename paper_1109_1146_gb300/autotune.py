@@ -4,9 +4,8 @@ class), for batched solves and for single solves.
 For every class present in a list of instances it solves one representative
 instance (real data from the list) with each candidate configuration through
 the C ABI, keeps the fastest by the library's own device timing, and caches
-the choice in a JSON file so later runs reuse it.  Batched solves run no
-global relabel, so their candidates vary the tile and partial discharges;
-single solves also vary the global-relabel period (2D).
+the choice in a JSON file so later runs reuse it.  Candidates vary the tile,
+partial discharges and the global-relabel period.
 """
 from __future__ import annotations
 
@@ -26,16 +25,23 @@ CANDIDATES = {
 }
 
 
-# global-relabel periods tried for single 2D solves (0 = never)
+# global-relabel periods tried (0 = never); the relabel exists for 2D tiles and
+# for 3D tiles 32 voxels wide
 GLR_PERIODS = (0, 4, 8)
 
 
-def candidates(conn: int, single: bool):
-    """(tile, opts kwargs) candidates of one connectivity."""
-    base = CANDIDATES[conn]
-    if not single or conn == 6:
-        return [(t, dict(kw, global_relabel_period=0)) for t, kw in base]
-    return [(t, dict(kw, global_relabel_period=p)) for t, kw in base for p in GLR_PERIODS]
+def _relabel_supported(conn: int, tile) -> bool:
+    return conn != 6 or tile[0] == 32
+
+
+def candidates(conn: int, single: bool = False):
+    """(tile, opts kwargs) candidates of one connectivity (the same for single
+    and batched solves; `single` only separates the cache entries)."""
+    out = []
+    for t, kw in CANDIDATES[conn]:
+        periods = GLR_PERIODS if _relabel_supported(conn, t) else (0,)
+        out += [(t, dict(kw, global_relabel_period=p)) for p in periods]
+    return out
 
 
 def size_class(dims) -> int:

@@ -432,7 +432,8 @@ __global__ void batch_loop_ctl_kernel(const int *any, int *lc, cudaGraphConditio
     const int s = lc[kLoopSweep] + 1;
     lc[kLoopSweep] = s;
     lc[kLoopActive] = *any;
-    cudaGraphSetConditional(handle, (*any && s < lc[kLoopCap]) ? 1u : 0u);
+    const int P = lc[kLoopPeriod];
+    cudaGraphSetConditional(handle, (*any && s < lc[kLoopCap] && !(P > 0 && s % P == 0)) ? 1u : 0u);
 }
 
 // ---- batched sweep kernels: one block per (instance, region) of the batch table
@@ -492,6 +493,16 @@ __global__ void batch_end_kernel(const Inst *insts, unsigned char *done, int *sw
         const int *c = insts[i].st.ctr;
         sweeps[i] += 1;
         if (c[kActiveRegions] == 0 || c[kError]) done[i] = 1;
+        else atomicAdd(any, 1);
+    }
+}
+
+// after a relabel of the batch: instances left without an active region are
+// done (as a single solve stops there); any = instances still active
+__global__ void batch_relabel_end_kernel(const Inst *insts, unsigned char *done, int *any, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        if (done[i]) continue;
+        if (insts[i].st.ctr[kActiveRegions] == 0) done[i] = 1;
         else atomicAdd(any, 1);
     }
 }
@@ -1161,6 +1172,33 @@ struct BatchBufs {
     }
 };
 
+// The global relabel of every unfinished instance of a batch that supports it,
+// on the batch stream (as after a sweep of a single solve: same sequence).
+// Returns in *any_left the number of instances still active afterwards.
+static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *insts, unsigned char *done_dev,
+                               int *any_dev, int *any_left, cudaStream_t s) {
+    mf_grid *g = grids[0];
+    std::vector<unsigned char> done(count);
+    CK(cudaMemcpyAsync(done.data(), done_dev, count, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i) {
+        mf_grid *h = grids[i];
+        if (done[i] || !glr_supported(h)) continue;
+        int levels = 0;
+        const cudaError_t e = h->ndim == 2 ? glr2d(h->conn, h->g, h->st, h->cut_scratch, h->h_ctr, &levels, s)
+                                           : glr3d(h->g, h->st, h->cut_scratch, h->h_ctr, &levels, s);
+        if (e != cudaSuccess) return fail(g, MF_ECUDA, std::string("batched global relabel: ") + cudaGetErrorString(e));
+        h->stats.global_relabels++;
+        h->stats.relabel_levels += levels;
+    }
+    CK(cudaMemsetAsync(any_dev, 0, sizeof(int), s));
+    batch_relabel_end_kernel<<<(count + 255) / 256, 256, 0, s>>>(insts, done_dev, any_dev, count);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(any_left, any_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return MF_OK;
+}
+
 mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, mf_stats *stats) {
     mf_grid *g = nullptr;  // for CK: errors are reported on the first handle
     if (!grids || count < 1) return fail(nullptr, MF_EINVAL, "grids must be a non-empty array");
@@ -1290,6 +1328,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         CK(cudaMalloc(&B.loop, sizeof(int) * kLoopWords));
         int init[kLoopWords] = {0};
         init[kLoopCap] = (int)std::min<long long>(cap, INT_MAX);
+        init[kLoopPeriod] = std::max(0, o.global_relabel_period);
         memcpy(g->h_ctr, init, sizeof(init));
         CK(cudaMemcpyAsync(B.loop, g->h_ctr, sizeof(init), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
@@ -1316,13 +1355,26 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         if (e != cudaSuccess || e2 != cudaSuccess)
             return fail(g, MF_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
         CK(cudaGraphInstantiate(&B.exec, B.graph, 0));
-        CK(cudaGraphLaunch(B.exec, s));
-        CK(cudaMemcpyAsync(g->h_ctr, B.loop, sizeof(init), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        launches += (long long)g->h_ctr[kLoopSweep] * (per_sweep + 1);
-        if (g->h_ctr[kLoopActive] && g->h_ctr[kLoopSweep] >= cap)
-            rs = fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left in the batch");
+        int loopst[kLoopWords];
+        for (int before = 0;;) {
+            CK(cudaGraphLaunch(B.exec, s));
+            CK(cudaMemcpyAsync(g->h_ctr, B.loop, sizeof(init), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            memcpy(loopst, g->h_ctr, sizeof(loopst));
+            launches += (long long)(loopst[kLoopSweep] - before) * (per_sweep + 1);
+            before = loopst[kLoopSweep];
+            if (!loopst[kLoopActive]) break;
+            if (loopst[kLoopSweep] >= cap) {
+                rs = fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left in the batch");
+                break;
+            }
+            // stopped at a multiple of the relabel period
+            mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], s);
+            if (st != MF_OK) return st;
+            if (!g->h_ctr[0]) break;
+        }
     } else {
+        const int P = std::max(0, o.global_relabel_period);
         for (int sweep = 0;; ++sweep) {
             CK(enqueue_sweep(s, sweep, nullptr));
             launches += per_sweep;
@@ -1332,6 +1384,11 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
             if (sweep + 1 >= cap) {
                 rs = fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left in the batch");
                 break;
+            }
+            if (P > 0 && (sweep + 1) % P == 0) {
+                mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], s);
+                if (st != MF_OK) return st;
+                if (!g->h_ctr[0]) break;
             }
         }
     }
