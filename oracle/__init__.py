@@ -18,7 +18,11 @@ Augmentation and Push-Relabel"):
                       nothing with max-flow);
   * ``boundary_size`` — |B| of Sec. 4.1 (the union of the region boundaries
                       B^R of Eq. 2) by its definition, and the sweep bound
-                      2|B|^2 + 1 of the P-ARD termination theorem (Sec. 4.4).
+                      2|B|^2 + 1 of the P-ARD termination theorem (Sec. 4.4);
+  * ``region_distance`` — the region distance d* of Sec. 4.1 (eq. 3) by a
+                      0-1 BFS over the residual graph.
+  ``oracle.cnn`` and ``oracle.warm`` hold the float64 warm-start network and
+  the projection of a prediction to a preflow.
 
 Every function here is pinned by the ``-m "not gpu"`` tests against values
 fixed by mathematics (brute force on tiny inputs, closed forms, special
@@ -245,3 +249,58 @@ def sweep_bound(dims, conn, tile):
     """2|B|^2 + 1: the P-ARD sweep bound (Sec. 4.4)."""
     b = boundary_size(dims, conn, tile)
     return 2 * b * b + 1
+
+
+def region_distance(dims, conn, tile, res, tres):
+    """Exact region distance d*(u) (Sec. 4.1, eq. 3): the least number of
+    inter-region arcs on a residual path from u to t, the arcs inside a region
+    counting 0; -1 where t is unreachable.  A 0-1 BFS from {u : c_f(u,t) > 0}
+    over reversed residual arcs (pure Python: small grids only)."""
+    from collections import deque
+    X, Y, Z = _dims(dims).tolist()
+    tx, ty, tz = (tuple(tile) + (1, 1))[:3]
+    n = X * Y * Z
+    H = len(_FWD[conn])
+    res = np.asarray(res, dtype=np.int64).reshape(2 * H, n)
+    RX, RY = (X + tx - 1) // tx, (Y + ty - 1) // ty
+
+    def coords(v):
+        return v % X, (v // X) % Y, v // (X * Y)
+
+    def region(x, y, z):
+        return (z // tz * RY + y // ty) * RX + x // tx
+
+    # in-arcs of w: (u, d) with u + D(d) = w and c_f(u -> w) > 0
+    arcs = []
+    for h, (dx, dy, dz) in enumerate(_FWD[conn]):
+        arcs.append((2 * h, dx, dy, dz))
+        arcs.append((2 * h + 1, -dx, -dy, -dz))
+    dist = np.full(n, -1, dtype=np.int64)
+    q = deque()
+    for v in np.flatnonzero(np.asarray(tres) > 0):
+        dist[v] = 0
+        q.append(int(v))
+    done = np.zeros(n, dtype=bool)
+    while q:
+        w = q.popleft()
+        if done[w]:
+            continue
+        done[w] = True
+        wx, wy, wz = coords(w)
+        rw = region(wx, wy, wz)
+        for d, dx, dy, dz in arcs:
+            ux, uy, uz = wx - dx, wy - dy, wz - dz
+            if not (0 <= ux < X and 0 <= uy < Y and 0 <= uz < Z):
+                continue
+            u = (uz * Y + uy) * X + ux
+            if res[d, u] <= 0:
+                continue
+            c = 0 if region(ux, uy, uz) == rw else 1
+            nd = dist[w] + c
+            if dist[u] < 0 or nd < dist[u]:
+                dist[u] = nd
+                if c == 0:
+                    q.appendleft(u)
+                else:
+                    q.append(u)
+    return dist

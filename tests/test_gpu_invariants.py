@@ -128,3 +128,29 @@ def test_certify_needs_a_finished_solve():
         g.set_caps(inst.cs, inst.ct, inst.nlink)
         with pytest.raises(Exception):
             g.certify()
+
+
+@pytest.mark.parametrize("conn,dims,tile", [(4, (96, 80, 1), (32, 32, 1)), (8, (100, 70, 1), (64, 64, 1)),
+                                            (8, (90, 66, 1), (64, 32, 1)), (6, (64, 24, 20), (32, 8, 4)),
+                                            (6, (40, 30, 20), (32, 8, 8))])
+def test_global_relabel_labels_are_region_distances(conn, dims, tile):
+    # labels stay lower bounds of the region distance d* (non-increasing on
+    # inner residual arcs, +1 at most across regions), so the relabel's
+    # max(d, d*) is d* itself: after every sweep with P = 1 the labels equal
+    # the oracle's 0-1 BFS distances (d_inf where t is unreachable)
+    inst = (grids.volume_3d(*dims, seed=5) if conn == 6 else
+            grids.segmentation_2d(dims[0], dims[1], 5, conn=conn, hard_seed_frac=0.03))
+    checked = 0
+    with Grid(inst.dims, conn, tile=tile) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        g.begin(default_opts(global_relabel_period=1))
+        for _ in range(500):
+            if g.sweep() == 0:
+                break
+            lab, dinf = g.get_labels()
+            res, tres, _ = g.get_residual()
+            d = oracle.region_distance(inst.dims, conn, tile, res, tres)
+            np.testing.assert_array_equal(lab, np.where(d >= 0, d, dinf))
+            checked += 1
+        g.finish()
+    assert checked >= 1

@@ -218,3 +218,28 @@ def test_load_model_reads_the_trainers_file(tmp_path):
         net.load(str(f64))
     with pytest.raises(mf.MFError, match="cannot open"):
         net.load(str(tmp_path / "missing.npy"))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("noise", [0.05, 0.5])
+def test_projection_matches_oracle(conn, noise):
+    # the projected preflow of the library equals the oracle's, bit for bit
+    from oracle import warm as owarm
+    inst = grids.segmentation_2d(97, 83, 5, conn=conn, hard_seed_frac=0.02)
+    t, _ = _solved_targets(inst)
+    gen = torch.Generator(device=DEV).manual_seed(7)
+    pred = (t + noise * torch.randn(t.shape, generator=gen, device=DEV)).contiguous()
+    with Grid(inst.dims, conn) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        _, rounds = g.warm_start(pred)
+        g.begin(default_opts(warm_start=1))
+        res, tres, exc = g.get_residual()
+        g.finish()
+    ref = owarm.project(inst.dims, conn, inst.cs, inst.ct, inst.nlink, pred.cpu().numpy().reshape(conn + 2, -1))
+    assert ref is not None
+    F, ft, E, r = ref
+    assert r == rounds
+    rres, rtres, rexc = owarm.residual(inst.dims, conn, inst.cs, inst.ct, inst.nlink, F, ft)
+    np.testing.assert_array_equal(res, rres)
+    np.testing.assert_array_equal(tres, rtres)
+    np.testing.assert_array_equal(exc, rexc)
