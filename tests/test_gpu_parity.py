@@ -198,3 +198,22 @@ def test_resume_after_sweep_cap_and_get_flow():
         got["res"], got["tres"], got["exc"] = g.get_residual()
         np.testing.assert_array_equal(g.get_flow(), got["res"])
     assert_parity(inst, got)
+
+
+@pytest.mark.parametrize("conn,tile", [(8, (32, 32, 1)), (4, (64, 64, 1)), (6, (32, 8, 4))])
+def test_round_cap_reports_and_leaves_a_valid_state(conn, tile):
+    # one Augment round per stage cannot finish a discharge here: the device
+    # loop stops at the cap, sets the error word, and the host reports
+    # MF_EROUNDLIMIT; the preflow stays feasible and a normal solve afterwards
+    # on the same handle is exact
+    from paper_1109_1146_gb300 import Grid, MFError
+    inst = (grids.volume_3d(40, 24, 16, 4) if conn == 6 else
+            grids.segmentation_2d(120, 90, 4, conn=conn, hard_seed_frac=0.03))
+    with Grid(inst.dims, conn, tile=tile) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        with pytest.raises(MFError, match="ROUNDLIMIT"):
+            g.solve(opts(max_rounds=1))
+        res, tres, exc = g.get_residual()
+        assert (res >= 0).all() and (tres >= 0).all() and (exc >= 0).all()
+        got = gpu_solve(inst, tile=tile)
+    assert_parity(inst, got)

@@ -243,3 +243,24 @@ def test_projection_matches_oracle(conn, noise):
     np.testing.assert_array_equal(res, rres)
     np.testing.assert_array_equal(tres, rtres)
     np.testing.assert_array_equal(exc, rexc)
+
+
+def test_projection_round_cap_falls_back_to_cold():
+    # a prediction whose trims need many rounds, with a cap of one round:
+    # mf_warm_start reports MF_EROUNDLIMIT, the warm solve starts cold, and the
+    # result is exact
+    inst = grids.config3(11, side=128)
+    t, _ = _solved_targets(inst)
+    pred = t * 3.0  # large over-predictions cascade through many trim rounds
+    net = mf.CNN(channels=6, seed=1)
+    with Grid(inst.dims, 4) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        st, rounds = g.warm_start(pred, max_rounds=1, check=False)
+        assert st == mf.MF_EROUNDLIMIT
+        ws = g.solve(default_opts(warm_start=0))
+        assert ws.projection_rounds == 0
+        got = {"flow": g.flow_value(), "smin": g.get_cut(0), "smax": g.get_cut(1)}
+        got["res"], got["tres"], got["exc"] = g.get_residual()
+        _, _, _, used = warmstart.warm_solve(g, net, default_opts(), max_rounds=1)
+        assert g.flow_value() == got["flow"]  # warm if the projection fit in one round, else cold
+    assert_parity(inst, got)
