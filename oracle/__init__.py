@@ -20,7 +20,9 @@ Augmentation and Push-Relabel"):
                       B^R of Eq. 2) by its definition, and the sweep bound
                       2|B|^2 + 1 of the P-ARD termination theorem (Sec. 4.4);
   * ``region_distance`` — the region distance d* of Sec. 4.1 (eq. 3) by a
-                      0-1 BFS over the residual graph.
+                      0-1 BFS over the residual graph;
+  * ``boundary_relabel`` — the boundary-relabel heuristic of Sec. 6.1 on an
+                      explicit auxiliary graph of (region, label) groups.
   ``oracle.cnn`` and ``oracle.warm`` hold the float64 warm-start network and
   the projection of a prediction to a preflow.
 
@@ -304,3 +306,94 @@ def region_distance(dims, conn, tile, res, tres):
                 else:
                     q.append(u)
     return dist
+
+
+def boundary_relabel(dims, conn, tile, res, lab, dinf):
+    """Boundary-relabel heuristic (Sec. 6.1, the auxiliary graph of its
+    figure, the update d := max(d, d')).
+
+    Only boundary vertices (B of Sec. 4.1) with d < d_inf take part.  They are
+    grouped by (region, label).  Within a region, consecutive group labels
+    l_i < l_{i+1} get a length-0 arc (l_i) -> (l_{i+1}): validity lets a
+    vertex reach higher labels of its region but not lower ones.  Every
+    residual arc (u, w) between two regions, both ends with d < d_inf, gives a
+    length-1 arc group(u) -> group(w).  d' of a group is its distance to the
+    groups of label 0 (a 0-1 BFS on reversed arcs), d_inf if none is reached.
+
+    The section defines d' on B only; inner vertices are read here as
+    follows (the reading keeps the labeling valid, because d' never
+    decreases along a region's label order): a vertex v of region R with
+    0 < d(v) < d_inf gets d'(v) = the least d' of R's groups with label >=
+    d(v), d_inf if there is none; d(v) = 0 keeps 0.  For a boundary vertex
+    this is its own group's d'.  Returns max(d, d') clipped to d_inf
+    (int64[n]).  Requires a labeling valid in the strong form the region
+    relabel yields (non-increasing along residual arcs inside a region)."""
+    from collections import deque
+    X, Y, Z = _dims(dims).tolist()
+    tx, ty, tz = (tuple(tile) + (1, 1))[:3]
+    n = X * Y * Z
+    H = len(_FWD[conn])
+    res = np.asarray(res, dtype=np.int64).reshape(2 * H, n)
+    lab = np.asarray(lab, dtype=np.int64).ravel()
+    RX, RY = (X + tx - 1) // tx, (Y + ty - 1) // ty
+    inB = boundary_mask(dims, conn, tile)
+
+    def region(v):
+        x, y, z = v % X, (v // X) % Y, v // (X * Y)
+        return (z // tz * RY + y // ty) * RX + x // tx
+
+    # groups (R, l) of boundary vertices with finite labels
+    node = {}
+    labels_of = {}
+    for u in np.flatnonzero(inB & (lab < dinf)):
+        key = (region(int(u)), int(lab[u]))
+        if key not in node:
+            node[key] = len(node)
+            labels_of.setdefault(key[0], []).append(key[1])
+    rev = [[] for _ in node]  # rev[b] = [(a, length)] for the arcs a -> b
+    for R, ls in labels_of.items():
+        ls.sort()
+        for a, b in zip(ls, ls[1:]):
+            rev[node[(R, b)]].append((node[(R, a)], 0))
+    arcs = []
+    for h, (dx, dy, dz) in enumerate(_FWD[conn]):
+        arcs.append((2 * h, dx, dy, dz))
+        arcs.append((2 * h + 1, -dx, -dy, -dz))
+    for d, dx, dy, dz in arcs:
+        for u in np.flatnonzero(res[d] > 0):
+            u = int(u)
+            if lab[u] >= dinf:
+                continue
+            x, y, z = u % X + dx, (u // X) % Y + dy, u // (X * Y) + dz
+            if not (0 <= x < X and 0 <= y < Y and 0 <= z < Z):
+                continue
+            w = (z * Y + y) * X + x
+            if lab[w] >= dinf or region(u) == region(w):
+                continue
+            rev[node[(region(w), int(lab[w]))]].append((node[(region(u), int(lab[u]))], 1))
+    # 0-1 BFS from the label-0 groups over reversed arcs
+    INF = np.iinfo(np.int64).max
+    dist = [INF] * len(node)
+    q = deque()
+    for (R, l), i in node.items():
+        if l == 0:
+            dist[i] = 0
+            q.append(i)
+    while q:
+        b = q.popleft()
+        for a, ln in rev[b]:
+            if dist[b] + ln < dist[a]:
+                dist[a] = dist[b] + ln
+                (q.appendleft if ln == 0 else q.append)(a)
+    out = lab.copy()
+    for v in range(n):
+        l = int(lab[v])
+        if l == 0 or l >= dinf:
+            continue
+        R = region(v)
+        best = INF
+        for m in labels_of.get(R, []):
+            if m >= l:
+                best = min(best, dist[node[(R, m)]])
+        out[v] = dinf if best == INF else min(dinf, max(l, best))
+    return out
