@@ -71,7 +71,9 @@ typedef struct {
     int32_t warm_start;            /* 1: start from the preflow of the last mf_warm_start instead of Init's zero flow */
     int32_t graph_loop;            /* 1: mf_solve runs the sweeps as one CUDA graph with a device-side while loop
                                       (per-phase times ms_discharge / ms_fuse are then not measured); default 0 */
-    int32_t reserved[8];
+    int32_t boundary_relabel_period; /* P > 0: boundary-relabel heuristic (Sec. 6.1) after every P-th sweep in
+                                        which the global relabel does not run; any grid and tile; 0 = off (default) */
+    int32_t reserved[7];
 } mf_opts;
 
 /* Statistics of the last mf_solve (all optional reading). */
@@ -92,7 +94,9 @@ typedef struct {
     int32_t global_relabels;     /* exact region-distance relabels run (opts.global_relabel_period) */
     int32_t relabel_levels;      /* BFS levels of those relabels, summed */
     int32_t projection_rounds;   /* rounds of the warm-start projection (0 for a cold start) */
-    int32_t reserved[5];
+    int32_t boundary_relabels;   /* boundary relabels applied (opts.boundary_relabel_period) */
+    int32_t boundary_relabel_levels; /* levels of their searches over the auxiliary graph, summed */
+    int32_t reserved[3];
 } mf_stats;
 
 /* Fill *opts with the defaults listed in mf_opts. */
@@ -155,6 +159,27 @@ mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats);
 mf_status mf_begin(mf_grid *g, const mf_opts *opts);
 mf_status mf_sweep(mf_grid *g, int32_t *active_regions);
 mf_status mf_finish(mf_grid *g);
+
+/*
+ * Boundary-relabel heuristic of Sec. 6.1 on the current state (after mf_begin
+ * or an mf_sweep; mf_solve runs it by itself with opts.boundary_relabel_period).
+ * From the labels of the boundary vertices and the residual arcs between
+ * regions alone it builds the section's auxiliary graph: one node per
+ * (region, label) group, a length-0 arc from each group to the next higher
+ * label of its region, a length-1 arc along each residual arc between regions.
+ * The distance d' of a group to the label-0 groups is a valid lower bound on
+ * the region distance, and every label becomes max(d, d').  A vertex inside a
+ * region with label x > 0 takes the least d' of its region's groups with
+ * label >= x (d_inf if none), so the labeling stays valid.  The gap histogram
+ * and the region activity are rebuilt.
+ *   info  int32[4] (nullable): [0] regions active afterwards, [1] levels of the
+ *         search, [2] faces whose step list was shortened (their extra steps
+ *         merged into one, which only weakens d'; 0 means d' is exact),
+ *         [3] 1 if applied, 0 if the internal breakpoint pool overflowed (the
+ *         labels are then unchanged).
+ * Errors: MF_ESTATE before mf_begin; MF_ENOMEM / MF_ECUDA.
+ */
+mf_status mf_boundary_relabel(mf_grid *g, int32_t *info);
 
 /*
  * Batched solve: every grid of the array (each with capacities set, all on

@@ -27,6 +27,8 @@ struct mf_grid {
     DevState st{};
     unsigned char *smin = nullptr, *tset = nullptr;
     void *cut_scratch = nullptr;                      // 2D cut: bit masks and sets
+    void *br_scratch = nullptr;                       // boundary relabel (allocated at first use)
+    int *h_br = nullptr;                              // pinned words of the boundary relabel
     int *warmF = nullptr, *warmFt = nullptr, *warmE = nullptr;  // projected initial flows (warm start)
     bool warm_ready = false;
     int warm_rounds = 0;
@@ -745,6 +747,8 @@ static void free_all(mf_grid *h) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    if (h->br_scratch) cudaFree(h->br_scratch);
+    if (h->h_br) cudaFreeHost(h->h_br);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -919,6 +923,48 @@ static cudaError_t glr_run(mf_grid *g, int *levels) {
                         : glr3d(g->g, g->st, g->cut_scratch, g->h_ctr, levels, g->stream);
 }
 
+// which relabel (if any) follows sweep count s: the exact global relabel
+// where its period divides s, else the boundary relabel where its period does
+static bool glr_due(const mf_grid *g, int s) {
+    const int P = g->opts.global_relabel_period;
+    return P > 0 && s % P == 0 && glr_supported(g);
+}
+static bool br_due(const mf_grid *g, int s) {
+    const int P = g->opts.boundary_relabel_period;
+    return P > 0 && s % P == 0 && !glr_due(g, s);
+}
+// the graph loops stop where either relabel may be due
+static int relabel_stop_period(const mf_opts &o, bool glr_ok) {
+    const int a = glr_ok ? std::max(0, o.global_relabel_period) : 0, b = std::max(0, o.boundary_relabel_period);
+    if (!a) return b;
+    if (!b) return a;
+    int x = a, y = b;
+    while (y) { const int t = x % y; x = y; y = t; }
+    return x;
+}
+
+// one boundary relabel (Sec. 6.1) on g's stream; *active = regions active after it
+static mf_status br_step(mf_grid *g, cudaStream_t s, int *active, BrResult *r) {
+    if (!g->br_scratch) {
+        CK(cudaMalloc(&g->br_scratch, br_scratch_bytes(g->g, g->conn)));
+        CK(cudaMallocHost((void **)&g->h_br, 8 * 4));
+    }
+    BrResult res{};
+    CK(boundary_relabel(g->conn, g->g, g->st, g->br_scratch, g->h_br, &res, s));
+    g->launches += res.launches;
+    if (res.applied) {
+        g->stats.boundary_relabels++;
+        g->stats.boundary_relabel_levels += res.levels;
+    }
+    if (active) {
+        CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *active = g->h_ctr[kActiveRegions];
+    }
+    if (r) *r = res;
+    return MF_OK;
+}
+
 static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     SweepArgs sa{};
     sa.sweep = g->sweep;
@@ -951,8 +997,7 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
         return fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
     }
     int active = g->h_ctr[kActiveRegions];
-    const int P = g->opts.global_relabel_period;
-    if (P > 0 && active > 0 && g->sweep % P == 0 && glr_supported(g)) {
+    if (active > 0 && glr_due(g, g->sweep)) {
         // exact region-distance relabel (raises labels to max(d, d*)), then the
         // activity of every region is recomputed from the new labels
         int levels = 0;
@@ -963,6 +1008,9 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
         g->stats.global_relabels++;
         g->stats.relabel_levels += levels;
         g->launches += 4 + levels;
+    } else if (active > 0 && br_due(g, g->sweep)) {
+        mf_status bs = br_step(g, g->stream, &active, nullptr);
+        if (bs != MF_OK) return bs;
     }
     if (active_out) *active_out = active;
     return MF_OK;
@@ -972,6 +1020,22 @@ mf_status mf_sweep(mf_grid *g, int32_t *active) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!g->begun) return fail(g, MF_ESTATE, "mf_begin has not been called");
     return run_sweep(g, active);
+}
+
+mf_status mf_boundary_relabel(mf_grid *g, int32_t *info) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!g->begun) return fail(g, MF_ESTATE, "mf_begin has not been called");
+    int active = 0;
+    BrResult r{};
+    mf_status s = br_step(g, g->stream, &active, &r);
+    if (s != MF_OK) return s;
+    if (info) {
+        info[0] = active;
+        info[1] = r.levels;
+        info[2] = r.merged;
+        info[3] = r.applied;
+    }
+    return MF_OK;
 }
 
 mf_status mf_finish(mf_grid *g) {
@@ -1077,7 +1141,7 @@ static mf_status build_graph(mf_grid *g) {
 static mf_status run_graph_loop(mf_grid *g, long long cap) {
     mf_status s = build_graph(g);
     if (s != MF_OK) return s;
-    const int P = (g->opts.global_relabel_period > 0 && glr_supported(g)) ? g->opts.global_relabel_period : 0;
+    const int P = relabel_stop_period(g->opts, glr_supported(g));
     int init[kLoopWords] = {0};
     init[kLoopSweep] = g->sweep;
     init[kLoopCap] = (int)std::min<long long>(cap, INT_MAX);
@@ -1099,7 +1163,7 @@ static mf_status run_graph_loop(mf_grid *g, long long cap) {
         int active = g->h_loop[kLoopActive];
         if (active == 0) return MF_OK;
         if (g->sweep >= cap) return fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left");
-        if (P > 0 && g->sweep % P == 0) {
+        if (glr_due(g, g->sweep)) {
             int levels = 0;
             CK(glr_run(g, &levels));
             CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
@@ -1108,6 +1172,10 @@ static mf_status run_graph_loop(mf_grid *g, long long cap) {
             g->stats.global_relabels++;
             g->stats.relabel_levels += levels;
             g->launches += 4 + levels;
+            if (active == 0) return MF_OK;
+        } else if (br_due(g, g->sweep)) {
+            mf_status bs = br_step(g, g->stream, &active, nullptr);
+            if (bs != MF_OK) return bs;
             if (active == 0) return MF_OK;
         }
     }
@@ -1176,14 +1244,20 @@ struct BatchBufs {
 // on the batch stream (as after a sweep of a single solve: same sequence).
 // Returns in *any_left the number of instances still active afterwards.
 static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *insts, unsigned char *done_dev,
-                               int *any_dev, int *any_left, cudaStream_t s) {
+                               int *any_dev, int *any_left, int sweep, cudaStream_t s) {
     mf_grid *g = grids[0];
     std::vector<unsigned char> done(count);
     CK(cudaMemcpyAsync(done.data(), done_dev, count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     for (int i = 0; i < count; ++i) {
         mf_grid *h = grids[i];
-        if (done[i] || !glr_supported(h)) continue;
+        if (done[i]) continue;
+        if (br_due(h, sweep)) {
+            mf_status bs = br_step(h, s, nullptr, nullptr);
+            if (bs != MF_OK) return fail(g, bs, std::string("batched boundary relabel: ") + h->err);
+            continue;
+        }
+        if (!glr_due(h, sweep)) continue;
         int levels = 0;
         const cudaError_t e = h->ndim == 2 ? glr2d(h->conn, h->g, h->st, h->cut_scratch, h->h_ctr, &levels, s)
                                            : glr3d(h->g, h->st, h->cut_scratch, h->h_ctr, &levels, s);
@@ -1328,7 +1402,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         CK(cudaMalloc(&B.loop, sizeof(int) * kLoopWords));
         int init[kLoopWords] = {0};
         init[kLoopCap] = (int)std::min<long long>(cap, INT_MAX);
-        init[kLoopPeriod] = std::max(0, o.global_relabel_period);
+        init[kLoopPeriod] = relabel_stop_period(o, true);
         memcpy(g->h_ctr, init, sizeof(init));
         CK(cudaMemcpyAsync(B.loop, g->h_ctr, sizeof(init), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
@@ -1369,12 +1443,12 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
                 break;
             }
             // stopped at a multiple of the relabel period
-            mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], s);
+            mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], loopst[kLoopSweep], s);
             if (st != MF_OK) return st;
             if (!g->h_ctr[0]) break;
         }
     } else {
-        const int P = std::max(0, o.global_relabel_period);
+        const int P = relabel_stop_period(o, true);
         for (int sweep = 0;; ++sweep) {
             CK(enqueue_sweep(s, sweep, nullptr));
             launches += per_sweep;
@@ -1386,7 +1460,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
                 break;
             }
             if (P > 0 && (sweep + 1) % P == 0) {
-                mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], s);
+                mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], sweep + 1, s);
                 if (st != MF_OK) return st;
                 if (!g->h_ctr[0]) break;
             }

@@ -190,6 +190,18 @@ cudaError_t launch_project_rounds(int conn, const Geom &g, const int *cs, const 
                                   int *flags, int max_rounds, cudaStream_t s);
 cudaError_t launch_warm_init(int conn, const Geom &g, const DevState &st, const int *cs, const int *ct, const int *nl,
                              const int *F, const int *ft, const int *E, cudaStream_t s);
+// brelabel.cu: boundary-relabel heuristic (Sec. 6.1), any grid and tile
+struct BrResult {
+    int levels;    // levels of the search over the auxiliary graph
+    int merged;    // faces whose staircase was shortened (0: d' exact)
+    int applied;   // 0: the breakpoint pool overflowed and nothing changed
+    int launches;  // kernels launched
+};
+size_t br_scratch_bytes(const Geom &g, int conn);
+// h_words: pinned host buffer of >= 8 ints; leaves st.ctr[kActiveRegions] =
+// regions active under the new labels when applied
+cudaError_t boundary_relabel(int conn, const Geom &g, const DevState &st, void *scratch, int *h_words,
+                             BrResult *res, cudaStream_t s);
 // ard_discharge2d.cu
 bool discharge2d_supported(int conn, int tx, int ty);
 cudaError_t launch_discharge2d_batch(int conn, int tx, int ty, const Inst *insts, const int2 *items,

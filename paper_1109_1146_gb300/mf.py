@@ -22,7 +22,7 @@ STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "
 
 # every symbol include/mf.h declares
 EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
-           "mf_finish", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
+           "mf_finish", "mf_boundary_relabel", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
            "mf_last_error", "mf_min_cut_2d_noalloc", "mf_solve_batch", "mf_warm_features", "mf_warm_targets",
            "mf_warm_start", "mf_certify", "mf_get_flow", "mf_load_model", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
            "mf_cnn_get_params", "mf_cnn_set_params", "mf_cnn_get_grads", "mf_cnn_forward", "mf_cnn_infer",
@@ -34,7 +34,8 @@ class mf_opts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("partial_discharge", ctypes.c_int32),
                 ("global_gap", ctypes.c_int32), ("global_relabel_period", ctypes.c_int32),
                 ("max_rounds", ctypes.c_int32), ("kernel_variant", ctypes.c_int32),
-                ("warm_start", ctypes.c_int32), ("graph_loop", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("warm_start", ctypes.c_int32), ("graph_loop", ctypes.c_int32),
+                ("boundary_relabel_period", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class mf_stats(ctypes.Structure):
@@ -45,7 +46,8 @@ class mf_stats(ctypes.Structure):
                 ("ms_init", ctypes.c_double), ("ms_sweeps", ctypes.c_double), ("ms_cut", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_discharge", ctypes.c_double), ("ms_fuse", ctypes.c_double),
                 ("global_relabels", ctypes.c_int32), ("relabel_levels", ctypes.c_int32),
-                ("projection_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("projection_rounds", ctypes.c_int32), ("boundary_relabels", ctypes.c_int32),
+                ("boundary_relabel_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -68,6 +70,7 @@ SIGNATURES = {
     "mf_begin": (_I, [_P, ctypes.POINTER(mf_opts)]),
     "mf_sweep": (_I, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "mf_finish": (_I, [_P]),
+    "mf_boundary_relabel": (_I, [_P, _P]),
     "mf_get_cut": (_I, [_P, _P, _I, _I]),
     "mf_flow_value": (_I, [_P, ctypes.POINTER(_I64)]),
     "mf_get_residual": (_I, [_P, _P, _P, _P, _I]),
@@ -254,6 +257,13 @@ class Grid:
 
     def finish(self):
         self._check(self._lib.mf_finish(self._h))
+
+    def boundary_relabel(self) -> dict:
+        """One boundary relabel (Sec. 6.1) on the current state (after begin or
+        a sweep): dict(active, levels, merged, applied)."""
+        info = (ctypes.c_int32 * 4)()
+        self._check(self._lib.mf_boundary_relabel(self._h, ctypes.addressof(info)))
+        return {"active": info[0], "levels": info[1], "merged": info[2], "applied": bool(info[3])}
 
     def get_cut(self, which=0, out=None):
         if out is None:
