@@ -5,10 +5,12 @@ For every class present in a list of instances it solves one representative
 instance (real data from the list) with each candidate configuration through
 the C ABI, keeps the fastest by the library's own device timing, and caches
 the choice in a JSON file so later runs reuse it.  Candidates vary the tile,
-partial discharges and the global-relabel period.
+partial discharges, the global-relabel period and the boundary-relabel
+heuristic (Sec. 6.1).
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import math
 import os
@@ -27,7 +29,9 @@ CANDIDATES = {
 
 # global-relabel periods tried (0 = never); the relabel exists for 2D tiles and
 # for 3D tiles 32 voxels wide
-GLR_PERIODS = (0, 4, 8)
+GLR_PERIODS = (0, 2, 4, 8)
+# boundary-relabel period tried without the global relabel (any tile)
+BR_PERIOD = 2
 
 
 def _relabel_supported(conn: int, tile) -> bool:
@@ -41,6 +45,7 @@ def candidates(conn: int, single: bool = False):
     for t, kw in CANDIDATES[conn]:
         periods = GLR_PERIODS if _relabel_supported(conn, t) else (0,)
         out += [(t, dict(kw, global_relabel_period=p)) for p in periods]
+        out.append((t, dict(kw, global_relabel_period=0, boundary_relabel_period=BR_PERIOD)))
     return out
 
 
@@ -53,7 +58,10 @@ def size_class(dims) -> int:
 
 
 def key_of(inst, single: bool = False) -> str:
-    return f"{'single_' if single else ''}c{inst.conn}_s{size_class(inst.dims)}"
+    """Cache key: connectivity, size class and a digest of the candidate set
+    (a cache written for other candidates is not reused)."""
+    fp = hashlib.sha1(repr(candidates(inst.conn)).encode()).hexdigest()[:8]
+    return f"{'single_' if single else ''}c{inst.conn}_s{size_class(inst.dims)}_{fp}"
 
 
 def _time_config(inst, tile, kw, reps):

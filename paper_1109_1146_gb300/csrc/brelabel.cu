@@ -17,11 +17,12 @@
 // For each (region, neighbour) face the pairs (m(u), d(u)), m(u) the least
 // finite label u reaches across the face, are reduced to their Pareto
 // staircase (m ascending, d ascending) once per call, so a level step is a
-// short scan.  Only regions next to a region whose threshold changed at the
-// previous level are re-examined.  d'(v) for a vertex of R with label x > 0 is
-// the first level k with L_k(R) >= x (d_inf if none); every change of L(R) is
-// recorded as a breakpoint (L, k).  Inner vertices use the same rule, which
-// keeps the labeling valid (d' is monotone in the label inside a region).
+// short scan; level 1 (all neighbours at threshold 0) is taken while the
+// staircases are built.  Only regions next to a region whose threshold changed
+// at the previous level are re-examined.  d'(v) for a vertex of R with label
+// x > 0 is the first level k with L_k(R) >= x (d_inf if none); every change of
+// L(R) is recorded as a breakpoint (L, k).  Inner vertices use the same rule,
+// which keeps the labeling valid (d' is monotone in the label inside a region).
 //
 // A face with more than kStair staircase steps keeps the first kStair - 1 and
 // one step (next m, highest d) for the rest: that only adds arcs to the
@@ -47,7 +48,7 @@ constexpr int kBuildWarps = 8;     // warps per block of the staircase build
 
 // scratch layout (all offsets in bytes, 16-aligned)
 struct BrLayout {
-    size_t stair, scount, lcur, lnext, front0, front1, bphead, bp, bpnext, words, total;
+    size_t stair, lb0, lb1, front0, front1, bphead, bp, bpnext, words, total;
     long long pool;
 };
 
@@ -59,9 +60,8 @@ __host__ __device__ inline BrLayout br_layout(const Geom &g, int conn) {
     L.pool = (long long)nr * kPoolPerRegion + 1024;
     size_t o = 0;
     L.stair = o;  o += align16(faces * kStair * sizeof(int2));
-    L.scount = o; o += align16(faces * 4);
-    L.lcur = o;   o += align16(nr * 4);
-    L.lnext = o;  o += align16(nr * 4);
+    L.lb0 = o;    o += align16(nr * 4);
+    L.lb1 = o;    o += align16(nr * 4);
     L.front0 = o; o += align16(nr * 4);
     L.front1 = o; o += align16(nr * 4);
     L.bphead = o; o += align16(nr * 4);
@@ -75,9 +75,14 @@ __host__ __device__ inline BrLayout br_layout(const Geom &g, int conn) {
 // words[]: level counters (3, triple-buffered), pool head, overflow, merged faces, levels
 enum BrWord { kCnt0 = 0, kPoolHead = 3, kOverflow = 4, kMerged = 5, kLevels = 6, kBrWords = 8 };
 
+// Thresholds live in two buffers by level parity: at the start of level k,
+// lb[(k-1)&1][x] = L_{k-1}(x) for every region x; level k raises into
+// lb[k&1] (after copying the regions that changed at level k-1 forward), so
+// one grid barrier per level suffices.  The staircase of a face is kStair
+// int2 (m, d) with unused steps m = INT_MAX.
 struct BrPtrs {
     int2 *stair;
-    int *scount, *lcur, *lnext, *front0, *front1, *bphead;
+    int *lb[2], *front[2], *bphead;
     int2 *bp;
     int *bpnext, *words;
     long long pool;
@@ -86,9 +91,18 @@ struct BrPtrs {
 inline BrPtrs br_ptrs(const Geom &g, int conn, void *scratch) {
     const BrLayout L = br_layout(g, conn);
     char *b = (char *)scratch;
-    return BrPtrs{(int2 *)(b + L.stair), (int *)(b + L.scount), (int *)(b + L.lcur), (int *)(b + L.lnext),
-                  (int *)(b + L.front0), (int *)(b + L.front1), (int *)(b + L.bphead), (int2 *)(b + L.bp),
-                  (int *)(b + L.bpnext), (int *)(b + L.words), L.pool};
+    BrPtrs P{};
+    P.stair = (int2 *)(b + L.stair);
+    P.lb[0] = (int *)(b + L.lb0);
+    P.lb[1] = (int *)(b + L.lb1);
+    P.front[0] = (int *)(b + L.front0);
+    P.front[1] = (int *)(b + L.front1);
+    P.bphead = (int *)(b + L.bphead);
+    P.bp = (int2 *)(b + L.bp);
+    P.bpnext = (int *)(b + L.bpnext);
+    P.words = (int *)(b + L.words);
+    P.pool = L.pool;
+    return P;
 }
 
 __device__ __forceinline__ int region_at(const Geom &g, int x, int y, int z) {
@@ -104,9 +118,9 @@ __device__ void build_face(const Geom &g, const DevState &st, const BrPtrs &P, i
     const int ox = arc_dx(CONN, j), oy = arc_dy(CONN, j), oz = arc_dz(CONN, j);
     const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
     const int qx = rx + ox, qy = ry + oy, qz = rz + oz;
-    int *cnt = &P.scount[(size_t)r * CONN + j];
+    int2 *out = &P.stair[((size_t)r * CONN + j) * kStair];
     if (qx < 0 || qx >= g.RX || qy < 0 || qy >= g.RY || qz < 0 || qz >= g.RZ) {
-        if (lane == 0) *cnt = 0;
+        if (lane < kStair) out[lane] = make_int2(INT_MAX, 0);
         return;
     }
     const int x0 = rx * g.tx, y0 = ry * g.ty, z0 = rz * g.tz;
@@ -143,8 +157,7 @@ __device__ void build_face(const Geom &g, const DevState &st, const BrPtrs &P, i
     }
     __syncwarp();
     lmax_all = __reduce_max_sync(0xffffffffu, lmax_all);
-    int2 *out = &P.stair[((size_t)r * CONN + j) * kStair];
-    int k = 0, best = 0, prev = -1;
+    int k = 0, best = 0, prev = -1, first_m = INT_MAX, first_l = 0;
     bool merged = false;
     while (best < lmax_all && k < kStair) {
         // next distinct reach label above prev, and the highest label reaching it
@@ -163,14 +176,24 @@ __device__ void build_face(const Geom &g, const DevState &st, const BrPtrs &P, i
                 merged = true;
             }
             if (lane == 0) out[k] = make_int2(mc, lc);
+            if (k == 0) {
+                first_m = mc;
+                first_l = lc;
+            }
             ++k;
             best = lc;
         }
         prev = mc;
     }
+    if (lane >= k && lane < kStair) out[lane] = make_int2(INT_MAX, 0);
     if (lane == 0) {
-        *cnt = k;
         if (merged) atomicAdd(&P.words[kMerged], 1);
+        // level 1: the neighbour's threshold L_0 is 0, so the face raises r to
+        // the label of its first step if that step reaches label 0
+        if (first_m == 0 && first_l > 0) {
+            const int old = atomicMax(&P.lb[1][r], first_l);
+            if (old == 0) P.front[1][atomicAdd(&P.words[kCnt0 + 1], 1)] = r;
+        }
     }
 }
 
@@ -185,63 +208,65 @@ __global__ void br_build_kernel(const Geom g, const DevState st, const BrPtrs P,
     build_face<CONN>(g, st, P, (int)(item / CONN), (int)(item % CONN), sm, sl, fmax);
 }
 
-// All levels in one cooperative launch.  Level k: (A) every face of a region
-// next to a region whose threshold changed at level k-1 (all regions at
-// k = 1) is read with that neighbour's threshold and raises the region's next
-// threshold; (B) the raised regions commit their thresholds and record the
-// breakpoint (L, k).  The counters are triple-buffered so that none is reset
-// while another thread may still read it.
+// Levels 2, 3, ... in one cooperative launch (level 1 is done by the build).
+// Level k walks the faces toward every region q raised at level k-1: q's
+// threshold is first copied forward into lb[k&1] and its breakpoint
+// (L_{k-1}(q), k-1) recorded; then each neighbour r reads its face toward q
+// with L_{k-1}(q) and raises lb[k&1][r].  The counters of raised regions are
+// triple-buffered so that none is reset while a thread may still read it.
 template <int CONN>
 __global__ void br_levels_kernel(const Geom g, const BrPtrs P, int max_levels) {
     cg::grid_group grid = cg::this_grid();
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nth = (long long)gridDim.x * blockDim.x;
     int *words = P.words;
-    int k = 1;
+    int k = 2;
     for (; k <= max_levels; ++k) {
-        const int *fin = (k & 1) ? P.front1 : P.front0;
-        int *fout = (k & 1) ? P.front0 : P.front1;
-        const int nin = k == 1 ? g.nreg : *(volatile int *)&words[kCnt0 + (k - 1) % 3];
+        const bool odd = k & 1;
+        const int *fin = odd ? P.front[0] : P.front[1];
+        int *fout = odd ? P.front[1] : P.front[0];
+        const int *lprev = odd ? P.lb[0] : P.lb[1];
+        int *lnew = odd ? P.lb[1] : P.lb[0];
+        const int nin = *(volatile int *)&words[kCnt0 + (k - 1) % 3];
         int *cout = &words[kCnt0 + k % 3];
         for (long long t = tid; t < (long long)nin * CONN; t += nth) {
             const int idx = (int)(t / CONN), j = (int)(t % CONN);
-            const int q = k == 1 ? idx : fin[idx];
+            const int q = fin[idx];
+            const int Lq = lprev[q];
+            if (j == 0) {
+                atomicMax(&lnew[q], Lq);
+                const int e = atomicAdd(&words[kPoolHead], 1);
+                if (e < P.pool) {
+                    P.bp[e] = make_int2(Lq, k - 1);
+                    P.bpnext[e] = P.bphead[q];
+                    P.bphead[q] = e;
+                } else {
+                    words[kOverflow] = 1;
+                }
+            }
             const int qx = q % g.RX, qy = (q / g.RX) % g.RY, qz = q / (g.RX * g.RY);
             const int rx = qx + arc_dx(CONN, j), ry = qy + arc_dy(CONN, j), rz = qz + arc_dz(CONN, j);
             if (rx < 0 || rx >= g.RX || ry < 0 || ry >= g.RY || rz < 0 || rz >= g.RZ) continue;
             const int r = (rz * g.RY + ry) * g.RX + rx;
-            const size_t f = (size_t)r * CONN + (j ^ 1);  // r's face toward q
-            const int Lq = P.lcur[q], Lr = P.lcur[r];
-            const int ns = P.scount[f];
+            const int4 *st4 = (const int4 *)&P.stair[((size_t)r * CONN + (j ^ 1)) * kStair];  // r's face toward q
+            int4 s4[kStair / 2];
+#pragma unroll
+            for (int e = 0; e < kStair / 2; ++e) s4[e] = st4[e];
+            const int Lr = lprev[r];
             int c = 0;
-            for (int e = 0; e < ns; ++e) {
-                const int2 s = P.stair[f * kStair + e];
-                if (s.x > Lq) break;
-                c = s.y;
+#pragma unroll
+            for (int e = 0; e < kStair / 2; ++e) {
+                if (s4[e].x <= Lq) c = s4[e].y;
+                if (s4[e].z <= Lq) c = s4[e].w;
             }
             if (c > Lr) {
-                const int old = atomicMax(&P.lnext[r], c);
-                if (old == Lr) fout[atomicAdd(cout, 1)] = r;  // first raise of r at this level
-            }
-        }
-        grid.sync();
-        const int nout = *(volatile int *)cout;
-        for (long long t = tid; t < nout; t += nth) {
-            const int r = fout[t];
-            const int L = P.lnext[r];
-            P.lcur[r] = L;
-            const int e = atomicAdd(&words[kPoolHead], 1);
-            if (e < P.pool) {
-                P.bp[e] = make_int2(L, k);
-                P.bpnext[e] = P.bphead[r];
-                P.bphead[r] = e;
-            } else {
-                words[kOverflow] = 1;
+                const int old = atomicMax(&lnew[r], c);
+                if (old <= Lr) fout[atomicAdd(cout, 1)] = r;  // first raise of r at this level
             }
         }
         if (tid == 0) words[kCnt0 + (k + 1) % 3] = 0;
         grid.sync();
-        if (nout == 0) break;
+        if (*(volatile int *)cout == 0) break;
     }
     if (tid == 0) {
         words[kLevels] = k;
@@ -249,61 +274,85 @@ __global__ void br_levels_kernel(const Geom g, const BrPtrs P, int max_levels) {
     }
 }
 
-// d := max(d, d') on every vertex; rebuild the boundary-label histogram and
-// the region activity from the new labels.
-template <int CONN>
-__global__ void br_apply_kernel(const Geom g, const DevState st, const BrPtrs P) {
-    constexpr int SB = 2048;  // labels below SB are counted in shared memory first
-    __shared__ int sh[SB];
-    for (int b = threadIdx.x; b < SB; b += blockDim.x) sh[b] = 0;
-    __syncthreads();
-    const long long pool = P.pool;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.n;
-         v += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((long long)g.X * g.Y));
-        const int r = region_at(g, x, y, z);
-        int l = st.lab[v];
-        if (l > 0 && l < g.dinf) {
-            int k = INT_MAX;
-            long long steps = 0;
-            for (int e = P.bphead[r]; e >= 0 && steps < pool; e = P.bpnext[e], ++steps) {
-                const int2 b = P.bp[e];
-                if (b.x < l) break;
-                k = b.y;
-            }
-            const int nl = k == INT_MAX ? g.dinf : min(g.dinf, max(l, k));
-            if (nl != l) {
-                st.lab[v] = nl;
-                l = nl;
-            }
-        }
-        if (l >= g.dinf) continue;
-        if (st.exc[v] > 0) st.active[r] = 1;
-        const int lx = x & (g.tx - 1), ly = y & (g.ty - 1), lz = z & (g.tz - 1);
-        const bool border = lx == 0 || lx == g.tx - 1 || ly == 0 || ly == g.ty - 1 ||
-                            (CONN == 6 && (lz == 0 || lz == g.tz - 1));
-        if (!border) continue;
-        bool inB = false;
-#pragma unroll
-        for (int d = 0; d < CONN; ++d) {
-            const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d), wz = z + arc_dz(CONN, d);
-            if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y || wz < 0 || wz >= g.Z) continue;
-            if (region_at(g, wx, wy, wz) != r) inB = true;
-        }
-        if (!inB) continue;
-        if (l < SB) atomicAdd(&sh[l], 1);
-        else atomicAdd(&st.hist[l < kHistBins ? l : kHistBins], 1);
+// d := max(d, d') on every vertex, one block per region: the region's
+// breakpoints (newest first: L and level descending) are read into shared
+// memory; the boundary-label histogram gets the changes (warp-aggregated);
+// the region's activity (an excess vertex below d_inf) is set from the new
+// labels and counted.  With an overflowed breakpoint pool the labels stay.
+constexpr int kApplyThreads = 256;
+constexpr int kBpShared = 64;
+
+__device__ __forceinline__ void hist_move(int *hist, int from, int to, bool on) {
+    // every lane of the warp calls this; lanes with on move one count from -> to
+    const unsigned act = __ballot_sync(0xffffffffu, on);
+    if (!act) return;
+    const int lane = threadIdx.x & 31;
+    if (on) {
+        const unsigned mf = __match_any_sync(act, from);
+        if (lane == __ffs(mf) - 1 && from < 0x7fffffff) atomicSub(&hist[from < kHistBins ? from : kHistBins], __popc(mf));
+        const unsigned mt = __match_any_sync(act, to);
+        if (lane == __ffs(mt) - 1 && to < 0x7fffffff) atomicAdd(&hist[to < kHistBins ? to : kHistBins], __popc(mt));
     }
-    __syncthreads();
-    for (int b = threadIdx.x; b < SB; b += blockDim.x)
-        if (sh[b]) atomicAdd(&st.hist[b], sh[b]);
 }
 
-__global__ void br_count_active_kernel(const DevState st, int nreg) {
-    int c = 0;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreg; r += gridDim.x * blockDim.x) c += st.active[r] != 0;
-    c = __reduce_add_sync(0xffffffffu, c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
+template <int CONN>
+__global__ void __launch_bounds__(kApplyThreads) br_apply_kernel(const Geom g, const DevState st, const BrPtrs P) {
+    __shared__ int2 sbp[kBpShared];
+    __shared__ int s_nbp, s_act;
+    const bool apply = P.words[kOverflow] == 0;
+    const int V = g.tx * g.ty * g.tz;
+    for (int r = blockIdx.x; r < g.nreg; r += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int nb = 0;
+            for (int e = apply ? P.bphead[r] : -1; e >= 0 && nb < kBpShared; e = P.bpnext[e]) sbp[nb++] = P.bp[e];
+            s_nbp = nb;
+            s_act = 0;
+        }
+        __syncthreads();
+        const int nbp = s_nbp;
+        const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+        int act = 0;
+        for (int i0 = 0; i0 < V; i0 += kApplyThreads) {
+            const int i = i0 + threadIdx.x;
+            const int lx = i & (g.tx - 1), ly = (i >> g.sx) & (g.ty - 1), lz = i >> (g.sx + g.sy);
+            const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
+            const bool in = i < V && x < g.X && y < g.Y && z < g.Z;
+            const size_t v = in ? ((size_t)z * g.Y + y) * g.X + x : 0;
+            int l = in ? st.lab[v] : 0, nl = l;
+            if (in && apply && l > 0 && l < g.dinf) {
+                int k = INT_MAX;
+                int e = 0;
+                for (; e < nbp && sbp[e].x >= l; ++e) k = sbp[e].y;
+                if (e == kBpShared) {  // a longer list: walk on in global memory
+                    int q = P.bphead[r];
+                    for (int s2 = 0; s2 < kBpShared; ++s2) q = P.bpnext[q];
+                    for (long long steps = 0; q >= 0 && steps < P.pool; q = P.bpnext[q], ++steps) {
+                        const int2 b = P.bp[q];
+                        if (b.x < l) break;
+                        k = b.y;
+                    }
+                }
+                nl = k == INT_MAX ? g.dinf : min(g.dinf, max(l, k));
+                if (nl != l) st.lab[v] = nl;
+            }
+            const bool border = lx == 0 || lx == g.tx - 1 || ly == 0 || ly == g.ty - 1 ||
+                                (CONN == 6 && (lz == 0 || lz == g.tz - 1));
+            // in B iff a straight neighbour lies in another region (a diagonal
+            // neighbour in another region implies a straight one)
+            const bool inB = in && border &&
+                             ((lx == 0 && x > 0) || (lx == g.tx - 1 && x + 1 < g.X) || (ly == 0 && y > 0) ||
+                              (ly == g.ty - 1 && y + 1 < g.Y) ||
+                              (CONN == 6 && ((lz == 0 && z > 0) || (lz == g.tz - 1 && z + 1 < g.Z))));
+            hist_move(st.hist, l < g.dinf ? l : 0x7fffffff, nl < g.dinf ? nl : 0x7fffffff, inB && nl != l);
+            if (in && nl < g.dinf && !act && st.exc[v] > 0) act = 1;
+        }
+        act = __syncthreads_or(act);
+        if (threadIdx.x == 0) {
+            st.active[r] = (unsigned char)act;
+            if (act) atomicAdd(&st.ctr[kActiveRegions], 1);
+        }
+        __syncthreads();
+    }
 }
 
 int max_face(const Geom &g, int conn) {
@@ -316,9 +365,10 @@ cudaError_t br_impl(const Geom &g, const DevState &st, void *scratch, int *h_wor
     const BrPtrs P = br_ptrs(g, CONN, scratch);
     const BrLayout L = br_layout(g, CONN);
     const size_t nr = (size_t)g.nreg;
-    cudaError_t e = cudaMemsetAsync((char *)scratch + L.lcur, 0, 2 * align16(nr * 4), s);  // lcur, lnext
+    cudaError_t e = cudaMemsetAsync((char *)scratch + L.lb0, 0, L.front0 - L.lb0, s);  // both threshold buffers
     if (e == cudaSuccess) e = cudaMemsetAsync(P.bphead, 0xff, nr * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(P.words, 0, 64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&st.ctr[kActiveRegions], 0, 4, s);
     if (e != cudaSuccess) return e;
     const int fmax = max_face(g, CONN);
     const long long faces = (long long)nr * CONN;
@@ -337,29 +387,24 @@ cudaError_t br_impl(const Geom &g, const DevState &st, void *scratch, int *h_wor
         max_blocks = per_sm * sms;
         if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
     }
-    const int nblocks = (int)std::max<long long>(1, std::min<long long>((faces + 255) / 256, max_blocks));
+    // the level steps are short: a few hundred blocks keep the grid barrier cheap
+    const int nblocks = (int)std::max<long long>(1, std::min<long long>({(faces + 255) / 256, (long long)max_blocks, 608}));
     Geom gg = g;
     BrPtrs pp = P;
     int max_levels = g.dinf + 1;
     void *args[] = {&gg, &pp, &max_levels};
     e = cudaLaunchCooperativeKernel((const void *)br_levels_kernel<CONN>, dim3(nblocks), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    br_apply_kernel<CONN><<<(unsigned)std::min<size_t>(nr, 152 * 16), kApplyThreads, 0, s>>>(g, st, P);
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_words, P.words, kBrWords * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
     res->levels = h_words[kLevels];
     res->merged = h_words[kMerged];
     res->applied = h_words[kOverflow] == 0;
-    res->launches = 2;
-    if (!res->applied) return cudaSuccess;
-    e = cudaMemsetAsync(st.hist, 0, (kHistBins + 1) * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(st.active, 0, nr, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&st.ctr[kActiveRegions], 0, 4, s);
-    if (e != cudaSuccess) return e;
-    const int nb = (int)std::min<long long>((g.n + 255) / 256, 152 * 32);
-    br_apply_kernel<CONN><<<nb, 256, 0, s>>>(g, st, P);
-    br_count_active_kernel<<<(g.nreg + 255) / 256, 256, 0, s>>>(st, g.nreg);
-    res->launches += 2;
-    return cudaGetLastError();
+    res->launches = 3;
+    return cudaSuccess;
 }
 
 }  // namespace
