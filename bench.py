@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark: exact max-flow / min-cut solve of the 2048x2048 8-connected
-segmentation grid (4.19M vertices, 33.5M arcs, 5% hard seeds at 10^6,
-1024 regions of 64x64) by the CUDA P-ARD solver, through the C ABI.
+segmentation grid (4.19M vertices, 33.5M arcs, 5% hard seeds at 10^6; tile
+and schedule from the autotuner) by the CUDA P-ARD solver, through the C ABI.
 
 One step = one mf_solve from capacities already resident on the device:
 Init, all sweeps of Algorithm 2 (discharge, fusion, global gap), the cut
@@ -460,6 +460,64 @@ def run_batch_warm(args):
     print(json.dumps(line), flush=True)
 
 
+RELABEL_SCHEDULES = {
+    "none": dict(global_relabel_period=0),
+    "glr2": dict(global_relabel_period=2),
+    "glr4": dict(global_relabel_period=4),
+    "glr8": dict(global_relabel_period=8),
+    "br1": dict(global_relabel_period=0, boundary_relabel_period=1),
+    "br2": dict(global_relabel_period=0, boundary_relabel_period=2),
+    "pd": dict(global_relabel_period=0, partial_discharge=1),
+    "pd+br1": dict(global_relabel_period=0, partial_discharge=1, boundary_relabel_period=1),
+    "br1+glr8": dict(global_relabel_period=8, boundary_relabel_period=1),
+}
+
+
+def run_relabel(args):
+    """Relabel schedules compared on the named workloads: no relabel, the exact
+    global relabel every P sweeps (glrP), the boundary-relabel heuristic of
+    Sec. 6.1 every P sweeps (brP), partial discharges (pd) and combinations.
+    One JSON line per (workload, schedule): median device ms of a solve,
+    sweeps, discharges and the relabels run; every schedule must reach the
+    same flow value."""
+    from gen import grids
+    from paper_1109_1146_gb300 import Grid, default_opts, warmstart
+
+    glr = ["none", "glr2", "glr4", "glr8", "br1", "br2", "pd", "pd+br1", "br1+glr8"]
+    no_glr = ["none", "br1", "br2", "pd", "pd+br1"]
+    cases = [("seg2d 2048x2048 8-connected (config of the headline)", lambda: grids.config1(0), (32, 32, 1), glr),
+             ("seg2d 1024x1024 4-connected, held-out seed of the warm-start set",
+              lambda: grids.config3(warmstart.EVAL_SEED0), (32, 32, 1), glr),
+             ("seg2d 256x256 4-connected", lambda: grids.config0(0), (32, 32, 1), glr),
+             ("volume 256x256x128 6-connected", lambda: grids.config2(0, dims=(256, 256, 128)), (32, 8, 4), glr),
+             ("volume 256x256x128 6-connected, 16^3 tiles (no global relabel)",
+              lambda: grids.config2(0, dims=(256, 256, 128)), (16, 16, 16), no_glr),
+             ("volume 512x512x384 6-connected", lambda: grids.config2(0), (32, 8, 4),
+              ["glr4", "br1", "br2", "br1+glr8"])]
+    if args.relabel_case >= 0:
+        cases = [cases[args.relabel_case]]
+    for name, make, tile, scheds in cases:
+        if args.relabel_schedule:
+            scheds = [args.relabel_schedule]
+        inst = make()
+        flows = set()
+        with Grid(inst.dims, inst.conn, tile=tile) as g:
+            g.set_caps(inst.cs, inst.ct, inst.nlink)
+            for sn in scheds:
+                opts = default_opts(**RELABEL_SCHEDULES[sn])
+                runs = [g.solve(opts) for _ in range(args.warmup + args.steps)][args.warmup:]
+                st = runs[-1]
+                flows.add(g.flow_value())
+                print(json.dumps({"workload": "relabel", "instance": name, "tile": list(tile), "schedule": sn,
+                                  "opts": RELABEL_SCHEDULES[sn], "ms": round(statistics.median(r.ms_total for r in runs), 3),
+                                  "sweeps": st.sweeps, "discharges": st.discharges,
+                                  "global_relabels": st.global_relabels, "boundary_relabels": st.boundary_relabels,
+                                  "boundary_relabel_levels": st.boundary_relabel_levels,
+                                  "ms_discharge": round(st.ms_discharge, 3), "ms_fuse": round(st.ms_fuse, 3)}),
+                      flush=True)
+        assert len(flows) == 1, f"schedules disagree on {name}: {flows}"
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -493,8 +551,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="seg2048", choices=["seg2048", "batch", "batch_warm"])
+    ap.add_argument("--workload", default="seg2048", choices=["seg2048", "batch", "batch_warm", "relabel"])
     ap.add_argument("--batch-count", type=int, default=0, help="first N instances of the batch (0 = all 512)")
+    ap.add_argument("--relabel-case", type=int, default=-1, help="relabel workload: only this instance (index)")
+    ap.add_argument("--relabel-schedule", default="", help="relabel workload: only this schedule")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -504,6 +564,8 @@ def main():
         run_batch(args)
     elif args.workload == "batch_warm":
         run_batch_warm(args)
+    elif args.workload == "relabel":
+        run_relabel(args)
     else:
         run_ours(args)
 
