@@ -113,7 +113,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
     u64 *s_T = s_R + N * TY;              // [TY] residual arc to t
     u64 *s_E = s_T + TY;                  // [TY] positive excess
     u64 *s_inc = s_E + TY;                // [TY] vertices that joined the closure
-    u64 *s_vis = s_inc + TY;              // [TY] final closure
+    u64 *s_vis = s_inc + TY;              // [TY] final closure (during Augment rounds: excess received)
     u64 *s_layer = s_vis + TY;            // [LCAP+1][TY] BFS layers
     int *s_hl = (int *)(s_layer + (LCAP + 1) * TY);  // [HL] labels of B^R
     int *s_hmin = s_hl + C::HL;           // [PER] min label over residual boundary arcs of a perimeter vertex
@@ -399,6 +399,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
                         const u64 ex = s_E[y] & Cl[j];
                         vis[j] = fr[j];
                         s_layer[1 * TY + y] = fr[j];
+                        s_vis[y] = 0ull;  // vertices that receive excess in this round's push
                         if (fr[j] & ex) lmax = 1;
                         want[j] = ex & ~vis[j];
                         pending |= want[j] != 0ull;
@@ -445,12 +446,16 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
                 // layer L-1 (to T_k from layer 1), so every arc has one writer per step.
                 // The masks R_d are exact for the arcs from layer L to L-1 until layer L
                 // pushes, so A_d = R_d & (layer L-1 seen through arc d) lists the
-                // admissible arcs of a whole row at once.
+                // admissible arcs of a whole row at once.  Only vertices that had
+                // excess when the round began (s_E) or received some in an earlier
+                // step of it (s_vis) can push, so rows without such a vertex of
+                // layer L are passed over.
+                u64 *s_recv = s_vis;
                 for (int L = Lmax; L >= 1; --L) {
                     const int tgL = deep_tag(epoch, L), tgL1 = deep_tag(epoch, L - 1);
                     const bool lo_mask = L - 1 <= LCAP;
                     for (int y = warp; y < TY; y += NW) {
-                        const u64 P = L <= LCAP ? s_layer[L * TY + y] : ~0ull;
+                        const u64 P = (L <= LCAP ? s_layer[L * TY + y] : ~0ull) & (s_E[y] | s_recv[y]);
                         if (!P) continue;
                         u64 A[N];
                         if (L > 1 && lo_mask) {
@@ -513,6 +518,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
                                     s_cap[d * V + i] = c - dl;
                                     s_cap[(d ^ 1) * V + j] += dl;
                                     atomicAdd(&s_exc[j], dl);
+                                    atomicOr((unsigned *)&s_recv[ny] + (nx >> 5), 1u << (nx & 31));
                                     e -= dl;
                                 }
                             }
