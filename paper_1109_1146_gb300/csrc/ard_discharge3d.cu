@@ -118,7 +118,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
     u32 *s_T = s_R + N * NR;                // [NR]
     u32 *s_E = s_T + NR;                    // [NR]
     u32 *s_inc = s_E + NR;                  // [NR]
-    u32 *s_vis = s_inc + NR;                // [NR]
+    u32 *s_vis = s_inc + NR;                // [NR] final closure (during Augment rounds: excess received)
     u32 *s_layer = s_vis + NR;              // [LCAP+1][NR]
     int *s_hl = (int *)(s_layer + (LCAP + 1) * NR);  // [HL] labels of B^R
     int *s_hm = s_hl + C::HL;               // [HL] label of the halo cell if its arc is residual, else INT_MAX
@@ -377,6 +377,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                         const u32 ex = s_E[rho] & Cl[j];  // excess that can reach T_k lies in the closure
                         vis[j] = fr[j];
                         s_layer[1 * NR + rho] = fr[j];
+                        s_vis[rho] = 0u;  // vertices that receive excess in this round's push
                         if (fr[j] & ex) lmax = 1;
                         want[j] = ex & ~vis[j];
                         pending |= want[j] != 0u;
@@ -418,12 +419,16 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                 if (Lmax == 0) break;  // no excess vertex reaches T_k: stage done
                 ++rounds;
                 // layered push, top layer first: layer L pushes only to layer L-1
-                // (to T_k from layer 1), so every arc has one writer per step
+                // (to T_k from layer 1), so every arc has one writer per step.
+                // Only vertices that had excess when the round began (s_E) or
+                // received some in an earlier step of it (s_vis) can push, so
+                // rows without such a vertex of layer L are passed over.
+                u32 *s_recv = s_vis;
                 for (int L = Lmax; L >= 1; --L) {
                     const int tgL = deep_tag3(epoch, L), tgL1 = deep_tag3(epoch, L - 1);
                     const bool lo_mask = L - 1 <= LCAP;
                     for (int rho = warp; rho < NR; rho += NW) {
-                        const u32 P = L <= LCAP ? s_layer[L * NR + rho] : FULL;
+                        const u32 P = (L <= LCAP ? s_layer[L * NR + rho] : FULL) & (s_E[rho] | s_recv[rho]);
                         if (!P) continue;
                         u32 A[N];
                         if (L > 1 && lo_mask) {
@@ -484,6 +489,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                                     s_cap[d * V + i] = c - dl;
                                     s_cap[(d ^ 1) * V + j] += dl;
                                     atomicAdd(&s_exc[j], dl);
+                                    atomicOr(&s_recv[j >> 5], 1u << (j & 31));
                                     e -= dl;
                                 }
                             }
