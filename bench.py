@@ -470,6 +470,9 @@ RELABEL_SCHEDULES = {
     "pd": dict(global_relabel_period=0, partial_discharge=1),
     "pd+br1": dict(global_relabel_period=0, partial_discharge=1, boundary_relabel_period=1),
     "br1+glr8": dict(global_relabel_period=8, boundary_relabel_period=1),
+    "glr8f1": dict(global_relabel_period=8, global_relabel_first=1),
+    "glr8f2": dict(global_relabel_period=8, global_relabel_first=2),
+    "glr4f1": dict(global_relabel_period=4, global_relabel_first=1),
 }
 
 

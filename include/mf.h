@@ -73,7 +73,9 @@ typedef struct {
                                       (per-phase times ms_discharge / ms_fuse are then not measured); default 0 */
     int32_t boundary_relabel_period; /* P > 0: boundary-relabel heuristic (Sec. 6.1) after every P-th sweep in
                                         which the global relabel does not run; any grid and tile; 0 = off (default) */
-    int32_t reserved[7];
+    int32_t global_relabel_first;  /* F > 0: the global relabel also runs after sweep F (where it is supported),
+                                      besides every global_relabel_period-th sweep; 0 = off (default) */
+    int32_t reserved[6];
 } mf_opts;
 
 /* Statistics of the last mf_solve (all optional reading). */

@@ -408,12 +408,18 @@ __global__ void finish_flags_kernel(const DevState st, int nreg) {
 
 // ---- device-side sweep loop (CUDA graph with a conditional while node) ------
 // loopctl: [0] sweeps done (the next sweep's index), [1] sweeps that found a
-// gap, [2] sweep cap, [3] global-relabel period P (0: none), [4] active regions
-// after the last sweep, [5] error flag of the last sweep.  The loop continues
-// while no error was raised, some region is active, the cap is not reached
-// and the sweep count is not a multiple of P (the host then runs the global
-// relabel and relaunches the graph).
-enum { kLoopSweep = 0, kLoopGaps, kLoopCap, kLoopPeriod, kLoopActive, kLoopError, kLoopWords = 8 };
+// gap, [2] sweep cap, [3] relabel period P (0: none), [4] active regions
+// after the last sweep, [5] error flag of the last sweep, [6] an extra sweep
+// count F after which to stop (0: none).  The loop continues while no error
+// was raised, some region is active, the cap is not reached and the sweep
+// count is neither a multiple of P nor F (the host then runs the relabel due
+// and relaunches the graph).
+enum { kLoopSweep = 0, kLoopGaps, kLoopCap, kLoopPeriod, kLoopActive, kLoopError, kLoopFirst, kLoopWords = 8 };
+
+__device__ __forceinline__ bool loop_stop_at(const int *lc, int s) {
+    const int P = lc[kLoopPeriod], F = lc[kLoopFirst];
+    return (P > 0 && s % P == 0) || (F > 0 && s == F);
+}
 
 __global__ void loop_ctl_kernel(const int *ctr, int *lc, cudaGraphConditionalHandle handle) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -423,8 +429,7 @@ __global__ void loop_ctl_kernel(const int *ctr, int *lc, cudaGraphConditionalHan
     if (gap > 0) lc[kLoopGaps] += 1;
     lc[kLoopActive] = active;
     lc[kLoopError] = err;
-    const int P = lc[kLoopPeriod];
-    const bool cont = !err && active > 0 && s < lc[kLoopCap] && !(P > 0 && s % P == 0);
+    const bool cont = !err && active > 0 && s < lc[kLoopCap] && !loop_stop_at(lc, s);
     cudaGraphSetConditional(handle, cont ? 1u : 0u);
 }
 
@@ -434,8 +439,7 @@ __global__ void batch_loop_ctl_kernel(const int *any, int *lc, cudaGraphConditio
     const int s = lc[kLoopSweep] + 1;
     lc[kLoopSweep] = s;
     lc[kLoopActive] = *any;
-    const int P = lc[kLoopPeriod];
-    cudaGraphSetConditional(handle, (*any && s < lc[kLoopCap] && !(P > 0 && s % P == 0)) ? 1u : 0u);
+    cudaGraphSetConditional(handle, (*any && s < lc[kLoopCap] && !loop_stop_at(lc, s)) ? 1u : 0u);
 }
 
 // ---- batched sweep kernels: one block per (instance, region) of the batch table
@@ -926,8 +930,8 @@ static cudaError_t glr_run(mf_grid *g, int *levels) {
 // which relabel (if any) follows sweep count s: the exact global relabel
 // where its period divides s, else the boundary relabel where its period does
 static bool glr_due(const mf_grid *g, int s) {
-    const int P = g->opts.global_relabel_period;
-    return P > 0 && s % P == 0 && glr_supported(g);
+    const int P = g->opts.global_relabel_period, F = g->opts.global_relabel_first;
+    return ((P > 0 && s % P == 0) || (F > 0 && s == F)) && glr_supported(g);
 }
 static bool br_due(const mf_grid *g, int s) {
     const int P = g->opts.boundary_relabel_period;
@@ -1146,6 +1150,7 @@ static mf_status run_graph_loop(mf_grid *g, long long cap) {
     init[kLoopSweep] = g->sweep;
     init[kLoopCap] = (int)std::min<long long>(cap, INT_MAX);
     init[kLoopPeriod] = P;
+    init[kLoopFirst] = glr_supported(g) ? std::max(0, g->opts.global_relabel_first) : 0;
     memcpy(g->h_loop, init, sizeof(init));
     CK(cudaMemcpyAsync(g->loopctl, g->h_loop, kLoopWords * 4, cudaMemcpyHostToDevice, g->stream));
     const int per_sweep = g->opts.global_gap ? 6 : 5;
@@ -1403,6 +1408,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         int init[kLoopWords] = {0};
         init[kLoopCap] = (int)std::min<long long>(cap, INT_MAX);
         init[kLoopPeriod] = relabel_stop_period(o, true);
+        init[kLoopFirst] = std::max(0, o.global_relabel_first);
         memcpy(g->h_ctr, init, sizeof(init));
         CK(cudaMemcpyAsync(B.loop, g->h_ctr, sizeof(init), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
@@ -1459,7 +1465,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
                 rs = fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left in the batch");
                 break;
             }
-            if (P > 0 && (sweep + 1) % P == 0) {
+            if ((P > 0 && (sweep + 1) % P == 0) || (o.global_relabel_first > 0 && sweep + 1 == o.global_relabel_first)) {
                 mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], sweep + 1, s);
                 if (st != MF_OK) return st;
                 if (!g->h_ctr[0]) break;

@@ -35,7 +35,8 @@ class mf_opts(ctypes.Structure):
                 ("global_gap", ctypes.c_int32), ("global_relabel_period", ctypes.c_int32),
                 ("max_rounds", ctypes.c_int32), ("kernel_variant", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("graph_loop", ctypes.c_int32),
-                ("boundary_relabel_period", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("boundary_relabel_period", ctypes.c_int32), ("global_relabel_first", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class mf_stats(ctypes.Structure):

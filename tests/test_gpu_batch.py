@@ -32,7 +32,9 @@ def _batch_instances():
 @pytest.mark.parametrize("kw", [dict(global_relabel_period=0), dict(partial_discharge=1, global_relabel_period=0),
                                 dict(global_relabel_period=0, graph_loop=1),
                                 dict(partial_discharge=1, global_relabel_period=0, graph_loop=1),
-                                dict(global_relabel_period=2), dict(global_relabel_period=3, graph_loop=1)])
+                                dict(global_relabel_period=2), dict(global_relabel_period=3, graph_loop=1),
+                                dict(global_relabel_period=8, global_relabel_first=1),
+                                dict(global_relabel_period=4, global_relabel_first=1, graph_loop=1)])
 def test_batch_matches_oracle_and_single_solves(kw):
     insts = _batch_instances()
     opts = default_opts(**kw)

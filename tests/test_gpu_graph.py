@@ -18,7 +18,9 @@ pytestmark = pytest.mark.gpu
     (lambda: grids.volume_3d(70, 37, 30, 2), (32, 16, 8)),
 ])
 @pytest.mark.parametrize("kw", [dict(), dict(partial_discharge=1), dict(global_relabel_period=2),
-                                dict(global_relabel_period=3, partial_discharge=1, global_gap=0)])
+                                dict(global_relabel_period=3, partial_discharge=1, global_gap=0),
+                                dict(global_relabel_period=8, global_relabel_first=1),
+                                dict(global_relabel_period=0, global_relabel_first=2)])
 def test_graph_loop_equals_host_loop(make, tile, kw):
     inst = make()
     host = gpu_solve(inst, tile=tile, opts=opts(**kw))
