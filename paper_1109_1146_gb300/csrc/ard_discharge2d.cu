@@ -132,10 +132,12 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
     if (tid == 0) s_flow = 0;
 
     // rebuild the row masks from the planes (all threads; a warp covers 32
-    // consecutive vertices of one row, so one ballot gives half a row word)
-    auto rebuild_masks = [&]() {
+    // consecutive vertices of one row, so one ballot gives half a row word);
+    // with only_round, just the rows the last Augment round changed (s_dirty 2)
+    auto rebuild_masks = [&](bool only_round) {
         for (int i = tid; i < V; i += NT) {
             const int lx = i % TX, ly = i / TX;
+            if (only_round && s_dirty[ly] != 2) continue;  // the same row for the whole warp
             const int hw = (ly * 2 + (lx >> 5));
 #pragma unroll
             for (int d = 0; d < N; ++d) {
@@ -227,7 +229,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
         }
     }
     __syncthreads();
-    rebuild_masks();
+    rebuild_masks(false);
     rebuild_hmin();
     __syncthreads();
     DIAG_LAP(0);
@@ -527,14 +529,16 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
                         }
                         if (__any_sync(0xffffffffu, pushed) && lane < 3) {
                             const int yy = y - 1 + lane;
-                            if (yy >= 0 && yy < TY) s_dirty[yy] = 1;
+                            if (yy >= 0 && yy < TY) s_dirty[yy] = 2;  // changed in this round
                         }
                     }
                     __syncthreads();
                 }
-                rebuild_masks();
+                rebuild_masks(true);  // a push changes rows y-1..y+1 only
                 rebuild_hmin();
                 __syncthreads();
+                for (int y = tid; y < TY; y += NT)
+                    if (s_dirty[y] == 2) s_dirty[y] = 1;
                 DIAG_LAP(7);
                 DIAG_ADD(8, Lmax);
             }
