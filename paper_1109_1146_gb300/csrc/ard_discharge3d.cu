@@ -142,9 +142,11 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
         const int y = rho % TY, z = rho / TY;
         return d == 2 ? y < TY - 1 : d == 3 ? y > 0 : d == 4 ? z < TZ - 1 : d == 5 ? z > 0 : true;
     };
-    auto rebuild_masks = [&]() {
+    // with only_round, just the rows the last Augment round changed (s_dirty 2)
+    auto rebuild_masks = [&](bool only_round) {
         for (int i = tid; i < V; i += NT) {
             const int rho = i / TX;
+            if (only_round && s_dirty[rho] != 2) continue;  // the same row for the whole warp
 #pragma unroll
             for (int d = 0; d < N; ++d) {
                 const unsigned b = __ballot_sync(FULL, s_cap[d * V + i] > 0);
@@ -215,7 +217,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
         }
     }
     __syncthreads();
-    rebuild_masks();
+    rebuild_masks(false);
     rebuild_hm();
     __syncthreads();
 
@@ -499,14 +501,16 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                         if (__any_sync(FULL, pushed) && lane < 5) {
                             const int o = lane == 0 ? -TY : lane == 1 ? -1 : lane == 2 ? 0 : lane == 3 ? 1 : TY;
                             const int rr = rho + o;
-                            if (rr >= 0 && rr < NR) s_dirty[rr] = 1;
+                            if (rr >= 0 && rr < NR) s_dirty[rr] = 2;  // changed in this round
                         }
                     }
                     __syncthreads();
                 }
-                rebuild_masks();
+                rebuild_masks(true);  // a push changes its row and the rows one step away in y and z only
                 rebuild_hm();
                 __syncthreads();
+                for (int rho = tid; rho < NR; rho += NT)
+                    if (s_dirty[rho] == 2) s_dirty[rho] = 1;
             }
             if (warp == 0) cl_valid = false;  // the residual graph changed
         }
