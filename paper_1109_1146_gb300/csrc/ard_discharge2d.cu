@@ -57,7 +57,7 @@ struct Cfg2D {
     // as masks so that four fit in shared memory; deeper layers use label tags)
     static constexpr bool DENSE = CONN == 8 && TX == 32;
     static constexpr int LCAP = DENSE ? 24 : 64;       // BFS layers kept as masks
-    static constexpr int MINB = DENSE ? 4 : 1;         // resident blocks per SM the registers must allow
+    static constexpr int MINB = DENSE ? 4 : (CONN == 4 && TX == 32) ? 4 : 1;  // resident blocks per SM the registers must allow
     static constexpr size_t smem = (size_t)(N + 3) * V * 4                  // cap, tcap, exc, lab
                                    + (size_t)(N + 4) * TY * 8               // R[N], T, E, inc, vis
                                    + (size_t)(LCAP + 1) * TY * 8            // BFS layers 1..LCAP
