@@ -24,7 +24,8 @@ Augmentation and Push-Relabel"):
   * ``boundary_relabel`` — the boundary-relabel heuristic of Sec. 6.1 on an
                       explicit auxiliary graph of (region, label) groups.
   ``oracle.cnn`` and ``oracle.warm`` hold the float64 warm-start network and
-  the projection of a prediction to a preflow.
+  the projection of a prediction to a preflow; ``oracle.reduction`` the
+  region reduction of Sec. 8 on explicit per-region networks.
 
 Every function here is pinned by the ``-m "not gpu"`` tests against values
 fixed by mathematics (brute force on tiny inputs, closed forms, special
