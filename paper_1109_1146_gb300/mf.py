@@ -122,7 +122,15 @@ def load(path: str = LIBPATH):
     return lib
 
 
+_OPT_FIELDS = {name for name, _ in mf_opts._fields_ if name != "reserved"}
+
+
 def default_opts(**kw) -> mf_opts:
+    """mf_opts with the library's defaults, then the given fields (an unknown
+    name raises instead of becoming a Python attribute the library never sees)."""
+    unknown = set(kw) - _OPT_FIELDS
+    if unknown:
+        raise TypeError(f"unknown mf_opts fields: {sorted(unknown)}")
     o = mf_opts()
     load().mf_default_opts(ctypes.byref(o))
     for k, v in kw.items():
