@@ -32,6 +32,12 @@ def test_client_compiles_and_links_as_c99(client):
     assert os.access(client, os.X_OK)
 
 
+def test_header_compiles_as_cpp():
+    # the extern "C" guards let C++ callers include the header unchanged
+    subprocess.run(["g++", "-std=c++17", "-Wall", "-Wextra", "-Werror", "-x", "c++", "-fsyntax-only",
+                    os.path.join(ROOT, "include", "mf.h")], check=True, capture_output=True)
+
+
 def _write(path, inst, tile):
     ndim = 3 if inst.conn == 6 else 2
     hdr = np.array([ndim, inst.conn, *inst.dims, *tile], dtype="<i4")
