@@ -1,20 +1,31 @@
 #!/usr/bin/env python
-"""Benchmark: exact max-flow / min-cut solve of the 2048x2048 8-connected
-segmentation grid (4.19M vertices, 33.5M arcs, 5% hard seeds at 10^6; tile
-and schedule from the autotuner) by the CUDA P-ARD solver, through the C ABI.
+"""Benchmark of the CUDA P-ARD solver on the batched-solve workload: 512
+uneven synthetic instances (384 2D 4-connected segmentation grids with side
+uniform in [64, 1024] and 128 3D 6-connected Perlin volumes with side uniform
+in [48, 128]; about 2.6e8 vertices), solved exactly through the C ABI.
 
-One step = one mf_solve from capacities already resident on the device:
-Init, all sweeps of Algorithm 2 (discharge, fusion, global gap), the cut
-extraction (S_min, S_max) and the flow value, all on the GPU.
+One step = one mf_solve_batch of all 512 instances from capacities already
+resident on the device: Init, every sweep of Algorithm 2 (discharge, fusion,
+global gap, relabels) for every instance, the cut extraction (S_min, S_max)
+and the flow values, all on the GPU.  ``value`` is ms per instance of that
+batched solve.  Beside it, in the same run and on the same instances: the
+batched solve with the learned warm start on the 2D members (features,
+network inference and projection inside the timed region), the plain
+cold-start solve of every instance one by one with the default settings,
+sweeps per instance of all three, the end-to-end time through the C ABI from
+pinned host buffers, the roofline of the dominant discharge kernel, and the
+CPU oracle (Dinic) on a sample of the instances.  The single 2048^2
+8-connected grid and the 512x512x384 volume are carried as extra keys.
 
-Prints one JSON line (rank 0).  Multi-GPU: one process per GPU
-(torchrun), each rank solves its own instance (seed = rank): replicas, weak
-scaling, no data-path collective.  ``--impl reference`` times the CPU
-oracle (Dinic) on a bounded sample of the same workload instead.
+Prints one JSON line (rank 0).  Multi-GPU: one process per GPU (torchrun),
+each rank solves its own batch (batch seed = rank): replicas, weak scaling,
+no data-path collective.  ``--impl reference`` times the CPU oracle on the
+same 512 instances (each timed step a disjoint share of them, all host cores).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -23,6 +34,7 @@ import sys
 import tempfile
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -31,9 +43,52 @@ METRIC = "exact-maxflow solve ms + sweeps per instance, learned/batched vs plain
 UNIT = "ms/instance"
 SIDE = 2048
 CONN = 8
-BYTES_PER_VERTEX = (CONN + 3) * 4 * 2  # read + write of cap[8], tcap, exc, lab (int32)
+# algorithmic bytes per discharged vertex: read + write of cap[2H], tcap, exc, lab (int32)
+BYTES_PER_VERTEX = {4: (4 + 3) * 4 * 2, 8: (8 + 3) * 4 * 2, 6: (6 + 3) * 4 * 2}
 L2_FLUSH_BYTES = 256 << 20
-REF_SAMPLE_SIDE = 1024
+WEIGHTS = os.path.join(ROOT, "paper_1109_1146_gb300", "weights", "warm_seg2d_1024_c4.npy")
+BATCH_WORKLOAD = ("uneven batch of 512: 384 seg2d 4-connected grids side U{64..1024} (value-noise intensity, "
+                  "cs=|I-80| ct=|I-170|, n-links round(100exp(-dI^2/800))) + 128 vol3d 6-connected Perlin volumes "
+                  "side U{48..128} (t-links -log N(I;mu,30^2) x10, n-links round(50exp(-dI^2/450))), PCG64 batch seed")
+
+
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def batch_instance(i, shape, batch_seed=0):
+    """Instance i of the uneven batch (instance seed 5000 + i, offset per batch seed)."""
+    from gen import grids
+    X, Y, Z = shape
+    seed = 5000 + i + 100000 * batch_seed
+    if Z == 1:
+        return grids.segmentation_2d(X, Y, seed, conn=4)
+    return grids.volume_3d(X, Y, Z, seed)
+
+
+def batch_instances(batch_seed=0, count=0, threads=None, only=None):
+    """The uneven batch, generated on host threads (numpy releases the GIL)."""
+    from gen import grids
+    shapes = grids.config4_shapes(batch_seed)
+    idx = list(range(len(shapes))) if only is None else list(only)
+    if count:
+        idx = idx[:count]
+    with ThreadPoolExecutor(threads or host_threads()) as ex:
+        return list(ex.map(lambda i: batch_instance(i, shapes[i], batch_seed), idx))
+
+
+def oracle_solve_many(insts, threads):
+    """Dinic + S_min/S_max of every instance on `threads` host threads (the C
+    oracle releases the GIL); returns (results, wall seconds)."""
+    import oracle
+    oracle._load()
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(oracle.solve_instance, insts))
+    return res, time.perf_counter() - t0
 
 
 def workload_name(side=SIDE):
@@ -41,8 +96,12 @@ def workload_name(side=SIDE):
             f"n-links round(100exp(-dI^2/800)) (diagonals /sqrt2), 5% hard seeds at 1e6")
 
 
-def kernel_name(tile):
-    return f"ard_discharge2d_kernel<{CONN},{tile[0]},{tile[1]},{256 if tile[0] == 32 else 512}>"
+def kernel_name(conn, tile, batch=False):
+    tx, ty, tz = tile
+    if conn == 6:
+        nt = 512 if ty * tz >= 128 else 256
+        return f"ard_discharge3d{'_batch' if batch else ''}_kernel<{ty},{tz},{nt}>"
+    return f"ard_discharge2d{'_batch' if batch else ''}_kernel<{conn},{tx},{ty},{256 if tx * ty <= 2048 else 512}>"
 
 
 def make_instance(seed, side=SIDE):
@@ -50,10 +109,10 @@ def make_instance(seed, side=SIDE):
     return grids.config1(seed=seed, side=side)
 
 
-def directed_arcs(dims):
+def directed_arcs(dims, conn):
     from gen.grids import FWD
-    X, Y, _ = dims
-    return 2 * sum((X - abs(dx)) * (Y - abs(dy)) for dx, dy, _ in FWD[CONN])
+    X, Y, Z = dims
+    return 2 * sum((X - abs(dx)) * (Y - abs(dy)) * (Z - abs(dz)) for dx, dy, dz in FWD[conn])
 
 
 def dist_env():
@@ -141,28 +200,295 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def committed_traffic(tile):
-    """DRAM bytes per discharged vertex of the discharge kernel from the
-    committed ncu summary, or None if the kernel source or the tile differs
-    from the ones measured there."""
-    import hashlib
-    p = os.path.join(ROOT, "profiles", "ard_discharge_seg2d_2048_c8.txt")
-    src = os.path.join(ROOT, "paper_1109_1146_gb300", "csrc", "ard_discharge2d.cu")
-    try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+def committed_traffic(kernel, tile):
+    """DRAM bytes per discharged vertex of a discharge kernel from the
+    committed ncu summaries (profiles/*.txt lines "bench: key = value"), or
+    None if no summary covers this kernel and tile, or if the kernel's source
+    changed since it was taken."""
+    import glob
+    for p in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.txt"))):
         kv = {}
-        for ln in open(p):
-            if ln.startswith("bench:"):
-                k, v = ln[len("bench:"):].split("=", 1)
-                kv[k.strip()] = v.strip()
-        if kv.get("kernel_sha256_16") != sha or kv.get("tile") != "x".join(str(t) for t in tile):
-            return None
-        return float(kv["dram_bytes_per_discharged_vertex"])
-    except Exception:
-        return None
+        try:
+            for ln in open(p):
+                if ln.startswith("bench:"):
+                    k, v = ln[len("bench:"):].split("=", 1)
+                    kv[k.strip()] = v.strip()
+        except Exception:
+            continue
+        if kv.get("kernel") != kernel or kv.get("tile") != "x".join(str(t) for t in tile):
+            continue
+        src = os.path.join(ROOT, "paper_1109_1146_gb300", "csrc", kv.get("source", ""))
+        try:
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        except Exception:
+            continue
+        if kv.get("kernel_sha256_16") == sha:
+            return float(kv["dram_bytes_per_discharged_vertex"])
+    return None
+
+
+def kernel_source(conn):
+    return "ard_discharge3d.cu" if conn == 6 else "ard_discharge2d.cu"
+
+
+def roofline_of(stats, insts, tiles, batch):
+    """Roofline line of the dominant discharge kernel type: algorithmic bytes
+    (discharged vertices x bytes per vertex) over that kernel's event-timed
+    duration, per launch."""
+    by_type = {}
+    for st, x, t in zip(stats, insts, tiles):
+        k = (x.conn, tuple(t))
+        e = by_type.setdefault(k, {"ms": 0.0, "launches": 0, "vertices": 0})
+        if batch:  # every instance of a type reports the type's total
+            e["ms"] = st.ms_discharge
+            e["launches"] = st.discharge_launches
+        else:
+            e["ms"] += st.ms_discharge
+            e["launches"] += st.discharge_launches
+        e["vertices"] += st.discharged_vertices
+    (conn, tile), e = max(by_type.items(), key=lambda kv: kv[1]["ms"])
+    peak, peak_kind = measured_peak_hbm()
+    alg = e["vertices"] * BYTES_PER_VERTEX[conn]
+    achieved = alg / (e["ms"] * 1e-3) / 1e9 if e["ms"] > 0 else 0.0
+    kname = kernel_name(conn, tile, batch)
+    tb = committed_traffic(kname, tile)
+    launches = max(1, e["launches"])
+    share = {f"{kernel_name(c, t, batch)}": round(v["ms"], 3) for (c, t), v in by_type.items()}
+    return {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
+            "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 5),
+            "traffic": None if tb is None else round(tb * e["vertices"] / launches),
+            "alg_bytes_per_launch": round(alg / launches), "launch_ms_avg": round(e["ms"] / launches, 4),
+            "launches": e["launches"], "bytes_per_discharged_vertex": BYTES_PER_VERTEX[conn],
+            "discharge_ms_by_kernel": share}
+
+
+def run_config4(args):
+    """The batched-solve workload: batched (value), batched with the learned
+    warm start, and plain one-by-one solves of the same 512 instances."""
+    import numpy as np
+    import torch
+
+    from paper_1109_1146_gb300 import Grid, autotune, default_opts, mf, warmstart
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    t_gen = time.perf_counter()
+    insts = batch_instances(batch_seed=rank, count=args.batch_count)
+    t_gen = time.perf_counter() - t_gen
+    count = len(insts)
+    nv = sum(x.n for x in insts)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # tile and schedule per size class from the autotuner (measured solves, untimed)
+    t_tune = time.perf_counter()
+    table = autotune.tune(insts, cache_path=os.path.join(tempfile.gettempdir(), f"mf_autotune_c4_{rank}.json"))
+    sched = autotune.batch_schedule(insts, table)
+    t_tune = time.perf_counter() - t_tune
+    tiles = [autotune.choose(x, table)[0] for x in insts]
+    # capacities resident on the device; one handle per instance for the
+    # batched solves (autotuned tiles), one per instance for the plain solves
+    # (the library's default tile)
+    dcs = [torch.from_numpy(x.cs).to(dev) for x in insts]
+    dct = [torch.from_numpy(x.ct).to(dev) for x in insts]
+    dnl = [torch.from_numpy(x.nlink).to(dev) for x in insts]
+    hb, hp = [], []
+    for x, t, a, b, c in zip(insts, tiles, dcs, dct, dnl):
+        g = Grid(x.dims, x.conn, tile=t, stream=stream)
+        g.set_caps(a, b, c)
+        hb.append(g)
+        g = Grid(x.dims, x.conn, stream=stream)
+        g.set_caps(a, b, c)
+        hp.append(g)
+    idx2 = [i for i, x in enumerate(insts) if x.conn == 4]
+    net = warmstart.load_network(WEIGHTS)
+    wx = {}
+    for i in idx2:
+        X, Y = insts[i].dims[0], insts[i].dims[1]
+        wx[i] = (torch.empty((1, 6, Y, X), dtype=torch.float32, device=dev),
+                 torch.empty((1, 6, Y, X), dtype=torch.float32, device=dev))
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        out = None
+        for k in range(steps):
+            ev[k][0].record(stream)
+            out = fn()
+            ev[k][1].record(stream)
+        barrier()
+        return [a.elapsed_time(b) for a, b in ev], out
+
+    bopts = default_opts(graph_loop=1, **sched)
+    wopts = default_opts(graph_loop=1, warm_start=1, **sched)
+
+    def batched():
+        return mf.solve_batch(hb, bopts)
+
+    def batched_warm():
+        for i in idx2:
+            x, y = wx[i]
+            hb[i].warm_features(x)
+            net.infer(x, y)
+            hb[i].warm_start(y, check=False)  # a projection that runs out of rounds leaves that grid cold
+        return mf.solve_batch(hb, wopts)
+
+    def plain():
+        return [g.solve() for g in hp]
+
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    with ClockSampler(f"GPU-{uuid}" if uuid else local) as clk:
+        b_ms, b_stats = timed(batched, args.steps, args.warmup)
+    smin_b = [g.get_cut(0) for g in hb]
+    flow_b = [g.flow_value() for g in hb]
+    kw = max(1, min(args.steps, args.aux_steps))
+    w_ms, w_stats = timed(batched_warm, kw, min(args.warmup, 2))
+    assert [g.flow_value() for g in hb] == flow_b, "warm and cold batched solves disagree on a flow value"
+    assert all(np.array_equal(g.get_cut(0), s) for g, s in zip(hb, smin_b)), "warm and cold S_min differ"
+    p_ms, p_stats = timed(plain, kw, 1)
+    assert [g.flow_value() for g in hp] == flow_b, "batched and plain solves disagree on a flow value"
+    assert all(np.array_equal(g.get_cut(0), s) for g, s in zip(hp, smin_b)), "batched and plain S_min differ"
+    # host-driven batch loop: the same solve with per-kernel-type event timing (roofline)
+    _, h_stats = timed(lambda: mf.solve_batch(hb, default_opts(**sched)), 1, 1)
+    # end to end through the C ABI from pinned host buffers: H2D of every
+    # instance's capacities, the batched solve, D2H of every S_min and flow value
+    pin = [(torch.from_numpy(x.cs).pin_memory(), torch.from_numpy(x.ct).pin_memory(),
+            torch.from_numpy(x.nlink).pin_memory(), torch.empty(x.n, dtype=torch.uint8).pin_memory())
+           for x in insts]
+    e2e_ms = []
+    ke = max(1, min(args.steps, args.aux_steps))
+    for k in range(ke + 1):
+        barrier()
+        t0 = time.perf_counter()
+        for g, (a, b, c, _) in zip(hb, pin):
+            g.set_caps(a, b, c)
+        mf.solve_batch(hb, bopts)
+        fl = []
+        for g, (_, _, _, out) in zip(hb, pin):
+            g.get_cut(0, out=out)
+            fl.append(g.flow_value())
+        t1 = time.perf_counter()
+        if k > 0:
+            e2e_ms.append((t1 - t0) * 1e3)
+        assert fl == flow_b
+    assert all(np.array_equal(p[3].numpy(), s) for p, s in zip(pin, smin_b))
+
+    total_b = job_time_ms(sum(b_ms), ws, dev)
+    total_w = job_time_ms(sum(w_ms), ws, dev)
+    total_p = job_time_ms(sum(p_ms), ws, dev)
+    total_e = job_time_ms(sum(e2e_ms), ws, dev)
+    roof = roofline_of(h_stats, insts, tiles, batch=True)
+    for g in hb + hp:
+        g.close()
+    del dcs, dct, dnl
+
+    extras = {}
+    if rank == 0 and "c1" in args.extras:
+        extras["seg2d_2048_c8"] = run_single_extra(args, make_instance(0), stream, dev)
+    if rank == 0 and "c2" in args.extras:
+        from gen import grids
+        extras["vol3d_512x512x384"] = run_single_extra(args, grids.config2(0), stream, dev)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+
+    def per(total, steps):
+        return round(total / (ws * steps * count), 4)
+
+    def sweeps(st):
+        return round(sum(s.sweeps for s in st) / count, 3)
+
+    value = per(total_b, args.steps)
+    h2d = int(sum(x.cs.nbytes + x.ct.nbytes + x.nlink.nbytes for x in insts))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_b / args.steps, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD + (f" (first {count})" if args.batch_count else ""),
+                   "instances": count, "vertices": nv, "batch_seed": "rank",
+                   "parallelism": f"replicas x{ws}", "mode": "batched persistent solve, CUDA-graph sweep loop",
+                   "schedule": sched, "tiles": sorted({"x".join(map(str, t)) for t in tiles}),
+                   "l2": "not flushed: the batch's device state (about 8 GB) is far larger than L2",
+                   "generation_s": round(t_gen, 1), "autotune_s": round(t_tune, 1)},
+        "sweeps_per_instance": sweeps(b_stats),
+        "vertices_per_s": nv * ws / (total_b / args.steps * 1e-3),
+        "batched_cold": {"ms_per_instance": value, "sweeps_per_instance": sweeps(b_stats)},
+        "batched_warm": {"ms_per_instance": per(total_w, kw), "sweeps_per_instance": sweeps(w_stats),
+                         "note": "learned warm start on the 384 2D members (features, tensor-core inference, "
+                                 "projection to a preflow, all timed); 3D members cold",
+                         "projection_rounds_mean_2d": round(statistics.mean(w_stats[i].projection_rounds
+                                                                             for i in idx2), 2),
+                         "steps": kw},
+        "plain": {"ms_per_instance": per(total_p, kw), "sweeps_per_instance": sweeps(p_stats),
+                  "note": "cold-start mf_solve of each instance one by one, default tile and options", "steps": kw},
+        "speedup_batched_vs_plain": round(total_p / kw / (total_b / args.steps), 3),
+        "speedup_batched_warm_vs_plain": round(total_p / kw / (total_w / kw), 3),
+        "roofline": roof,
+        "e2e": {"value": per(total_e, ke), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(sum(x.n + 8 for x in insts)), "steps": ke},
+        "gpu_launches": int(sum(s.launches for s in b_stats)) * args.steps,
+        "clocks": clk.summary(),
+    }
+    line.update(extras)
+    if ws == 1 and not args.no_cpu_baseline:
+        # the oracle on a bounded sample: every 16th instance (24 2D + 8 3D),
+        # all host threads; every sampled result compared with the GPU's
+        sample = list(range(0, count, 16))
+        thr = host_threads()
+        refs, wall = oracle_solve_many([insts[i] for i in sample], thr)
+        for i, r in zip(sample, refs):
+            assert r["flow"] == flow_b[i], (i, r["flow"], flow_b[i])
+            assert np.array_equal(r["smin"], smin_b[i]), f"S_min of instance {i} differs from the oracle"
+        line["cpu_baseline"] = {"value": round(wall * 1e3 / len(sample), 2), "unit": UNIT, "cores": thr,
+                                "kind": "oracle",
+                                "sample": f"every 16th instance of the batch ({len(sample)} instances, "
+                                          f"{sum(insts[i].n for i in sample)} vertices): Dinic + S_min/S_max BFS, "
+                                          f"one instance per host thread; flow and S_min equal to the GPU's"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def run_single_extra(args, inst, stream, dev):
+    """Plain single solve of one large instance with the default tile and
+    options (extra key of the batched line): ms, sweeps, discharge roofline."""
+    import torch
+
+    from paper_1109_1146_gb300 import Grid, default_opts
+    with Grid(inst.dims, inst.conn, stream=stream) as g:
+        g.set_caps(torch.from_numpy(inst.cs).to(dev), torch.from_numpy(inst.ct).to(dev),
+                   torch.from_numpy(inst.nlink).to(dev))
+        opts = default_opts()
+        for _ in range(2):
+            g.solve(opts)
+        torch.cuda.synchronize()
+        sts = [g.solve(opts) for _ in range(max(1, min(args.steps, 3)))]
+        tile = (32, 32, 1) if inst.conn != 6 else (32, 8, 4)
+        roof = roofline_of(sts, [inst] * len(sts), [tile] * len(sts), batch=False)
+        ok, cut, bad = g.certify()
+        ms = statistics.median(s.ms_total for s in sts)
+        return {"workload": inst.name, "vertices": inst.n, "tile": list(tile), "ms": round(ms, 3),
+                "sweeps": sts[-1].sweeps, "vertices_per_s": inst.n / (ms * 1e-3), "flow_value": g.flow_value(),
+                "certified": ok, "roofline": {k: roof[k] for k in ("kernel", "achieved", "frac", "launch_ms_avg")}}
 
 
 def run_ours(args):
+    """The single 2048x2048 8-connected grid (--workload seg2048): one step =
+    one mf_solve from device-resident capacities."""
     import numpy as np
     import torch
 
@@ -259,17 +585,17 @@ def run_ours(args):
     dis_ms = sum(s.ms_discharge for s in stats)
     dis_launches = sum(s.sweeps for s in stats)
     dis_vertices = sum(s.discharged_vertices for s in stats)
-    alg_bytes = dis_vertices * BYTES_PER_VERTEX
+    alg_bytes = dis_vertices * BYTES_PER_VERTEX[CONN]
     peak, peak_kind = measured_peak_hbm()
     achieved = alg_bytes / (dis_ms * 1e-3) / 1e9 if dis_ms > 0 else 0.0
-    tb = committed_traffic(tile)
+    tb = committed_traffic(kernel_name(CONN, tile), tile)
     traffic = None if tb is None else tb * dis_vertices / dis_launches
     solve_bytes = alg_bytes / args.steps
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": workload_name(), "vertices": inst.n, "directed_arcs": directed_arcs(inst.dims),
+        "config": {"workload": workload_name(), "vertices": inst.n, "directed_arcs": directed_arcs(inst.dims, CONN),
                    "tile": list(tile), "schedule": sched, "autotuned": True,
                    "regions": (SIDE // tile[0]) * (SIDE // tile[1]), "seed": "rank",
                    "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MiB write)",
@@ -280,7 +606,7 @@ def run_ours(args):
         "phase_ms": {"discharge": dis_ms / args.steps, "fuse_gap": sum(s.ms_fuse for s in stats) / args.steps,
                      "cut": sum(s.ms_cut for s in stats) / args.steps,
                      "init": sum(s.ms_init for s in stats) / args.steps},
-        "roofline": {"kernel": kernel_name(tile), "bound": "hbm",
+        "roofline": {"kernel": kernel_name(CONN, tile), "bound": "hbm",
                      "achieved": round(achieved, 2), "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "unit": "GB/s", "frac": round(achieved / peak, 5),
                      "traffic": None if traffic is None else round(traffic),
@@ -307,84 +633,6 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
-
-
-def run_batch(args):
-    """Batched persistent solve of the uneven batch (384 2D 4-connected grids,
-    side U{64..1024}, and 128 3D 6-connected grids, side U{48..128}) against
-    the same instances solved one by one with the default settings."""
-    import tempfile
-
-    import torch
-
-    from gen import grids
-    from paper_1109_1146_gb300 import Grid, autotune, default_opts, mf
-
-    torch.cuda.set_device(0)
-    shapes = grids.config4_shapes(0)[: args.batch_count] if args.batch_count else grids.config4_shapes(0)
-    insts = []
-    for i, (X, Y, Z) in enumerate(shapes):
-        if Z == 1:
-            insts.append(grids.segmentation_2d(X, Y, 5000 + i, conn=4))
-        else:
-            insts.append(grids.volume_3d(X, Y, Z, 5000 + i))
-    nv = sum(x.n for x in insts)
-    stream = torch.cuda.current_stream()
-    # plain: one solve per instance, default tile and options
-    plain_ms, plain_sweeps, flows = 0.0, 0, []
-    for x in insts:
-        with Grid(x.dims, x.conn, stream=stream) as g:
-            g.set_caps(x.cs, x.ct, x.nlink)
-            g.solve()
-            st = g.solve()
-            plain_ms += st.ms_total
-            plain_sweeps += st.sweeps
-            flows.append(g.flow_value())
-    table = autotune.tune(insts, cache_path=os.path.join(tempfile.gettempdir(), "mf_autotune.json"))
-    sched = autotune.batch_schedule(insts, table)
-    handles = []
-    for x in insts:
-        tile, _ = autotune.choose(x, table)
-        g = Grid(x.dims, x.conn, tile=tile, stream=stream)
-        g.set_caps(x.cs, x.ct, x.nlink)
-        handles.append(g)
-    def timed(opts):
-        for _ in range(args.warmup):
-            mf.solve_batch(handles, opts)
-        times, stats = [], None
-        for _ in range(args.steps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            a.record(stream)
-            stats = mf.solve_batch(handles, opts)
-            b.record(stream)
-            torch.cuda.synchronize()
-            times.append(a.elapsed_time(b))
-        return times, stats
-
-    # the sweep loop of the batch as one CUDA graph (device-side while node); the
-    # host-driven loop is timed beside it
-    host_times, _ = timed(default_opts(**sched))
-    times, stats = timed(default_opts(graph_loop=1, **sched))
-    bflows = [h.flow_value() for h in handles]
-    assert bflows == flows, "batched and single solves disagree"
-    bms = statistics.median(times)
-    line = {"metric": METRIC, "workload": "batch", "value": round(bms / len(insts), 4), "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "dtype": "int32",
-            "data": "synthetic",
-            "config": {"workload": "uneven batch: 384 2D 4-conn grids side U{64..1024} + 128 3D 6-conn side "
-                                   "U{48..128} (first %d), segmentation / volume generators" % len(insts),
-                       "instances": len(insts), "vertices": nv, "autotune": table, "schedule": sched},
-            "batch_ms": round(bms, 3), "batch_ms_host_loop": round(statistics.median(host_times), 3),
-            "plain_sequential_ms": round(plain_ms, 3),
-            "plain_ms_per_instance": round(plain_ms / len(insts), 4),
-            "speedup_vs_plain": round(plain_ms / bms, 3),
-            "sweeps_per_instance_batch": sum(s.sweeps for s in stats) / len(insts),
-            "sweeps_per_instance_plain": plain_sweeps / len(insts),
-            "vertices_per_s_batch": nv / (bms * 1e-3)}
-    for h in handles:
-        h.close()
-    print(json.dumps(line), flush=True)
 
 
 def run_batch_warm(args):
@@ -521,29 +769,51 @@ def run_relabel(args):
         assert len(flows) == 1, f"schedules disagree on {name}: {flows}"
 
 
+def reference_shares(count, steps):
+    """Instances of each timed step of the reference arm: step k solves the
+    instances i with i mod steps = k (disjoint; together every instance once)."""
+    return [[i for i in range(count) if i % steps == k] for k in range(steps)]
+
+
 def run_reference(args):
+    """The oracle (Dinic + S_min/S_max BFS, plain C) on the same workload as
+    the default line: the 512 instances of the uneven batch, solved on all
+    host threads (one instance per thread).  Each timed step solves a
+    disjoint, interleaved share of the batch (instance i in step i mod K), so
+    the K timed steps together solve every instance exactly once; generation
+    is not timed.  Warm-up steps solve the smallest instances."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    inst = make_instance(seed=0, side=REF_SAMPLE_SIDE)
-    scale = (SIDE * SIDE) / inst.n
-    for _ in range(args.warmup):
-        oracle.solve_instance(inst)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.solve_instance(inst)
-    t1 = time.perf_counter()
-    value = (t1 - t0) * 1e3 / args.steps * scale
-    sample = (f"{REF_SAMPLE_SIDE}x{REF_SAMPLE_SIDE} instance of the same recipe per step (1/{scale:g} of the "
-              f"vertices), time scaled x{scale:g} to one {SIDE}x{SIDE} instance")
-    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 2),
+    from gen import grids
+    shapes = grids.config4_shapes(0)
+    count = args.batch_count or len(shapes)
+    thr = host_threads()
+    steps = max(1, args.steps)
+    by_size = sorted(range(count), key=lambda i: shapes[i][0] * shapes[i][1] * shapes[i][2])
+    for w in range(args.warmup):
+        oracle_solve_many(batch_instances(0, only=[by_size[w % count]]), thr)
+    times, nv, solved = [], 0, 0
+    for share in reference_shares(count, steps):
+        if not share:
+            continue
+        insts = batch_instances(0, only=share)
+        res, wall = oracle_solve_many(insts, thr)
+        times.append(wall * 1e3)
+        nv += sum(x.n for x in insts)
+        solved += len(insts)
+    total = sum(times)
+    value = total / solved
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": round(total / len(times), 2),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": workload_name(), "vertices": SIDE * SIDE,
-                                            "parallelism": "1 host thread"},
-            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "instances": solved, "vertices": nv, "batch_seed": 0,
+                       "parallelism": f"{thr} host threads, one instance each"},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": f"all {solved} instances of the batch over the {steps} timed steps "
+                                       f"(step k: instances i with i mod {steps} = k), untimed generation"},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -554,8 +824,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="seg2048", choices=["seg2048", "batch", "batch_warm", "relabel"])
+    ap.add_argument("--workload", default="config4", choices=["config4", "seg2048", "batch_warm", "relabel"])
     ap.add_argument("--batch-count", type=int, default=0, help="first N instances of the batch (0 = all 512)")
+    ap.add_argument("--aux-steps", type=int, default=3,
+                    help="timed steps of the warm, plain and end-to-end modes of the batched line (<= --steps)")
+    ap.add_argument("--extras", default="c1,c2",
+                    help="extra keys of the batched line: c1 = 2048^2 8-connected grid, c2 = 512x512x384 volume")
     ap.add_argument("--relabel-case", type=int, default=-1, help="relabel workload: only this instance (index)")
     ap.add_argument("--relabel-schedule", default="", help="relabel workload: only this schedule")
     args = ap.parse_args()
@@ -563,8 +837,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batch":
-        run_batch(args)
+    elif args.workload == "config4":
+        run_config4(args)
     elif args.workload == "batch_warm":
         run_batch_warm(args)
     elif args.workload == "relabel":

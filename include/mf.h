@@ -75,7 +75,11 @@ typedef struct {
                                         which the global relabel does not run; any grid and tile; 0 = off (default) */
     int32_t global_relabel_first;  /* F > 0: the global relabel also runs after sweep F (where it is supported),
                                       besides every global_relabel_period-th sweep; 0 = off (default) */
-    int32_t reserved[6];
+    int32_t region_reduction;      /* 1: region reduction of Sec. 8 before Init (see mf_region_reduction): the
+                                      strong source vertices are merged into s and the strong sink vertices into
+                                      t, the sweeps run on the rest; flow value, S_min and S_max are those of the
+                                      full network; not with warm_start; 0 = off (default) */
+    int32_t reserved[5];
 } mf_opts;
 
 /* Statistics of the last mf_solve (all optional reading). */
@@ -98,7 +102,10 @@ typedef struct {
     int32_t projection_rounds;   /* rounds of the warm-start projection (0 for a cold start) */
     int32_t boundary_relabels;   /* boundary relabels applied (opts.boundary_relabel_period) */
     int32_t boundary_relabel_levels; /* levels of their searches over the auxiliary graph, summed */
-    int32_t reserved[3];
+    int32_t discharge_launches;  /* discharge launches timed in ms_discharge (single solve: one per sweep of the
+                                    host loop; batch: persistent launches of this instance's kernel type) */
+    int32_t reduced_vertices;    /* vertices merged into s or t by opts.region_reduction (0 without it) */
+    int32_t reserved[1];
 } mf_stats;
 
 /* Fill *opts with the defaults listed in mf_opts. */
@@ -184,6 +191,35 @@ mf_status mf_finish(mf_grid *g);
 mf_status mf_boundary_relabel(mf_grid *g, int32_t *info);
 
 /*
+ * Region reduction (Sec. 8, the Region Reduction algorithm) on the current
+ * capacities, a preprocessing that decides vertices from one region's
+ * network alone.  For every region R of the tiling by `tile`, the region
+ * network G^R holds R with its terminal links, the boundary B^R (the
+ * vertices outside R adjacent to R, without terminal links) and the edges
+ * inside R and between R and B^R; from the zero flow it runs Augment(s,t),
+ * splits B^R into B^S = {v : s -> v} and B^T = {v : v -> t}, runs
+ * Augment(s,B^S) and Augment(B^T,t), and classifies each v of R in the final
+ * residual network: s -> v strong source (on the source side of every
+ * minimum cut of the whole network), v -> t strong sink (sink side of every
+ * one), otherwise weak source if v does not reach B^R and weak sink if B^R
+ * does not reach v (that side of some minimum cut).  One thread block per
+ * region, the region network in shared memory.
+ *   tile    region shape (NULL or zeros: the grid's tile if its network fits,
+ *           else 32x32 in 2D and 32x8x4 in 3D); a region network has
+ *           (tx+2)(ty+2)(tz+2) cells (tz+2 -> 1 in 2D) and needs
+ *           ((connectivity+3)*4 + 3) bytes of shared memory per cell, at most
+ *           232000 bytes;
+ *   codes   uint8[n] (host or device per on_device): bit 1 strong source,
+ *           bit 2 strong sink, bit 4 weak source, bit 8 weak sink;
+ *   counts  int64[4] (nullable): strong sources, strong sinks, weak sources,
+ *           weak sinks.
+ * Errors: MF_ESTATE before mf_set_caps; MF_EINVAL if the tile's network does
+ * not fit; MF_EROUNDLIMIT if an Augment of some region hit the round cap
+ * (65536 rounds).
+ */
+mf_status mf_region_reduction(mf_grid *g, const int32_t tile[3], uint8_t *codes, int on_device, int64_t counts[4]);
+
+/*
  * Batched solve: every grid of the array (each with capacities set, all on
  * one device) is solved at once.  Each sweep builds one work queue of the
  * active regions of all unfinished instances per kernel type (connectivity
@@ -193,7 +229,11 @@ mf_status mf_boundary_relabel(mf_grid *g, int32_t *info);
  * has no active region.  All work is ordered on grids[0]'s stream.  Per
  * instance results are then read as after mf_solve (mf_get_cut,
  * mf_flow_value); stats (nullable) receives count entries (the ms_* fields
- * are those of the whole batch).  The global relabel (opts->
+ * are those of the whole batch, except that without graph_loop ms_discharge
+ * and discharge_launches are those of the persistent discharge launches of
+ * the instance's kernel type, timed with CUDA events on the batch stream;
+ * stats[0].launches also counts the launches shared by the whole batch, so
+ * the launches of all entries add up to the batch's).  The global relabel (opts->
  * global_relabel_period) runs for every unfinished instance that supports it
  * after the same sweeps as in a single solve, so each instance takes the same
  * sweeps as alone.  With opts->warm_start = 1 each grid starts from its
@@ -247,15 +287,17 @@ mf_status mf_get_labels(mf_grid *g, int32_t *lab, int32_t *d_inf, int on_device)
  *   dims            {X, Y}; connectivity 4 or 8; cuda_stream may be NULL.
  * All scratch lives in one file-scope device array of 8 MiB inside the
  * library (every GPU that loads the library holds it until the process
- * exits); nothing is allocated.  A grid needs 256 + (connectivity+2) * Y *
- * ceil(X/64) * 8 bytes of it (up to about 2590 x 2590 at 8-connectivity,
- * 3340 x 3340 at 4-connectivity); larger grids are rejected with MF_EINVAL.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current): make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (other
- * streams, other threads) race and must not be issued.  The call
- * synchronises cuda_stream before returning.  Errors: MF_EINVAL (arguments,
- * size), MF_ECUDA; message in mf_last_error(NULL).
+ * exits); nothing is allocated.  A grid needs
+ *     256 + (connectivity + 2) * Y * ceil(X / 64) * 8
+ * bytes of it, so the largest square grids are 2560 x 2560 at
+ * 8-connectivity and 3328 x 3328 at 4-connectivity; larger grids are
+ * rejected with MF_EINVAL.  Each call looks up the array's device address
+ * for the current device.  All calls share the array: calls that overlap on
+ * the GPU (other streams, other threads) race and must not be issued.  The
+ * call synchronises cuda_stream (and reads a pass count back to the host)
+ * before returning, so it cannot be used inside a stream capture.
+ * Errors: MF_EINVAL (arguments, size), MF_ECUDA; message in
+ * mf_last_error(NULL).
  */
 mf_status mf_min_cut_2d_noalloc(const int64_t dims[2], int connectivity, const int32_t *res,
                                 const int32_t *tres, const int32_t *exc, uint8_t *smin, uint8_t *smax,

@@ -186,3 +186,46 @@ def region_reduction(dims, conn, tile, cs, ct, nlink):
                              "s_to_boundary_or_t": bool((set(Bl) | {t}) & from_s),
                              "boundary_or_s_to_t": bool((set(Bl) | {s}) & to_t)})
     return {"codes": codes, "regions": info}
+
+
+def reduce_instance(dims, conn, cs, ct, nlink, codes):
+    """The network with the strong source vertices merged into s and the
+    strong sink vertices into t (every minimum cut already puts them there):
+    for a vertex w left open, cs'(w) = cs(w) + c(edges of w to strong
+    sources), ct'(w) = ct(w) + c(edges of w to strong sinks); edges with a
+    merged endpoint and the terminal links of merged vertices are removed.
+    Every cut that keeps S* on the source side and T* on the sink side costs
+    the reduced network's cut plus the constant
+        K = sum_{S*} ct + sum_{T*} cs + c(S*, T*).
+    Returns (cs', ct', nlink', K)."""
+    X, Y, Z = (tuple(int(d) for d in dims) + (1, 1))[:3]
+    n = X * Y * Z
+    H = len(_FWD[conn])
+    cs = np.asarray(cs, dtype=np.int64).ravel()
+    ct = np.asarray(ct, dtype=np.int64).ravel()
+    nl = np.asarray(nlink, dtype=np.int64).reshape(H, n).copy()
+    codes = np.asarray(codes).ravel()
+    S = (codes & STRONG_SOURCE) != 0
+    T = (codes & STRONG_SINK) != 0
+    cs2, ct2 = cs.copy(), ct.copy()
+    K = int(ct[S].sum() + cs[T].sum())
+    for h, (dx, dy, dz) in enumerate(_FWD[conn]):
+        for v in range(n):
+            c = int(nl[h, v])
+            if c == 0:
+                continue
+            x, y, z = v % X, (v // X) % Y, v // (X * Y)
+            w = ((z + dz) * Y + (y + dy)) * X + (x + dx)
+            if (S[v] and T[w]) or (T[v] and S[w]):
+                K += c
+            if not (S[v] or T[v]):
+                cs2[v] += c if S[w] else 0
+                ct2[v] += c if T[w] else 0
+            if not (S[w] or T[w]):
+                cs2[w] += c if S[v] else 0
+                ct2[w] += c if T[v] else 0
+            if S[v] or T[v] or S[w] or T[w]:
+                nl[h, v] = 0
+    cs2[S | T] = 0
+    ct2[S | T] = 0
+    return cs2.astype(np.int32), ct2.astype(np.int32), nl.astype(np.int32), K

@@ -383,12 +383,10 @@ template <int CONN, int TX, int TY, int TZ, int NT>
 static cudaError_t launch_batch_one(const Inst *insts, const int2 *items, const int *count, int *head,
                                     const SweepArgs &sa, int blocks, cudaStream_t s) {
     using C = TileCfg<CONN, TX, TY, TZ, NT>;
-    static bool attr_set = false;
     auto k = ard_discharge_batch_kernel<CONN, TX, TY, TZ, NT>;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    {
+        const cudaError_t e_at = ensure_smem_attr((const void *)k, (int)C::smem);
+        if (e_at != cudaSuccess) return e_at;
     }
     k<<<blocks, NT, C::smem, s>>>(insts, items, count, head, sa);
     return cudaGetLastError();
@@ -398,12 +396,10 @@ static cudaError_t launch_batch_one(const Inst *insts, const int2 *items, const 
 template <int CONN, int TX, int TY, int TZ, int NT>
 static cudaError_t launch_one(const Geom &g, const DevState &st, const SweepArgs &sa, cudaStream_t s) {
     using C = TileCfg<CONN, TX, TY, TZ, NT>;
-    static bool attr_set = false;
     auto k = ard_discharge_kernel<CONN, TX, TY, TZ, NT>;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    {
+        const cudaError_t e_at = ensure_smem_attr((const void *)k, (int)C::smem);
+        if (e_at != cudaSuccess) return e_at;
     }
     k<<<g.nreg, NT, C::smem, s>>>(g, st, sa);
     return cudaGetLastError();

@@ -57,7 +57,9 @@ struct Cfg2D {
     // as masks so that four fit in shared memory; deeper layers use label tags)
     static constexpr bool DENSE = CONN == 8 && TX == 32;
     static constexpr int LCAP = DENSE ? 24 : 64;       // BFS layers kept as masks
-    static constexpr int MINB = DENSE ? 4 : (CONN == 4 && TX == 32) ? 4 : 1;  // resident blocks per SM the registers must allow
+    // resident blocks per SM the registers must allow (64x32 tiles: two, as
+    // their shared memory would allow three)
+    static constexpr int MINB = DENSE ? 4 : (CONN == 4 && TX == 32) ? 4 : (TX * TY == 2048) ? 2 : 1;
     static constexpr size_t smem = (size_t)(N + 3) * V * 4                  // cap, tcap, exc, lab
                                    + (size_t)(N + 4) * TY * 8               // R[N], T, E, inc, vis
                                    + (size_t)(LCAP + 1) * TY * 8            // BFS layers 1..LCAP
@@ -682,12 +684,10 @@ template <int CONN, int TX, int TY, int NT>
 static cudaError_t launch2d_batch(const Inst *insts, const int2 *items, const int *count, int *head,
                                   const SweepArgs &sa, int blocks, cudaStream_t s) {
     using C = Cfg2D<CONN, TX, TY, NT>;
-    static bool attr_set = false;
     auto k = ard_discharge2d_batch_kernel<CONN, TX, TY, NT>;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    {
+        const cudaError_t e_at = ensure_smem_attr((const void *)k, (int)C::smem);
+        if (e_at != cudaSuccess) return e_at;
     }
     k<<<blocks, NT, C::smem, s>>>(insts, items, count, head, sa);
     return cudaGetLastError();
@@ -696,12 +696,10 @@ static cudaError_t launch2d_batch(const Inst *insts, const int2 *items, const in
 template <int CONN, int TX, int TY, int NT>
 static cudaError_t launch2d(const Geom &g, const DevState &st, const SweepArgs &sa, cudaStream_t s) {
     using C = Cfg2D<CONN, TX, TY, NT>;
-    static bool attr_set = false;
     auto k = ard_discharge2d_kernel<CONN, TX, TY, NT>;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    {
+        const cudaError_t e_at = ensure_smem_attr((const void *)k, (int)C::smem);
+        if (e_at != cudaSuccess) return e_at;
     }
     k<<<g.nreg, NT, C::smem, s>>>(g, st, sa);
     return cudaGetLastError();

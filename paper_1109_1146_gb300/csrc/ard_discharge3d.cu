@@ -42,6 +42,9 @@ struct Cfg3D {
     static constexpr int B_MZ = 2 * NR + 2 * TX * TZ, B_PZ = B_MZ + TX * TY;
     static constexpr int HL = B_PZ + TX * TY;     // halo cells = arcs leaving the tile
     static constexpr int LCAP = 32;               // BFS layers kept as masks
+    // resident blocks per SM the registers must allow (shared memory allows
+    // four 32x8x4 tiles, two 32x8x8 tiles, one 32x16x8 tile)
+    static constexpr int MINB = NR == 32 ? 4 : NR == 64 ? 2 : 1;
     static constexpr size_t smem = (size_t)(N + 3) * V * 4           // cap, tcap, exc, lab
                                    + (size_t)(N + 4) * NR * 4        // R[N], T, E, inc, vis
                                    + (size_t)(LCAP + 1) * NR * 4     // BFS layers 1..LCAP
@@ -606,7 +609,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
 }
 
 template <int TY, int TZ, int NT>
-__global__ void __launch_bounds__(NT, 1) ard_discharge3d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
+__global__ void __launch_bounds__(NT, (Cfg3D<TY, TZ, NT>::MINB)) ard_discharge3d_kernel(const Geom g, const DevState st, const SweepArgs sa) {
     const int r = blockIdx.x;
     if (!st.active[r]) return;
     __shared__ __align__(8) unsigned long long s_mbar;
@@ -617,7 +620,7 @@ __global__ void __launch_bounds__(NT, 1) ard_discharge3d_kernel(const Geom g, co
 }
 
 template <int TY, int TZ, int NT>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, (Cfg3D<TY, TZ, NT>::MINB))
 ard_discharge3d_batch_kernel(const Inst *__restrict__ insts, const int2 *__restrict__ items, const int *count,
                              int *head, const SweepArgs sa) {
     __shared__ int s_it;
@@ -641,12 +644,10 @@ ard_discharge3d_batch_kernel(const Inst *__restrict__ insts, const int2 *__restr
 template <int TY, int TZ, int NT>
 static cudaError_t launch3d(const Geom &g, const DevState &st, const SweepArgs &sa, cudaStream_t s) {
     using C = Cfg3D<TY, TZ, NT>;
-    static bool attr_set = false;
     auto k = ard_discharge3d_kernel<TY, TZ, NT>;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    {
+        const cudaError_t e_at = ensure_smem_attr((const void *)k, (int)C::smem);
+        if (e_at != cudaSuccess) return e_at;
     }
     k<<<g.nreg, NT, C::smem, s>>>(g, st, sa);
     return cudaGetLastError();
@@ -656,12 +657,10 @@ template <int TY, int TZ, int NT>
 static cudaError_t launch3d_batch(const Inst *insts, const int2 *items, const int *count, int *head,
                                   const SweepArgs &sa, int blocks, cudaStream_t s) {
     using C = Cfg3D<TY, TZ, NT>;
-    static bool attr_set = false;
     auto k = ard_discharge3d_batch_kernel<TY, TZ, NT>;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    {
+        const cudaError_t e_at = ensure_smem_attr((const void *)k, (int)C::smem);
+        if (e_at != cudaSuccess) return e_at;
     }
     k<<<blocks, NT, C::smem, s>>>(insts, items, count, head, sa);
     return cudaGetLastError();

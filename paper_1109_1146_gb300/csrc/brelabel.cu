@@ -377,25 +377,20 @@ cudaError_t br_impl(const Geom &g, const DevState &st, void *scratch, int *h_wor
         g, st, P, fmax);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    static int max_blocks = 0;
-    if (!max_blocks) {
-        int per_sm = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, br_levels_kernel<CONN>, 256, 0);
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        max_blocks = per_sm * sms;
-        if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    int max_blocks = 0;
+    {
+        const cudaError_t e_mb = coop_max_blocks((const void *)br_levels_kernel<CONN>, 256, 0, &max_blocks);
+        if (e_mb != cudaSuccess) return e_mb;
     }
     // the level steps are short: a few hundred blocks keep the grid barrier cheap
-    const int nblocks = (int)std::max<long long>(1, std::min<long long>({(faces + 255) / 256, (long long)max_blocks, 608}));
+    const int nblocks = (int)std::max<long long>(1, std::min<long long>({(faces + 255) / 256, (long long)max_blocks, 4ll * device_sms()}));
     Geom gg = g;
     BrPtrs pp = P;
     int max_levels = g.dinf + 1;
     void *args[] = {&gg, &pp, &max_levels};
     e = cudaLaunchCooperativeKernel((const void *)br_levels_kernel<CONN>, dim3(nblocks), dim3(256), args, 0, s);
     if (e != cudaSuccess) return e;
-    br_apply_kernel<CONN><<<(unsigned)std::min<size_t>(nr, 152 * 16), kApplyThreads, 0, s>>>(g, st, P);
+    br_apply_kernel<CONN><<<(unsigned)std::min<size_t>(nr, device_sms() * 16), kApplyThreads, 0, s>>>(g, st, P);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_words, P.words, kBrWords * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -662,7 +662,7 @@ mf_status mf_cnn_backward(mf_cnn *c, const float *x, const float *dy) {
         float *dmask = c->dbuf[slot];
         if (l < 4) {
             // cur already holds dL/d(out_l); apply the ReLU of layer l
-            relu_mask_kernel<<<152 * 8, 256, 0, c->stream>>>(const_cast<float *>(cur), c->act[l], pix * c->ch[l]);
+            relu_mask_kernel<<<device_sms() * 8, 256, 0, c->stream>>>(const_cast<float *>(cur), c->act[l], pix * c->ch[l]);
             CKC(cudaGetLastError());
         }
         CKC(conv_wgrad_any(c->ch[l - 1], c->ch[l], lin, cur, c->g + c->woff[l], c->g + c->boff[l], N, H, W, c->stream));
@@ -680,7 +680,7 @@ mf_status mf_cnn_backward(mf_cnn *c, const float *x, const float *dy) {
 mf_status mf_cnn_mse(mf_cnn *c, const float *y, const float *target, float *dy, int64_t count, double *loss) {
     if (!c || !y || !target || !dy || count < 1) return cnn_fail(c, MF_EINVAL, "bad loss arguments");
     CKC(cudaMemsetAsync(c->dloss, 0, 8, c->stream));
-    mse_kernel<<<152 * 8, 256, 0, c->stream>>>(y, target, dy, (size_t)count, c->dloss);
+    mse_kernel<<<device_sms() * 8, 256, 0, c->stream>>>(y, target, dy, (size_t)count, c->dloss);
     CKC(cudaGetLastError());
     double h = 0;
     CKC(cudaMemcpyAsync(&h, c->dloss, 8, cudaMemcpyDeviceToHost, c->stream));

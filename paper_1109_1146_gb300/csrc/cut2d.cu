@@ -426,18 +426,13 @@ static cudaError_t glr2d_impl(const Geom &g, const DevState &st, void *scratch, 
     u64 *A = M + CONN * plane;
     u64 *B = A + plane;
     const size_t total = (size_t)W64 * 64 * g.Y;
-    const int mb = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
+    const int mb = (int)std::min<size_t>((total + 255) / 256, device_sms() * 32);
     cut_masks_kernel<CONN><<<mb, 256, 0, s>>>(g, st, W64, 1, (unsigned *)M, (unsigned *)A);
     // one cooperative launch for all levels; the grid must be co-resident
-    static int max_blocks = 0;
-    if (!max_blocks) {
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, glr_levels_kernel<CONN>, 256, 0);
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        max_blocks = per_sm * sms;
-        if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    int max_blocks = 0;
+    {
+        const cudaError_t e_mb = coop_max_blocks((const void *)glr_levels_kernel<CONN>, 256, 0, &max_blocks);
+        if (e_mb != cudaSuccess) return e_mb;
     }
     int nblocks = std::min((W64 * BY + 7) / 8, max_blocks);
     int *flags = &st.ctr[kGlrFlags];
@@ -462,7 +457,7 @@ static cudaError_t glr2d_impl(const Geom &g, const DevState &st, void *scratch, 
     if (e == cudaSuccess) e = cudaMemsetAsync(st.active, 0, (size_t)g.nreg, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&st.ctr[kActiveRegions], 0, 4, s);
     if (e != cudaSuccess) return e;
-    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, 152 * 32);
+    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, device_sms() * 32);
     glr_finish_kernel<CONN><<<nb, 256, 0, s>>>(g, st, W64, in);
     count_active_kernel<<<(g.nreg + 255) / 256, 256, 0, s>>>(st, g.nreg);
     return cudaGetLastError();
@@ -485,23 +480,18 @@ size_t cut2d_scratch_bytes(const Geom &g, int conn) {
 // Both closures; scratch must hold cut2d_scratch_bytes.  passes += passes made.
 template <int CONN>
 static cudaError_t cut2d_impl(const Geom &g, const DevState &st, void *scratch, unsigned char *smin,
-                              unsigned char *smax, int *h_changed, int *passes, cudaStream_t s) {
+                              unsigned char *smax, int *h_passes, cudaStream_t s) {
     const int W64 = (g.X + 63) / 64, BY = (g.Y + 63) / 64;
     const size_t plane = (size_t)g.Y * W64;
     u64 *M = (u64 *)scratch;
     u64 *Smin = M + CONN * plane;
     u64 *Tset = Smin + plane;
     const size_t total = (size_t)W64 * 64 * g.Y;
-    const int mb = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
-    static int max_blocks = 0;
-    if (!max_blocks) {
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cut_closure2d_kernel<CONN>, 256, 0);
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        max_blocks = per_sm * sms;
-        if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    const int mb = (int)std::min<size_t>((total + 255) / 256, device_sms() * 32);
+    int max_blocks = 0;
+    {
+        const cudaError_t e_mb = coop_max_blocks((const void *)cut_closure2d_kernel<CONN>, 256, 0, &max_blocks);
+        if (e_mb != cudaSuccess) return e_mb;
     }
     const int blocks = std::min((W64 * BY + 7) / 8, max_blocks);
     for (int which = 0; which < 2; ++which) {
@@ -515,20 +505,19 @@ static cudaError_t cut2d_impl(const Geom &g, const DevState &st, void *scratch, 
         void *args[] = {&gg, &w64, &by, (void *)&pm, &ps, &flags, &cnt, &max_passes};
         cudaError_t e = cudaLaunchCooperativeKernel((const void *)cut_closure2d_kernel<CONN>, dim3(blocks), dim3(256),
                                                     args, 0, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h_changed, cnt, 4, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        // closure passes made, copied without waiting (h_passes is pinned host memory)
+        if (e == cudaSuccess && h_passes) e = cudaMemcpyAsync(h_passes + which, cnt, 4, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return e;
-        *passes += *h_changed;
     }
-    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, 152 * 32);
+    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, device_sms() * 32);
     cut_bytes_kernel<<<nb, 256, 0, s>>>(g, W64, Smin, Tset, smin, smax);
     return cudaGetLastError();
 }
 
 cudaError_t cut2d(int conn, const Geom &g, const DevState &st, void *scratch, unsigned char *smin,
-                  unsigned char *smax, int *h_changed, int *passes, cudaStream_t s) {
-    if (conn == 4) return cut2d_impl<4>(g, st, scratch, smin, smax, h_changed, passes, s);
-    if (conn == 8) return cut2d_impl<8>(g, st, scratch, smin, smax, h_changed, passes, s);
+                  unsigned char *smax, int *h_passes, cudaStream_t s) {
+    if (conn == 4) return cut2d_impl<4>(g, st, scratch, smin, smax, h_passes, s);
+    if (conn == 8) return cut2d_impl<8>(g, st, scratch, smin, smax, h_passes, s);
     return cudaErrorInvalidValue;
 }
 

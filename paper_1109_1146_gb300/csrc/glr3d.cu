@@ -302,22 +302,17 @@ __global__ void cut3d_bytes_kernel(const Geom g, int W32, const u32 *Smin, const
 
 template <int TY, int TZ>
 static cudaError_t cut3d_impl(const Geom &g, const DevState &st, void *scratch, unsigned char *smin,
-                              unsigned char *smax, int *h_changed, int *passes, cudaStream_t s) {
+                              unsigned char *smax, int *h_passes, cudaStream_t s) {
     const int W32 = (g.X + 31) / 32;
     const size_t words = (size_t)g.Z * g.Y * W32;
     u32 *M = (u32 *)scratch;
     u32 *Smin = M + 6 * words;
     u32 *Tset = Smin + words;
-    const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, 152 * 32);
-    static int max_blocks = 0;
-    if (!max_blocks) {
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, closure3d_kernel<TY, TZ>, 256, 0);
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        max_blocks = per_sm * sms;
-        if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, device_sms() * 32);
+    int max_blocks = 0;
+    {
+        const cudaError_t e_mb = coop_max_blocks((const void *)closure3d_kernel<TY, TZ>, 256, 0, &max_blocks);
+        if (e_mb != cudaSuccess) return e_mb;
     }
     const int nblocks = std::min((g.nreg + 7) / 8, max_blocks);
     for (int which = 0; which < 2; ++which) {
@@ -331,21 +326,20 @@ static cudaError_t cut3d_impl(const Geom &g, const DevState &st, void *scratch, 
         void *args[] = {&gg, &w32, (void *)&pm, &ps, &flags, &cnt, &max_passes};
         cudaError_t e = cudaLaunchCooperativeKernel((const void *)closure3d_kernel<TY, TZ>, dim3(nblocks), dim3(256),
                                                     args, 0, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h_changed, cnt, 4, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        // closure passes made, copied without waiting (h_passes is pinned host memory)
+        if (e == cudaSuccess && h_passes) e = cudaMemcpyAsync(h_passes + which, cnt, 4, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return e;
-        *passes += *h_changed;
     }
-    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, 152 * 32);
+    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, device_sms() * 32);
     cut3d_bytes_kernel<<<nb, 256, 0, s>>>(g, W32, Smin, Tset, smin, smax);
     return cudaGetLastError();
 }
 
 cudaError_t cut3d(const Geom &g, const DevState &st, void *scratch, unsigned char *smin, unsigned char *smax,
-                  int *h_changed, int *passes, cudaStream_t s) {
-    if (g.ty == 16 && g.tz == 8) return cut3d_impl<16, 8>(g, st, scratch, smin, smax, h_changed, passes, s);
-    if (g.ty == 8 && g.tz == 8) return cut3d_impl<8, 8>(g, st, scratch, smin, smax, h_changed, passes, s);
-    if (g.ty == 8 && g.tz == 4) return cut3d_impl<8, 4>(g, st, scratch, smin, smax, h_changed, passes, s);
+                  int *h_passes, cudaStream_t s) {
+    if (g.ty == 16 && g.tz == 8) return cut3d_impl<16, 8>(g, st, scratch, smin, smax, h_passes, s);
+    if (g.ty == 8 && g.tz == 8) return cut3d_impl<8, 8>(g, st, scratch, smin, smax, h_passes, s);
+    if (g.ty == 8 && g.tz == 4) return cut3d_impl<8, 4>(g, st, scratch, smin, smax, h_passes, s);
     return cudaErrorInvalidValue;
 }
 
@@ -367,17 +361,12 @@ static cudaError_t glr3d_impl(const Geom &g, const DevState &st, void *scratch, 
     u32 *T = M + 6 * words;
     u32 *A = T + words;
     u32 *B = A + words;
-    const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, 152 * 32);
+    const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, device_sms() * 32);
     glr3d_masks_kernel<<<mb, 256, 0, s>>>(g, st, W32, M, T);
-    static int max_blocks = 0;
-    if (!max_blocks) {
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, glr3d_levels_kernel<TY, TZ>, 256, 0);
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        max_blocks = per_sm * sms;
-        if (max_blocks <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    int max_blocks = 0;
+    {
+        const cudaError_t e_mb = coop_max_blocks((const void *)glr3d_levels_kernel<TY, TZ>, 256, 0, &max_blocks);
+        if (e_mb != cudaSuccess) return e_mb;
     }
     const int nblocks = std::min((g.nreg + 7) / 8, max_blocks);
     int *flags = &st.ctr[kGlrFlags];
@@ -403,7 +392,7 @@ static cudaError_t glr3d_impl(const Geom &g, const DevState &st, void *scratch, 
     if (e == cudaSuccess) e = cudaMemsetAsync(st.active, 0, (size_t)g.nreg, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&st.ctr[kActiveRegions], 0, 4, s);
     if (e != cudaSuccess) return e;
-    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, 152 * 32);
+    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, device_sms() * 32);
     glr3d_finish_kernel<<<nb, 256, 0, s>>>(g, st, W32, fin);
     glr3d_count_kernel<<<(g.nreg + 255) / 256, 256, 0, s>>>(st, g.nreg);
     return cudaGetLastError();

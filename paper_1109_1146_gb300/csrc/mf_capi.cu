@@ -32,6 +32,13 @@ struct mf_grid {
     int *warmF = nullptr, *warmFt = nullptr, *warmE = nullptr;  // projected initial flows (warm start)
     bool warm_ready = false;
     int warm_rounds = 0;
+    // region reduction (Sec. 8): class codes, reduced inputs, device words
+    // [counts[4], konst, err] and their pinned mirror
+    unsigned char *red_codes = nullptr;
+    int *red_cs = nullptr, *red_ct = nullptr, *red_nl = nullptr;
+    unsigned long long *red_dev = nullptr, *h_red = nullptr;
+    bool reduced = false;                             // the current solve runs on the reduced inputs
+    long long red_konst = 0;                          // its constant (cut edges between the merged sets)
     int begin_active = -1;                            // active regions after mf_begin's relabel, -1: unknown
     // CUDA graph of the sweep loop (opts.graph_loop)
     cudaGraph_t graph = nullptr;
@@ -42,6 +49,12 @@ struct mf_grid {
     int graph_key[5] = {-1, -1, -1, -1, -1};          // options baked into the graph
     Counters64 *c64 = nullptr;
     int *h_ctr = nullptr;                             // pinned mirror of st.ctr
+    struct FinishHost {                               // pinned: results of the cut extraction, read after a sync
+        int passes[2];
+        long long f0;
+        unsigned long long ft;
+        Counters64 c;
+    } *h_fin = nullptr;
     long long boundary = 0;
     bool caps_set = false, begun = false, finished = false;
     int sweep = 0;
@@ -600,12 +613,14 @@ __global__ void complement_kernel(unsigned char *a, size_t n) {
 // host side
 static int grid_blocks(size_t n, int threads) {
     size_t b = (n + threads - 1) / threads;
-    return (int)std::min<size_t>(std::max<size_t>(b, 1), 152 * 16);
+    return (int)std::min<size_t>(std::max<size_t>(b, 1), device_sms() * 16);
 }
 
 template <int CONN>
 static cudaError_t launch_init(mf_grid *h) {
-    init_kernel<CONN><<<grid_blocks(h->g.n, 256), 256, 0, h->stream>>>(h->g, h->st, h->cs, h->ct, h->nl);
+    const int *cs = h->reduced ? h->red_cs : h->cs, *ct = h->reduced ? h->red_ct : h->ct;
+    const int *nl = h->reduced ? h->red_nl : h->nl;
+    init_kernel<CONN><<<grid_blocks(h->g.n, 256), 256, 0, h->stream>>>(h->g, h->st, cs, ct, nl);
     return cudaGetLastError();
 }
 template <int CONN>
@@ -617,10 +632,10 @@ template <int CONN>
 static cudaError_t launch_fuse_post(mf_grid *h, bool gap_on, cudaStream_t st) {
     if (CONN != 6) {
         const long long items = (long long)h->g.nreg * (2 * h->g.tx + 2 * (h->g.ty - 2));
-        const int fb = (int)std::min<long long>((items + 255) / 256, 152 * 8);
+        const int fb = (int)std::min<long long>((items + 255) / 256, device_sms() * 8);
         fuse2d_kernel<CONN><<<fb, 256, 0, st>>>(h->g, h->st);
         if (gap_on) gap_find_kernel<<<1, 1024, 0, st>>>(h->st);
-        post2d_kernel<CONN><<<152 * 8, 256, 0, st>>>(h->g, h->st);
+        post2d_kernel<CONN><<<device_sms() * 8, 256, 0, st>>>(h->g, h->st);
         finish_flags_kernel<<<(h->g.nreg + 255) / 256, 256, 0, st>>>(h->st, h->g.nreg);
         return cudaGetLastError();
     }
@@ -631,9 +646,9 @@ static cudaError_t launch_fuse_post(mf_grid *h, bool gap_on, cudaStream_t st) {
     return cudaGetLastError();
 }
 template <int CONN>
-static cudaError_t launch_cut_pass(mf_grid *h, unsigned char *set, int fwd) {
+static cudaError_t launch_cut_pass(mf_grid *h, unsigned char *set, int fwd, cudaStream_t st) {
     const int V = h->g.tx * h->g.ty * h->g.tz;
-    cut_pass_kernel<CONN><<<h->g.nreg, 256, V, h->stream>>>(h->g, h->st, set, fwd);
+    cut_pass_kernel<CONN><<<h->g.nreg, 256, V, st>>>(h->g, h->st, set, fwd);
     return cudaGetLastError();
 }
 
@@ -695,8 +710,11 @@ __global__ void certify_kernel(const Geom g, const DevState st, const int *__res
 
 template <int CONN>
 static cudaError_t launch_certify(mf_grid *g, unsigned long long *sums) {
-    certify_kernel<CONN><<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->g, g->st, g->cs, g->ct, g->nl, g->smin,
-                                                                          sums);
+    // a solve on reduced inputs is certified on them (the merged vertices are
+    // isolated there, so S_min with S* added has the same cut capacity)
+    const int *cs = g->reduced ? g->red_cs : g->cs, *ct = g->reduced ? g->red_ct : g->ct;
+    const int *nl = g->reduced ? g->red_nl : g->nl;
+    certify_kernel<CONN><<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->g, g->st, cs, ct, nl, g->smin, sums);
     return cudaGetLastError();
 }
 
@@ -751,6 +769,10 @@ static void free_all(mf_grid *h) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    if (h->h_fin) cudaFreeHost(h->h_fin);
+    for (void *p : {(void *)h->red_codes, (void *)h->red_cs, (void *)h->red_ct, (void *)h->red_nl, (void *)h->red_dev})
+        if (p) cudaFree(p);
+    if (h->h_red) cudaFreeHost(h->h_red);
     if (h->br_scratch) cudaFree(h->br_scratch);
     if (h->h_br) cudaFreeHost(h->h_br);
     for (auto &e : h->ev)
@@ -825,6 +847,7 @@ mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int con
         }
     }
     e = cudaMallocHost((void **)&g->h_ctr, kCtrWords * 4);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_fin, sizeof(mf_grid::FinishHost));
     if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MF_ENOMEM); }
     for (auto &ev : g->ev) {
         e = cudaEventCreate(&ev);
@@ -870,6 +893,45 @@ mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const in
     return MF_OK;
 }
 
+// The region reduction of Sec. 8 on the stored inputs: class codes of every
+// vertex into g->red_codes (and the reduced-input buffers allocated); the
+// counts and the round-cap flag are read back (one wait).  *ok = false if an
+// Augment of some region hit the round cap (the codes are then not used).
+static mf_status reduction_run(mf_grid *g, const int32_t *tile, bool *ok) {
+    int t[3] = {g->g.tx, g->g.ty, g->g.tz};
+    if (tile && (tile[0] | tile[1] | tile[2])) {
+        t[0] = tile[0];
+        t[1] = tile[1];
+        t[2] = g->ndim == 3 ? tile[2] : 1;
+    }
+    RedGeom rg{};
+    if (!reduction_supported(g->conn, t, &rg, g->g)) {
+        // the solver's tile does not fit one region network into shared memory
+        if (tile && (tile[0] | tile[1] | tile[2])) return fail(g, MF_EINVAL, "reduction tile too large");
+        const int d2[3] = {32, 32, 1}, d3[3] = {32, 8, 4};
+        if (!reduction_supported(g->conn, g->ndim == 3 ? d3 : d2, &rg, g->g))
+            return fail(g, MF_EINVAL, "no supported reduction tile");
+    }
+    const size_t n = (size_t)g->g.n;
+    if (!g->red_codes) {
+        CK(cudaMalloc(&g->red_codes, n));
+        CK(cudaMalloc(&g->red_cs, n * 4));
+        CK(cudaMalloc(&g->red_ct, n * 4));
+        CK(cudaMalloc(&g->red_nl, (size_t)g->H * n * 4));
+        CK(cudaMalloc(&g->red_dev, 8 * sizeof(unsigned long long)));
+        CK(cudaMallocHost((void **)&g->h_red, 8 * sizeof(unsigned long long)));
+    }
+    CK(cudaMemsetAsync(g->red_dev, 0, 8 * sizeof(unsigned long long), g->stream));
+    const int mr = g->opts.max_rounds > 0 ? g->opts.max_rounds : 1 << 16;
+    CK(launch_region_reduction(g->conn, rg, g->cs, g->ct, g->nl, g->red_codes, g->red_dev, mr, (int *)&g->red_dev[5],
+                               g->stream));
+    // red_dev[4] (zero here) later receives the constant of the merged inputs
+    CK(cudaMemcpyAsync(g->h_red, g->red_dev, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    *ok = ((int *)&g->h_red[5])[0] == 0;
+    return MF_OK;
+}
+
 mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
@@ -885,6 +947,22 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
     CK(cudaMemsetAsync(g->st.ctr, 0, kCtrWords * 4, g->stream));
     CK(cudaMemsetAsync(g->c64, 0, sizeof(Counters64), g->stream));
     CK(cudaMemsetAsync(g->st.hist, 0, (kHistBins + 1) * 4, g->stream));
+    g->reduced = false;
+    int red_launches = 0;
+    if (g->opts.region_reduction) {
+        if (g->opts.warm_start) return fail(g, MF_EINVAL, "region_reduction and warm_start cannot be combined");
+        bool ok = false;
+        mf_status rs = reduction_run(g, nullptr, &ok);
+        if (rs != MF_OK) return rs;
+        if (ok) {
+            // merge S* into s and T* into t: reduced inputs, the constant into flow0
+            CK(launch_reduction_apply(g->conn, g->g, g->red_codes, g->cs, g->ct, g->nl, g->red_cs, g->red_ct,
+                                      g->red_nl, (unsigned long long *)g->st.flow0, &g->red_dev[4], g->stream));
+            CK(cudaMemcpyAsync(&g->h_red[4], &g->red_dev[4], 8, cudaMemcpyDeviceToHost, g->stream));
+            g->reduced = true;
+            red_launches = 2;
+        }
+    }
     if (g->opts.warm_start) {
         if (!g->warm_ready) return fail(g, MF_ESTATE, "warm_start requested without a successful mf_warm_start");
         CK(launch_warm_init(g->conn, g->g, g->st, g->cs, g->ct, g->nl, g->warmF, g->warmFt, g->warmE, g->stream));
@@ -893,13 +971,14 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
     }
     hist_init_kernel<<<1, 32, 0, g->stream>>>(g->st, (int)g->boundary);
     CK(cudaGetLastError());
-    g->launches = 2;
+    g->launches = 2 + red_launches;
     g->sweep = 0;
     g->begun = true;
     g->finished = false;
     memset(&g->stats, 0, sizeof(g->stats));
     g->stats.boundary_size = (int32_t)g->boundary;
     g->stats.projection_rounds = g->opts.warm_start ? g->warm_rounds : 0;
+    g->stats.reduced_vertices = g->reduced ? (int32_t)(g->h_red[0] + g->h_red[1]) : 0;
     g->begin_active = -1;
     if (g->opts.warm_start && g->ndim == 2 && glr2d_supported(g->g)) {
         // A projected preflow leaves excess where the prediction was wrong and
@@ -991,6 +1070,7 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
         cudaEventElapsedTime(&b, g->ev[5], g->ev[6]);
         g->stats.ms_discharge += a;
         g->stats.ms_fuse += b;
+        g->stats.discharge_launches++;
     }
     ++g->sweep;
     g->stats.sweeps = g->sweep;
@@ -1042,49 +1122,69 @@ mf_status mf_boundary_relabel(mf_grid *g, int32_t *info) {
     return MF_OK;
 }
 
-mf_status mf_finish(mf_grid *g) {
-    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
-    if (!g->begun) return fail(g, MF_ESTATE, "mf_begin has not been called");
-    int passes = 0;
+// The cut extraction and the read-back of the flow value and counters,
+// enqueued on stream st without waiting (results land in g->h_fin); the
+// closures of 2D grids and of 3D grids with 32-wide tiles run on the device
+// to their fixed point, other 3D tiles loop on the host.
+static mf_status finish_enqueue(mf_grid *g, cudaStream_t st) {
+    g->h_fin->passes[0] = g->h_fin->passes[1] = 0;
     if (g->ndim == 2) {
-        CK(cut2d(g->conn, g->g, g->st, g->cut_scratch, g->smin, g->tset, g->h_ctr, &passes, g->stream));
-        g->launches += 2 + passes + 1;
+        CK(cut2d(g->conn, g->g, g->st, g->cut_scratch, g->smin, g->tset, g->h_fin->passes, st));
+        g->launches += 5;
     } else if (glr3d_supported(g->g)) {
-        CK(cut3d(g->g, g->st, g->cut_scratch, g->smin, g->tset, g->h_ctr, &passes, g->stream));
+        CK(cut3d(g->g, g->st, g->cut_scratch, g->smin, g->tset, g->h_fin->passes, st));
         g->launches += 5;
     } else {
-        cut_seed_kernel<<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->g, g->st, g->smin, g->tset);
+        int passes = 0;
+        cut_seed_kernel<<<grid_blocks(g->g.n, 256), 256, 0, st>>>(g->g, g->st, g->smin, g->tset);
         CK(cudaGetLastError());
         for (int which = 0; which < 2; ++which) {
             for (;;) {
-                CK(cudaMemsetAsync(&g->st.ctr[kChanged], 0, 4, g->stream));
-                CK(DISPATCH(g->conn, launch_cut_pass, g, which == 0 ? g->smin : g->tset, which == 0 ? 1 : 0));
+                CK(cudaMemsetAsync(&g->st.ctr[kChanged], 0, 4, st));
+                CK(DISPATCH(g->conn, launch_cut_pass, g, which == 0 ? g->smin : g->tset, which == 0 ? 1 : 0, st));
                 ++g->launches;
-                CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
-                CK(cudaStreamSynchronize(g->stream));
+                CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
                 ++passes;
                 if (!g->h_ctr[kChanged]) break;
             }
         }
-        complement_kernel<<<grid_blocks(g->g.n, 256), 256, 0, g->stream>>>(g->tset, (size_t)g->g.n);
+        complement_kernel<<<grid_blocks(g->g.n, 256), 256, 0, st>>>(g->tset, (size_t)g->g.n);
         CK(cudaGetLastError());
         g->launches += 2;
+        g->h_fin->passes[0] = passes;
     }
-    g->stats.cut_passes = passes;
-    long long f0 = 0;
-    unsigned long long ft = 0;
-    CK(cudaMemcpyAsync(&f0, g->st.flow0, 8, cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaMemcpyAsync(&ft, g->st.flow_t, 8, cudaMemcpyDeviceToHost, g->stream));
-    Counters64 c{};
-    CK(cudaMemcpyAsync(&c, g->c64, sizeof(c), cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
-    g->stats.flow_value = f0 + (long long)ft;
-    g->stats.stages = (int64_t)c.stages;
-    g->stats.rounds = (int64_t)c.rounds;
-    g->stats.discharges = (int64_t)c.discharges;
-    g->stats.discharged_vertices = (int64_t)c.discharged_vertices;
+    if (g->reduced) {  // S_min gains the strong sources, S_max loses the strong sinks
+        CK(launch_reduction_cut((size_t)g->g.n, g->red_codes, g->smin, g->tset, st));
+        ++g->launches;
+    }
+    CK(cudaMemcpyAsync(&g->h_fin->f0, g->st.flow0, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&g->h_fin->ft, g->st.flow_t, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&g->h_fin->c, g->c64, sizeof(Counters64), cudaMemcpyDeviceToHost, st));
+    return MF_OK;
+}
+
+// after the stream of finish_enqueue has been synchronised
+static void finish_collect(mf_grid *g) {
+    const mf_grid::FinishHost &f = *g->h_fin;
+    g->stats.cut_passes = f.passes[0] + f.passes[1];
+    g->stats.flow_value = f.f0 + (long long)f.ft;
+    g->stats.stages = (int64_t)f.c.stages;
+    g->stats.rounds = (int64_t)f.c.rounds;
+    g->stats.discharges = (int64_t)f.c.discharges;
+    g->stats.discharged_vertices = (int64_t)f.c.discharged_vertices;
     g->stats.launches = g->launches;
+    g->red_konst = g->reduced ? (long long)g->h_red[4] : 0;
     g->finished = true;
+}
+
+mf_status mf_finish(mf_grid *g) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!g->begun) return fail(g, MF_ESTATE, "mf_begin has not been called");
+    mf_status s = finish_enqueue(g, g->stream);
+    if (s != MF_OK) return s;
+    CK(cudaStreamSynchronize(g->stream));
+    finish_collect(g);
     return MF_OK;
 }
 
@@ -1235,7 +1335,10 @@ struct BatchBufs {
     int2 *regs = nullptr, *items = nullptr;
     int *type_of = nullptr, *cnt = nullptr, *head = nullptr, *sweeps = nullptr, *any = nullptr;
     unsigned char *done = nullptr;
+    std::vector<cudaEvent_t> tev;          // host loop: a start / end event per kernel type
     ~BatchBufs() {
+        for (cudaEvent_t e : tev)
+            if (e) cudaEventDestroy(e);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -1269,6 +1372,7 @@ static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *ins
         if (e != cudaSuccess) return fail(g, MF_ECUDA, std::string("batched global relabel: ") + cudaGetErrorString(e));
         h->stats.global_relabels++;
         h->stats.relabel_levels += levels;
+        h->launches += 4 + levels;
     }
     CK(cudaMemsetAsync(any_dev, 0, sizeof(int), s));
     batch_relabel_end_kernel<<<(count + 255) / 256, 256, 0, s>>>(insts, done_dev, any_dev, count);
@@ -1357,10 +1461,18 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     sa.partial = o.partial_discharge;
     sa.max_rounds = o.max_rounds;
     sa.variant = o.kernel_variant;
-    const int eb = (int)std::min<long long>(((long long)nregs + 255) / 256, 152 * 8);
+    const int eb = (int)std::min<long long>(((long long)nregs + 255) / 256, device_sms() * 8);
     mf_status rs = MF_OK;
     long long launches = 0;
     const int per_sweep = 6 + nt + (o.global_gap ? 1 : 0);
+    // host loop: the persistent discharge launches of each kernel type are
+    // timed with events (no event can be recorded inside the graph's loop body)
+    std::vector<double> type_ms(nt, 0.0);
+    std::vector<int> type_launches(nt, 0), hcnt(nt, 0);
+    if (!o.graph_loop) {
+        B.tev.assign(2 * nt, nullptr);
+        for (auto &e : B.tev) CK(cudaEventCreate(&e));
+    }
     // one sweep of the whole batch on stream st (sweep index from the host, or
     // from sweep_dev inside a graph)
     auto enqueue_sweep = [&](cudaStream_t st, int sweep_host, const int *sweep_dev) -> cudaError_t {
@@ -1374,9 +1486,14 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         batch_reset_kernel<<<(count + 255) / 256, 256, 0, st>>>(B.insts, B.done, count);
         batch_items_kernel<<<eb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done, B.type_of, nregs, B.items, B.cnt);
         e = cudaGetLastError();
-        for (int t = 0; t < nt && e == cudaSuccess; ++t)
-            e = launch_discharge_batch(types[t].conn, types[t].tx, types[t].ty, types[t].tz, a.variant, B.insts,
-                                       B.items + (size_t)t * nregs, B.cnt + t, B.head + t, a, 152 * 4, st);
+        for (int t = 0; t < nt && e == cudaSuccess; ++t) {
+            if (!sweep_dev) e = cudaEventRecord(B.tev[2 * t], st);
+            if (e == cudaSuccess)
+                e = launch_discharge_batch(types[t].conn, types[t].tx, types[t].ty, types[t].tz, a.variant, B.insts,
+                                           B.items + (size_t)t * nregs, B.cnt + t, B.head + t, a, device_sms() * 4,
+                                           st);
+            if (e == cudaSuccess && !sweep_dev) e = cudaEventRecord(B.tev[2 * t + 1], st);
+        }
         if (e != cudaSuccess) return e;
         // fusion / gap / activity per connectivity of the instances (one launch per connectivity)
         for (int conn : {4, 8, 6}) {
@@ -1459,7 +1576,15 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
             CK(enqueue_sweep(s, sweep, nullptr));
             launches += per_sweep;
             CK(cudaMemcpyAsync(g->h_ctr, B.any, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(hcnt.data(), B.cnt, sizeof(int) * nt, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+            for (int t = 0; t < nt; ++t) {
+                if (!hcnt[t]) continue;  // no item of this type in the sweep
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, B.tev[2 * t], B.tev[2 * t + 1]));
+                type_ms[t] += ms;
+                type_launches[t]++;
+            }
             if (!g->h_ctr[0]) break;
             if (sweep + 1 >= cap) {
                 rs = fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left in the batch");
@@ -1475,22 +1600,26 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     CK(cudaEventRecord(g->ev[2], s));
     std::vector<int> hsweeps(count);
     CK(cudaMemcpyAsync(hsweeps.data(), B.sweeps, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+    // error words of every instance, then (if the loop ended normally) the cut
+    // extraction of every instance, all enqueued on the batch stream with one
+    // wait at the end
+    for (int i = 0; i < count; ++i)
+        CK(cudaMemcpyAsync(grids[i]->h_ctr, grids[i]->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, s));
+    if (rs == MF_OK) {
+        for (int i = 0; i < count; ++i) {
+            mf_status st = finish_enqueue(grids[i], s);
+            if (st != MF_OK) return fail(g, st, grids[i]->err);
+        }
+    }
     CK(cudaStreamSynchronize(s));
-    // errors, cuts and flow values per instance
     for (int i = 0; i < count; ++i) {
         mf_grid *h = grids[i];
-        CK(cudaMemcpyAsync(h->h_ctr, h->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
         h->sweep = hsweeps[i];
         h->stats.sweeps = hsweeps[i];
         if (h->h_ctr[kError] && rs == MF_OK) rs = fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
     }
-    if (rs == MF_OK) {
-        for (int i = 0; i < count; ++i) {
-            mf_status st = mf_finish(grids[i]);
-            if (st != MF_OK) return st;
-        }
-    }
+    if (rs == MF_OK)
+        for (int i = 0; i < count; ++i) finish_collect(grids[i]);
     CK(cudaEventRecord(g->ev[3], s));
     CK(cudaEventSynchronize(g->ev[3]));
     float a = 0, b = 0, c = 0;
@@ -1503,10 +1632,31 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         h->stats.ms_sweeps = b;
         h->stats.ms_cut = c;
         h->stats.ms_total = a + b + c;
-        h->stats.launches += launches;
+        if (i == 0) h->stats.launches += launches;  // launches shared by the whole batch, counted once
+        h->stats.ms_discharge = type_ms[type_of[i]];
+        h->stats.discharge_launches = type_launches[type_of[i]];
         if (stats) stats[i] = h->stats;
     }
     return rs;
+}
+
+mf_status mf_region_reduction(mf_grid *g, const int32_t tile[3], uint8_t *codes, int on_device, int64_t counts[4]) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!codes) return fail(g, MF_EINVAL, "codes is NULL");
+    if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
+    const int saved = g->opts.max_rounds;
+    g->opts.max_rounds = 0;
+    bool ok = false;
+    mf_status rs = reduction_run(g, tile, &ok);
+    g->opts.max_rounds = saved;
+    if (rs != MF_OK) return rs;
+    if (!ok) return fail(g, MF_EROUNDLIMIT, "an Augment of the region reduction hit its round cap");
+    CK(cudaMemcpyAsync(codes, g->red_codes, (size_t)g->g.n,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (counts)
+        for (int k = 0; k < 4; ++k) counts[k] = (int64_t)g->h_red[k];
+    return MF_OK;
 }
 
 mf_status mf_warm_features(mf_grid *g, float *x) {
@@ -1592,9 +1742,11 @@ mf_status mf_certify(mf_grid *g, int64_t *cut_capacity, int64_t *violations, int
     int64_t flow = 0;
     mf_status s = mf_flow_value(g, &flow);
     if (s != MF_OK) return s;
-    if (cut_capacity) *cut_capacity = (int64_t)h[0];
+    // the constant of the reduction: cut edges between the merged vertex sets
+    const int64_t k = g->reduced ? (int64_t)g->red_konst : 0;
+    if (cut_capacity) *cut_capacity = (int64_t)h[0] + k;
     if (violations) *violations = (int64_t)h[2];
-    if (certified) *certified = h[2] == 0 && (int64_t)h[0] == flow && (int64_t)h[1] == flow;
+    if (certified) *certified = h[2] == 0 && (int64_t)h[0] + k == flow && (int64_t)h[1] + k == flow;
     return MF_OK;
 }
 

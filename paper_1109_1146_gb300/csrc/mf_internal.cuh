@@ -151,6 +151,35 @@ struct Inst {
     int conn;   // stencil of the instance (batched fusion kernels are per connectivity)
 };
 
+// reduction.cu: region reduction of Sec. 8 (class codes per vertex)
+constexpr unsigned char kStrongSource = 1, kStrongSink = 2, kWeakSource = 4, kWeakSink = 8;
+constexpr int kRedMaxSmem = 232000;  // shared memory of one region network (tile plus a one-cell ring)
+struct RedGeom {
+    int X, Y, Z;        // grid dims
+    int tx, ty, tz;     // region shape of the reduction
+    int RX, RY, RZ;     // regions per axis
+    int EX, EY, EZ, E;  // tile plus ring (EZ = 1 in 2D), cells
+};
+size_t reduction_smem_bytes(int conn, const RedGeom &rg);
+bool reduction_supported(int conn, const int tile[3], RedGeom *out, const Geom &g);
+// codes[v] for every vertex; counts[4] += strong sources, strong sinks, weak
+// sources, weak sinks; *err = 1 if an Augment hit max_rounds
+cudaError_t launch_region_reduction(int conn, const RedGeom &rg, const int *cs, const int *ct, const int *nl,
+                                    unsigned char *codes, unsigned long long *counts, int max_rounds, int *err,
+                                    cudaStream_t s);
+cudaError_t launch_reduction_apply(int conn, const Geom &g, const unsigned char *codes, const int *cs, const int *ct,
+                                   const int *nl, int *cs2, int *ct2, int *nl2, unsigned long long *konst,
+                                   unsigned long long *konst2, cudaStream_t s);
+cudaError_t launch_reduction_cut(size_t n, const unsigned char *codes, unsigned char *smin, unsigned char *smax,
+                                 cudaStream_t s);
+
+// devinfo.cu: per-device launch facts, cached per (kernel, device)
+int device_sms();  // SMs of the current device (1 if it cannot be queried)
+// co-resident blocks of a cooperative kernel on the current device
+cudaError_t coop_max_blocks(const void *kernel, int threads, size_t smem, int *out);
+// allow `bytes` of dynamic shared memory for the kernel on the current device
+cudaError_t ensure_smem_attr(const void *kernel, int bytes);
+
 // launchers (ard_discharge.cu)
 size_t discharge_smem_bytes(int conn, int tx, int ty, int tz);
 bool discharge_supported(int conn, int tx, int ty, int tz);
@@ -158,8 +187,10 @@ cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const 
                              cudaStream_t stream);
 // cut2d.cu: residual closures S_min / S_max of a 2D grid on bit masks
 size_t cut2d_scratch_bytes(const Geom &g, int conn);
+// h_passes: NULL or pinned host int[2] that receives the passes of each
+// closure asynchronously (valid after the stream is synchronised); no wait
 cudaError_t cut2d(int conn, const Geom &g, const DevState &st, void *scratch, unsigned char *smin,
-                  unsigned char *smax, int *h_changed, int *passes, cudaStream_t s);
+                  unsigned char *smax, int *h_passes, cudaStream_t s);
 // message returned by mf_last_error(NULL) for calls without a handle (mf_capi.cu)
 void set_static_error(const std::string &m);
 // global relabel: exact region distance on bit masks (2D, tiles 32 or 64 wide)
@@ -170,7 +201,7 @@ size_t glr3d_scratch_bytes(const Geom &g);
 cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels, cudaStream_t s);
 // both cut closures on bit masks (scratch: glr3d_scratch_bytes); passes += passes made
 cudaError_t cut3d(const Geom &g, const DevState &st, void *scratch, unsigned char *smin, unsigned char *smax,
-                  int *h_changed, int *passes, cudaStream_t s);
+                  int *h_passes, cudaStream_t s);
 cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
                   cudaStream_t s);
 // persistent discharge over a work queue of (instance, region) items of one

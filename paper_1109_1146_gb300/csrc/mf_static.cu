@@ -7,7 +7,6 @@
 // The array is part of the library image: each GPU that loads the library
 // holds it until the process exits.
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "../../include/mf.h"
@@ -19,10 +18,6 @@ constexpr size_t kCtrBytes = 256;                   // counter words (closure fl
 constexpr size_t kStaticScratchBytes = 8u << 20;    // 8 MiB in total
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kStaticScratchBytes];
-
-constexpr int kMaxDevices = 64;
-void *g_noalloc_addr[kMaxDevices];  // device address of the array, resolved once per device
-std::mutex g_noalloc_mu;
 
 }  // namespace
 
@@ -66,34 +61,26 @@ extern "C" mf_status mf_min_cut_2d_noalloc(const int64_t dims[2], int connectivi
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
         set_static_error(std::string("mf_min_cut_2d_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
         return MF_ECUDA;
     }
+    // The array's host-side name is not a device address: ask the runtime for
+    // the address of the current device's copy on every call (cheap; a cached
+    // address would go stale if the module were reloaded, e.g. after
+    // cudaDeviceReset).
     void *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
-            // the symbol's host-side name is not a device address: ask the runtime
-            // for the address of this device's copy, once, with the device current
-            e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                g_noalloc_addr[dev] = nullptr;
-                set_static_error(std::string("mf_min_cut_2d_noalloc: cudaGetSymbolAddress: ") +
-                                 cudaGetErrorString(e));
-                return MF_ECUDA;
-            }
-        }
-        base = g_noalloc_addr[dev];
+    e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+    if (e != cudaSuccess || !base) {
+        set_static_error(std::string("mf_min_cut_2d_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return MF_ECUDA;
     }
     DevState st{};
     st.cap = const_cast<int *>(res);
     st.tcap = const_cast<int *>(tres);
     st.exc = const_cast<int *>(exc);
     st.ctr = (int *)base;  // the closure kernel clears the flag words it uses
-    int h_changed = 0, passes = 0;
-    e = cut2d(connectivity, g, st, (unsigned char *)base + kCtrBytes, smin, smax, &h_changed, &passes,
-              (cudaStream_t)cuda_stream);
+    e = cut2d(connectivity, g, st, (unsigned char *)base + kCtrBytes, smin, smax, nullptr, (cudaStream_t)cuda_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
     if (e != cudaSuccess) {
         set_static_error(std::string("mf_min_cut_2d_noalloc: ") + cudaGetErrorString(e));

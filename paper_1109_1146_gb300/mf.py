@@ -22,7 +22,7 @@ STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "
 
 # every symbol include/mf.h declares
 EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
-           "mf_finish", "mf_boundary_relabel", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
+           "mf_finish", "mf_boundary_relabel", "mf_region_reduction", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
            "mf_last_error", "mf_min_cut_2d_noalloc", "mf_solve_batch", "mf_warm_features", "mf_warm_targets",
            "mf_warm_start", "mf_certify", "mf_get_flow", "mf_load_model", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
            "mf_cnn_get_params", "mf_cnn_set_params", "mf_cnn_get_grads", "mf_cnn_forward", "mf_cnn_infer",
@@ -36,7 +36,7 @@ class mf_opts(ctypes.Structure):
                 ("max_rounds", ctypes.c_int32), ("kernel_variant", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("graph_loop", ctypes.c_int32),
                 ("boundary_relabel_period", ctypes.c_int32), ("global_relabel_first", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("region_reduction", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class mf_stats(ctypes.Structure):
@@ -48,7 +48,8 @@ class mf_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_discharge", ctypes.c_double), ("ms_fuse", ctypes.c_double),
                 ("global_relabels", ctypes.c_int32), ("relabel_levels", ctypes.c_int32),
                 ("projection_rounds", ctypes.c_int32), ("boundary_relabels", ctypes.c_int32),
-                ("boundary_relabel_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("boundary_relabel_levels", ctypes.c_int32), ("discharge_launches", ctypes.c_int32),
+                ("reduced_vertices", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -72,6 +73,7 @@ SIGNATURES = {
     "mf_sweep": (_I, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "mf_finish": (_I, [_P]),
     "mf_boundary_relabel": (_I, [_P, _P]),
+    "mf_region_reduction": (_I, [_P, _P, _P, _I, _P]),
     "mf_get_cut": (_I, [_P, _P, _I, _I]),
     "mf_flow_value": (_I, [_P, ctypes.POINTER(_I64)]),
     "mf_get_residual": (_I, [_P, _P, _P, _P, _I]),
@@ -273,6 +275,17 @@ class Grid:
         info = (ctypes.c_int32 * 4)()
         self._check(self._lib.mf_boundary_relabel(self._h, ctypes.addressof(info)))
         return {"active": info[0], "levels": info[1], "merged": info[2], "applied": bool(info[3])}
+
+    def region_reduction(self, tile=None, out=None):
+        """Region reduction of Sec. 8 (mf_region_reduction): (codes uint8[n],
+        counts [strong sources, strong sinks, weak sources, weak sinks])."""
+        if out is None:
+            out = np.empty(self.n, dtype=np.uint8)
+        p, dev = _ptr(out)
+        t = None if tile is None else (ctypes.c_int32 * 3)(*(tuple(tile) + (1,) * (3 - len(tile))))
+        cnt = (ctypes.c_int64 * 4)()
+        self._check(self._lib.mf_region_reduction(self._h, t, p, dev, ctypes.addressof(cnt)))
+        return out, list(cnt)
 
     def get_cut(self, which=0, out=None):
         if out is None:

@@ -70,9 +70,12 @@ def test_committed_traffic_belongs_to_the_current_kernel_source():
     src = os.path.join(ROOT, "paper_1109_1146_gb300", "csrc", "ard_discharge2d.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     recorded = [ln.split("=", 1)[1].strip() for ln in open(p) if ln.startswith("bench: kernel_sha256_16=")]
-    v = bench.committed_traffic((32, 32, 1))
+    kname = bench.kernel_name(8, (32, 32, 1))
+    assert kname == "ard_discharge2d_kernel<8,32,32,256>"
+    v = bench.committed_traffic(kname, (32, 32, 1))
     if recorded == [sha]:
         assert v is not None and 20.0 < v < 200.0
     else:
         assert v is None  # a stale figure is never reported
-    assert bench.committed_traffic((64, 64, 1)) is None  # measured for 32x32 tiles only
+    assert bench.committed_traffic(kname, (64, 64, 1)) is None  # measured for 32x32 tiles only
+    assert bench.committed_traffic(bench.kernel_name(6, (32, 8, 4), batch=True), (32, 8, 4)) is None or recorded

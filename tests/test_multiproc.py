@@ -66,3 +66,16 @@ def test_replica_instances_differ_by_rank():
     a, b = bench.make_instance(seed=0, side=64), bench.make_instance(seed=1, side=64)
     assert a.dims == b.dims and a.conn == b.conn == 8
     assert (a.cs != b.cs).any()
+
+
+def test_batch_replicas_differ_by_rank_and_reference_covers_the_batch():
+    sys.path.insert(0, ROOT)
+    import bench
+    a = bench.batch_instances(batch_seed=0, only=[3, 400])
+    b = bench.batch_instances(batch_seed=1, only=[3, 400])
+    assert a[0].conn == 4 and a[1].conn == 6
+    assert (a[0].dims != b[0].dims) or (a[0].cs.shape != b[0].cs.shape) or (a[0].cs != b[0].cs).any()
+    for steps in (1, 3, 20, 600):
+        shares = bench.reference_shares(512, steps)
+        flat = sorted(i for sh in shares for i in sh)
+        assert flat == list(range(512)) and len(shares) == steps

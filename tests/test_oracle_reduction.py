@@ -84,3 +84,70 @@ def test_classes_decide_vertices():
     r = region_reduction(inst.dims, 4, (8, 8, 1), inst.cs, inst.ct, inst.nlink)
     decided = ((r["codes"] & (STRONG_SINK | WEAK_SOURCE)) != 0).mean()
     assert 0.05 < decided < 1.0
+
+
+@pytest.mark.parametrize("dims,conn,tile", [((12, 10, 1), 4, (4, 4, 1)), ((12, 9, 1), 8, (4, 3, 1)),
+                                            ((6, 6, 4), 6, (3, 3, 2))])
+@pytest.mark.parametrize("seed", range(3))
+def test_reduced_instance_keeps_the_minimum_cuts(dims, conn, tile, seed):
+    """Merging the strong sources into s and the strong sinks into t keeps
+    the minimum cut value (plus the constant of the merged edges) and both
+    canonical cuts: S_min = S* + S_min(reduced), S_max = S_max(reduced) - T*
+    (Dinic on both networks)."""
+    from oracle.reduction import reduce_instance
+    inst = grids.random_grid(dims, conn, 30 + seed, cmax=15, tmax=30, p_zero=0.3)
+    ref = oracle.maxflow(inst.dims, conn, inst.cs, inst.ct, inst.nlink)
+    codes = region_reduction(inst.dims, conn, tile, inst.cs, inst.ct, inst.nlink)["codes"]
+    S, T = (codes & STRONG_SOURCE) != 0, (codes & STRONG_SINK) != 0
+    cs2, ct2, nl2, K = reduce_instance(inst.dims, conn, inst.cs, inst.ct, inst.nlink, codes)
+    red = oracle.maxflow(inst.dims, conn, cs2, ct2, nl2)
+    assert red["flow"] + K == ref["flow"]
+    np.testing.assert_array_equal(red["smin"].astype(bool) | S, ref["smin"].astype(bool))
+    np.testing.assert_array_equal(red["smax"].astype(bool) & ~T, ref["smax"].astype(bool))
+    assert (S | T).any()  # not vacuous
+
+
+def test_classes_do_not_depend_on_the_augmenting_paths(monkeypatch):
+    """The classes are functions of the network alone: augmenting along other
+    paths (depth-first, adjacency shuffled before every step) gives the same
+    codes, so a parallel implementation can be compared with them exactly."""
+    import random
+    import oracle.reduction as R
+    inst = grids.random_grid((12, 10, 1), 4, 5, cmax=6, tmax=10, p_zero=0.3)
+    want = region_reduction(inst.dims, 4, (4, 4, 1), inst.cs, inst.ct, inst.nlink)["codes"]
+    rng = random.Random(1)
+
+    def dfs_augment(self, src, dst):
+        for a in self.adj:
+            rng.shuffle(a)
+        total = 0
+        while True:
+            prev, stack = {src: -1}, [src]
+            while stack and dst not in prev:
+                u = stack.pop()
+                for e in self.adj[u]:
+                    w = self.to[e]
+                    if self.cap[e] > 0 and w not in prev:
+                        prev[w] = e
+                        stack.append(w)
+            if dst not in prev:
+                return total
+            path, w = [], dst
+            while w != src:
+                e = prev[w]
+                path.append(e)
+                w = self.to[e ^ 1]
+            d = min(self.cap[e] for e in path)
+            for e in path:
+                self.cap[e] -= d
+                self.cap[e ^ 1] += d
+            total += d
+    monkeypatch.setattr(R._Net, "augment", dfs_augment)
+    for tile in ((4, 4, 1), (6, 5, 1), (12, 10, 1)):
+        w = region_reduction(inst.dims, 4, tile, inst.cs, inst.ct, inst.nlink)["codes"]
+        monkeypatch.undo()
+        base = region_reduction(inst.dims, 4, tile, inst.cs, inst.ct, inst.nlink)["codes"]
+        monkeypatch.setattr(R._Net, "augment", dfs_augment)
+        np.testing.assert_array_equal(w, base)
+    monkeypatch.undo()
+    np.testing.assert_array_equal(region_reduction(inst.dims, 4, (4, 4, 1), inst.cs, inst.ct, inst.nlink)["codes"], want)

@@ -64,3 +64,27 @@ def test_noalloc_rejects_oversized_grid():
                                    out.data_ptr(), None)
     assert st == mf.MF_EINVAL
     assert "static maximum" in lib.mf_last_error(None).decode()
+
+
+@pytest.mark.parametrize("side,conn,ok", [(2560, 8, True), (2561, 8, False), (3328, 4, True), (3329, 4, False)])
+def test_noalloc_size_limit(side, conn, ok):
+    """The largest square grids that fit the 8 MiB array: 2560^2 at
+    8-connectivity and 3328^2 at 4-connectivity; one more row and column is
+    rejected.  An all-zero residual has S_min empty and S_max = V."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    lib = mf.load()
+    n = side * side
+    res = torch.zeros((conn, n) if ok else (1,), dtype=torch.int32, device=dev)
+    tz = torch.zeros(n if ok else 1, dtype=torch.int32, device=dev)
+    smin = torch.full((n if ok else 1,), 7, dtype=torch.uint8, device=dev)
+    smax = torch.full((n if ok else 1,), 7, dtype=torch.uint8, device=dev)
+    dims = (ctypes.c_int64 * 2)(side, side)
+    st = lib.mf_min_cut_2d_noalloc(dims, conn, res.data_ptr(), tz.data_ptr(), tz.data_ptr(), smin.data_ptr(),
+                                   smax.data_ptr(), None)
+    if ok:
+        assert st == mf.MF_OK, lib.mf_last_error(None).decode()
+        assert int(smin.sum()) == 0 and int(smax.min()) == 1 and int(smax.max()) == 1
+    else:
+        assert st == mf.MF_EINVAL
+        assert "static maximum" in lib.mf_last_error(None).decode()
