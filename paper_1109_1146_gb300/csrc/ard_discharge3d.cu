@@ -29,6 +29,22 @@ namespace mf {
 
 typedef unsigned int u32;
 
+#ifdef MF_DIAG
+__device__ unsigned long long mf_diag3[32];
+}  // namespace mf
+extern "C" int mf_diag3_read(unsigned long long *out, int reset) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+    if (cudaMemcpyFromSymbol(out, mf::mf_diag3, sizeof(unsigned long long) * 32) != cudaSuccess) return 2;
+    if (reset) {
+        static const unsigned long long z[32] = {0};
+        if (cudaMemcpyToSymbol(mf::mf_diag3, z, sizeof(z)) != cudaSuccess) return 3;
+    }
+    return 0;
+}
+namespace mf {
+#define mf_diag mf_diag3
+#endif
+
 template <int TY, int TZ, int NT>
 struct Cfg3D {
     static constexpr int TX = 32, N = 6;
@@ -130,6 +146,9 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
     __shared__ unsigned long long s_flow;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    DIAG_DECL
+    const long long diag_t0 = clock64();
+    (void)diag_t0;
     const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
     const int ox = rx * TX, oy = ry * TY, oz = rz * TZ;
     const size_t n = (size_t)g.n;
@@ -223,6 +242,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
     rebuild_masks(false);
     rebuild_hm();
     __syncthreads();
+    DIAG_LAP(0);
 
     // ---- graph-warp helpers (warp 0) ------------------------------------------
     auto next_stage = [&](int k) -> int {
@@ -339,7 +359,9 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
 
     // ---- ARD stages ------------------------------------------------------------
     for (int k = 0;;) {
+        DIAG_MARK();
         if (warp == 0) {
+            DIAG_ADD(2, 1);
             u32 sd[RPL];
             seed_rows(k, sd);
             if (!cl_valid) {
@@ -356,6 +378,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
             }
         }
         __syncthreads();
+        DIAG_LAP(1);
         const int reach = s_ctl[0], kn = s_ctl[1];
         if (!any_aug) write_labels(k);  // labels stay exact until the first augmentation
         const bool aug = k <= klimit && !err;
@@ -370,7 +393,9 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                     __syncthreads();
                     epoch = 1;
                 }
+                DIAG_MARK();
                 if (warp == 0) {
+                    DIAG_ADD(5, 1);
                     u32 Rm[N][RPL], vis[RPL], fr[RPL], want[RPL];
                     load_masks(Rm);
                     seed_rows(k, fr);
@@ -418,8 +443,10 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                     }
                     lmax = __reduce_max_sync(FULL, lmax);
                     if (lane == 0) s_ctl[2] = lmax;
+                    DIAG_ADD(6, L);
                 }
                 __syncthreads();
+                DIAG_LAP(4);
                 const int Lmax = s_ctl[2];
                 if (Lmax == 0) break;  // no excess vertex reaches T_k: stage done
                 ++rounds;
@@ -509,11 +536,14 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                     }
                     __syncthreads();
                 }
+                DIAG_LAP(7);
                 rebuild_masks(true);  // a push changes its row and the rows one step away in y and z only
                 rebuild_hm();
                 __syncthreads();
                 for (int rho = tid; rho < NR; rho += NT)
                     if (s_dirty[rho] == 2) s_dirty[rho] = 1;
+                DIAG_LAP(3);
+                DIAG_ADD(8, Lmax);
             }
             if (warp == 0) cl_valid = false;  // the residual graph changed
         }
@@ -525,6 +555,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
 
     // ---- region-relabel after augmentation: d(u) = min{k : u -> T_k} -------------
     if (any_aug) {
+        DIAG_MARK();
         __syncthreads();
         if (warp == 0) {
 #pragma unroll
@@ -545,12 +576,14 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
             if (n2 == INT_MAX) break;
             k2 = n2;
         }
+        DIAG_LAP(9);
     }
     if (warp == 0) {
 #pragma unroll
         for (int j = 0; j < RPL; ++j) s_vis[lane * RPL + j] = Cl[j];
     }
     __syncthreads();
+    DIAG_MARK();
 
     // ---- write back: planes of rows that changed; labels and boundary flows always
     int left = 0;
@@ -595,6 +628,11 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
     if (lane == 0 && f) atomicAdd(&s_flow, f);
     __syncthreads();
     if (tid == 0) {
+        DIAG_LAP(10);
+        DIAG_ADD(11, clock64() - diag_t0);
+        DIAG_ADD(12, 1);
+        DIAG_ADD(13, rounds);
+        DIAG_FLUSH();
         if (s_flow) atomicAdd(st.flow_t, s_flow);
         st.disc[r] = 1;
         st.left_active[r] = (unsigned char)left;

@@ -375,8 +375,12 @@ __global__ void glr_levels_kernel(const Geom g, int W64, int BY, const u64 *__re
 // histogram (per-block shared counts for small labels, merged once) and mark
 // the regions that still hold an active vertex.
 template <int CONN>
-__global__ void glr_finish_kernel(const Geom g, const DevState st, int W64, const u64 *S) {
+__global__ void glr_finish_kernel(const Geom g, const DevState st, int W64, const u64 *A, const u64 *B) {
     constexpr int SB = 2048;  // labels below SB are counted in shared memory first
+    // the set of the last level run (levels = st.ctr[kGlrLevels]): level 0
+    // and the even levels write B, the odd levels A
+    const int last = st.ctr[kGlrLevels] - 1;
+    const u64 *S = (last % 2 == 1) ? A : B;
     __shared__ int sh[SB];
     for (int b = threadIdx.x; b < SB; b += blockDim.x) sh[b] = 0;
     __syncthreads();
@@ -418,8 +422,7 @@ __global__ void count_active_kernel(const DevState st, int nreg) {
 // Exact region-distance relabel of a 2D grid (tiles 32 or 64 wide).  Uses the
 // cut scratch (masks and two set buffers).  levels: number of BFS levels run.
 template <int CONN>
-static cudaError_t glr2d_impl(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
-                              cudaStream_t s) {
+static cudaError_t glr2d_impl(const Geom &g, const DevState &st, void *scratch, cudaStream_t s) {
     const int W64 = (g.X + 63) / 64, BY = (g.Y + 63) / 64;
     const size_t plane = (size_t)g.Y * W64;
     u64 *M = (u64 *)scratch;
@@ -446,29 +449,21 @@ static cudaError_t glr2d_impl(const Geom &g, const DevState &st, void *scratch, 
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)glr_levels_kernel<CONN>, dim3(nblocks), dim3(256),
                                                 args, 0, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(h_changed, lvl, 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    *levels = *h_changed;
-    // the last level written: odd levels write A, even levels write B
-    u64 *in = (*levels - 1) % 2 == 1 ? A : B;
-    if (*levels - 1 == 0) in = B;
     e = cudaMemsetAsync(st.hist, 0, (kHistBins + 1) * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(st.active, 0, (size_t)g.nreg, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&st.ctr[kActiveRegions], 0, 4, s);
     if (e != cudaSuccess) return e;
     const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, device_sms() * 32);
-    glr_finish_kernel<CONN><<<nb, 256, 0, s>>>(g, st, W64, in);
+    glr_finish_kernel<CONN><<<nb, 256, 0, s>>>(g, st, W64, A, B);
     count_active_kernel<<<(g.nreg + 255) / 256, 256, 0, s>>>(st, g.nreg);
     return cudaGetLastError();
 }
 
 bool glr2d_supported(const Geom &g) { return g.tz == 1 && g.Z == 1 && (g.tx == 64 || g.tx == 32); }
 
-cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
-                  cudaStream_t s) {
-    if (conn == 4) return glr2d_impl<4>(g, st, scratch, h_changed, levels, s);
-    if (conn == 8) return glr2d_impl<8>(g, st, scratch, h_changed, levels, s);
+cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, cudaStream_t s) {
+    if (conn == 4) return glr2d_impl<4>(g, st, scratch, s);
+    if (conn == 8) return glr2d_impl<8>(g, st, scratch, s);
     return cudaErrorInvalidValue;
 }
 

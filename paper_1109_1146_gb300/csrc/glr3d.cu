@@ -189,8 +189,12 @@ __global__ void glr3d_levels_kernel(const Geom g, int W32, const u32 *__restrict
 }
 
 // unreached vertices get d_inf; boundary-label histogram and region activity
-__global__ void glr3d_finish_kernel(const Geom g, const DevState st, int W32, const u32 *S) {
+__global__ void glr3d_finish_kernel(const Geom g, const DevState st, int W32, const u32 *A, const u32 *B) {
     constexpr int SB = 2048;
+    // the set of the last level run (levels = st.ctr[kGlrLevels]): level 0
+    // and the even levels write B, the odd levels A
+    const int last = st.ctr[kGlrLevels] - 1;
+    const u32 *S = (last % 2 == 1) ? A : B;
     __shared__ int sh[SB];
     for (int b = threadIdx.x; b < SB; b += blockDim.x) sh[b] = 0;
     __syncthreads();
@@ -353,8 +357,7 @@ size_t glr3d_scratch_bytes(const Geom &g) {
 }
 
 template <int TY, int TZ>
-static cudaError_t glr3d_impl(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
-                              cudaStream_t s) {
+static cudaError_t glr3d_impl(const Geom &g, const DevState &st, void *scratch, cudaStream_t s) {
     const int W32 = (g.X + 31) / 32;
     const size_t words = (size_t)g.Z * g.Y * W32;
     u32 *M = (u32 *)scratch;
@@ -381,27 +384,20 @@ static cudaError_t glr3d_impl(const Geom &g, const DevState &st, void *scratch, 
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)glr3d_levels_kernel<TY, TZ>, dim3(nblocks), dim3(256),
                                                 args, 0, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(h_changed, lvl, 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    *levels = *h_changed;
-    // level 0 writes B, odd levels A, even levels B; the last level run is levels - 1
-    const int last = *levels - 1;
-    const u32 *fin = (last % 2 == 1) ? A : B;
     e = cudaMemsetAsync(st.hist, 0, (kHistBins + 1) * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(st.active, 0, (size_t)g.nreg, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&st.ctr[kActiveRegions], 0, 4, s);
     if (e != cudaSuccess) return e;
     const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, device_sms() * 32);
-    glr3d_finish_kernel<<<nb, 256, 0, s>>>(g, st, W32, fin);
+    glr3d_finish_kernel<<<nb, 256, 0, s>>>(g, st, W32, A, B);
     glr3d_count_kernel<<<(g.nreg + 255) / 256, 256, 0, s>>>(st, g.nreg);
     return cudaGetLastError();
 }
 
-cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels, cudaStream_t s) {
-    if (g.ty == 16 && g.tz == 8) return glr3d_impl<16, 8>(g, st, scratch, h_changed, levels, s);
-    if (g.ty == 8 && g.tz == 8) return glr3d_impl<8, 8>(g, st, scratch, h_changed, levels, s);
-    if (g.ty == 8 && g.tz == 4) return glr3d_impl<8, 4>(g, st, scratch, h_changed, levels, s);
+cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, cudaStream_t s) {
+    if (g.ty == 16 && g.tz == 8) return glr3d_impl<16, 8>(g, st, scratch, s);
+    if (g.ty == 8 && g.tz == 8) return glr3d_impl<8, 8>(g, st, scratch, s);
+    if (g.ty == 8 && g.tz == 4) return glr3d_impl<8, 4>(g, st, scratch, s);
     return cudaErrorInvalidValue;
 }
 

@@ -179,63 +179,167 @@ __device__ __forceinline__ int hist_bin(int l) { return l < kHistBins ? l : kHis
 //   a refused push goes back to its sender (residual and excess restored).
 // Also commits the new boundary labels and keeps the histogram of boundary
 // labels (Sec. 5.3: the global gap needs labels of B only) up to date.
+// Fusion of one boundary vertex u = (lx, ly, lz) of region r (see above).
 template <int CONN>
-__device__ __forceinline__ void fuse_region(const Geom &g, const DevState &st, const int r) {
-    __shared__ int s_touch;
-    if (threadIdx.x == 0) s_touch = region_touched<CONN>(g, st, r);
-    __syncthreads();
-    if (!s_touch) return;
+__device__ __forceinline__ void fuse_cell(const Geom &g, const DevState &st, const int r, const int lx, const int ly,
+                                          const int lz, const bool discr) {
     const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
-    const int V = g.tx * g.ty * g.tz;
     const size_t n = (size_t)g.n;
-    const bool discr = st.disc[r];
-    for (int i = threadIdx.x; i < V; i += blockDim.x) {
-        const int lx = i & (g.tx - 1), ly = (i >> g.sx) & (g.ty - 1), lz = i >> (g.sx + g.sy);
-        if (lx != 0 && lx != g.tx - 1 && ly != 0 && ly != g.ty - 1 && (CONN != 6 || (lz != 0 && lz != g.tz - 1)))
-            continue;  // interior of the tile
-        const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
-        if (!in_grid(g, x, y, z)) continue;
-        const size_t u = ((size_t)z * g.Y + y) * g.X + x;
-        bool boundary = false;
-        int back_total = 0;
-        int du = -1;
+    const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
+    if (!in_grid(g, x, y, z)) return;
+    const size_t u = ((size_t)z * g.Y + y) * g.X + x;
+    bool boundary = false;
+    int back_total = 0;
+    int du = -1;
 #pragma unroll
-        for (int d = 0; d < CONN; ++d) {
-            const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d), wz = z + arc_dz(CONN, d);
-            if (!in_grid(g, wx, wy, wz)) continue;
-            const int rw = region_of(g, wx, wy, wz);
-            if (rw == r) continue;
-            if (!boundary) {
-                boundary = true;
-                du = discr ? st.lab_next[u] : st.lab[u];
-            }
-            const size_t w = ((size_t)wz * g.Y + wy) * g.X + wx;
-            const bool discw = st.disc[rw];
-            const int pu = discr ? st.bout[(size_t)d * n + u] : 0;
-            const int pw = discw ? st.bout[(size_t)(d ^ 1) * n + w] : 0;
-            if (!(pu | pw)) continue;  // no flow crossed this arc: nothing to accept or return
-            const int dw = discw ? st.lab_next[w] : st.lab[w];
-            const int back = (dw <= du + 1 ? 0 : pu) + (du <= dw + 1 ? pw : 0);
-            if (back) {
-                st.cap[(size_t)d * n + u] += back;
-                back_total += back;
-            }
+    for (int d = 0; d < CONN; ++d) {
+        const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d), wz = z + arc_dz(CONN, d);
+        if (!in_grid(g, wx, wy, wz)) continue;
+        const int rw = region_of(g, wx, wy, wz);
+        if (rw == r) continue;
+        if (!boundary) {
+            boundary = true;
+            du = discr ? st.lab_next[u] : st.lab[u];
         }
-        if (!boundary) continue;
-        if (back_total) st.exc[u] += back_total;
-        if (discr) {
-            const int old = st.lab[u];
-            if (old != du) {
-                if (old < g.dinf) atomicSub(&st.hist[hist_bin(old)], 1);
-                if (du < g.dinf) atomicAdd(&st.hist[hist_bin(du)], 1);
-                st.lab[u] = du;
-            }
+        const size_t w = ((size_t)wz * g.Y + wy) * g.X + wx;
+        const bool discw = st.disc[rw];
+        const int pu = discr ? st.bout[(size_t)d * n + u] : 0;
+        const int pw = discw ? st.bout[(size_t)(d ^ 1) * n + w] : 0;
+        if (!(pu | pw)) continue;  // no flow crossed this arc: nothing to accept or return
+        const int dw = discw ? st.lab_next[w] : st.lab[w];
+        const int back = (dw <= du + 1 ? 0 : pu) + (du <= dw + 1 ? pw : 0);
+        if (back) {
+            st.cap[(size_t)d * n + u] += back;
+            back_total += back;
+        }
+    }
+    if (!boundary) return;
+    if (back_total) st.exc[u] += back_total;
+    if (discr) {
+        const int old = st.lab[u];
+        if (old != du) {
+            if (old < g.dinf) atomicSub(&st.hist[hist_bin(old)], 1);
+            if (du < g.dinf) atomicAdd(&st.hist[hist_bin(du)], 1);
+            st.lab[u] = du;
         }
     }
 }
 
+// The cells on the surface of a tile, enumerated directly: in 2D the top and
+// bottom rows, then the left and right columns without their corners; in 3D
+// the two z faces, then the two y faces without their z edge rows, then the
+// two x faces without their y and z edges.  Tiles are at least 2 cells wide.
+__device__ __forceinline__ int surface_cells(const Geom &g, bool is3d) {
+    if (!is3d) return 2 * g.tx + 2 * (g.ty - 2);
+    return 2 * g.tx * g.ty + 2 * g.tx * (g.tz - 2) + 2 * (g.ty - 2) * (g.tz - 2);
+}
+__device__ __forceinline__ void surface_cell(const Geom &g, bool is3d, int p, int &lx, int &ly, int &lz) {
+    if (!is3d) {
+        lz = 0;
+        if (p < g.tx) { lx = p; ly = 0; }
+        else if (p < 2 * g.tx) { lx = p - g.tx; ly = g.ty - 1; }
+        else if (p < 2 * g.tx + g.ty - 2) { lx = 0; ly = 1 + p - 2 * g.tx; }
+        else { lx = g.tx - 1; ly = 1 + p - 2 * g.tx - (g.ty - 2); }
+        return;
+    }
+    const int A = g.tx * g.ty;
+    if (p < 2 * A) {
+        lz = p < A ? 0 : g.tz - 1;
+        const int q = p < A ? p : p - A;
+        lx = q % g.tx;
+        ly = q / g.tx;
+        return;
+    }
+    p -= 2 * A;
+    const int Bf = g.tx * (g.tz - 2);
+    if (p < 2 * Bf) {
+        ly = p < Bf ? 0 : g.ty - 1;
+        const int q = p < Bf ? p : p - Bf;
+        lx = q % g.tx;
+        lz = 1 + q / g.tx;
+        return;
+    }
+    p -= 2 * Bf;
+    const int Cf = (g.ty - 2) * (g.tz - 2);
+    lx = p < Cf ? 0 : g.tx - 1;
+    const int q = p < Cf ? p : p - Cf;
+    ly = 1 + q % (g.ty - 2);
+    lz = 1 + q / (g.ty - 2);
+}
+
+// Fusion of one touched region by one warp over the tile surface (only
+// surface cells can be boundary vertices).
 template <int CONN>
-__global__ void fuse_kernel(const Geom g, const DevState st) { fuse_region<CONN>(g, st, blockIdx.x); }
+__device__ __forceinline__ void fuse_region_warp(const Geom &g, const DevState &st, const int r) {
+    if (!region_touched<CONN>(g, st, r)) return;
+    const bool discr = st.disc[r];
+    const int P = surface_cells(g, CONN == 6);
+    for (int p = threadIdx.x & 31; p < P; p += 32) {
+        int lx, ly, lz;
+        surface_cell(g, CONN == 6, p, lx, ly, lz);
+        fuse_cell<CONN>(g, st, r, lx, ly, lz, discr);
+    }
+}
+
+// Activity of one region after the fusion (one warp): with a gap, every label
+// g < d < d_inf of the tile becomes d_inf first (all cells); a touched region
+// is active if its discharge left interior excess (left_active) or a surface
+// vertex has excess below d_inf.
+template <int CONN>
+__device__ __forceinline__ void post_region_warp(const Geom &g, const DevState &st, const int r, const int gap) {
+    const int lane = threadIdx.x & 31;
+    const bool touched = region_touched<CONN>(g, st, r);
+    if (!touched && gap == 0) return;
+    const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+    int act = touched ? st.left_active[r] : 0;
+    if (gap > 0) {
+        const int V = g.tx * g.ty * g.tz;
+        for (int i = lane; i < V; i += 32) {
+            const int lx = i & (g.tx - 1), ly = (i >> g.sx) & (g.ty - 1), lz = i >> (g.sx + g.sy);
+            const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
+            if (!in_grid(g, x, y, z)) continue;
+            const size_t u = ((size_t)z * g.Y + y) * g.X + x;
+            int l = st.lab[u];
+            if (l > gap && l < g.dinf) {
+                l = g.dinf;
+                st.lab[u] = l;
+            }
+            const bool border = lx == 0 || lx == g.tx - 1 || ly == 0 || ly == g.ty - 1 ||
+                                (CONN == 6 && (lz == 0 || lz == g.tz - 1));
+            if (touched && border && l < g.dinf && st.exc[u] > 0) act = 1;
+        }
+    } else {
+        const int P = surface_cells(g, CONN == 6);
+        for (int p = lane; p < P && !act; p += 32) {
+            int lx, ly, lz;
+            surface_cell(g, CONN == 6, p, lx, ly, lz);
+            const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
+            if (!in_grid(g, x, y, z)) continue;
+            const size_t u = ((size_t)z * g.Y + y) * g.X + x;
+            if (st.exc[u] > 0 && st.lab[u] < g.dinf) act = 1;
+        }
+    }
+    act = __any_sync(0xffffffffu, act);
+    if (lane == 0 && touched) {
+        st.active[r] = (unsigned char)act;
+        if (act) atomicAdd(&st.ctr[kActiveRegions], 1);
+    }
+}
+
+// single 3D grid: a warp per region, grid-stride
+template <int CONN>
+__global__ void fuse_warp_kernel(const Geom g, const DevState st) {
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < g.nreg; r += nw)
+        fuse_region_warp<CONN>(g, st, r);
+}
+template <int CONN>
+__global__ void post_warp_kernel(const Geom g, const DevState st) {
+    const int gap = st.ctr[kGap];
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < g.nreg; r += nw)
+        post_region_warp<CONN>(g, st, r, gap);
+}
 
 // Global gap (Sec. 5.1, with the boundary-label histogram of Sec. 5.3): the
 // smallest g > 0 below the highest boundary label with no boundary vertex
@@ -263,45 +367,6 @@ __device__ __forceinline__ void gap_find_body(const DevState &st) {
 }
 
 __global__ void gap_find_kernel(const DevState st) { gap_find_body(st); }
-
-// Apply the gap (all vertices of every region, only when a gap was found),
-// decide which regions discharge in the next sweep (only touched regions can
-// become active), reset the per-sweep flags.
-template <int CONN>
-__device__ __forceinline__ void post_region(const Geom &g, const DevState &st, const int r) {
-    const int gap = st.ctr[kGap];
-    __shared__ int s_touch;
-    if (threadIdx.x == 0) s_touch = region_touched<CONN>(g, st, r);
-    __syncthreads();
-    const bool touched = s_touch;
-    if (!touched && gap == 0) return;
-    const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
-    const int V = g.tx * g.ty * g.tz;
-    int act = touched ? st.left_active[r] : 0;
-    for (int i = threadIdx.x; i < V; i += blockDim.x) {
-        const int lx = i & (g.tx - 1), ly = (i >> g.sx) & (g.ty - 1), lz = i >> (g.sx + g.sy);
-        const bool border = lx == 0 || lx == g.tx - 1 || ly == 0 || ly == g.ty - 1 ||
-                            (CONN == 6 && (lz == 0 || lz == g.tz - 1));
-        if (gap == 0 && !border) continue;
-        const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
-        if (!in_grid(g, x, y, z)) continue;
-        const size_t u = ((size_t)z * g.Y + y) * g.X + x;
-        int l = st.lab[u];
-        if (gap > 0 && l > gap && l < g.dinf) {
-            l = g.dinf;
-            st.lab[u] = l;
-        }
-        if (touched && border && !act && l < g.dinf && st.exc[u] > 0) act = 1;
-    }
-    act = __syncthreads_or(act);
-    if (threadIdx.x == 0 && touched) {
-        st.active[r] = (unsigned char)act;
-        if (act) atomicAdd(&st.ctr[kActiveRegions], 1);
-    }
-}
-
-template <int CONN>
-__global__ void post_kernel(const Geom g, const DevState st) { post_region<CONN>(g, st, blockIdx.x); }
 
 // ---- 2D fusion and activity over perimeter items -----------------------------
 // One thread per (region, perimeter slot): only tile perimeters hold boundary
@@ -477,11 +542,15 @@ __global__ void batch_items_kernel(const Inst *insts, const int2 *regs, int nreg
     }
 }
 
+// batched fusion / activity: a warp per region of the whole batch, grid-stride
 template <int CONN>
-__global__ void fuse_batch_kernel(const Inst *insts, const int2 *regs, const unsigned char *done) {
-    const int2 w = regs[blockIdx.x];
-    if (done[w.x] || insts[w.x].conn != CONN) return;
-    fuse_region<CONN>(insts[w.x].g, insts[w.x].st, w.y);
+__global__ void fuse_batch_kernel(const Inst *insts, const int2 *regs, int nregs, const unsigned char *done) {
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nregs; i += nw) {
+        const int2 w = regs[i];
+        if (done[w.x] || insts[w.x].conn != CONN) continue;
+        fuse_region_warp<CONN>(insts[w.x].g, insts[w.x].st, w.y);
+    }
 }
 
 __global__ void gap_find_batch_kernel(const Inst *insts, const unsigned char *done) {
@@ -490,10 +559,13 @@ __global__ void gap_find_batch_kernel(const Inst *insts, const unsigned char *do
 }
 
 template <int CONN>
-__global__ void post_batch_kernel(const Inst *insts, const int2 *regs, const unsigned char *done) {
-    const int2 w = regs[blockIdx.x];
-    if (done[w.x] || insts[w.x].conn != CONN) return;
-    post_region<CONN>(insts[w.x].g, insts[w.x].st, w.y);
+__global__ void post_batch_kernel(const Inst *insts, const int2 *regs, int nregs, const unsigned char *done) {
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < nregs; i += nw) {
+        const int2 w = regs[i];
+        if (done[w.x] || insts[w.x].conn != CONN) continue;
+        post_region_warp<CONN>(insts[w.x].g, insts[w.x].st, w.y, insts[w.x].st.ctr[kGap]);
+    }
 }
 
 __global__ void clear_batch_kernel(const Inst *insts, const int2 *regs, int nregs, const unsigned char *done) {
@@ -639,9 +711,10 @@ static cudaError_t launch_fuse_post(mf_grid *h, bool gap_on, cudaStream_t st) {
         finish_flags_kernel<<<(h->g.nreg + 255) / 256, 256, 0, st>>>(h->st, h->g.nreg);
         return cudaGetLastError();
     }
-    fuse_kernel<CONN><<<h->g.nreg, 256, 0, st>>>(h->g, h->st);
+    const int wb = (int)std::min<long long>(((long long)h->g.nreg + 7) / 8, (long long)device_sms() * 8);
+    fuse_warp_kernel<CONN><<<wb, 256, 0, st>>>(h->g, h->st);
     if (gap_on) gap_find_kernel<<<1, 1024, 0, st>>>(h->st);
-    post_kernel<CONN><<<h->g.nreg, 256, 0, st>>>(h->g, h->st);
+    post_warp_kernel<CONN><<<wb, 256, 0, st>>>(h->g, h->st);
     clear_flags_kernel<<<(h->g.nreg + 255) / 256, 256, 0, st>>>(h->st, h->g.nreg);
     return cudaGetLastError();
 }
@@ -985,14 +1058,14 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
         // labels 0 everywhere; exact region distances (a valid labeling) put the
         // excess that cannot reach t at d-infinity before the first sweep, so
         // the sweeps only move the excess that still can.
-        int levels = 0;
-        CK(glr2d(g->conn, g->g, g->st, g->cut_scratch, g->h_ctr, &levels, g->stream));
+        CK(glr2d(g->conn, g->g, g->st, g->cut_scratch, g->stream));
         CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
         CK(cudaStreamSynchronize(g->stream));
+        const int levels = g->h_ctr[kGlrLevels];
         g->begin_active = g->h_ctr[kActiveRegions];
         g->stats.global_relabels = 1;
         g->stats.relabel_levels = levels;
-        g->launches += 4 + levels;
+        g->launches += 4;  // masks, the cooperative levels launch, finish, count
     }
     return MF_OK;
 }
@@ -1001,9 +1074,9 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
 static bool glr_supported(const mf_grid *g) {
     return g->ndim == 2 ? glr2d_supported(g->g) : glr3d_supported(g->g);
 }
-static cudaError_t glr_run(mf_grid *g, int *levels) {
-    return g->ndim == 2 ? glr2d(g->conn, g->g, g->st, g->cut_scratch, g->h_ctr, levels, g->stream)
-                        : glr3d(g->g, g->st, g->cut_scratch, g->h_ctr, levels, g->stream);
+// (enqueued without waiting; the levels run are left in st.ctr[kGlrLevels])
+static cudaError_t glr_run(mf_grid *g, cudaStream_t s) {
+    return g->ndim == 2 ? glr2d(g->conn, g->g, g->st, g->cut_scratch, s) : glr3d(g->g, g->st, g->cut_scratch, s);
 }
 
 // which relabel (if any) follows sweep count s: the exact global relabel
@@ -1084,14 +1157,14 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     if (active > 0 && glr_due(g, g->sweep)) {
         // exact region-distance relabel (raises labels to max(d, d*)), then the
         // activity of every region is recomputed from the new labels
-        int levels = 0;
-        CK(glr_run(g, &levels));
+        CK(glr_run(g, g->stream));
         CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
         CK(cudaStreamSynchronize(g->stream));
+        const int levels = g->h_ctr[kGlrLevels];
         active = g->h_ctr[kActiveRegions];
         g->stats.global_relabels++;
         g->stats.relabel_levels += levels;
-        g->launches += 4 + levels;
+        g->launches += 4;  // masks, the cooperative levels launch, finish, count
     } else if (active > 0 && br_due(g, g->sweep)) {
         mf_status bs = br_step(g, g->stream, &active, nullptr);
         if (bs != MF_OK) return bs;
@@ -1269,14 +1342,14 @@ static mf_status run_graph_loop(mf_grid *g, long long cap) {
         if (active == 0) return MF_OK;
         if (g->sweep >= cap) return fail(g, MF_ESWEEPLIMIT, "sweep cap reached with active vertices left");
         if (glr_due(g, g->sweep)) {
-            int levels = 0;
-            CK(glr_run(g, &levels));
+            CK(glr_run(g, g->stream));
             CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
             CK(cudaStreamSynchronize(g->stream));
+            const int levels = g->h_ctr[kGlrLevels];
             active = g->h_ctr[kActiveRegions];
             g->stats.global_relabels++;
             g->stats.relabel_levels += levels;
-            g->launches += 4 + levels;
+            g->launches += 4;  // masks, the cooperative levels launch, finish, count
             if (active == 0) return MF_OK;
         } else if (br_due(g, g->sweep)) {
             mf_status bs = br_step(g, g->stream, &active, nullptr);
@@ -1348,8 +1421,10 @@ struct BatchBufs {
     }
 };
 
-// The global relabel of every unfinished instance of a batch that supports it,
-// on the batch stream (as after a sweep of a single solve: same sequence).
+// The global relabel of every unfinished instance of a batch that supports it
+// (or the boundary relabel where that one is due), on the batch stream (as
+// after a sweep of a single solve: same sequence).  Everything is enqueued
+// first; one wait then reads every relabelled instance's level count.
 // Returns in *any_left the number of instances still active afterwards.
 static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *insts, unsigned char *done_dev,
                                int *any_dev, int *any_left, int sweep, cudaStream_t s) {
@@ -1357,6 +1432,7 @@ static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *ins
     std::vector<unsigned char> done(count);
     CK(cudaMemcpyAsync(done.data(), done_dev, count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    std::vector<int> glr;
     for (int i = 0; i < count; ++i) {
         mf_grid *h = grids[i];
         if (done[i]) continue;
@@ -1366,19 +1442,23 @@ static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *ins
             continue;
         }
         if (!glr_due(h, sweep)) continue;
-        int levels = 0;
-        const cudaError_t e = h->ndim == 2 ? glr2d(h->conn, h->g, h->st, h->cut_scratch, h->h_ctr, &levels, s)
-                                           : glr3d(h->g, h->st, h->cut_scratch, h->h_ctr, &levels, s);
+        const cudaError_t e = glr_run(h, s);
         if (e != cudaSuccess) return fail(g, MF_ECUDA, std::string("batched global relabel: ") + cudaGetErrorString(e));
-        h->stats.global_relabels++;
-        h->stats.relabel_levels += levels;
-        h->launches += 4 + levels;
+        CK(cudaMemcpyAsync(&h->h_ctr[kGlrLevels], &h->st.ctr[kGlrLevels], 4, cudaMemcpyDeviceToHost, s));
+        glr.push_back(i);
     }
     CK(cudaMemsetAsync(any_dev, 0, sizeof(int), s));
     batch_relabel_end_kernel<<<(count + 255) / 256, 256, 0, s>>>(insts, done_dev, any_dev, count);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(any_left, any_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    for (int i : glr) {
+        mf_grid *h = grids[i];
+        const int levels = h->h_ctr[kGlrLevels];
+        h->stats.global_relabels++;
+        h->stats.relabel_levels += levels;
+        h->launches += 4;  // masks, the cooperative levels launch, finish, count
+    }
     return MF_OK;
 }
 
@@ -1462,6 +1542,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     sa.max_rounds = o.max_rounds;
     sa.variant = o.kernel_variant;
     const int eb = (int)std::min<long long>(((long long)nregs + 255) / 256, device_sms() * 8);
+    const int wbb = (int)std::min<long long>(((long long)nregs + 7) / 8, (long long)device_sms() * 8);
     mf_status rs = MF_OK;
     long long launches = 0;
     const int per_sweep = 6 + nt + (o.global_gap ? 1 : 0);
@@ -1500,18 +1581,18 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
             bool has = false;
             for (auto &ty : types) has |= ty.conn == conn;
             if (!has) continue;
-            if (conn == 4) fuse_batch_kernel<4><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
-            if (conn == 8) fuse_batch_kernel<8><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
-            if (conn == 6) fuse_batch_kernel<6><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
+            if (conn == 4) fuse_batch_kernel<4><<<wbb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done);
+            if (conn == 8) fuse_batch_kernel<8><<<wbb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done);
+            if (conn == 6) fuse_batch_kernel<6><<<wbb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done);
         }
         if (o.global_gap) gap_find_batch_kernel<<<count, 1024, 0, st>>>(B.insts, B.done);
         for (int conn : {4, 8, 6}) {
             bool has = false;
             for (auto &ty : types) has |= ty.conn == conn;
             if (!has) continue;
-            if (conn == 4) post_batch_kernel<4><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
-            if (conn == 8) post_batch_kernel<8><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
-            if (conn == 6) post_batch_kernel<6><<<nregs, 256, 0, st>>>(B.insts, B.regs, B.done);
+            if (conn == 4) post_batch_kernel<4><<<wbb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done);
+            if (conn == 8) post_batch_kernel<8><<<wbb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done);
+            if (conn == 6) post_batch_kernel<6><<<wbb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done);
         }
         clear_batch_kernel<<<eb, 256, 0, st>>>(B.insts, B.regs, nregs, B.done);
         batch_end_kernel<<<(count + 255) / 256, 256, 0, st>>>(B.insts, B.done, B.sweeps, B.any, count);
@@ -1693,7 +1774,7 @@ mf_status mf_warm_start(mf_grid *g, const float *pred, int32_t max_rounds, int32
     CK(launch_project_init(g->conn, g->g, g->cs, g->ct, g->nl, pred, g->warmF, g->warmFt, g->stream));
     CK(launch_project_rounds(g->conn, g->g, g->cs, g->ct, g->warmF, g->warmFt, g->warmE, &g->st.ctr[kGlrFlags],
                              max_rounds, g->stream));
-    CK(cudaMemcpyAsync(g->h_ctr, &g->st.ctr[kGlrFlags], 3 * 4, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(g->h_ctr, &g->st.ctr[kGlrFlags], 4 * 4, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     const int r = g->h_ctr[2];
     if (r < 0) {

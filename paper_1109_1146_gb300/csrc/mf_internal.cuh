@@ -198,12 +198,13 @@ bool glr2d_supported(const Geom &g);
 // glr3d.cu: the same relabel for 3D 6-connected grids with 32-wide tiles
 bool glr3d_supported(const Geom &g);
 size_t glr3d_scratch_bytes(const Geom &g);
-cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels, cudaStream_t s);
+// the relabels enqueue everything without waiting; the number of BFS levels
+// run is left in st.ctr[kGlrLevels]
+cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, cudaStream_t s);
 // both cut closures on bit masks (scratch: glr3d_scratch_bytes); passes += passes made
 cudaError_t cut3d(const Geom &g, const DevState &st, void *scratch, unsigned char *smin, unsigned char *smax,
                   int *h_passes, cudaStream_t s);
-cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, int *h_changed, int *levels,
-                  cudaStream_t s);
+cudaError_t glr2d(int conn, const Geom &g, const DevState &st, void *scratch, cudaStream_t s);
 // persistent discharge over a work queue of (instance, region) items of one
 // kernel type (connectivity, tile); blocks pull items until *count is reached
 cudaError_t launch_discharge_batch(int conn, int tx, int ty, int tz, int variant, const Inst *insts,
@@ -216,7 +217,8 @@ cudaError_t launch_warm_targets(int conn, const Geom &g, const DevState &st, con
                                 const int *nl, float *t, cudaStream_t s);
 cudaError_t launch_project_init(int conn, const Geom &g, const int *cs, const int *ct, const int *nl, const float *p,
                                 int *F, int *ft, cudaStream_t s);
-// all trim rounds in one cooperative launch; flags: 3 ints (flags[2] = rounds, -1: limit hit)
+// the trims in one cooperative launch, tile-local phases; flags: 4 ints
+// (flags[2] = phases run, -1: no preflow reachable or the phase cap hit)
 cudaError_t launch_project_rounds(int conn, const Geom &g, const int *cs, const int *ct, int *F, int *ft, int *E,
                                   int *flags, int max_rounds, cudaStream_t s);
 cudaError_t launch_warm_init(int conn, const Geom &g, const DevState &st, const int *cs, const int *ct, const int *nl,

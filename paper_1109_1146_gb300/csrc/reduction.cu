@@ -17,8 +17,10 @@
 //      sink (an infinite arc into a super sink that is removed afterwards);
 //   4. Augment(B^T, t): every B^T vertex gets a supply equal to its residual
 //      out-capacity (no flow out of it can exceed that, so the supply acts as
-//      an infinite arc from a super source), the same rounds, then the
-//      supply left at B^T is dropped with the super source;
+//      an infinite arc from a super source), the same rounds; the supply that
+//      got stuck on the way is pushed back to B^T (so that the residual
+//      network is that of a maximum flow from B^T to t, not of a preflow), and
+//      what is left at B^T is dropped with the super source;
 //   5. classes of the vertices of R in the final residual network: s -> v
 //      strong source, v -> t strong sink, otherwise weak source if v does not
 //      reach B^R and weak sink if B^R does not reach v.
@@ -127,10 +129,11 @@ __global__ void __launch_bounds__(kRedThreads) region_reduction_kernel(const Red
     __syncthreads();
 
     // ---- Augment: rounds of BFS to the sinks + layered push ------------------------
-    // sinks: residual arc to t, and with absorb the B^S vertices
-    auto bfs = [&](bool absorb) -> int {
+    // sinks: a residual arc to t (use_t), and the vertices flagged `absorb`
+    // (each with an infinite arc into a super sink)
+    auto bfs = [&](unsigned char absorb, bool use_t) -> int {
         for (int c = tid; c < E; c += kRedThreads)
-            dist[c] = (tcap[c] > 0 || (absorb && (fl[c] & F_BS))) ? 1 : kDistInf;
+            dist[c] = ((use_t && tcap[c] > 0) || (fl[c] & absorb)) ? 1 : kDistInf;
         if (tid == 0) s_max = 0;
         __syncthreads();
         for (int L = 1;; ++L) {
@@ -159,20 +162,20 @@ __global__ void __launch_bounds__(kRedThreads) region_reduction_kernel(const Red
         __syncthreads();
         return res;
     };
-    auto push = [&](int Lmax, bool absorb) {
+    auto push = [&](int Lmax, unsigned char absorb, bool use_t) {
         for (int L = Lmax; L >= 1; --L) {
             for (int c = tid; c < E; c += kRedThreads) {
                 if (dist[c] != L) continue;
                 int e = exc[c];
                 if (e <= 0) continue;
                 if (L == 1) {
-                    const int tc = tcap[c];
+                    const int tc = use_t ? tcap[c] : 0;
                     if (tc > 0) {
                         const int dl = min(e, tc);
                         tcap[c] = tc - dl;
                         e -= dl;
                     }
-                    if (absorb && (fl[c] & F_BS)) e = 0;  // into the super sink
+                    if (fl[c] & absorb) e = 0;  // into the super sink
                 } else {
                     const unsigned a = am[c];
 #pragma unroll
@@ -196,15 +199,15 @@ __global__ void __launch_bounds__(kRedThreads) region_reduction_kernel(const Red
         }
     };
     bool ok = true;
-    auto augment = [&](bool absorb) {
+    auto augment = [&](unsigned char absorb, bool use_t) {
         for (int round = 0; ok; ++round) {
             if (round >= max_rounds) {
                 ok = false;
                 break;
             }
-            const int Lmax = bfs(absorb);
+            const int Lmax = bfs(absorb, use_t);
             if (Lmax == 0) break;
-            push(Lmax, absorb);
+            push(Lmax, absorb, use_t);
         }
     };
     // residual closure of the cells with bit `bit` set in cl (seeded by the
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(kRedThreads) region_reduction_kernel(const Red
     };
 
     // 1. Augment(s, t)
-    augment(false);
+    augment(0, true);
     // 2. B^S: boundary vertices in the closure of the excess; B^T: boundary
     //    vertices that reach t
     for (int c = tid; c < E; c += kRedThreads) {
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kRedThreads) region_reduction_kernel(const Red
     }
     __syncthreads();
     // 3. Augment(s, B^S)
-    augment(true);
+    augment(F_BS, true);
     // strong sources: the closure of the excess left (B^S absorbed theirs);
     // step 4 works where s does not reach, so this set stays final
     for (int c = tid; c < E; c += kRedThreads) cl[c] = exc[c] > 0 ? C_S : 0;
@@ -270,7 +273,13 @@ __global__ void __launch_bounds__(kRedThreads) region_reduction_kernel(const Red
         exc[c] = (int)min(sup, (long long)INT_MAX);
     }
     __syncthreads();
-    augment(false);
+    augment(0, true);
+    // The supply that did not reach t sits as excess on the way; in a flow
+    // (not a preflow) it would never have left B^T, and the arcs it used
+    // would still be residual.  Push it back to B^T (B^T absorbing, t not a
+    // sink): what is left is a maximum flow from B^T to t.  The excess of the
+    // strong sources cannot reach B^R and stays.
+    augment(F_BT, false);
     for (int c = tid; c < E; c += kRedThreads)
         if (fl[c] & F_BT) exc[c] = 0;  // the super source leaves with its supply
     // 5. final closures: v -> t, v -> B^R, B^R -> v

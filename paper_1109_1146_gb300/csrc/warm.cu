@@ -17,7 +17,9 @@
 //   then, in synchronous rounds, every vertex with negative excess lowers its
 //   own outflow (sink flow first, then arcs 0..N-1) by its deficit, until no
 //   excess is negative.  Lowering an outflow only moves flow toward zero, so
-//   capacities stay respected; a round cap ends with a cold start instead.
+//   capacities stay respected; a vertex that cannot be fixed, or a phase cap,
+//   ends with a cold start instead.  The rounds are computed tile by tile
+//   (see project_tiles_kernel), which reaches the same preflow.
 #include <algorithm>
 #include <cstdint>
 
@@ -93,78 +95,144 @@ __global__ void project_init_kernel(const Geom g, const int *cs, const int *ct, 
     }
 }
 
-// a vertex with a deficit lowers its own outflows (an edge carries flow one
-// way, so only its tail ever lowers it: no two threads write one edge)
-template <int CONN>
-__device__ __forceinline__ void trim_vertex(const Geom &g, size_t v, const int *E, int *F, int *ft) {
-    const size_t n = (size_t)g.n;
-    int def = -E[v];
-    if (def <= 0) return;
-    const int px = (int)(v % g.X), py = (int)(v / g.X);
-    int r = min(ft[v], def);
-    ft[v] -= r;
-    def -= r;
-#pragma unroll
-    for (int d = 0; d < CONN; ++d) {
-        if (def == 0) break;
-        const int h = d >> 1;
-        if (!(d & 1)) {
-            const int f = F[h * n + v];
-            if (f > 0) {
-                r = min(f, def);
-                F[h * n + v] = f - r;
-                def -= r;
-            }
-        } else {
-            const int wx = px - fwd_dx(CONN, h), wy = py - fwd_dy(CONN, h);
-            if (!ingrid2(g, wx, wy)) continue;
-            const size_t w = (size_t)wy * g.X + wx;
-            const int f = F[h * n + w];  // flow w -> v; negative means v -> w
-            if (f < 0) {
-                r = min(-f, def);
-                F[h * n + w] = f + r;
-                def -= r;
-            }
-        }
-    }
-}
+// The trims, organised by tiles.  Let D_v be the total outflow a vertex has
+// trimmed; the greedy order (sink flow first, then arcs 0..N-1) makes its
+// outflows a function of D_v alone, and its excess grows with D_v and falls
+// as its neighbours trim (their outflows are its inflows).  A synchronous
+// round sets D_v := max(D_v, T_v(D)), T_v(D) = the trim that would make its
+// excess 0 given its neighbours' trims, a map that is monotone in D.  From
+// D = 0 such updates can only climb to the least fixed point of
+// D = max(0, T(D)), and they stop exactly there, in whatever order they are
+// applied (stale neighbour values only give smaller steps).  So the rounds
+// below, local to 32x32 tiles, reach bit for bit the preflow the synchronous
+// rounds reach.  A tile iterates its vertices in shared memory until none of
+// them has a deficit, given the flows on the edges into it from outside;
+// phases of all tiles repeat (one grid barrier each) until no tile changed
+// an edge whose other end lies in another tile.  A vertex whose deficit
+// exceeds all its remaining outflow can never be fixed (its trims are at
+// their maximum and its inflows can only fall): the projection fails.
+// Only the tail of an edge (the endpoint its flow leaves) ever lowers it, so
+// every flow value has one writer.
+constexpr int kProjTile = 32;
 
-// All projection rounds in one cooperative launch: each round computes every
-// excess (flagging a negative one), and if some excess is negative and rounds
-// remain, trims.  flags[0..1] alternate between rounds (the host zeroes both
-// first); flags[2] receives the number of trim rounds made, or -1 if
-// max_rounds trims left a negative excess.  Every loop is bounded by
-// max_rounds; the grid is co-resident, so every grid.sync returns.
 template <int CONN>
-__global__ void project_rounds_kernel(const Geom g, const int *cs, const int *ct, int *F, int *ft, int *E, int *flags,
-                                      int max_rounds) {
+__global__ void __launch_bounds__(256) project_tiles_kernel(const Geom g, const int *cs, const int *ct, int *F, int *ft,
+                                                            int *E, int *flags, int max_phases) {
+    constexpr int H = CONN / 2, TP = kProjTile, EW = TP + 2, EXT = EW * EW;
     cg::grid_group grid = cg::this_grid();
+    __shared__ int Fs[H][EXT];   // flows of the edges whose lower endpoint is in the tile or its ring
+    __shared__ int F0[H][EXT];   // as loaded (only changed values are written back)
+    __shared__ int fts[TP * TP];
+    __shared__ int bs[TP * TP];  // cs - min(cs, ct)
     const size_t n = (size_t)g.n;
-    for (int r = 0;; ++r) {
-        int any = 0;
-        for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
-            const int px = (int)(v % g.X), py = (int)(v / g.X);
-            long long e = (long long)cs[v] - min(cs[v], ct[v]) - ft[v];
+    const int tid = threadIdx.x;
+    const int TXn = (g.X + TP - 1) / TP, TYn = (g.Y + TP - 1) / TP, ntiles = TXn * TYn;
+    int phase = 0;
+    for (;; ++phase) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int ox = (t % TXn) * TP, oy = (t / TXn) * TP;
+            for (int c = tid; c < EXT; c += blockDim.x) {
+                const int x = ox - 1 + c % EW, y = oy - 1 + c / EW;
+                const bool in = ingrid2(g, x, y);
 #pragma unroll
-            for (int h = 0; h < CONN / 2; ++h) {
-                e -= F[h * n + v];
-                const int wx = px - fwd_dx(CONN, h), wy = py - fwd_dy(CONN, h);
-                if (ingrid2(g, wx, wy)) e += F[h * n + (size_t)wy * g.X + wx];
+                for (int h = 0; h < H; ++h) {
+                    const int f = in ? F[h * n + (size_t)y * g.X + x] : 0;
+                    Fs[h][c] = f;
+                    F0[h][c] = f;
+                }
             }
-            E[v] = (int)e;
-            any |= e < 0;
+            for (int i = tid; i < TP * TP; i += blockDim.x) {
+                const int x = ox + i % TP, y = oy + i / TP;
+                const bool in = ingrid2(g, x, y);
+                const size_t v = (size_t)y * g.X + x;
+                fts[i] = in ? ft[v] : 0;
+                bs[i] = in ? cs[v] - min(cs[v], ct[v]) : 0;
+            }
+            __syncthreads();
+            int cross = 0, bad = 0;
+            for (int it = 0;; ++it) {
+                int changed = 0;
+                for (int i = tid; i < TP * TP; i += blockDim.x) {
+                    const int lx = i % TP, ly = i / TP;
+                    if (!ingrid2(g, ox + lx, oy + ly)) continue;
+                    const int c = (ly + 1) * EW + (lx + 1);
+                    long long e = (long long)bs[i] - fts[i];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        e -= Fs[h][c];
+                        e += Fs[h][c - fwd_dx(CONN, h) - fwd_dy(CONN, h) * EW];
+                    }
+                    if (e >= 0) continue;
+                    int def = (int)-e;
+                    changed = 1;
+                    int r = min(fts[i], def);
+                    fts[i] -= r;
+                    def -= r;
+#pragma unroll
+                    for (int d = 0; d < CONN; ++d) {
+                        if (def == 0) break;
+                        const int h = d >> 1;
+                        // the edge of arc d: stored at c (d even) or at its tail cell (d odd)
+                        const int cc = (d & 1) ? c - fwd_dx(CONN, h) - fwd_dy(CONN, h) * EW : c;
+                        const int f = Fs[h][cc];
+                        const int out = (d & 1) ? -f : f;  // v's outflow on this edge
+                        if (out <= 0) continue;
+                        r = min(out, def);
+                        Fs[h][cc] = (d & 1) ? f + r : f - r;
+                        def -= r;
+                        const int nx = lx + arc_dx(CONN, d), ny = ly + arc_dy(CONN, d);
+                        if (nx < 0 || nx >= TP || ny < 0 || ny >= TP) cross = 1;  // the head is in another tile
+                    }
+                    if (def > 0) bad = 1;
+                }
+                if (!__syncthreads_or(changed)) break;
+                if (it >= (1 << 16)) {  // never expected: report a failure, not a false convergence
+                    bad = 1;
+                    break;
+                }
+            }
+            bad = __syncthreads_or(bad);
+            cross = __syncthreads_or(cross);
+            // write back what this tile's vertices trimmed (they are the tails)
+            for (int c = tid; c < EXT; c += blockDim.x) {
+                const int x = ox - 1 + c % EW, y = oy - 1 + c / EW;
+                if (!ingrid2(g, x, y)) continue;
+#pragma unroll
+                for (int h = 0; h < H; ++h)
+                    if (Fs[h][c] != F0[h][c]) F[h * n + (size_t)y * g.X + x] = Fs[h][c];
+            }
+            for (int i = tid; i < TP * TP; i += blockDim.x) {
+                const int x = ox + i % TP, y = oy + i / TP;
+                if (ingrid2(g, x, y)) ft[(size_t)y * g.X + x] = fts[i];
+            }
+            if (tid == 0) {
+                if (cross) atomicOr(&flags[phase & 1], 1);
+                if (bad) atomicOr(&flags[3], 1);
+            }
+            __syncthreads();  // the shared arrays are reused by the next tile
         }
-        if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(&flags[r & 1], 1);
         grid.sync();
-        const int neg = *(volatile int *)&flags[r & 1];
-        if (!neg || r >= max_rounds) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) flags[2] = neg ? -1 : r;
-            return;
+        const int cross = *(volatile int *)&flags[phase & 1];
+        const int bad = *(volatile int *)&flags[3];
+        if (bad || !cross || phase + 1 >= max_phases) {
+            if (blockIdx.x == 0 && tid == 0) flags[2] = (bad || cross) ? -1 : phase + 1;
+            break;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(r + 1) & 1] = 0;  // read by nobody since the last sync
-        for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
-            trim_vertex<CONN>(g, v, E, F, ft);
-        grid.sync();
+        if (blockIdx.x == 0 && tid == 0) flags[(phase + 1) & 1] = 0;
+        grid.sync();  // the cleared word is seen before the next phase sets it
+    }
+    grid.sync();
+    // excess of the final preflow
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + tid; v < n; v += (size_t)gridDim.x * blockDim.x) {
+        const int px = (int)(v % g.X), py = (int)(v / g.X);
+        long long e = (long long)cs[v] - min(cs[v], ct[v]) - ft[v];
+#pragma unroll
+        for (int h = 0; h < CONN / 2; ++h) {
+            e -= F[h * n + v];
+            const int wx = px - fwd_dx(CONN, h), wy = py - fwd_dy(CONN, h);
+            if (ingrid2(g, wx, wy)) e += F[h * n + (size_t)wy * g.X + wx];
+        }
+        E[v] = (int)e;
     }
 }
 
@@ -237,18 +305,15 @@ cudaError_t launch_project_init(int conn, const Geom &g, const int *cs, const in
 }
 cudaError_t launch_project_rounds(int conn, const Geom &g, const int *cs, const int *ct, int *F, int *ft, int *E,
                                   int *flags, int max_rounds, cudaStream_t s) {
-    const void *kern = conn == 4 ? (const void *)project_rounds_kernel<4>
-                     : conn == 8 ? (const void *)project_rounds_kernel<8> : nullptr;
+    const void *kern = conn == 4 ? (const void *)project_tiles_kernel<4>
+                     : conn == 8 ? (const void *)project_tiles_kernel<8> : nullptr;
     if (!kern) return cudaErrorInvalidValue;
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    int max_blocks = 0;
+    cudaError_t e = coop_max_blocks(kern, 256, 0, &max_blocks);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    const size_t want = ((size_t)g.n + 255) / 256;
-    const int blocks = (int)std::min<size_t>(want ? want : 1, (size_t)per_sm * sms);
-    e = cudaMemsetAsync(flags, 0, 3 * sizeof(int), s);
+    const long long tiles = (long long)((g.X + kProjTile - 1) / kProjTile) * ((g.Y + kProjTile - 1) / kProjTile);
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(tiles, max_blocks));
+    e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     Geom gg = g;
     const int *a_cs = cs, *a_ct = ct;
