@@ -335,12 +335,16 @@ def run_config4(args):
     def batched():
         return mf.solve_batch(hb, bopts)
 
+    preds = [None] * count
+    for i in idx2:
+        preds[i] = wx[i][1]
+
     def batched_warm():
         for i in idx2:
             x, y = wx[i]
             hb[i].warm_features(x)
             net.infer(x, y)
-            hb[i].warm_start(y, check=False)  # a projection that runs out of rounds leaves that grid cold
+        mf.warm_start_batch(hb, preds)  # a grid whose projection fails stays cold
         return mf.solve_batch(hb, wopts)
 
     def plain():
@@ -388,6 +392,12 @@ def run_config4(args):
     total_p = job_time_ms(sum(p_ms), ws, dev)
     total_e = job_time_ms(sum(e2e_ms), ws, dev)
     roof = roofline_of(h_stats, insts, tiles, batch=True)
+    h0 = h_stats[0]
+    dis_total = sum(roof["discharge_ms_by_kernel"].values())
+    breakdown = {"note": "one host-driven batched solve (events): ms of the whole batch by phase",
+                 "total": round(h0.ms_total, 2), "init": round(h0.ms_init, 2), "cut": round(h0.ms_cut, 2),
+                 "discharge": round(dis_total, 2), "relabel": round(h0.ms_relabel, 2),
+                 "fusion_gap_activity_and_loop": round(h0.ms_sweeps - dis_total - h0.ms_relabel, 2)}
     for g in hb + hp:
         g.close()
     del dcs, dct, dnl
@@ -437,6 +447,7 @@ def run_config4(args):
         "speedup_batched_vs_plain": round(total_p / kw / (total_b / args.steps), 3),
         "speedup_batched_warm_vs_plain": round(total_p / kw / (total_w / kw), 3),
         "roofline": roof,
+        "breakdown_ms": breakdown,
         "e2e": {"value": per(total_e, ke), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(sum(x.n + 8 for x in insts)), "steps": ke},
         "gpu_launches": int(sum(s.launches for s in b_stats)) * args.steps,

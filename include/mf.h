@@ -106,6 +106,8 @@ typedef struct {
                                     host loop; batch: persistent launches of this instance's kernel type) */
     int32_t reduced_vertices;    /* vertices merged into s or t by opts.region_reduction (0 without it) */
     int32_t reserved[1];
+    double ms_relabel;           /* device time of the global and boundary relabels after sweeps (host-driven
+                                    loops: CUDA events around each; a batch reports the whole batch's) */
 } mf_stats;
 
 /* Fill *opts with the defaults listed in mf_opts. */
@@ -132,6 +134,22 @@ void mf_default_opts(mf_opts *opts);
  */
 mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int connectivity,
                          const int32_t tile[3], void *cuda_stream);
+
+/*
+ * mf_create_grid with placement flags.  MF_STATE_HOST keeps the residual
+ * planes, excess, labels, boundary outflows and the stored inputs (about
+ * (3H+6)*4 bytes per vertex) in pinned host memory (the Grace memory of a
+ * GB300 node): the kernels stage each region from there and write it back
+ * over NVLink-C2C with plain loads and stores, the GPU keeps only the
+ * per-region flags, counters, cut and relabel masks (a few bytes per
+ * vertex).  This is the out-of-core mode of the sequential and streaming
+ * variants (Sec. 4.3, Sec. 5.3: only the regions being discharged need to
+ * be in fast memory); results are identical to device placement.
+ * flags = 0 is mf_create_grid.  MF_EINVAL for unknown flags.
+ */
+#define MF_STATE_HOST 1
+mf_status mf_create_grid_ex(mf_grid **out, int ndim, const int64_t dims[3], int connectivity,
+                            const int32_t tile[3], void *cuda_stream, int flags);
 
 /*
  * Set the capacities (Sec. 2: c : E -> N0, cs / ct the terminal links).
@@ -317,8 +335,13 @@ mf_status mf_min_cut_2d_noalloc(const int64_t dims[2], int connectivity, const i
  *     clamped to [-c, c]; sink flow round(S p[N+1][v]) clamped to
  *     [0, ct - min(cs,ct)]; every s-link saturated; then synchronous rounds in
  *     which each vertex with negative excess lowers its own outflows (sink
- *     first, then arcs 0..N-1) until no excess is negative.  max_rounds <= 0
- *     means 4096; *rounds (nullable) receives the rounds used.  The next
+ *     first, then arcs 0..N-1) until no excess is negative.  The rounds are
+ *     computed in phases over 32x32 tiles (a tile trims until none of its
+ *     vertices has a deficit; phases repeat until no flow between tiles
+ *     changes), which reaches the same preflow: any order of these trims
+ *     ends at the least fixed point of a monotone map.  max_rounds <= 0 means
+ *     4096 and caps the phases; *rounds (nullable) receives the phases run (0
+ *     if the prediction already projected to a preflow).  The next
  *     mf_solve / mf_begin with opts.warm_start = 1 starts from this preflow;
  *     its labels are the exact region distances to t in the residual graph of
  *     that preflow (the global relabel, counted in stats.global_relabels) on
@@ -329,6 +352,13 @@ mf_status mf_min_cut_2d_noalloc(const int64_t dims[2], int connectivity, const i
 mf_status mf_warm_features(mf_grid *g, float *x);
 mf_status mf_warm_targets(mf_grid *g, float *t);
 mf_status mf_warm_start(mf_grid *g, const float *pred, int32_t max_rounds, int32_t *rounds);
+/* mf_warm_start for many grids with one wait: the projections are enqueued
+ * on grids[0]'s stream.  preds[i] as in mf_warm_start, or NULL to leave grid
+ * i cold; rounds (nullable, count entries) receives each grid's phases, or -1
+ * where no preflow was reached (that grid then starts cold).  The next
+ * mf_solve_batch with opts.warm_start = 1 starts every projected grid warm. */
+mf_status mf_warm_start_batch(mf_grid *const *grids, int count, const float *const *preds, int32_t max_rounds,
+                              int32_t *rounds);
 
 /*
  * The network of the warm start: four 3x3 convolutions (zero padding),

@@ -162,10 +162,13 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
         else { x = TX - 1; y = p - 2 * TX - TY; }
     };
     // hmin[p] = min{d(w) : residual arc from the perimeter vertex to w in B^R}
-    auto rebuild_hmin = [&]() {
+    // with only_round, just the slots whose row the last Augment round changed
+    // (a boundary arc's residual changes only by a push of its own cell)
+    auto rebuild_hmin = [&](bool only_round) {
         for (int p = tid; p < C::PER; p += NT) {
             int x, y;
             per_xy(p, x, y);
+            if (only_round && s_dirty[y] != 2) continue;
             int m = INT_MAX;
 #pragma unroll
             for (int d = 0; d < N; ++d) {
@@ -179,7 +182,9 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
 
     // ---- stage the tile --------------------------------------------------------
     const bool full = ox + TX <= g.X && oy + TY <= g.Y;
-    const bool vec = full && (g.X % 4) == 0;  // every row starts on a 16-byte boundary
+    // bulk copies need every row on a 16-byte boundary; planes in host memory
+    // are read with plain loads
+    const bool vec = full && (g.X % 4) == 0 && !st.host;
     if (vec) {
         // one bulk copy per row of every plane (cap[N], tcap, exc are adjacent in
         // shared memory) against the block's transaction barrier, spread over
@@ -232,7 +237,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
     }
     __syncthreads();
     rebuild_masks(false);
-    rebuild_hmin();
+    rebuild_hmin(false);
     __syncthreads();
     DIAG_LAP(0);
 
@@ -537,7 +542,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
                     __syncthreads();
                 }
                 rebuild_masks(true);  // a push changes rows y-1..y+1 only
-                rebuild_hmin();
+                rebuild_hmin(true);
                 __syncthreads();
                 for (int y = tid; y < TY; y += NT)
                     if (s_dirty[y] == 2) s_dirty[y] = 1;

@@ -182,18 +182,24 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
             }
         }
     };
-    auto rebuild_hm = [&]() {
+    // with only_round, just the cells whose row the last Augment round changed
+    // (a boundary arc's residual changes only by a push of its own cell)
+    auto rebuild_hm = [&](bool only_round) {
         for (int h = tid; h < C::HL; h += NT) {
             int lx, ly, lz, d;
             halo3_src<TY, TZ>(h, lx, ly, lz, d);
-            const int i = (lz * TY + ly) * TX + lx;
+            const int rho = lz * TY + ly;
+            if (only_round && s_dirty[rho] != 2) continue;
+            const int i = rho * TX + lx;
             s_hm[h] = s_cap[d * V + i] > 0 ? s_hl[h] : INT_MAX;
         }
     };
 
     // ---- stage the tile --------------------------------------------------------
     const bool full = ox + TX <= g.X && oy + TY <= g.Y && oz + TZ <= g.Z;
-    const bool vec = full && (g.X % 4) == 0;  // every row starts on a 16-byte boundary
+    // bulk copies need every row on a 16-byte boundary; planes in host memory
+    // are read with plain loads
+    const bool vec = full && (g.X % 4) == 0 && !st.host;
     if (vec) {
         // one bulk copy per row of every plane (cap[N], tcap, exc are adjacent in
         // shared memory) against the block's transaction barrier, spread over
@@ -240,7 +246,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
     }
     __syncthreads();
     rebuild_masks(false);
-    rebuild_hm();
+    rebuild_hm(false);
     __syncthreads();
     DIAG_LAP(0);
 
@@ -538,7 +544,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                 }
                 DIAG_LAP(7);
                 rebuild_masks(true);  // a push changes its row and the rows one step away in y and z only
-                rebuild_hm();
+                rebuild_hm(true);
                 __syncthreads();
                 for (int rho = tid; rho < NR; rho += NT)
                     if (s_dirty[rho] == 2) s_dirty[rho] = 1;

@@ -19,6 +19,7 @@ using namespace mf;
 
 struct mf_grid {
     int ndim = 0, conn = 0, H = 0, N = 0;
+    bool host_state = false;                          // MF_STATE_HOST: planes and inputs in host memory
     Geom g{};
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -40,6 +41,9 @@ struct mf_grid {
     bool reduced = false;                             // the current solve runs on the reduced inputs
     long long red_konst = 0;                          // its constant (cut edges between the merged sets)
     int begin_active = -1;                            // active regions after mf_begin's relabel, -1: unknown
+    bool begin_pending = false;                       // that relabel's counts are still in flight to h_ctr
+    int *h_warm = nullptr;                            // pinned: the projection's flag words, read after a wait
+    bool warm_pending = false;
     // CUDA graph of the sweep loop (opts.graph_loop)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -60,7 +64,7 @@ struct mf_grid {
     int sweep = 0;
     mf_opts opts{};
     mf_stats stats{};
-    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     long long launches = 0;
     std::string err;
 };
@@ -835,14 +839,20 @@ static void free_all(mf_grid *h) {
     h->cap_stream = nullptr;
     h->loopctl = nullptr;
     h->h_loop = nullptr;
-    void *ptrs[] = {h->cs, h->ct, h->nl, h->st.cap, h->st.tcap, h->st.exc, h->st.lab, h->st.lab_next,
-                    h->st.bout, h->st.active, h->st.disc, h->st.left_active, h->st.flow_t, h->st.flow0,
+    void *planes[] = {h->cs, h->ct, h->nl, h->st.cap, h->st.tcap, h->st.exc, h->st.lab, h->st.lab_next, h->st.bout};
+    for (void *p : planes)
+        if (p) {
+            if (h->host_state) cudaFreeHost(p);
+            else cudaFree(p);
+        }
+    void *ptrs[] = {h->st.active, h->st.disc, h->st.left_active, h->st.flow_t, h->st.flow0,
                     h->st.hist, h->st.ctr, h->smin, h->tset, h->c64, h->cut_scratch, h->warmF, h->warmFt,
                     h->warmE};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
     if (h->h_fin) cudaFreeHost(h->h_fin);
+    if (h->h_warm) cudaFreeHost(h->h_warm);
     for (void *p : {(void *)h->red_codes, (void *)h->red_cs, (void *)h->red_ct, (void *)h->red_nl, (void *)h->red_dev})
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -855,7 +865,13 @@ static void free_all(mf_grid *h) {
 
 mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int connectivity,
                          const int32_t tile[3], void *cuda_stream) {
+    return mf_create_grid_ex(out, ndim, dims, connectivity, tile, cuda_stream, 0);
+}
+
+mf_status mf_create_grid_ex(mf_grid **out, int ndim, const int64_t dims[3], int connectivity,
+                            const int32_t tile[3], void *cuda_stream, int flags) {
     mf_grid *g = nullptr;
+    if (flags & ~MF_STATE_HOST) return fail(nullptr, MF_EINVAL, "unknown flags");
     if (!out) return fail(nullptr, MF_EINVAL, "out is NULL");
     *out = nullptr;
     if (!dims) return fail(nullptr, MF_EINVAL, "dims is NULL");
@@ -878,6 +894,8 @@ mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int con
     g = new (std::nothrow) mf_grid();
     if (!g) return fail(nullptr, MF_ENOMEM, "host allocation failed");
     g->ndim = ndim;
+    g->host_state = (flags & MF_STATE_HOST) != 0;
+    g->st.host = g->host_state ? 1 : 0;
     g->conn = connectivity;
     g->H = connectivity / 2;
     g->N = connectivity;
@@ -901,10 +919,20 @@ mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int con
     }
     const size_t N = (size_t)connectivity;
     const size_t n = (size_t)nll;
-    struct A { void **p; size_t bytes; } allocs[] = {
+    // the planes and stored inputs: device memory, or with MF_STATE_HOST pinned
+    // host memory that the kernels read and write over NVLink-C2C
+    struct A { void **p; size_t bytes; } planes[] = {
         {(void **)&g->cs, n * 4}, {(void **)&g->ct, n * 4}, {(void **)&g->nl, (N / 2) * n * 4},
         {(void **)&g->st.cap, N * n * 4}, {(void **)&g->st.tcap, n * 4}, {(void **)&g->st.exc, n * 4},
-        {(void **)&g->st.lab, n * 4}, {(void **)&g->st.lab_next, n * 4}, {(void **)&g->st.bout, N * n * 4},
+        {(void **)&g->st.lab, n * 4}, {(void **)&g->st.lab_next, n * 4}, {(void **)&g->st.bout, N * n * 4}};
+    for (auto &a : planes) {
+        e = g->host_state ? cudaMallocHost(a.p, a.bytes) : cudaMalloc(a.p, a.bytes);
+        if (e != cudaSuccess) {
+            g->err = std::string(g->host_state ? "cudaMallocHost: " : "cudaMalloc: ") + cudaGetErrorString(e);
+            return bail(e == cudaErrorMemoryAllocation ? MF_ENOMEM : MF_ECUDA);
+        }
+    }
+    A allocs[] = {
         {(void **)&g->st.active, (size_t)G.nreg}, {(void **)&g->st.disc, (size_t)G.nreg},
         {(void **)&g->st.left_active, (size_t)G.nreg}, {(void **)&g->st.flow_t, 8}, {(void **)&g->st.flow0, 8},
         {(void **)&g->st.hist, (kHistBins + 1) * 4}, {(void **)&g->st.ctr, kCtrWords * 4},
@@ -928,8 +956,9 @@ mf_status mf_create_grid(mf_grid **out, int ndim, const int64_t dims[3], int con
     }
     e = cudaMemsetAsync(g->st.disc, 0, (size_t)G.nreg, g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->st.left_active, 0, (size_t)G.nreg, g->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->st.bout, 0, N * n * 4, g->stream);
+    if (e == cudaSuccess && !g->host_state) e = cudaMemsetAsync(g->st.bout, 0, N * n * 4, g->stream);
     if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MF_ECUDA); }
+    if (g->host_state) memset(g->st.bout, 0, N * n * 4);
     mf_default_opts(&g->opts);
     *out = g;
     return MF_OK;
@@ -950,7 +979,8 @@ mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const in
     g->caps_set = false;
     g->begun = g->finished = false;
     g->warm_ready = false;
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    (void)on_device;  // unified addressing: the copy direction follows from the pointers
+    const cudaMemcpyKind kind = cudaMemcpyDefault;
     CK(cudaMemcpyAsync(g->cs, cs, n * 4, kind, g->stream));
     CK(cudaMemcpyAsync(g->ct, ct, n * 4, kind, g->stream));
     CK(cudaMemcpyAsync(g->nl, nlink, H * n * 4, kind, g->stream));
@@ -1005,7 +1035,21 @@ static mf_status reduction_run(mf_grid *g, const int32_t *tile, bool *ok) {
     return MF_OK;
 }
 
-mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
+// counts of the relabel of a warm mf_begin, after the stream has been waited for
+static void begin_collect(mf_grid *g) {
+    if (!g->begin_pending) return;
+    g->begin_active = g->h_ctr[kActiveRegions];
+    g->stats.relabel_levels = g->h_ctr[kGlrLevels];
+    g->begin_pending = false;
+}
+
+// defer: leave the relabel of a warm start in flight (a batch waits once for
+// all its grids and then calls begin_collect)
+static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer);
+
+mf_status mf_begin(mf_grid *g, const mf_opts *opts) { return begin_impl(g, opts, false); }
+
+static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
     if (opts) g->opts = *opts;
@@ -1060,12 +1104,13 @@ mf_status mf_begin(mf_grid *g, const mf_opts *opts) {
         // the sweeps only move the excess that still can.
         CK(glr2d(g->conn, g->g, g->st, g->cut_scratch, g->stream));
         CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
-        CK(cudaStreamSynchronize(g->stream));
-        const int levels = g->h_ctr[kGlrLevels];
-        g->begin_active = g->h_ctr[kActiveRegions];
+        g->begin_pending = true;
         g->stats.global_relabels = 1;
-        g->stats.relabel_levels = levels;
         g->launches += 4;  // masks, the cooperative levels launch, finish, count
+        if (!defer) {
+            CK(cudaStreamSynchronize(g->stream));
+            begin_collect(g);
+        }
     }
     return MF_OK;
 }
@@ -1154,6 +1199,8 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
         return fail(g, MF_EROUNDLIMIT, "an Augment stage hit max_rounds");
     }
     int active = g->h_ctr[kActiveRegions];
+    const bool relabel = active > 0 && (glr_due(g, g->sweep) || br_due(g, g->sweep));
+    if (relabel) CK(cudaEventRecord(g->ev[7], g->stream));
     if (active > 0 && glr_due(g, g->sweep)) {
         // exact region-distance relabel (raises labels to max(d, d*)), then the
         // activity of every region is recomputed from the new labels
@@ -1168,6 +1215,13 @@ static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
     } else if (active > 0 && br_due(g, g->sweep)) {
         mf_status bs = br_step(g, g->stream, &active, nullptr);
         if (bs != MF_OK) return bs;
+    }
+    if (relabel) {  // both relabels end with a wait on the stream
+        CK(cudaEventRecord(g->ev[8], g->stream));
+        CK(cudaEventSynchronize(g->ev[8]));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g->ev[7], g->ev[8]);
+        g->stats.ms_relabel += ms;
     }
     if (active_out) *active_out = active;
     return MF_OK;
@@ -1427,11 +1481,12 @@ struct BatchBufs {
 // first; one wait then reads every relabelled instance's level count.
 // Returns in *any_left the number of instances still active afterwards.
 static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *insts, unsigned char *done_dev,
-                               int *any_dev, int *any_left, int sweep, cudaStream_t s) {
+                               int *any_dev, int *any_left, int sweep, cudaStream_t s, double *ms_total) {
     mf_grid *g = grids[0];
     std::vector<unsigned char> done(count);
     CK(cudaMemcpyAsync(done.data(), done_dev, count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    CK(cudaEventRecord(g->ev[7], s));
     std::vector<int> glr;
     for (int i = 0; i < count; ++i) {
         mf_grid *h = grids[i];
@@ -1451,7 +1506,11 @@ static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *ins
     batch_relabel_end_kernel<<<(count + 255) / 256, 256, 0, s>>>(insts, done_dev, any_dev, count);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(any_left, any_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(g->ev[8], s));
     CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->ev[7], g->ev[8]);
+    *ms_total += ms;
     for (int i : glr) {
         mf_grid *h = grids[i];
         const int levels = h->h_ctr[kGlrLevels];
@@ -1485,7 +1544,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         if (opts) oi = *opts;
         else mf_default_opts(&oi);
         if (oi.warm_start && !grids[i]->warm_ready) oi.warm_start = 0;
-        mf_status st = mf_begin(grids[i], &oi);
+        mf_status st = begin_impl(grids[i], &oi, grids[i]->stream == s);
         if (st != MF_OK) return st;
         if (grids[i]->stream != s) {
             cudaError_t e = cudaStreamSynchronize(grids[i]->stream);
@@ -1494,6 +1553,14 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         const long long b = grids[i]->boundary;
         cap = std::max(cap, g->opts.max_sweeps > 0 ? (long long)g->opts.max_sweeps
                                                     : std::min<long long>(2 * b * b + 1, 1ll << 30));
+    }
+    // the relabels of warm starts were left in flight: one wait for all; a grid
+    // whose initial labels already show a maximum preflow makes no sweep
+    CK(cudaStreamSynchronize(s));
+    std::vector<unsigned char> done0(count, 0);
+    for (int i = 0; i < count; ++i) {
+        begin_collect(grids[i]);
+        if (grids[i]->begin_active == 0) done0[i] = 1;
     }
     CK(cudaEventRecord(g->ev[1], s));
     // kernel types (connectivity, tile) and the table of all regions
@@ -1535,7 +1602,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     CK(cudaMemcpyAsync(B.regs, hregs.data(), sizeof(int2) * nregs, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.type_of, type_of.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(B.sweeps, 0, sizeof(int) * count, s));
-    CK(cudaMemsetAsync(B.done, 0, count, s));
+    CK(cudaMemcpyAsync(B.done, done0.data(), count, cudaMemcpyHostToDevice, s));
     const mf_opts &o = g->opts;
     SweepArgs sa{};
     sa.partial = o.partial_discharge;
@@ -1549,6 +1616,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     // host loop: the persistent discharge launches of each kernel type are
     // timed with events (no event can be recorded inside the graph's loop body)
     std::vector<double> type_ms(nt, 0.0);
+    double relabel_ms = 0.0;
     std::vector<int> type_launches(nt, 0), hcnt(nt, 0);
     if (!o.graph_loop) {
         B.tev.assign(2 * nt, nullptr);
@@ -1647,7 +1715,8 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
                 break;
             }
             // stopped at a multiple of the relabel period
-            mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], loopst[kLoopSweep], s);
+            mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], loopst[kLoopSweep], s,
+                                         &relabel_ms);
             if (st != MF_OK) return st;
             if (!g->h_ctr[0]) break;
         }
@@ -1672,7 +1741,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
                 break;
             }
             if ((P > 0 && (sweep + 1) % P == 0) || (o.global_relabel_first > 0 && sweep + 1 == o.global_relabel_first)) {
-                mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], sweep + 1, s);
+                mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], sweep + 1, s, &relabel_ms);
                 if (st != MF_OK) return st;
                 if (!g->h_ctr[0]) break;
             }
@@ -1716,6 +1785,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         if (i == 0) h->stats.launches += launches;  // launches shared by the whole batch, counted once
         h->stats.ms_discharge = type_ms[type_of[i]];
         h->stats.discharge_launches = type_launches[type_of[i]];
+        h->stats.ms_relabel = relabel_ms;
         if (stats) stats[i] = h->stats;
     }
     return rs;
@@ -1758,32 +1828,77 @@ mf_status mf_warm_targets(mf_grid *g, float *t) {
     return MF_OK;
 }
 
-mf_status mf_warm_start(mf_grid *g, const float *pred, int32_t max_rounds, int32_t *rounds) {
-    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
-    if (!pred) return fail(g, MF_EINVAL, "pred is NULL");
-    if (g->ndim != 2) return fail(g, MF_EINVAL, "the warm start is for 2D grids");
-    if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
+// The projection of a prediction, enqueued on stream st; its flag words go to
+// the grid's pinned h_warm (warm_collect reads them after a wait).
+static mf_status warm_enqueue(mf_grid *g, const float *pred, int32_t max_rounds, cudaStream_t st) {
     g->warm_ready = false;
+    g->warm_pending = false;
     const size_t n = (size_t)g->g.n;
     if (!g->warmF) {
         CK(cudaMalloc(&g->warmF, (size_t)g->H * n * 4));
         CK(cudaMalloc(&g->warmFt, n * 4));
         CK(cudaMalloc(&g->warmE, n * 4));
+        CK(cudaMallocHost((void **)&g->h_warm, 8 * 4));
     }
     if (max_rounds <= 0) max_rounds = 4096;
-    CK(launch_project_init(g->conn, g->g, g->cs, g->ct, g->nl, pred, g->warmF, g->warmFt, g->stream));
+    CK(launch_project_init(g->conn, g->g, g->cs, g->ct, g->nl, pred, g->warmF, g->warmFt, st));
     CK(launch_project_rounds(g->conn, g->g, g->cs, g->ct, g->warmF, g->warmFt, g->warmE, &g->st.ctr[kGlrFlags],
-                             max_rounds, g->stream));
-    CK(cudaMemcpyAsync(g->h_ctr, &g->st.ctr[kGlrFlags], 4 * 4, cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
-    const int r = g->h_ctr[2];
-    if (r < 0) {
-        if (rounds) *rounds = max_rounds;
-        return fail(g, MF_EROUNDLIMIT, "projection did not reach a preflow within max_rounds");
-    }
+                             max_rounds, st));
+    CK(cudaMemcpyAsync(g->h_warm, &g->st.ctr[kGlrFlags], 5 * 4, cudaMemcpyDeviceToHost, st));
+    g->warm_pending = true;
+    return MF_OK;
+}
+
+// after the wait: the phases run (-1: no preflow; the grid then stays cold)
+static int warm_collect(mf_grid *g) {
+    if (!g->warm_pending) return -1;
+    g->warm_pending = false;
+    const int r = g->h_warm[2];
+    if (r < 0) return -1;
     g->warm_rounds = r;
     g->warm_ready = true;
+    return r;
+}
+
+mf_status mf_warm_start(mf_grid *g, const float *pred, int32_t max_rounds, int32_t *rounds) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    if (!pred) return fail(g, MF_EINVAL, "pred is NULL");
+    if (g->ndim != 2) return fail(g, MF_EINVAL, "the warm start is for 2D grids");
+    if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
+    mf_status s = warm_enqueue(g, pred, max_rounds, g->stream);
+    if (s != MF_OK) return s;
+    CK(cudaStreamSynchronize(g->stream));
+    const int r = warm_collect(g);
+    if (r < 0) {
+        if (rounds) *rounds = max_rounds <= 0 ? 4096 : max_rounds;
+        return fail(g, MF_EROUNDLIMIT, "projection did not reach a preflow within max_rounds");
+    }
     if (rounds) *rounds = r;
+    return MF_OK;
+}
+
+mf_status mf_warm_start_batch(mf_grid *const *grids, int count, const float *const *preds, int32_t max_rounds,
+                              int32_t *rounds) {
+    if (!grids || !preds || count < 1) return fail(nullptr, MF_EINVAL, "grids and preds must be non-empty arrays");
+    mf_grid *g = grids[0];
+    if (!g) return fail(nullptr, MF_EINVAL, "null grid in the batch");
+    cudaStream_t s = g->stream;
+    for (int i = 0; i < count; ++i) {
+        mf_grid *h = grids[i];
+        if (!h) return fail(g, MF_EINVAL, "null grid in the batch");
+        if (!preds[i]) continue;
+        if (h->ndim != 2) return fail(g, MF_EINVAL, "the warm start is for 2D grids");
+        if (!h->caps_set) return fail(g, MF_ESTATE, "a grid of the batch has no capacities");
+        if (h->device != g->device) return fail(g, MF_EINVAL, "all grids must be on one device");
+        if (h->stream != s) CK(cudaStreamSynchronize(h->stream));  // its earlier work precedes the batch stream's
+        mf_status st = warm_enqueue(h, preds[i], max_rounds, s);
+        if (st != MF_OK) return fail(g, st, h->err);
+    }
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i) {
+        const int r = preds[i] ? warm_collect(grids[i]) : -1;
+        if (rounds) rounds[i] = r;
+    }
     return MF_OK;
 }
 
@@ -1835,7 +1950,8 @@ mf_status mf_get_residual(mf_grid *g, int32_t *res, int32_t *tres, int32_t *exc,
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!g->begun) return fail(g, MF_ESTATE, "no solve");
     const size_t n = (size_t)g->g.n;
-    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    (void)on_device;  // unified addressing: the direction follows from the pointers (planes may be host memory)
+    const cudaMemcpyKind k = cudaMemcpyDefault;
     if (res) CK(cudaMemcpyAsync(res, g->st.cap, (size_t)g->N * n * 4, k, g->stream));
     if (tres) CK(cudaMemcpyAsync(tres, g->st.tcap, n * 4, k, g->stream));
     if (exc) CK(cudaMemcpyAsync(exc, g->st.exc, n * 4, k, g->stream));
@@ -1854,8 +1970,7 @@ mf_status mf_get_labels(mf_grid *g, int32_t *lab, int32_t *d_inf, int on_device)
     if (d_inf) *d_inf = g->g.dinf;
     if (lab) {
         if (!g->begun) return fail(g, MF_ESTATE, "no solve");
-        CK(cudaMemcpyAsync(lab, g->st.lab, (size_t)g->g.n * 4,
-                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaMemcpyAsync(lab, g->st.lab, (size_t)g->g.n * 4, cudaMemcpyDefault, g->stream));
         CK(cudaStreamSynchronize(g->stream));
     }
     return MF_OK;

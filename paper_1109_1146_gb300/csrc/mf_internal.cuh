@@ -53,6 +53,7 @@ struct DevState {
     long long *flow0;            // sum of min(cs, ct) (terminal reduction)
     int *hist;                   // [kHistBins + 1] labels of boundary vertices
     int *ctr;                    // small counters, see Ctr
+    int host;                    // nonzero: the planes live in host (Grace) memory, read over NVLink-C2C
 };
 
 // indices into DevState::ctr
@@ -217,8 +218,9 @@ cudaError_t launch_warm_targets(int conn, const Geom &g, const DevState &st, con
                                 const int *nl, float *t, cudaStream_t s);
 cudaError_t launch_project_init(int conn, const Geom &g, const int *cs, const int *ct, const int *nl, const float *p,
                                 int *F, int *ft, cudaStream_t s);
-// the trims in one cooperative launch, tile-local phases; flags: 4 ints
-// (flags[2] = phases run, -1: no preflow reachable or the phase cap hit)
+// the trims in one cooperative launch, tile-local phases; flags: 5 ints
+// (flags[2] = phases run, 0 if nothing was trimmed, -1: no preflow
+// reachable or the phase cap hit)
 cudaError_t launch_project_rounds(int conn, const Geom &g, const int *cs, const int *ct, int *F, int *ft, int *E,
                                   int *flags, int max_rounds, cudaStream_t s);
 cudaError_t launch_warm_init(int conn, const Geom &g, const DevState &st, const int *cs, const int *ct, const int *nl,

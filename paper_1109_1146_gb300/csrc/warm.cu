@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) project_tiles_kernel(const Geom g, const 
                 bs[i] = in ? cs[v] - min(cs[v], ct[v]) : 0;
             }
             __syncthreads();
-            int cross = 0, bad = 0;
+            int cross = 0, bad = 0, trimmed = 0;
             for (int it = 0;; ++it) {
                 int changed = 0;
                 for (int i = tid; i < TP * TP; i += blockDim.x) {
@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(256) project_tiles_kernel(const Geom g, const 
                     if (def > 0) bad = 1;
                 }
                 if (!__syncthreads_or(changed)) break;
+                trimmed = 1;
                 if (it >= (1 << 16)) {  // never expected: report a failure, not a false convergence
                     bad = 1;
                     break;
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(256) project_tiles_kernel(const Geom g, const 
             if (tid == 0) {
                 if (cross) atomicOr(&flags[phase & 1], 1);
                 if (bad) atomicOr(&flags[3], 1);
+                if (trimmed) atomicOr(&flags[4], 1);
             }
             __syncthreads();  // the shared arrays are reused by the next tile
         }
@@ -215,7 +217,9 @@ __global__ void __launch_bounds__(256) project_tiles_kernel(const Geom g, const 
         const int cross = *(volatile int *)&flags[phase & 1];
         const int bad = *(volatile int *)&flags[3];
         if (bad || !cross || phase + 1 >= max_phases) {
-            if (blockIdx.x == 0 && tid == 0) flags[2] = (bad || cross) ? -1 : phase + 1;
+            // phases that trimmed (0: the prediction already was a preflow)
+            const int any = *(volatile int *)&flags[4];
+            if (blockIdx.x == 0 && tid == 0) flags[2] = (bad || cross) ? -1 : (any ? phase + 1 : 0);
             break;
         }
         if (blockIdx.x == 0 && tid == 0) flags[(phase + 1) & 1] = 0;
@@ -313,7 +317,7 @@ cudaError_t launch_project_rounds(int conn, const Geom &g, const int *cs, const 
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)((g.X + kProjTile - 1) / kProjTile) * ((g.Y + kProjTile - 1) / kProjTile);
     const int blocks = (int)std::max<long long>(1, std::min<long long>(tiles, max_blocks));
-    e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s);
+    e = cudaMemsetAsync(flags, 0, 5 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     Geom gg = g;
     const int *a_cs = cs, *a_ct = ct;

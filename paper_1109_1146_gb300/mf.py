@@ -17,14 +17,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(_HERE, "_lib", "libmf.so")
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EOVERFLOW, MF_ESWEEPLIMIT, MF_EROUNDLIMIT, MF_ESTATE = range(8)
+MF_STATE_HOST = 1
 STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "MF_ESWEEPLIMIT",
                 "MF_EROUNDLIMIT", "MF_ESTATE"]
 
 # every symbol include/mf.h declares
-EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
+EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_create_grid_ex", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
            "mf_finish", "mf_boundary_relabel", "mf_region_reduction", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
            "mf_last_error", "mf_min_cut_2d_noalloc", "mf_solve_batch", "mf_warm_features", "mf_warm_targets",
-           "mf_warm_start", "mf_certify", "mf_get_flow", "mf_load_model", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
+           "mf_warm_start", "mf_warm_start_batch", "mf_certify", "mf_get_flow", "mf_load_model", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
            "mf_cnn_get_params", "mf_cnn_set_params", "mf_cnn_get_grads", "mf_cnn_forward", "mf_cnn_infer",
            "mf_cnn_zero_grad",
            "mf_cnn_backward", "mf_cnn_mse", "mf_cnn_adam_step"]
@@ -49,7 +50,8 @@ class mf_stats(ctypes.Structure):
                 ("global_relabels", ctypes.c_int32), ("relabel_levels", ctypes.c_int32),
                 ("projection_rounds", ctypes.c_int32), ("boundary_relabels", ctypes.c_int32),
                 ("boundary_relabel_levels", ctypes.c_int32), ("discharge_launches", ctypes.c_int32),
-                ("reduced_vertices", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("reduced_vertices", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+                ("ms_relabel", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -67,6 +69,7 @@ _P, _I, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
 SIGNATURES = {
     "mf_default_opts": (None, [ctypes.POINTER(mf_opts)]),
     "mf_create_grid": (_I, [ctypes.POINTER(_P), _I, _P, _I, _P, _P]),
+    "mf_create_grid_ex": (_I, [ctypes.POINTER(_P), _I, _P, _I, _P, _P, _I]),
     "mf_set_caps": (_I, [_P, _P, _P, _P, _I]),
     "mf_solve": (_I, [_P, ctypes.POINTER(mf_opts), ctypes.POINTER(mf_stats)]),
     "mf_begin": (_I, [_P, ctypes.POINTER(mf_opts)]),
@@ -85,6 +88,7 @@ SIGNATURES = {
     "mf_warm_features": (_I, [_P, _P]),
     "mf_warm_targets": (_I, [_P, _P]),
     "mf_warm_start": (_I, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "mf_warm_start_batch": (_I, [_P, _I, _P, ctypes.c_int32, _P]),
     "mf_get_flow": (_I, [_P, _P]),
     "mf_load_model": (_I, [_P, ctypes.c_char_p]),
     "mf_certify": (_I, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32)]),
@@ -189,6 +193,20 @@ def min_cut_2d_noalloc(dims, connectivity, res, tres, exc, smin, smax, stream=No
         raise MFError(st, lib.mf_last_error(None).decode())
 
 
+def warm_start_batch(grids, preds, max_rounds=0):
+    """mf_warm_start_batch: preds[i] a device float tensor [N+2, n] or None;
+    returns the phases of each grid (-1: no preflow, cold)."""
+    lib = load()
+    n = len(grids)
+    arr = (ctypes.c_void_p * n)(*[g._h.value for g in grids])
+    ps = (ctypes.c_void_p * n)(*[None if p is None else _ptr(p)[0] for p in preds])
+    rounds = (ctypes.c_int32 * n)()
+    st = lib.mf_warm_start_batch(arr, n, ps, int(max_rounds), rounds)
+    if st != MF_OK:
+        raise MFError(st, lib.mf_last_error(grids[0]._h).decode())
+    return list(rounds)
+
+
 def solve_batch(grids, opts: mf_opts | None = None):
     """mf_solve_batch over a list of Grid objects; returns their mf_stats."""
     lib = load()
@@ -204,7 +222,8 @@ def solve_batch(grids, opts: mf_opts | None = None):
 class Grid:
     """One grid instance (owns a mf_grid handle)."""
 
-    def __init__(self, dims, connectivity, tile=None, stream=None):
+    def __init__(self, dims, connectivity, tile=None, stream=None, host_state=False):
+        """host_state: the planes live in pinned host memory (MF_STATE_HOST)."""
         lib = load()
         dims = tuple(int(d) for d in dims) + (1,) * (3 - len(dims))
         self.ndim = 3 if connectivity == 6 else 2
@@ -216,7 +235,7 @@ class Grid:
         t = None if tile is None else (ctypes.c_int32 * 3)(*(tuple(tile) + (1,) * (3 - len(tile))))
         s = _stream_arg(stream)
         h = ctypes.c_void_p()
-        st = lib.mf_create_grid(ctypes.byref(h), self.ndim, d, connectivity, t, s)
+        st = lib.mf_create_grid_ex(ctypes.byref(h), self.ndim, d, connectivity, t, s, MF_STATE_HOST if host_state else 0)
         if st != MF_OK:
             raise MFError(st, lib.mf_last_error(None).decode())
         self._h = h
