@@ -69,11 +69,14 @@ def batch_instance(i, shape, batch_seed=0):
     return grids.volume_3d(X, Y, Z, seed)
 
 
-def batch_instances(batch_seed=0, count=0, threads=None, only=None):
-    """The uneven batch, generated on host threads (numpy releases the GIL)."""
+def batch_instances(batch_seed=0, count=0, threads=None, only=None, kind="all"):
+    """The uneven batch, generated on host threads (numpy releases the GIL);
+    kind "2d" / "3d" keeps only those members."""
     from gen import grids
     shapes = grids.config4_shapes(batch_seed)
     idx = list(range(len(shapes))) if only is None else list(only)
+    if kind != "all":
+        idx = [i for i in idx if (shapes[i][2] == 1) == (kind == "2d")]
     if count:
         idx = idx[:count]
     with ThreadPoolExecutor(threads or host_threads()) as ex:
@@ -258,7 +261,8 @@ def roofline_of(stats, insts, tiles, batch):
             "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 5),
             "traffic": None if tb is None else round(tb * e["vertices"] / launches),
             "alg_bytes_per_launch": round(alg / launches), "launch_ms_avg": round(e["ms"] / launches, 4),
-            "launches": e["launches"], "bytes_per_discharged_vertex": BYTES_PER_VERTEX[conn],
+            "launches": e["launches"], "discharged_vertices": e["vertices"],
+            "bytes_per_discharged_vertex": BYTES_PER_VERTEX[conn],
             "discharge_ms_by_kernel": share}
 
 
@@ -277,7 +281,7 @@ def run_config4(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     t_gen = time.perf_counter()
-    insts = batch_instances(batch_seed=rank, count=args.batch_count)
+    insts = batch_instances(batch_seed=rank, count=args.batch_count, kind=args.batch_kind)
     t_gen = time.perf_counter() - t_gen
     count = len(insts)
     nv = sum(x.n for x in insts)
@@ -403,8 +407,10 @@ def run_config4(args):
     del dcs, dct, dnl
 
     extras = {}
-    if rank == 0 and "c1" in args.extras:
+    if rank == 0 and "c1" in args.extras.split(","):
         extras["seg2d_2048_c8"] = run_single_extra(args, make_instance(0), stream, dev)
+    if rank == 0 and "c1h" in args.extras.split(","):
+        extras["seg2d_2048_c8_grace_state"] = run_single_extra(args, make_instance(0), stream, dev, host_state=True)
     if rank == 0 and "c2" in args.extras:
         from gen import grids
         extras["vol3d_512x512x384"] = run_single_extra(args, grids.config2(0), stream, dev)
@@ -427,7 +433,8 @@ def run_config4(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_b / args.steps, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD + (f" (first {count})" if args.batch_count else ""),
+        "config": {"workload": BATCH_WORKLOAD + (f" ({args.batch_kind} members only)" if args.batch_kind != "all" else "")
+                   + (f" (first {count})" if args.batch_count else ""),
                    "instances": count, "vertices": nv, "batch_seed": "rank",
                    "parallelism": f"replicas x{ws}", "mode": "batched persistent solve, CUDA-graph sweep loop",
                    "schedule": sched, "tiles": sorted({"x".join(map(str, t)) for t in tiles}),
@@ -439,8 +446,8 @@ def run_config4(args):
         "batched_warm": {"ms_per_instance": per(total_w, kw), "sweeps_per_instance": sweeps(w_stats),
                          "note": "learned warm start on the 384 2D members (features, tensor-core inference, "
                                  "projection to a preflow, all timed); 3D members cold",
-                         "projection_rounds_mean_2d": round(statistics.mean(w_stats[i].projection_rounds
-                                                                             for i in idx2), 2),
+                         "projection_phases_mean_2d": round(statistics.mean([w_stats[i].projection_rounds
+                                                                              for i in idx2] or [0]), 2),
                          "steps": kw},
         "plain": {"ms_per_instance": per(total_p, kw), "sweeps_per_instance": sweeps(p_stats),
                   "note": "cold-start mf_solve of each instance one by one, default tile and options", "steps": kw},
@@ -474,13 +481,14 @@ def run_config4(args):
         torch.distributed.destroy_process_group()
 
 
-def run_single_extra(args, inst, stream, dev):
+def run_single_extra(args, inst, stream, dev, host_state=False):
     """Plain single solve of one large instance with the default tile and
-    options (extra key of the batched line): ms, sweeps, discharge roofline."""
+    options (extra key of the batched line): ms, sweeps, discharge roofline;
+    host_state keeps the grid's planes in Grace memory (MF_STATE_HOST)."""
     import torch
 
     from paper_1109_1146_gb300 import Grid, default_opts
-    with Grid(inst.dims, inst.conn, stream=stream) as g:
+    with Grid(inst.dims, inst.conn, stream=stream, host_state=host_state) as g:
         g.set_caps(torch.from_numpy(inst.cs).to(dev), torch.from_numpy(inst.ct).to(dev),
                    torch.from_numpy(inst.nlink).to(dev))
         opts = default_opts()
@@ -492,7 +500,10 @@ def run_single_extra(args, inst, stream, dev):
         roof = roofline_of(sts, [inst] * len(sts), [tile] * len(sts), batch=False)
         ok, cut, bad = g.certify()
         ms = statistics.median(s.ms_total for s in sts)
+        plane_bytes = sum(s_.discharged_vertices for s_ in sts) / len(sts) * BYTES_PER_VERTEX[inst.conn]
         return {"workload": inst.name, "vertices": inst.n, "tile": list(tile), "ms": round(ms, 3),
+                "state": "pinned host (Grace) memory over NVLink-C2C" if host_state else "device (HBM)",
+                "discharge_plane_bytes_per_solve": int(plane_bytes),
                 "sweeps": sts[-1].sweeps, "vertices_per_s": inst.n / (ms * 1e-3), "flow_value": g.flow_value(),
                 "certified": ok, "roofline": {k: roof[k] for k in ("kernel", "achieved", "frac", "launch_ms_avg")}}
 
@@ -719,6 +730,41 @@ def run_batch_warm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_prd(args):
+    """P-ARD against P-PRD (Discharge = PRD, kernel_variant 2) on the paper's
+    synthetic family (Sec. 7.1: 4-connected, excess U[-500, 500], constant
+    strength): sweeps and device ms of both on the same instances and
+    schedule (global relabel every 4 sweeps), over strength, size and region
+    size; every pair must reach the same flow value."""
+    from gen import grids
+    from paper_1109_1146_gb300 import Grid, default_opts
+
+    cases = [(1000, s, (32, 32, 1)) for s in (20, 50, 150, 400, 1000)]
+    cases += [(n, 150, (32, 32, 1)) for n in (250, 500, 2000)]
+    cases += [(1000, 150, t) for t in ((64, 64, 1), (64, 32, 1))]
+    for side, strength, tile in cases:
+        rows = {}
+        for seed in range(args.prd_seeds):
+            inst = grids.paper_synthetic(side, side, seed, strength=strength)
+            flows = set()
+            with Grid(inst.dims, 4, tile=tile) as g:
+                g.set_caps(inst.cs, inst.ct, inst.nlink)
+                for name, variant in (("ard", 0), ("prd", 2)):
+                    opts = default_opts(kernel_variant=variant)
+                    g.solve(opts)
+                    st = g.solve(opts)
+                    flows.add(g.flow_value())
+                    r = rows.setdefault(name, {"sweeps": [], "ms": [], "rounds": []})
+                    r["sweeps"].append(st.sweeps)
+                    r["ms"].append(st.ms_total)
+                    r["rounds"].append(st.rounds / max(1, st.discharges))
+            assert len(flows) == 1, (side, strength, seed, flows)
+        print(json.dumps({"workload": "prd", "instance": f"paper synthetic {side}x{side} 4-connected",
+                          "strength": strength, "tile": list(tile), "seeds": args.prd_seeds,
+                          **{f"{k}_{m}_mean": round(statistics.mean(v[m]), 3) for k, v in rows.items() for m in v}}),
+              flush=True)
+
+
 RELABEL_SCHEDULES = {
     "none": dict(global_relabel_period=0),
     "glr2": dict(global_relabel_period=2),
@@ -835,12 +881,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="config4", choices=["config4", "seg2048", "batch_warm", "relabel"])
+    ap.add_argument("--workload", default="config4", choices=["config4", "seg2048", "batch_warm", "relabel", "prd"])
+    ap.add_argument("--prd-seeds", type=int, default=3, help="prd workload: instances per point")
     ap.add_argument("--batch-count", type=int, default=0, help="first N instances of the batch (0 = all 512)")
+    ap.add_argument("--batch-kind", default="all", choices=["all", "2d", "3d"],
+                    help="batched line: all members, or only the 2D / 3D ones")
     ap.add_argument("--aux-steps", type=int, default=3,
                     help="timed steps of the warm, plain and end-to-end modes of the batched line (<= --steps)")
-    ap.add_argument("--extras", default="c1,c2",
-                    help="extra keys of the batched line: c1 = 2048^2 8-connected grid, c2 = 512x512x384 volume")
+    ap.add_argument("--extras", default="c1,c1h,c2",
+                    help="extra keys of the batched line: c1 = 2048^2 8-connected grid, c1h = the same with its "
+                         "state in Grace memory, c2 = 512x512x384 volume")
     ap.add_argument("--relabel-case", type=int, default=-1, help="relabel workload: only this instance (index)")
     ap.add_argument("--relabel-schedule", default="", help="relabel workload: only this schedule")
     args = ap.parse_args()
@@ -854,6 +904,8 @@ def main():
         run_batch_warm(args)
     elif args.workload == "relabel":
         run_relabel(args)
+    elif args.workload == "prd":
+        run_prd(args)
     else:
         run_ours(args)
 

@@ -67,7 +67,10 @@ typedef struct {
     int32_t global_relabel_period; /* P > 0: exact region-distance relabel after every P-th sweep (2D grids and
                                       3D grids with 32-wide tiles; Sec. 4.1 distance); 0 = off; default 4 */
     int32_t max_rounds;            /* cap on Augment rounds per stage inside one discharge; 0 = default 65536 */
-    int32_t kernel_variant;        /* 0: bit-parallel 2D / 3D discharge where the tile allows (default); 1: generic kernel */
+    int32_t kernel_variant;        /* 0: bit-parallel 2D / 3D discharge where the tile allows (default); 1: generic kernel;
+                                      2: Discharge = PRD (push-relabel region discharge of Sec. 3, exact region-relabel
+                                      with unit arc lengths every round): the P-PRD algorithm on the same sweep loop,
+                                      labels up to d_inf = n, global gap off, sweep cap 2n^2; for comparison */
     int32_t warm_start;            /* 1: start from the preflow of the last mf_warm_start instead of Init's zero flow */
     int32_t graph_loop;            /* 1: mf_solve runs the sweeps as one CUDA graph with a device-side while loop
                                       (per-phase times ms_discharge / ms_fuse are then not measured); default 0 */

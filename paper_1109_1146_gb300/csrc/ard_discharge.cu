@@ -149,9 +149,113 @@ __device__ __forceinline__ void discharge_region(const Geom &g, const DevState &
     long long flow_acc = 0;
     int rounds = 0, stages = 0;
     bool err = false;
+    const bool prd = sa.variant == 2;
+
+    // ---- Procedure PRD (Sec. 3): push-relabel inside R ------------------------
+    // Rounds of an exact relabel (the region-relabel of Sec. 5.1 with unit
+    // arc lengths: dist(u) = 1 if u -> t, else the least d(w) + 1 over the
+    // residual arcs into boundary vertices w, and dist(v) + 1 over residual
+    // arcs inside R; the largest labels that stay valid given d on B^R, so
+    // never below the current ones) followed by pushes along admissible arcs
+    // (dist(u) = dist(v) + 1) from the highest excess layer down, until no
+    // vertex of R with excess has a label below d_inf.
+    if (prd) {
+        ++stages;
+        for (int round = 0;; ++round) {
+            if (round >= sa.max_rounds) { err = true; break; }
+#pragma unroll
+            for (int q = 0; q < VPT; ++q) {
+                const int i = my_i[q];
+                if (i >= V) continue;
+                int dv = s_tcap[i] > 0 ? 1 : kInf;
+#pragma unroll
+                for (int d = 0; d < N; ++d)
+                    if ((halo_m[q] >> d & 1u) && s_cap[d * V + i] > 0) {
+                        const int h = s_hlab[hbase[q] + hoff(d)];
+                        if (h < dinf && h + 1 < dv) dv = h + 1;
+                    }
+                s_dist[i] = dv;
+            }
+            __syncthreads();
+            for (;;) {  // relax to the fixed point (values only fall; a stale read only delays)
+                int ch = 0;
+#pragma unroll
+                for (int q = 0; q < VPT; ++q) {
+                    const int i = my_i[q];
+                    if (i >= V) continue;
+                    int dv = s_dist[i];
+#pragma unroll
+                    for (int d = 0; d < N; ++d) {
+                        if (!(in_m[q] >> d & 1u) || s_cap[d * V + i] <= 0) continue;
+                        const int dj = s_dist[i + ioff(d)];
+                        if (dj != kInf && dj + 1 < dv) dv = dj + 1;
+                    }
+                    if (dv < s_dist[i]) {
+                        s_dist[i] = dv;
+                        ch = 1;
+                    }
+                }
+                if (!__syncthreads_or(ch)) break;
+            }
+            int lm = 0;
+#pragma unroll
+            for (int q = 0; q < VPT; ++q) {
+                const int i = my_i[q];
+                if (i < V && s_exc[i] > 0 && s_dist[i] < dinf && s_dist[i] > lm) lm = s_dist[i];
+            }
+            int Lc = block_reduce_max(lm, s_red, ph);
+            if (Lc == 0) break;  // no active vertex left in R
+            ++rounds;
+            while (Lc >= 1) {
+#pragma unroll
+                for (int q = 0; q < VPT; ++q) {
+                    const int i = my_i[q];
+                    if (i >= V || s_dist[i] != Lc) continue;
+                    int e = s_exc[i];
+                    if (e <= 0) continue;
+                    if (Lc == 1 && s_tcap[i] > 0) {
+                        const int dl = min(e, s_tcap[i]);
+                        s_tcap[i] -= dl;
+                        e -= dl;
+                        flow_acc += dl;
+                    }
+#pragma unroll
+                    for (int d = 0; d < N; ++d) {
+                        if (e == 0) break;
+                        const int c = s_cap[d * V + i];
+                        if (c <= 0) continue;
+                        if (halo_m[q] >> d & 1u) {  // out of the region, to a boundary vertex one label lower
+                            if (s_hlab[hbase[q] + hoff(d)] + 1 != Lc) continue;
+                            const int dl = min(e, c);
+                            s_cap[d * V + i] = c - dl;
+                            e -= dl;
+                        } else if (in_m[q] >> d & 1u) {
+                            const int j = i + ioff(d);
+                            if (s_dist[j] != Lc - 1) continue;
+                            const int dl = min(e, c);
+                            s_cap[d * V + i] = c - dl;
+                            s_cap[(d ^ 1) * V + j] += dl;
+                            atomicAdd(&s_exc[j], dl);
+                            e -= dl;
+                        }
+                    }
+                    s_exc[i] = e;
+                }
+                __syncthreads();
+                // the next lower layer that holds excess
+                int nx = 0;
+#pragma unroll
+                for (int q = 0; q < VPT; ++q) {
+                    const int i = my_i[q];
+                    if (i < V && s_exc[i] > 0 && s_dist[i] < Lc && s_dist[i] > nx) nx = s_dist[i];
+                }
+                Lc = block_reduce_max(nx, s_red, ph);
+            }
+        }
+    }
 
     // ---- Augment(R, T_k) for every stage ------------------------------------
-    for (int k = 0;;) {
+    for (int k = 0; !prd;) {
         if (k > klimit) break;
         ++stages;
         for (int round = 0;; ++round) {
@@ -261,6 +365,7 @@ __device__ __forceinline__ void discharge_region(const Geom &g, const DevState &
     }
 
     // ---- region-relabel: d(u) = min{k : u -> T_k}, else d_inf ----------------
+    // (PRD keeps the exact unit-length labels of its last round)
     auto flood = [&](int k) {
         for (;;) {
             int ch = 0;
@@ -280,6 +385,7 @@ __device__ __forceinline__ void discharge_region(const Geom &g, const DevState &
             if (!__syncthreads_or(ch)) break;
         }
     };
+    if (!prd) {
 #pragma unroll
     for (int q = 0; q < VPT; ++q) {
         const int i = my_i[q];
@@ -287,7 +393,8 @@ __device__ __forceinline__ void discharge_region(const Geom &g, const DevState &
     }
     __syncthreads();
     flood(0);
-    for (int k = 0;;) {
+    }
+    for (int k = 0; !prd;) {
         const int kn = next_stage(k);
         if (kn == INT_MAX) break;
         k = kn;
@@ -328,7 +435,7 @@ __device__ __forceinline__ void discharge_region(const Geom &g, const DevState &
         }
         st.tcap[v] = s_tcap[i];
         st.exc[v] = s_exc[i];
-        const int lab = s_dist[i] == kInf ? dinf : s_dist[i];
+        const int lab = s_dist[i] >= dinf ? dinf : s_dist[i];
         if (halo_m[q]) st.lab_next[v] = lab;  // boundary vertex: fused after the sweep
         else st.lab[v] = lab;
         if (s_exc[i] > 0 && lab < dinf) left = 1;

@@ -1055,6 +1055,18 @@ static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer) {
     if (opts) g->opts = *opts;
     else mf_default_opts(&g->opts);
     if (g->opts.max_rounds <= 0) g->opts.max_rounds = 1 << 16;
+    if (g->opts.kernel_variant < 0 || g->opts.kernel_variant > 2) return fail(g, MF_EINVAL, "kernel_variant must be 0, 1 or 2");
+    // Discharge = PRD (kernel_variant 2): distance labels with unit arc lengths
+    // reach up to n - 1, so d_inf = n; the global gap on boundary labels relies
+    // on ARD's region distances (labels drop only between regions) and is off
+    if (g->opts.kernel_variant == 2) {
+        if (g->opts.warm_start || g->opts.region_reduction)
+            return fail(g, MF_EINVAL, "the PRD discharge runs cold and unreduced");
+        g->g.dinf = (int)std::max<long long>(g->g.n, 1);
+        g->opts.global_gap = 0;
+    } else {
+        g->g.dinf = (int)std::max<long long>(g->boundary, 1);
+    }
     const size_t nreg = (size_t)g->g.nreg;
     CK(cudaMemsetAsync(g->st.active, 0, nreg, g->stream));
     CK(cudaMemsetAsync(g->st.disc, 0, nreg, g->stream));
@@ -1419,8 +1431,9 @@ mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats) {
     mf_status s = mf_begin(g, opts);
     if (s != MF_OK) return s;
     CK(cudaEventRecord(g->ev[1], g->stream));
-    long long cap = g->opts.max_sweeps > 0 ? g->opts.max_sweeps
-                                            : std::min<long long>(2 * g->boundary * g->boundary + 1, 1ll << 30);
+    // sweep bounds: 2|B|^2+1 for ARD (Sec. 4.4), 2n^2 for PRD (Sec. 3)
+    const long long nb = g->opts.kernel_variant == 2 ? (long long)g->g.n : g->boundary;
+    long long cap = g->opts.max_sweeps > 0 ? g->opts.max_sweeps : std::min<long long>(2 * nb * nb + 1, 1ll << 30);
     mf_status rs = MF_OK;
     if (g->opts.graph_loop && g->begin_active != 0) rs = run_graph_loop(g, cap);
     else while (g->begin_active != 0) {  // 0: the initial labels already show a maximum preflow
@@ -1550,7 +1563,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
             cudaError_t e = cudaStreamSynchronize(grids[i]->stream);
             if (e != cudaSuccess) return fail(g, MF_ECUDA, cudaGetErrorString(e));
         }
-        const long long b = grids[i]->boundary;
+        const long long b = grids[i]->opts.kernel_variant == 2 ? (long long)grids[i]->g.n : grids[i]->boundary;
         cap = std::max(cap, g->opts.max_sweeps > 0 ? (long long)g->opts.max_sweeps
                                                     : std::min<long long>(2 * b * b + 1, 1ll << 30));
     }

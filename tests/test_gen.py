@@ -77,3 +77,23 @@ def test_config4_shapes():
     assert len(sh) == 512
     assert all(64 <= s[0] <= 1024 and s[2] == 1 for s in sh[:384])
     assert all(48 <= s[0] <= 128 and s[0] == s[2] for s in sh[384:])
+
+
+def test_paper_synthetic_family():
+    # Sec. 7.1: excess/deficit uniform in [-500, 500] as one terminal link per
+    # node, every edge the constant strength, 4-connected (displacements
+    # (0,1), (1,0)); edges leaving the grid have no capacity
+    inst = grids.paper_synthetic(60, 40, 3, strength=150)
+    assert inst.conn == 4 and inst.dims == (60, 40, 1)
+    assert ((inst.cs == 0) | (inst.ct == 0)).all()
+    e = inst.cs.astype(int) - inst.ct.astype(int)
+    assert e.min() >= -500 and e.max() <= 500 and e.min() < -400 and e.max() > 400
+    assert abs(e.mean()) < 40
+    nl = inst.nlink.reshape(2, 40, 60)
+    assert (nl[0, :, :59] == 150).all() and (nl[0, :, 59] == 0).all()
+    assert (nl[1, :39, :] == 150).all() and (nl[1, 39, :] == 0).all()
+    again = grids.paper_synthetic(60, 40, 3, strength=150)
+    assert (again.cs == inst.cs).all() and (again.ct == inst.ct).all()
+    import pytest
+    with pytest.raises(ValueError):
+        grids.paper_synthetic(10, 10, 0, connectivity=8)
