@@ -16,6 +16,7 @@
 // the pass; passes repeat until no block changes.
 #include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include <cooperative_groups.h>
 
@@ -457,6 +458,226 @@ static cudaError_t glr2d_impl(const Geom &g, const DevState &st, void *scratch, 
     glr_finish_kernel<CONN><<<nb, 256, 0, s>>>(g, st, W64, A, B);
     count_active_kernel<<<(g.nreg + 255) / 256, 256, 0, s>>>(st, g.nreg);
     return cudaGetLastError();
+}
+
+// ---- the same relabel for many 2D grids at once (batched solves) -------------
+// One cooperative launch runs the levels of every grid of a batch that is due
+// for a relabel: a work unit is (grid, 64x64 block), a warp takes units in
+// turn, the grid barrier separates levels.  A grid whose set did not grow at
+// a level has its final set and is skipped from then on; its level count is
+// recorded when it stops.  The finish (d_inf for unreached vertices, the
+// boundary-label histogram, region activity) and the count of active regions
+// are one launch each over all grids.
+template <int CONN>
+__device__ __forceinline__ bool glr2d_unit(const GlrJob2 &J, int blk, const u64 *in, u64 *out, int level) {
+    GlrBlock<CONN> B;
+    glr_load_block<CONN>(J.g, J.W64, blk, J.M, B);
+    return glr_level_block<CONN>(J.g, J.W64, B, in, out, level, J.st.lab);
+}
+
+__global__ void glr2d_batch_levels_kernel(const GlrJob2 *__restrict__ jobs, int njobs, const int *__restrict__ unit_job,
+                                          int nunits, int *any, int max_levels) {
+    cg::grid_group grid = cg::this_grid();
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (int u = wid; u < nunits; u += nwarps) {
+        const GlrJob2 &J = jobs[unit_job[u]];
+        const int blk = u - J.unit0;
+        if (J.conn == 4) glr2d_unit<4>(J, blk, J.A, J.B, 0);
+        else glr2d_unit<8>(J, blk, J.A, J.B, 0);
+    }
+    if (blockIdx.x == 0) {
+        for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+            jobs[j].st.ctr[kGlrFlags + 1] = 0;
+            jobs[j].st.ctr[kGlrFlags + 2] = 0;
+        }
+        if (threadIdx.x == 0) any[1] = any[2] = 0;
+    }
+    grid.sync();
+    int level = 1;
+    for (; level < max_levels; ++level) {
+        const int f = level % 3, fp = (level + 2) % 3;  // this level's words, the previous level's
+        bool grew_any = false;
+        for (int u = wid; u < nunits; u += nwarps) {
+            const int j = unit_job[u];
+            const GlrJob2 &J = jobs[j];
+            if (level > 1 && !*(volatile int *)&J.st.ctr[kGlrFlags + fp]) continue;  // stopped growing
+            const u64 *in = (level & 1) ? J.B : J.A;
+            u64 *out = (level & 1) ? J.A : J.B;
+            const bool grew = J.conn == 4 ? glr2d_unit<4>(J, u - J.unit0, in, out, level)
+                                          : glr2d_unit<8>(J, u - J.unit0, in, out, level);
+            if (grew && lane == 0) atomicOr(&J.st.ctr[kGlrFlags + f], 1);
+            grew_any |= grew;
+        }
+        if (grew_any && lane == 0) atomicOr(&any[f], 1);
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < njobs; j += blockDim.x) jobs[j].st.ctr[kGlrFlags + (level + 1) % 3] = 0;
+            if (threadIdx.x == 0) any[(level + 1) % 3] = 0;
+        }
+        grid.sync();
+        // a grid that ran this level and did not grow ends here: its sets of
+        // this level and the previous one are equal
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+                const int *c = jobs[j].st.ctr;
+                const bool ran = level == 1 || *(volatile const int *)&c[kGlrFlags + fp];
+                if (ran && !*(volatile const int *)&c[kGlrFlags + f]) jobs[j].st.ctr[kGlrLevels] = level + 1;
+            }
+        }
+        if (!*(volatile int *)&any[f]) break;
+    }
+    if (level >= max_levels && blockIdx.x == 0)  // still growing at the cap: their last level is level - 1
+        for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+            const int *c = jobs[j].st.ctr;
+            if (*(volatile const int *)&c[kGlrFlags + (level + 2) % 3]) jobs[j].st.ctr[kGlrLevels] = level;
+        }
+}
+
+// per grid (one block each): clear its histogram, region activity and active count
+__global__ void glr_batch_reset_kernel(const GlrJob2 *__restrict__ jobs) {
+    const DevState &st = jobs[blockIdx.x].st;
+    const int nreg = jobs[blockIdx.x].g.nreg;
+    for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x) st.hist[b] = 0;
+    for (int r = threadIdx.x; r < nreg; r += blockDim.x) st.active[r] = 0;
+    if (threadIdx.x == 0) st.ctr[kActiveRegions] = 0;
+}
+
+// the finish of every grid: a block per (grid, chunk of 16384 vertices)
+constexpr int kFinishChunk = 16384;
+template <int CONN>
+__device__ __forceinline__ void glr2d_finish_chunk(const GlrJob2 &J, size_t v0, size_t v1, int *sh, int SB) {
+    const Geom &g = J.g;
+    const DevState &st = J.st;
+    const int last = st.ctr[kGlrLevels] - 1;
+    const u64 *S = (last % 2 == 1) ? J.A : J.B;
+    for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const int y = (int)(v / g.X), x = (int)(v % g.X);
+        int l = st.lab[v];
+        if (!((S[(size_t)y * J.W64 + (x >> 6)] >> (x & 63)) & 1ull)) {
+            l = g.dinf;
+            st.lab[v] = l;
+        }
+        if (l >= g.dinf) continue;
+        const int r = ((y >> g.sy) * g.RX) + (x >> g.sx);
+        if (st.exc[v] > 0) st.active[r] = 1;
+        const int lx = x & (g.tx - 1), ly = y & (g.ty - 1);
+        if (lx != 0 && lx != g.tx - 1 && ly != 0 && ly != g.ty - 1) continue;
+        bool inB = false;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d);
+            if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y) continue;
+            if (((wy >> g.sy) * g.RX + (wx >> g.sx)) != r) inB = true;
+        }
+        if (!inB) continue;
+        if (l < SB) atomicAdd(&sh[l], 1);
+        else atomicAdd(&st.hist[l < kHistBins ? l : kHistBins], 1);
+    }
+}
+
+__global__ void glr2d_batch_finish_kernel(const GlrJob2 *__restrict__ jobs, const int2 *__restrict__ chunks, int nchunks) {
+    constexpr int SB = 2048;
+    __shared__ int sh[SB];
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int2 w = chunks[c];
+        const GlrJob2 &J = jobs[w.x];
+        for (int b = threadIdx.x; b < SB; b += blockDim.x) sh[b] = 0;
+        __syncthreads();
+        const size_t v0 = (size_t)w.y * kFinishChunk, v1 = min((size_t)J.g.n, v0 + kFinishChunk);
+        if (J.conn == 4) glr2d_finish_chunk<4>(J, v0, v1, sh, SB);
+        else glr2d_finish_chunk<8>(J, v0, v1, sh, SB);
+        __syncthreads();
+        for (int b = threadIdx.x; b < SB; b += blockDim.x)
+            if (sh[b]) atomicAdd(&J.st.hist[b], sh[b]);
+        __syncthreads();
+    }
+}
+
+// per grid (one block each): count its active regions
+__global__ void glr_batch_count_kernel(const GlrJob2 *__restrict__ jobs) {
+    const DevState &st = jobs[blockIdx.x].st;
+    const int nreg = jobs[blockIdx.x].g.nreg;
+    int c = 0;
+    for (int r = threadIdx.x; r < nreg; r += blockDim.x) c += st.active[r] != 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
+}
+
+cudaError_t glr2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, cudaStream_t s) {
+    const int njobs = (int)jobs_in.size();
+    if (njobs == 0) return cudaSuccess;
+    std::vector<GlrJob2> jobs(jobs_in);
+    std::vector<int> unit_job;
+    std::vector<int2> chunks;
+    for (int j = 0; j < njobs; ++j) {
+        GlrJob2 &J = jobs[j];
+        J.W64 = (J.g.X + 63) / 64;
+        J.BY = (J.g.Y + 63) / 64;
+        const size_t plane = (size_t)J.g.Y * J.W64;
+        J.M = (u64 *)J.scratch;
+        J.A = J.M + J.conn * plane;
+        J.B = J.A + plane;
+        J.unit0 = (int)unit_job.size();
+        for (int b = 0; b < J.W64 * J.BY; ++b) unit_job.push_back(j);
+        const int nc = (int)((J.g.n + kFinishChunk - 1) / kFinishChunk);
+        for (int c = 0; c < nc; ++c) chunks.push_back(make_int2(j, c));
+    }
+    cudaError_t e = bb.reserve(njobs * sizeof(GlrJob2), unit_job.size() * sizeof(int), chunks.size() * sizeof(int2));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(bb.jobs, jobs.data(), njobs * sizeof(GlrJob2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bb.units, unit_job.data(), unit_job.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bb.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    for (const GlrJob2 &J : jobs) {  // residual masks and the level-0 seeds of every grid
+        const size_t total = (size_t)J.W64 * 64 * J.g.Y;
+        const int mb = (int)std::min<size_t>((total + 255) / 256, (size_t)device_sms() * 32);
+        if (J.conn == 4) cut_masks_kernel<4><<<mb, 256, 0, s>>>(J.g, J.st, J.W64, 1, (unsigned *)J.M, (unsigned *)J.A);
+        else cut_masks_kernel<8><<<mb, 256, 0, s>>>(J.g, J.st, J.W64, 1, (unsigned *)J.M, (unsigned *)J.A);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int max_blocks = 0;
+    e = coop_max_blocks((const void *)glr2d_batch_levels_kernel, 256, 0, &max_blocks);
+    if (e != cudaSuccess) return e;
+    const int nunits = (int)unit_job.size();
+    const int nblocks = std::max(1, std::min((nunits + 7) / 8, max_blocks));
+    const GlrJob2 *pj = (const GlrJob2 *)bb.jobs;
+    const int *pu = (const int *)bb.units;
+    int *pany = bb.any;
+    int nj = njobs, nu = nunits, ml = 1 << 20;
+    void *args[] = {(void *)&pj, &nj, (void *)&pu, &nu, &pany, &ml};
+    e = cudaLaunchCooperativeKernel((const void *)glr2d_batch_levels_kernel, dim3(nblocks), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    glr_batch_reset_kernel<<<njobs, 256, 0, s>>>(pj);
+    const int nch = (int)chunks.size();
+    glr2d_batch_finish_kernel<<<std::min(nch, device_sms() * 8), 256, 0, s>>>(pj, (const int2 *)bb.chunks, nch);
+    glr_batch_count_kernel<<<njobs, 256, 0, s>>>(pj);
+    return cudaGetLastError();
+}
+
+cudaError_t GlrBatchBufs::reserve(size_t jobs_bytes, size_t units_bytes, size_t chunks_bytes) {
+    auto grow = [](void **p, size_t &cap, size_t want) -> cudaError_t {
+        if (want <= cap) return cudaSuccess;
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    };
+    cudaError_t e = grow(&jobs, jobs_cap, jobs_bytes);
+    if (e == cudaSuccess) e = grow(&units, units_cap, units_bytes);
+    if (e == cudaSuccess) e = grow(&chunks, chunks_cap, chunks_bytes);
+    if (e == cudaSuccess && !any) e = cudaMalloc(&any, 4 * sizeof(int));
+    return e;
+}
+
+GlrBatchBufs::~GlrBatchBufs() {
+    for (void *p : {jobs, units, chunks, (void *)any})
+        if (p) cudaFree(p);
 }
 
 bool glr2d_supported(const Geom &g) { return g.tz == 1 && g.Z == 1 && (g.tx == 64 || g.tx == 32); }

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <vector>
 
 #include <cooperative_groups.h>
 
@@ -345,6 +346,192 @@ cudaError_t cut3d(const Geom &g, const DevState &st, void *scratch, unsigned cha
     if (g.ty == 8 && g.tz == 8) return cut3d_impl<8, 8>(g, st, scratch, smin, smax, h_passes, s);
     if (g.ty == 8 && g.tz == 4) return cut3d_impl<8, 4>(g, st, scratch, smin, smax, h_passes, s);
     return cudaErrorInvalidValue;
+}
+
+// ---- the same relabel for many 3D grids at once (batched solves) -------------
+// As glr2d_batch: one cooperative launch runs the levels of every due grid, a
+// work unit is (grid, region), a warp per unit; then one finish launch over
+// (grid, chunk) units and one count.  The masks keep the layout above; the
+// job's A/B fields hold the grid's level sets (u32 words here).
+template <int TY, int TZ>
+__device__ __forceinline__ bool glr3d_unit(const GlrJob2 &J, int r, const u32 *in, u32 *out, int level) {
+    const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
+    const u32 *M = (const u32 *)J.M;
+    const u32 *T = M + 6 * words;
+    return glr3d_region<TY, TZ>(J.g, J.W64, r, M, T, in, out, level, J.st.lab);
+}
+
+__device__ __forceinline__ bool glr3d_unit_any(const GlrJob2 &J, int r, const u32 *in, u32 *out, int level) {
+    if (J.g.ty == 16) return glr3d_unit<16, 8>(J, r, in, out, level);
+    if (J.g.tz == 8) return glr3d_unit<8, 8>(J, r, in, out, level);
+    return glr3d_unit<8, 4>(J, r, in, out, level);
+}
+
+__global__ void glr3d_batch_levels_kernel(const GlrJob2 *__restrict__ jobs, int njobs, const int *__restrict__ unit_job,
+                                          int nunits, int *any, int max_levels) {
+    cg::grid_group grid = cg::this_grid();
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (int u = wid; u < nunits; u += nwarps) {
+        const GlrJob2 &J = jobs[unit_job[u]];
+        glr3d_unit_any(J, u - J.unit0, nullptr, (u32 *)J.B, 0);
+    }
+    if (blockIdx.x == 0) {
+        for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+            jobs[j].st.ctr[kGlrFlags + 1] = 0;
+            jobs[j].st.ctr[kGlrFlags + 2] = 0;
+        }
+        if (threadIdx.x == 0) any[1] = any[2] = 0;
+    }
+    grid.sync();
+    int level = 1;
+    for (; level < max_levels; ++level) {
+        const int f = level % 3, fp = (level + 2) % 3;
+        bool grew_any = false;
+        for (int u = wid; u < nunits; u += nwarps) {
+            const GlrJob2 &J = jobs[unit_job[u]];
+            if (level > 1 && !*(volatile int *)&J.st.ctr[kGlrFlags + fp]) continue;  // stopped growing
+            const u32 *in = (const u32 *)((level & 1) ? J.B : J.A);
+            u32 *out = (u32 *)((level & 1) ? J.A : J.B);
+            const bool grew = glr3d_unit_any(J, u - J.unit0, in, out, level);
+            if (grew && lane == 0) atomicOr(&J.st.ctr[kGlrFlags + f], 1);
+            grew_any |= grew;
+        }
+        if (grew_any && lane == 0) atomicOr(&any[f], 1);
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < njobs; j += blockDim.x) jobs[j].st.ctr[kGlrFlags + (level + 1) % 3] = 0;
+            if (threadIdx.x == 0) any[(level + 1) % 3] = 0;
+        }
+        grid.sync();
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+                const int *c = jobs[j].st.ctr;
+                const bool ran = level == 1 || *(volatile const int *)&c[kGlrFlags + fp];
+                if (ran && !*(volatile const int *)&c[kGlrFlags + f]) jobs[j].st.ctr[kGlrLevels] = level + 1;
+            }
+        }
+        if (!*(volatile int *)&any[f]) break;
+    }
+    if (level >= max_levels && blockIdx.x == 0)
+        for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+            const int *c = jobs[j].st.ctr;
+            if (*(volatile const int *)&c[kGlrFlags + (level + 2) % 3]) jobs[j].st.ctr[kGlrLevels] = level;
+        }
+}
+
+__global__ void glr3d_batch_reset_kernel(const GlrJob2 *__restrict__ jobs) {
+    const DevState &st = jobs[blockIdx.x].st;
+    const int nreg = jobs[blockIdx.x].g.nreg;
+    for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x) st.hist[b] = 0;
+    for (int r = threadIdx.x; r < nreg; r += blockDim.x) st.active[r] = 0;
+    if (threadIdx.x == 0) st.ctr[kActiveRegions] = 0;
+}
+
+constexpr int kFinishChunk3 = 16384;
+__global__ void glr3d_batch_finish_kernel(const GlrJob2 *__restrict__ jobs, const int2 *__restrict__ chunks, int nchunks) {
+    constexpr int SB = 2048;
+    __shared__ int sh[SB];
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int2 w = chunks[c];
+        const GlrJob2 &J = jobs[w.x];
+        const Geom &g = J.g;
+        const DevState &st = J.st;
+        for (int b = threadIdx.x; b < SB; b += blockDim.x) sh[b] = 0;
+        __syncthreads();
+        const int last = st.ctr[kGlrLevels] - 1;
+        const u32 *S = (const u32 *)((last % 2 == 1) ? J.A : J.B);
+        const size_t v0 = (size_t)w.y * kFinishChunk3, v1 = min((size_t)g.n, v0 + kFinishChunk3);
+        for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
+            int l = st.lab[v];
+            if (!((S[((size_t)z * g.Y + y) * J.W64 + (x >> 5)] >> (x & 31)) & 1u)) {
+                l = g.dinf;
+                st.lab[v] = l;
+            }
+            if (l >= g.dinf) continue;
+            const int r = ((z >> g.sz) * g.RY + (y >> g.sy)) * g.RX + (x >> g.sx);
+            if (st.exc[v] > 0) st.active[r] = 1;
+            bool inB = false;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                const int wx = x + arc_dx(6, d), wy = y + arc_dy(6, d), wz = z + arc_dz(6, d);
+                if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y || wz < 0 || wz >= g.Z) continue;
+                if (((wz >> g.sz) * g.RY + (wy >> g.sy)) * g.RX + (wx >> g.sx) != r) inB = true;
+            }
+            if (!inB) continue;
+            if (l < SB) atomicAdd(&sh[l], 1);
+            else atomicAdd(&st.hist[l < kHistBins ? l : kHistBins], 1);
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < SB; b += blockDim.x)
+            if (sh[b]) atomicAdd(&st.hist[b], sh[b]);
+        __syncthreads();
+    }
+}
+
+__global__ void glr3d_batch_count_kernel(const GlrJob2 *__restrict__ jobs) {
+    const DevState &st = jobs[blockIdx.x].st;
+    const int nreg = jobs[blockIdx.x].g.nreg;
+    int c = 0;
+    for (int r = threadIdx.x; r < nreg; r += blockDim.x) c += st.active[r] != 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
+}
+
+cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, cudaStream_t s) {
+    const int njobs = (int)jobs_in.size();
+    if (njobs == 0) return cudaSuccess;
+    std::vector<GlrJob2> jobs(jobs_in);
+    std::vector<int> unit_job;
+    std::vector<int2> chunks;
+    for (int j = 0; j < njobs; ++j) {
+        GlrJob2 &J = jobs[j];
+        J.W64 = (J.g.X + 31) / 32;  // here: 32-voxel words per row
+        J.BY = 0;
+        const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
+        u32 *M = (u32 *)J.scratch;
+        J.M = (unsigned long long *)M;
+        J.A = (unsigned long long *)(M + 7 * words);
+        J.B = (unsigned long long *)(M + 8 * words);
+        J.unit0 = (int)unit_job.size();
+        for (int r = 0; r < J.g.nreg; ++r) unit_job.push_back(j);
+        const int nc = (int)((J.g.n + kFinishChunk3 - 1) / kFinishChunk3);
+        for (int c = 0; c < nc; ++c) chunks.push_back(make_int2(j, c));
+    }
+    cudaError_t e = bb.reserve(njobs * sizeof(GlrJob2), unit_job.size() * sizeof(int), chunks.size() * sizeof(int2));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(bb.jobs, jobs.data(), njobs * sizeof(GlrJob2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bb.units, unit_job.data(), unit_job.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bb.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    for (const GlrJob2 &J : jobs) {
+        const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
+        const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, (size_t)device_sms() * 32);
+        u32 *M = (u32 *)J.M;
+        glr3d_masks_kernel<<<mb, 256, 0, s>>>(J.g, J.st, J.W64, M, M + 6 * words);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int max_blocks = 0;
+    e = coop_max_blocks((const void *)glr3d_batch_levels_kernel, 256, 0, &max_blocks);
+    if (e != cudaSuccess) return e;
+    const int nunits = (int)unit_job.size();
+    const int nblocks = std::max(1, std::min((nunits + 7) / 8, max_blocks));
+    const GlrJob2 *pj = (const GlrJob2 *)bb.jobs;
+    const int *pu = (const int *)bb.units;
+    int *pany = bb.any;
+    int nj = njobs, nu = nunits, ml = 1 << 20;
+    void *args[] = {(void *)&pj, &nj, (void *)&pu, &nu, &pany, &ml};
+    e = cudaLaunchCooperativeKernel((const void *)glr3d_batch_levels_kernel, dim3(nblocks), dim3(256), args, 0, s);
+    if (e != cudaSuccess) return e;
+    glr3d_batch_reset_kernel<<<njobs, 256, 0, s>>>(pj);
+    const int nch = (int)chunks.size();
+    glr3d_batch_finish_kernel<<<std::min(nch, device_sms() * 8), 256, 0, s>>>(pj, (const int2 *)bb.chunks, nch);
+    glr3d_batch_count_kernel<<<njobs, 256, 0, s>>>(pj);
+    return cudaGetLastError();
 }
 
 bool glr3d_supported(const Geom &g) {

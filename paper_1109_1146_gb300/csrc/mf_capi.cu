@@ -1476,6 +1476,7 @@ struct BatchBufs {
     int *type_of = nullptr, *cnt = nullptr, *head = nullptr, *sweeps = nullptr, *any = nullptr;
     unsigned char *done = nullptr;
     std::vector<cudaEvent_t> tev;          // host loop: a start / end event per kernel type
+    GlrBatchBufs glr2, glr3;               // tables of the batched global relabels
     ~BatchBufs() {
         for (cudaEvent_t e : tev)
             if (e) cudaEventDestroy(e);
@@ -1494,13 +1495,15 @@ struct BatchBufs {
 // first; one wait then reads every relabelled instance's level count.
 // Returns in *any_left the number of instances still active afterwards.
 static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *insts, unsigned char *done_dev,
-                               int *any_dev, int *any_left, int sweep, cudaStream_t s, double *ms_total) {
+                               int *any_dev, int *any_left, int sweep, cudaStream_t s, double *ms_total,
+                               GlrBatchBufs &glr2, GlrBatchBufs &glr3) {
     mf_grid *g = grids[0];
     std::vector<unsigned char> done(count);
     CK(cudaMemcpyAsync(done.data(), done_dev, count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaEventRecord(g->ev[7], s));
     std::vector<int> glr;
+    std::vector<GlrJob2> jobs2, jobs3;  // the global relabels of all due grids: one batched launch per dimension
     for (int i = 0; i < count; ++i) {
         mf_grid *h = grids[i];
         if (done[i]) continue;
@@ -1510,11 +1513,19 @@ static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *ins
             continue;
         }
         if (!glr_due(h, sweep)) continue;
-        const cudaError_t e = glr_run(h, s);
-        if (e != cudaSuccess) return fail(g, MF_ECUDA, std::string("batched global relabel: ") + cudaGetErrorString(e));
-        CK(cudaMemcpyAsync(&h->h_ctr[kGlrLevels], &h->st.ctr[kGlrLevels], 4, cudaMemcpyDeviceToHost, s));
+        GlrJob2 J{};
+        J.g = h->g;
+        J.st = h->st;
+        J.conn = h->conn;
+        J.scratch = h->cut_scratch;
+        (h->ndim == 2 ? jobs2 : jobs3).push_back(J);
         glr.push_back(i);
     }
+    cudaError_t eg = glr2d_batch(jobs2, glr2, s);
+    if (eg == cudaSuccess) eg = glr3d_batch(jobs3, glr3, s);
+    if (eg != cudaSuccess) return fail(g, MF_ECUDA, std::string("batched global relabel: ") + cudaGetErrorString(eg));
+    for (int i : glr)
+        CK(cudaMemcpyAsync(&grids[i]->h_ctr[kGlrLevels], &grids[i]->st.ctr[kGlrLevels], 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemsetAsync(any_dev, 0, sizeof(int), s));
     batch_relabel_end_kernel<<<(count + 255) / 256, 256, 0, s>>>(insts, done_dev, any_dev, count);
     CK(cudaGetLastError());
@@ -1529,8 +1540,10 @@ static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *ins
         const int levels = h->h_ctr[kGlrLevels];
         h->stats.global_relabels++;
         h->stats.relabel_levels += levels;
-        h->launches += 4;  // masks, the cooperative levels launch, finish, count
+        h->launches += 1;  // its masks; the batched levels, reset, finish and count launches are counted once below
     }
+    if (!jobs2.empty()) g->launches += 4;
+    if (!jobs3.empty()) g->launches += 4;
     return MF_OK;
 }
 
@@ -1729,7 +1742,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
             }
             // stopped at a multiple of the relabel period
             mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], loopst[kLoopSweep], s,
-                                         &relabel_ms);
+                                         &relabel_ms, B.glr2, B.glr3);
             if (st != MF_OK) return st;
             if (!g->h_ctr[0]) break;
         }
@@ -1754,7 +1767,8 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
                 break;
             }
             if ((P > 0 && (sweep + 1) % P == 0) || (o.global_relabel_first > 0 && sweep + 1 == o.global_relabel_first)) {
-                mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], sweep + 1, s, &relabel_ms);
+                mf_status st = batch_relabel(grids, count, B.insts, B.done, B.any, &g->h_ctr[0], sweep + 1, s, &relabel_ms,
+                                             B.glr2, B.glr3);
                 if (st != MF_OK) return st;
                 if (!g->h_ctr[0]) break;
             }

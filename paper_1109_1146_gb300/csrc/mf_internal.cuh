@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 namespace mf {
 
@@ -173,6 +174,29 @@ cudaError_t launch_reduction_apply(int conn, const Geom &g, const unsigned char 
                                    unsigned long long *konst2, cudaStream_t s);
 cudaError_t launch_reduction_cut(size_t n, const unsigned char *codes, unsigned char *smin, unsigned char *smax,
                                  cudaStream_t s);
+
+// batched global relabel (cut2d.cu for 2D grids, glr3d.cu for 3D grids with
+// 32-wide tiles): one grid of a batch; the launcher fills the derived fields
+struct GlrJob2 {
+    Geom g;
+    DevState st;
+    int conn;                        // 4 or 8 (2D); 6 with ty/tz variants (3D)
+    void *scratch;                   // the grid's cut scratch (masks and two level sets)
+    int W64, BY, unit0;              // derived: row words, 64-row blocks, first work unit
+    unsigned long long *M, *A, *B;   // derived: masks, level sets (2D)
+};
+// device tables of a batched relabel, grown as needed and reused
+struct GlrBatchBufs {
+    void *jobs = nullptr, *units = nullptr, *chunks = nullptr;
+    size_t jobs_cap = 0, units_cap = 0, chunks_cap = 0;
+    int *any = nullptr;
+    cudaError_t reserve(size_t jobs_bytes, size_t units_bytes, size_t chunks_bytes);
+    ~GlrBatchBufs();
+};
+// the relabel of every listed 2D grid (tiles 32 or 64 wide), enqueued without
+// waiting; each grid's levels land in its st.ctr[kGlrLevels]
+cudaError_t glr2d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, cudaStream_t s);
+cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, cudaStream_t s);
 
 // devinfo.cu: per-device launch facts, cached per (kernel, device)
 int device_sms();  // SMs of the current device (1 if it cannot be queried)
