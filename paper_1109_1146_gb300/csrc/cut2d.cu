@@ -658,6 +658,131 @@ cudaError_t glr2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
     return cudaGetLastError();
 }
 
+// ---- both cut closures of many 2D grids at once (batched solves) --------------
+// Per closure: the masks of every grid (one launch each), then one cooperative
+// launch of block passes over the units (grid, 64x64 block) of all grids, a
+// grid leaving the passes once a pass adds nothing to its set; then the bytes
+// of S_min and S_max of every grid in one launch.  The pass count of each
+// closure lands in the grid's st.ctr[kGlrLevels].
+__global__ void cut2d_batch_closure_kernel(const GlrJob2 *__restrict__ jobs, int njobs, const int *__restrict__ unit_job,
+                                           int nunits, int *any, int max_passes, int which) {
+    cg::grid_group grid = cg::this_grid();
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0) {
+        for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+            jobs[j].st.ctr[kGlrFlags + 1] = 0;
+            jobs[j].st.ctr[kGlrFlags + 2] = 0;
+        }
+        if (threadIdx.x == 0) any[1] = any[2] = 0;
+    }
+    grid.sync();
+    int pass = 1;
+    for (; pass <= max_passes; ++pass) {
+        const int f = pass % 3, fp = (pass + 2) % 3;
+        bool grew_any = false;
+        for (int u = wid; u < nunits; u += nwarps) {
+            const GlrJob2 &J = jobs[unit_job[u]];
+            if (pass > 1 && !*(volatile int *)&J.st.ctr[kGlrFlags + fp]) continue;  // closed
+            u64 *S = which == 0 ? J.A : J.B;
+            const bool grew = J.conn == 4 ? cut_block2d<4>(J.g, J.W64, u - J.unit0, J.M, S)
+                                          : cut_block2d<8>(J.g, J.W64, u - J.unit0, J.M, S);
+            if (grew && lane == 0) atomicOr(&J.st.ctr[kGlrFlags + f], 1);
+            grew_any |= grew;
+        }
+        if (grew_any && lane == 0) atomicOr(&any[f], 1);
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < njobs; j += blockDim.x) jobs[j].st.ctr[kGlrFlags + (pass + 1) % 3] = 0;
+            if (threadIdx.x == 0) any[(pass + 1) % 3] = 0;
+        }
+        grid.sync();
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+                const int *c = jobs[j].st.ctr;
+                const bool ran = pass == 1 || *(volatile const int *)&c[kGlrFlags + fp];
+                if (ran && !*(volatile const int *)&c[kGlrFlags + f]) jobs[j].st.ctr[kGlrLevels] = pass;
+            }
+        }
+        if (!*(volatile int *)&any[f]) break;
+    }
+}
+
+__global__ void cut2d_batch_bytes_kernel(const GlrJob2 *__restrict__ jobs, const int2 *__restrict__ chunks, int nchunks) {
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int2 w = chunks[c];
+        const GlrJob2 &J = jobs[w.x];
+        const size_t v0 = (size_t)w.y * kFinishChunk, v1 = min((size_t)J.g.n, v0 + kFinishChunk);
+        for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            const int y = (int)(v / J.g.X), x = (int)(v % J.g.X);
+            const size_t wd = (size_t)y * J.W64 + (x >> 6);
+            J.smin[v] = (J.A[wd] >> (x & 63)) & 1ull;
+            J.smax[v] = !((J.B[wd] >> (x & 63)) & 1ull);
+        }
+    }
+}
+
+cudaError_t cut2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, int *const *h_passes, cudaStream_t s) {
+    const int njobs = (int)jobs_in.size();
+    if (njobs == 0) return cudaSuccess;
+    std::vector<GlrJob2> jobs(jobs_in);
+    std::vector<int> unit_job;
+    std::vector<int2> chunks;
+    for (int j = 0; j < njobs; ++j) {
+        GlrJob2 &J = jobs[j];
+        J.W64 = (J.g.X + 63) / 64;
+        J.BY = (J.g.Y + 63) / 64;
+        const size_t plane = (size_t)J.g.Y * J.W64;
+        J.M = (u64 *)J.scratch;
+        J.A = J.M + J.conn * plane;  // S_min
+        J.B = J.A + plane;           // the set {v -> t}
+        J.unit0 = (int)unit_job.size();
+        for (int b = 0; b < J.W64 * J.BY; ++b) unit_job.push_back(j);
+        const int nc = (int)((J.g.n + kFinishChunk - 1) / kFinishChunk);
+        for (int c = 0; c < nc; ++c) chunks.push_back(make_int2(j, c));
+    }
+    cudaError_t e = bb.reserve(njobs * sizeof(GlrJob2), unit_job.size() * sizeof(int), chunks.size() * sizeof(int2));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(bb.jobs, jobs.data(), njobs * sizeof(GlrJob2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bb.units, unit_job.data(), unit_job.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bb.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    int max_blocks = 0;
+    e = coop_max_blocks((const void *)cut2d_batch_closure_kernel, 256, 0, &max_blocks);
+    if (e != cudaSuccess) return e;
+    const int nunits = (int)unit_job.size();
+    const int nblocks = std::max(1, std::min((nunits + 7) / 8, max_blocks));
+    for (int which = 0; which < 2; ++which) {
+        for (const GlrJob2 &J : jobs) {
+            const size_t total = (size_t)J.W64 * 64 * J.g.Y;
+            const int mb = (int)std::min<size_t>((total + 255) / 256, (size_t)device_sms() * 32);
+            unsigned *S = (unsigned *)(which == 0 ? J.A : J.B);
+            if (J.conn == 4) cut_masks_kernel<4><<<mb, 256, 0, s>>>(J.g, J.st, J.W64, which, (unsigned *)J.M, S);
+            else cut_masks_kernel<8><<<mb, 256, 0, s>>>(J.g, J.st, J.W64, which, (unsigned *)J.M, S);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const GlrJob2 *pj = (const GlrJob2 *)bb.jobs;
+        const int *pu = (const int *)bb.units;
+        int *pany = bb.any;
+        int nj = njobs, nu = nunits, mp = 1 << 20, wh = which;
+        void *args[] = {(void *)&pj, &nj, (void *)&pu, &nu, &pany, &mp, &wh};
+        e = cudaLaunchCooperativeKernel((const void *)cut2d_batch_closure_kernel, dim3(nblocks), dim3(256), args, 0, s);
+        if (e != cudaSuccess) return e;
+        if (h_passes)
+            for (int j = 0; j < njobs; ++j) {
+                e = cudaMemcpyAsync(h_passes[j] + which, &jobs[j].st.ctr[kGlrLevels], 4, cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess) return e;
+            }
+    }
+    const int nch = (int)chunks.size();
+    cut2d_batch_bytes_kernel<<<std::min(nch, device_sms() * 8), 256, 0, s>>>((const GlrJob2 *)bb.jobs,
+                                                                            (const int2 *)bb.chunks, nch);
+    return cudaGetLastError();
+}
+
 cudaError_t GlrBatchBufs::reserve(size_t jobs_bytes, size_t units_bytes, size_t chunks_bytes) {
     auto grow = [](void **p, size_t &cap, size_t want) -> cudaError_t {
         if (want <= cap) return cudaSuccess;

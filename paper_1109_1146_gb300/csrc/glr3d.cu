@@ -534,6 +534,132 @@ cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
     return cudaGetLastError();
 }
 
+// ---- both cut closures of many 3D grids at once (batched solves) --------------
+__global__ void cut3d_batch_closure_kernel(const GlrJob2 *__restrict__ jobs, int njobs, const int *__restrict__ unit_job,
+                                           int nunits, int *any, int max_passes, int which) {
+    cg::grid_group grid = cg::this_grid();
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0) {
+        for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+            jobs[j].st.ctr[kGlrFlags + 1] = 0;
+            jobs[j].st.ctr[kGlrFlags + 2] = 0;
+        }
+        if (threadIdx.x == 0) any[1] = any[2] = 0;
+    }
+    grid.sync();
+    int pass = 1;
+    for (; pass <= max_passes; ++pass) {
+        const int f = pass % 3, fp = (pass + 2) % 3;
+        bool grew_any = false;
+        for (int u = wid; u < nunits; u += nwarps) {
+            const GlrJob2 &J = jobs[unit_job[u]];
+            if (pass > 1 && !*(volatile int *)&J.st.ctr[kGlrFlags + fp]) continue;  // closed
+            u32 *S = (u32 *)(which == 0 ? J.A : J.B);
+            const u32 *M = (const u32 *)J.M;
+            const int r = u - J.unit0;
+            bool grew;
+            if (J.g.ty == 16) grew = glr3d_region<16, 8>(J.g, J.W64, r, M, nullptr, S, S, 1, nullptr);
+            else if (J.g.tz == 8) grew = glr3d_region<8, 8>(J.g, J.W64, r, M, nullptr, S, S, 1, nullptr);
+            else grew = glr3d_region<8, 4>(J.g, J.W64, r, M, nullptr, S, S, 1, nullptr);
+            if (grew && lane == 0) atomicOr(&J.st.ctr[kGlrFlags + f], 1);
+            grew_any |= grew;
+        }
+        if (grew_any && lane == 0) atomicOr(&any[f], 1);
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < njobs; j += blockDim.x) jobs[j].st.ctr[kGlrFlags + (pass + 1) % 3] = 0;
+            if (threadIdx.x == 0) any[(pass + 1) % 3] = 0;
+        }
+        grid.sync();
+        if (blockIdx.x == 0) {
+            for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+                const int *c = jobs[j].st.ctr;
+                const bool ran = pass == 1 || *(volatile const int *)&c[kGlrFlags + fp];
+                if (ran && !*(volatile const int *)&c[kGlrFlags + f]) jobs[j].st.ctr[kGlrLevels] = pass;
+            }
+        }
+        if (!*(volatile int *)&any[f]) break;
+    }
+}
+
+__global__ void cut3d_batch_bytes_kernel(const GlrJob2 *__restrict__ jobs, const int2 *__restrict__ chunks, int nchunks) {
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int2 w = chunks[c];
+        const GlrJob2 &J = jobs[w.x];
+        const Geom &g = J.g;
+        const u32 *Smin = (const u32 *)J.A, *Tset = (const u32 *)J.B;
+        const size_t v0 = (size_t)w.y * kFinishChunk3, v1 = min((size_t)g.n, v0 + kFinishChunk3);
+        for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
+            const size_t wd = ((size_t)z * g.Y + y) * J.W64 + (x >> 5);
+            J.smin[v] = (Smin[wd] >> (x & 31)) & 1u;
+            J.smax[v] = !((Tset[wd] >> (x & 31)) & 1u);
+        }
+    }
+}
+
+cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, int *const *h_passes, cudaStream_t s) {
+    const int njobs = (int)jobs_in.size();
+    if (njobs == 0) return cudaSuccess;
+    std::vector<GlrJob2> jobs(jobs_in);
+    std::vector<int> unit_job;
+    std::vector<int2> chunks;
+    for (int j = 0; j < njobs; ++j) {
+        GlrJob2 &J = jobs[j];
+        J.W64 = (J.g.X + 31) / 32;
+        J.BY = 0;
+        const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
+        u32 *M = (u32 *)J.scratch;
+        J.M = (unsigned long long *)M;
+        J.A = (unsigned long long *)(M + 6 * words);  // S_min (the layout of cut3d)
+        J.B = (unsigned long long *)(M + 7 * words);  // the set {v -> t}
+        J.unit0 = (int)unit_job.size();
+        for (int r = 0; r < J.g.nreg; ++r) unit_job.push_back(j);
+        const int nc = (int)((J.g.n + kFinishChunk3 - 1) / kFinishChunk3);
+        for (int c = 0; c < nc; ++c) chunks.push_back(make_int2(j, c));
+    }
+    cudaError_t e = bb.reserve(njobs * sizeof(GlrJob2), unit_job.size() * sizeof(int), chunks.size() * sizeof(int2));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(bb.jobs, jobs.data(), njobs * sizeof(GlrJob2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bb.units, unit_job.data(), unit_job.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bb.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    int max_blocks = 0;
+    e = coop_max_blocks((const void *)cut3d_batch_closure_kernel, 256, 0, &max_blocks);
+    if (e != cudaSuccess) return e;
+    const int nunits = (int)unit_job.size();
+    const int nblocks = std::max(1, std::min((nunits + 7) / 8, max_blocks));
+    for (int which = 0; which < 2; ++which) {
+        for (const GlrJob2 &J : jobs) {
+            const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
+            const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, (size_t)device_sms() * 32);
+            cut3d_masks_kernel<<<mb, 256, 0, s>>>(J.g, J.st, J.W64, which, (u32 *)J.M,
+                                                  (u32 *)(which == 0 ? J.A : J.B));
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const GlrJob2 *pj = (const GlrJob2 *)bb.jobs;
+        const int *pu = (const int *)bb.units;
+        int *pany = bb.any;
+        int nj = njobs, nu = nunits, mp = 1 << 20, wh = which;
+        void *args[] = {(void *)&pj, &nj, (void *)&pu, &nu, &pany, &mp, &wh};
+        e = cudaLaunchCooperativeKernel((const void *)cut3d_batch_closure_kernel, dim3(nblocks), dim3(256), args, 0, s);
+        if (e != cudaSuccess) return e;
+        if (h_passes)
+            for (int j = 0; j < njobs; ++j) {
+                e = cudaMemcpyAsync(h_passes[j] + which, &jobs[j].st.ctr[kGlrLevels], 4, cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess) return e;
+            }
+    }
+    const int nch = (int)chunks.size();
+    cut3d_batch_bytes_kernel<<<std::min(nch, device_sms() * 8), 256, 0, s>>>((const GlrJob2 *)bb.jobs,
+                                                                            (const int2 *)bb.chunks, nch);
+    return cudaGetLastError();
+}
+
 bool glr3d_supported(const Geom &g) {
     return g.tx == 32 && g.tz > 1 && ((g.ty == 16 && g.tz == 8) || (g.ty == 8 && g.tz == 8) || (g.ty == 8 && g.tz == 4));
 }

@@ -1265,9 +1265,11 @@ mf_status mf_boundary_relabel(mf_grid *g, int32_t *info) {
 // enqueued on stream st without waiting (results land in g->h_fin); the
 // closures of 2D grids and of 3D grids with 32-wide tiles run on the device
 // to their fixed point, other 3D tiles loop on the host.
-static mf_status finish_enqueue(mf_grid *g, cudaStream_t st) {
-    g->h_fin->passes[0] = g->h_fin->passes[1] = 0;
-    if (g->ndim == 2) {
+static mf_status finish_enqueue(mf_grid *g, cudaStream_t st, bool cut_done = false) {
+    if (!cut_done) g->h_fin->passes[0] = g->h_fin->passes[1] = 0;
+    if (cut_done) {
+        // the cut closures ran batched with other grids
+    } else if (g->ndim == 2) {
         CK(cut2d(g->conn, g->g, g->st, g->cut_scratch, g->smin, g->tset, g->h_fin->passes, st));
         g->launches += 5;
     } else if (glr3d_supported(g->g)) {
@@ -1783,8 +1785,34 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     for (int i = 0; i < count; ++i)
         CK(cudaMemcpyAsync(grids[i]->h_ctr, grids[i]->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, s));
     if (rs == MF_OK) {
+        // the cut closures of all grids with bit-mask cuts in one cooperative
+        // launch per closure and dimension, then each grid's read-back
+        std::vector<GlrJob2> j2, j3;
+        std::vector<int *> p2, p3;
+        std::vector<char> batched(count, 0);
         for (int i = 0; i < count; ++i) {
-            mf_status st = finish_enqueue(grids[i], s);
+            mf_grid *h = grids[i];
+            if (h->ndim == 3 && !glr3d_supported(h->g)) continue;
+            GlrJob2 J{};
+            J.g = h->g;
+            J.st = h->st;
+            J.conn = h->conn;
+            J.scratch = h->cut_scratch;
+            J.smin = h->smin;
+            J.smax = h->tset;
+            h->h_fin->passes[0] = h->h_fin->passes[1] = 0;
+            (h->ndim == 2 ? j2 : j3).push_back(J);
+            (h->ndim == 2 ? p2 : p3).push_back(h->h_fin->passes);
+            h->launches += 2;  // its masks
+            batched[i] = 1;
+        }
+        cudaError_t ec = cut2d_batch(j2, B.glr2, p2.data(), s);
+        if (ec == cudaSuccess) ec = cut3d_batch(j3, B.glr3, p3.data(), s);
+        if (ec != cudaSuccess) return fail(g, MF_ECUDA, std::string("batched cut: ") + cudaGetErrorString(ec));
+        if (!j2.empty()) launches += 3;  // two closures and the bytes
+        if (!j3.empty()) launches += 3;
+        for (int i = 0; i < count; ++i) {
+            mf_status st = finish_enqueue(grids[i], s, batched[i] != 0);
             if (st != MF_OK) return fail(g, st, grids[i]->err);
         }
     }

@@ -183,7 +183,8 @@ struct GlrJob2 {
     int conn;                        // 4 or 8 (2D); 6 with ty/tz variants (3D)
     void *scratch;                   // the grid's cut scratch (masks and two level sets)
     int W64, BY, unit0;              // derived: row words, 64-row blocks, first work unit
-    unsigned long long *M, *A, *B;   // derived: masks, level sets (2D)
+    unsigned long long *M, *A, *B;   // derived: masks, level sets / closure sets
+    unsigned char *smin, *smax;      // batched cut: the byte outputs
 };
 // device tables of a batched relabel, grown as needed and reused
 struct GlrBatchBufs {
@@ -197,6 +198,11 @@ struct GlrBatchBufs {
 // waiting; each grid's levels land in its st.ctr[kGlrLevels]
 cudaError_t glr2d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, cudaStream_t s);
 cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, cudaStream_t s);
+// both cut closures of every listed grid (2D; 3D with 32-wide tiles) and the
+// S_min / S_max bytes; h_passes[j] (pinned int[2] or NULL) receives the
+// passes of each closure asynchronously
+cudaError_t cut2d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, int *const *h_passes, cudaStream_t s);
+cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, int *const *h_passes, cudaStream_t s);
 
 // devinfo.cu: per-device launch facts, cached per (kernel, device)
 int device_sms();  // SMs of the current device (1 if it cannot be queried)
