@@ -79,3 +79,21 @@ def test_committed_traffic_belongs_to_the_current_kernel_source():
         assert v is None  # a stale figure is never reported
     assert bench.committed_traffic(kname, (64, 64, 1)) is None  # measured for 32x32 tiles only
     assert bench.committed_traffic(bench.kernel_name(6, (32, 8, 4), batch=True), (32, 8, 4)) is None or recorded
+
+
+def test_batch_kinds_and_the_3d_traffic_figure():
+    # the batched line's sub-workloads keep only their members, in batch order
+    d3 = bench.batch_instances(0, count=2, kind="3d")
+    assert [x.conn for x in d3] == [6, 6] and all(x.dims[0] == x.dims[1] == x.dims[2] for x in d3)
+    d2 = bench.batch_instances(0, count=2, kind="2d")
+    assert [x.conn for x in d2] == [4, 4]
+    # the committed DRAM figure of the dominant kernel belongs to its source, or is not reported
+    p = os.path.join(ROOT, "profiles", "ard_discharge3d_batch_3d24.txt")
+    src = os.path.join(ROOT, "paper_1109_1146_gb300", "csrc", "ard_discharge3d.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    recorded = [ln.split("=", 1)[1].strip() for ln in open(p) if ln.startswith("bench: kernel_sha256_16=")]
+    v = bench.committed_traffic(bench.kernel_name(6, (32, 8, 4), batch=True), (32, 8, 4))
+    if recorded == [sha]:
+        assert v is not None and 72.0 <= v < 200.0
+    else:
+        assert v is None
