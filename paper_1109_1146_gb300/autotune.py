@@ -23,7 +23,7 @@ CANDIDATES = {
         ((32, 32, 1), {"partial_discharge": 1})],
     8: [((64, 64, 1), {}), ((32, 32, 1), {}), ((64, 32, 1), {}), ((64, 64, 1), {"partial_discharge": 1}),
         ((32, 32, 1), {"partial_discharge": 1})],
-    6: [((32, 8, 4), {}), ((32, 8, 8), {}), ((32, 16, 8), {}), ((32, 8, 4), {"partial_discharge": 1})],
+    6: [((32, 8, 4), {}), ((32, 4, 4), {}), ((32, 8, 8), {}), ((32, 16, 8), {}), ((32, 8, 4), {"partial_discharge": 1})],
 }
 
 

@@ -523,7 +523,9 @@ static cudaError_t launch_one(const Geom &g, const DevState &st, const SweepArgs
     X(6, 8, 8, 8, 256)              \
     X(6, 32, 16, 8, 1024)           \
     X(6, 32, 8, 8, 256)             \
-    X(6, 32, 8, 4, 256)
+    X(6, 32, 8, 4, 256)             \
+    X(6, 32, 4, 4, 128)             \
+    X(6, 32, 8, 2, 128)
 
 bool discharge_supported(int conn, int tx, int ty, int tz) {
 #define X(c, a, b, z, t) if (conn == c && tx == a && ty == b && tz == z) return true;

@@ -51,7 +51,8 @@ struct Cfg3D {
     static constexpr int NR = TY * TZ;            // rows of the tile
     static constexpr int V = TX * NR;             // voxels
     static constexpr int NW = NT / 32;            // warps
-    static constexpr int RPL = NR / 32;           // rows per lane of the graph warp
+    static constexpr bool PART = NR < 32;         // 16-row tiles: lanes 16..31 of the graph warp hold no row
+    static constexpr int RPL = PART ? 1 : NR / 32;  // rows per lane of the graph warp
     static constexpr int LZ = TY / RPL;           // lanes between rows rho and rho + TY
     // halo faces: -x, +x (one cell per row), -y, +y (TX per z), -z, +z (TX per y)
     static constexpr int B_MX = 0, B_PX = NR, B_MY = 2 * NR, B_PY = 2 * NR + TX * TZ;
@@ -59,13 +60,14 @@ struct Cfg3D {
     static constexpr int HL = B_PZ + TX * TY;     // halo cells = arcs leaving the tile
     static constexpr int LCAP = 32;               // BFS layers kept as masks
     // resident blocks per SM the registers must allow (shared memory allows
-    // four 32x8x4 tiles, two 32x8x8 tiles, one 32x16x8 tile)
-    static constexpr int MINB = NR == 32 ? 4 : NR == 64 ? 2 : 1;
+    // eight 16-row tiles at 128 threads, four 32x8x4 tiles, two 32x8x8 tiles,
+    // one 32x16x8 tile)
+    static constexpr int MINB = NR == 16 ? 8 : NR == 32 ? 4 : NR == 64 ? 2 : 1;
     static constexpr size_t smem = (size_t)(N + 3) * V * 4           // cap, tcap, exc, lab
                                    + (size_t)(N + 4) * NR * 4        // R[N], T, E, inc, vis
                                    + (size_t)(LCAP + 1) * NR * 4     // BFS layers 1..LCAP
                                    + (size_t)2 * HL * 4 + NR + 64;   // halo labels, hm, dirty rows
-    static_assert(NR % 32 == 0 && TY % RPL == 0 && V % NT == 0 && NT % 32 == 0, "tile/threads mismatch");
+    static_assert((NR % 32 == 0 || NR == 16) && TY % RPL == 0 && V % NT == 0 && NT % 32 == 0, "tile/threads mismatch");
 };
 
 // Kogge-Stone fill inside one 32-bit row: x joins if x+1 is in g and pl[x]
@@ -146,6 +148,8 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
     __shared__ unsigned long long s_flow;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // does this lane of the graph warp hold tile rows (all do unless the tile has 16 rows)
+    const bool lrow = !C::PART || lane < NR;
     DIAG_DECL
     const long long diag_t0 = clock64();
     (void)diag_t0;
@@ -264,9 +268,12 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
             const int rho = lane * RPL + j;
-            u32 s = s_T[rho];
-            if (s_hm[C::B_MX + rho] < k) s |= 1u;
-            if (s_hm[C::B_PX + rho] < k) s |= 1u << (TX - 1);
+            u32 s = 0u;
+            if (lrow) {
+                s = s_T[rho];
+                if (s_hm[C::B_MX + rho] < k) s |= 1u;
+                if (s_hm[C::B_PX + rho] < k) s |= 1u << (TX - 1);
+            }
             sd[j] = s;
         }
         for (int z = 0; z < TZ; ++z) {
@@ -294,7 +301,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
 #pragma unroll
         for (int j = 0; j < RPL; ++j)
 #pragma unroll
-            for (int d = 0; d < N; ++d) Rm[d][j] = s_R[d * NR + lane * RPL + j];
+            for (int d = 0; d < N; ++d) Rm[d][j] = lrow ? s_R[d * NR + lane * RPL + j] : 0u;
     };
     // one backward BFS step: vertices with a residual arc into f
     auto expand = [&](const u32 (&Rm)[N][RPL], const u32 (&f)[RPL], u32 (&out)[RPL]) {
@@ -343,13 +350,15 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                 any |= f != 0u;
             }
         }
+        if (lrow) {
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) s_inc[lane * RPL + j] = inc[j];
+            for (int j = 0; j < RPL; ++j) s_inc[lane * RPL + j] = inc[j];
+        }
     };
     auto closure_meets_excess = [&]() -> bool {
         bool m = false;
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) m |= (Cl[j] & s_E[lane * RPL + j]) != 0u;
+        for (int j = 0; j < RPL; ++j) m |= lrow && (Cl[j] & s_E[lane * RPL + j]) != 0u;
         return __any_sync(FULL, m);
     };
     auto write_labels = [&](int k) {
@@ -410,10 +419,12 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
 #pragma unroll
                     for (int j = 0; j < RPL; ++j) {
                         const int rho = lane * RPL + j;
-                        const u32 ex = s_E[rho] & Cl[j];  // excess that can reach T_k lies in the closure
+                        const u32 ex = lrow ? s_E[rho] & Cl[j] : 0u;  // excess that can reach T_k lies in the closure
                         vis[j] = fr[j];
-                        s_layer[1 * NR + rho] = fr[j];
-                        s_vis[rho] = 0u;  // vertices that receive excess in this round's push
+                        if (lrow) {
+                            s_layer[1 * NR + rho] = fr[j];
+                            s_vis[rho] = 0u;  // vertices that receive excess in this round's push
+                        }
                         if (fr[j] & ex) lmax = 1;
                         want[j] = ex & ~vis[j];
                         pending |= want[j] != 0u;
@@ -437,7 +448,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                             vis[j] |= nf[j];
                             fr[j] = nf[j];
                             if (L <= LCAP) {
-                                s_layer[L * NR + rho] = nf[j];
+                                if (lrow) s_layer[L * NR + rho] = nf[j];
                             } else {
                                 const int tg = deep_tag3(epoch, L);
                                 for (u32 m = nf[j]; m; m &= m - 1) s_lab[rho * TX + __ffs((int)m) - 1] = tg;
@@ -584,7 +595,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
         }
         DIAG_LAP(9);
     }
-    if (warp == 0) {
+    if (warp == 0 && lrow) {
 #pragma unroll
         for (int j = 0; j < RPL; ++j) s_vis[lane * RPL + j] = Cl[j];
     }
@@ -706,18 +717,23 @@ static cudaError_t launch3d_batch(const Inst *insts, const int2 *items, const in
         const cudaError_t e_at = ensure_smem_attr((const void *)k, (int)C::smem);
         if (e_at != cudaSuccess) return e_at;
     }
-    k<<<blocks, NT, C::smem, s>>>(insts, items, count, head, sa);
+    // persistent blocks: at least as many as can be resident
+    const int resident = device_sms() * C::MINB;
+    k<<<blocks > resident ? blocks : resident, NT, C::smem, s>>>(insts, items, count, head, sa);
     return cudaGetLastError();
 }
 
 bool discharge3d_supported(int tx, int ty, int tz) {
-    return tx == 32 && ((ty == 16 && tz == 8) || (ty == 8 && tz == 8) || (ty == 8 && tz == 4));
+    return tx == 32 && ((ty == 16 && tz == 8) || (ty == 8 && tz == 8) || (ty == 8 && tz == 4) || (ty == 4 && tz == 4) ||
+                        (ty == 8 && tz == 2));
 }
 
 cudaError_t launch_discharge3d(const Geom &g, const DevState &st, const SweepArgs &sa, cudaStream_t stream) {
     if (g.tx == 32 && g.ty == 16 && g.tz == 8) return launch3d<16, 8, 512>(g, st, sa, stream);
     if (g.tx == 32 && g.ty == 8 && g.tz == 8) return launch3d<8, 8, 256>(g, st, sa, stream);
     if (g.tx == 32 && g.ty == 8 && g.tz == 4) return launch3d<8, 4, 256>(g, st, sa, stream);
+    if (g.tx == 32 && g.ty == 4 && g.tz == 4) return launch3d<4, 4, 128>(g, st, sa, stream);
+    if (g.tx == 32 && g.ty == 8 && g.tz == 2) return launch3d<8, 2, 128>(g, st, sa, stream);
     return cudaErrorInvalidValue;
 }
 
@@ -726,6 +742,8 @@ cudaError_t launch_discharge3d_batch(int tx, int ty, int tz, const Inst *insts, 
     if (tx == 32 && ty == 16 && tz == 8) return launch3d_batch<16, 8, 512>(insts, items, count, head, sa, blocks, stream);
     if (tx == 32 && ty == 8 && tz == 8) return launch3d_batch<8, 8, 256>(insts, items, count, head, sa, blocks, stream);
     if (tx == 32 && ty == 8 && tz == 4) return launch3d_batch<8, 4, 256>(insts, items, count, head, sa, blocks, stream);
+    if (tx == 32 && ty == 4 && tz == 4) return launch3d_batch<4, 4, 128>(insts, items, count, head, sa, blocks, stream);
+    if (tx == 32 && ty == 8 && tz == 2) return launch3d_batch<8, 2, 128>(insts, items, count, head, sa, blocks, stream);
     return cudaErrorInvalidValue;
 }
 

@@ -1,6 +1,6 @@
 // Exact region-distance relabel (the global relabel heuristic) and the cut
 // closures for 3D 6-connected grids tiled by 32-voxel-wide regions (32x16x8,
-// 32x8x8).
+// 32x8x8, 32x8x4, 32x4x4, 32x8x2).
 //
 // d*(u) = the least number of inter-region arcs on a residual path from u to
 // t (the region distance of Sec. 4.1, eq. 3).  Level sets S_0 ⊆ S_1 ⊆ ...:
@@ -53,7 +53,8 @@ __global__ void glr3d_masks_kernel(const Geom g, const DevState st, int W32, u32
 
 template <int TY, int TZ>
 struct Glr3 {
-    static constexpr int NR = TY * TZ, RPL = NR / 32, LZ = TY / RPL;
+    // 16-row tiles: lanes 16..31 hold no row
+    static constexpr int NR = TY * TZ, RPL = NR < 32 ? 1 : NR / 32, LZ = TY / RPL;
 };
 
 // One level for one region (a warp).  level 0 seeds from T; level l > 0 from
@@ -75,7 +76,7 @@ __device__ bool glr3d_region(const Geom &g, int W32, int r, const u32 *__restric
     for (int j = 0; j < RPL; ++j) {
         const int rho = lane * RPL + j, yl = rho % TY, zl = rho / TY;
         const int y = ry * TY + yl, z = rz * TZ + zl;
-        rowin[j] = y < g.Y && z < g.Z;
+        rowin[j] = rho < C::NR && y < g.Y && z < g.Z;
         wi[j] = ((size_t)z * g.Y + y) * W32 + rx;
         if (rowin[j]) {
 #pragma unroll
@@ -345,6 +346,8 @@ cudaError_t cut3d(const Geom &g, const DevState &st, void *scratch, unsigned cha
     if (g.ty == 16 && g.tz == 8) return cut3d_impl<16, 8>(g, st, scratch, smin, smax, h_passes, s);
     if (g.ty == 8 && g.tz == 8) return cut3d_impl<8, 8>(g, st, scratch, smin, smax, h_passes, s);
     if (g.ty == 8 && g.tz == 4) return cut3d_impl<8, 4>(g, st, scratch, smin, smax, h_passes, s);
+    if (g.ty == 4 && g.tz == 4) return cut3d_impl<4, 4>(g, st, scratch, smin, smax, h_passes, s);
+    if (g.ty == 8 && g.tz == 2) return cut3d_impl<8, 2>(g, st, scratch, smin, smax, h_passes, s);
     return cudaErrorInvalidValue;
 }
 
@@ -364,6 +367,8 @@ __device__ __forceinline__ bool glr3d_unit(const GlrJob2 &J, int r, const u32 *i
 __device__ __forceinline__ bool glr3d_unit_any(const GlrJob2 &J, int r, const u32 *in, u32 *out, int level) {
     if (J.g.ty == 16) return glr3d_unit<16, 8>(J, r, in, out, level);
     if (J.g.tz == 8) return glr3d_unit<8, 8>(J, r, in, out, level);
+    if (J.g.ty == 4) return glr3d_unit<4, 4>(J, r, in, out, level);
+    if (J.g.tz == 2) return glr3d_unit<8, 2>(J, r, in, out, level);
     return glr3d_unit<8, 4>(J, r, in, out, level);
 }
 
@@ -562,6 +567,8 @@ __global__ void cut3d_batch_closure_kernel(const GlrJob2 *__restrict__ jobs, int
             bool grew;
             if (J.g.ty == 16) grew = glr3d_region<16, 8>(J.g, J.W64, r, M, nullptr, S, S, 1, nullptr);
             else if (J.g.tz == 8) grew = glr3d_region<8, 8>(J.g, J.W64, r, M, nullptr, S, S, 1, nullptr);
+            else if (J.g.ty == 4) grew = glr3d_region<4, 4>(J.g, J.W64, r, M, nullptr, S, S, 1, nullptr);
+            else if (J.g.tz == 2) grew = glr3d_region<8, 2>(J.g, J.W64, r, M, nullptr, S, S, 1, nullptr);
             else grew = glr3d_region<8, 4>(J.g, J.W64, r, M, nullptr, S, S, 1, nullptr);
             if (grew && lane == 0) atomicOr(&J.st.ctr[kGlrFlags + f], 1);
             grew_any |= grew;
@@ -661,7 +668,8 @@ cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, i
 }
 
 bool glr3d_supported(const Geom &g) {
-    return g.tx == 32 && g.tz > 1 && ((g.ty == 16 && g.tz == 8) || (g.ty == 8 && g.tz == 8) || (g.ty == 8 && g.tz == 4));
+    return g.tx == 32 && g.tz > 1 && ((g.ty == 16 && g.tz == 8) || (g.ty == 8 && g.tz == 8) || (g.ty == 8 && g.tz == 4) ||
+                                      (g.ty == 4 && g.tz == 4) || (g.ty == 8 && g.tz == 2));
 }
 
 size_t glr3d_scratch_bytes(const Geom &g) {
@@ -711,6 +719,8 @@ cudaError_t glr3d(const Geom &g, const DevState &st, void *scratch, cudaStream_t
     if (g.ty == 16 && g.tz == 8) return glr3d_impl<16, 8>(g, st, scratch, s);
     if (g.ty == 8 && g.tz == 8) return glr3d_impl<8, 8>(g, st, scratch, s);
     if (g.ty == 8 && g.tz == 4) return glr3d_impl<8, 4>(g, st, scratch, s);
+    if (g.ty == 4 && g.tz == 4) return glr3d_impl<4, 4>(g, st, scratch, s);
+    if (g.ty == 8 && g.tz == 2) return glr3d_impl<8, 2>(g, st, scratch, s);
     return cudaErrorInvalidValue;
 }
 

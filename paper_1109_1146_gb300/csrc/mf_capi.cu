@@ -184,12 +184,15 @@ __device__ __forceinline__ int hist_bin(int l) { return l < kHistBins ? l : kHis
 // Also commits the new boundary labels and keeps the histogram of boundary
 // labels (Sec. 5.3: the global gap needs labels of B only) up to date.
 // Fusion of one boundary vertex u = (lx, ly, lz) of region r (see above).
+// The boundary-label histogram change is returned as (old bin, new bin), -1
+// where there is none, for the caller to aggregate over its warp.
 template <int CONN>
 __device__ __forceinline__ void fuse_cell(const Geom &g, const DevState &st, const int r, const int lx, const int ly,
-                                          const int lz, const bool discr) {
+                                          const int lz, const bool discr, int &bin_old, int &bin_new) {
     const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
     const size_t n = (size_t)g.n;
     const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
+    bin_old = bin_new = -1;
     if (!in_grid(g, x, y, z)) return;
     const size_t u = ((size_t)z * g.Y + y) * g.X + x;
     bool boundary = false;
@@ -222,11 +225,22 @@ __device__ __forceinline__ void fuse_cell(const Geom &g, const DevState &st, con
     if (discr) {
         const int old = st.lab[u];
         if (old != du) {
-            if (old < g.dinf) atomicSub(&st.hist[hist_bin(old)], 1);
-            if (du < g.dinf) atomicAdd(&st.hist[hist_bin(du)], 1);
+            if (old < g.dinf) bin_old = hist_bin(old);
+            if (du < g.dinf) bin_new = hist_bin(du);
             st.lab[u] = du;
         }
     }
+}
+
+// Histogram updates of a warp: lanes naming the same bin send one atomic
+// with their count (a sweep moves many boundary labels between the same few
+// bins, and per-vertex atomics on them serialise).
+__device__ __forceinline__ void hist_update_warp(int *hist, int bin_old, int bin_new) {
+    const int lane = threadIdx.x & 31;
+    const unsigned mo = __match_any_sync(0xffffffffu, bin_old);
+    if (bin_old >= 0 && lane == __ffs(mo) - 1) atomicSub(&hist[bin_old], __popc(mo));
+    const unsigned mn = __match_any_sync(0xffffffffu, bin_new);
+    if (bin_new >= 0 && lane == __ffs(mn) - 1) atomicAdd(&hist[bin_new], __popc(mn));
 }
 
 // The cells on the surface of a tile, enumerated directly: in 2D the top and
@@ -278,10 +292,15 @@ __device__ __forceinline__ void fuse_region_warp(const Geom &g, const DevState &
     if (!region_touched<CONN>(g, st, r)) return;
     const bool discr = st.disc[r];
     const int P = surface_cells(g, CONN == 6);
-    for (int p = threadIdx.x & 31; p < P; p += 32) {
-        int lx, ly, lz;
-        surface_cell(g, CONN == 6, p, lx, ly, lz);
-        fuse_cell<CONN>(g, st, r, lx, ly, lz, discr);
+    for (int p0 = 0; p0 < P; p0 += 32) {  // whole warp per step: the histogram update is a warp operation
+        const int p = p0 + (threadIdx.x & 31);
+        int bo = -1, bn = -1;
+        if (p < P) {
+            int lx, ly, lz;
+            surface_cell(g, CONN == 6, p, lx, ly, lz);
+            fuse_cell<CONN>(g, st, r, lx, ly, lz, discr, bo, bn);
+        }
+        hist_update_warp(st.hist, bo, bn);
     }
 }
 

@@ -25,6 +25,8 @@ def _batch_instances():
     out.append((grids.volume_3d(20, 20, 20, 8), (8, 8, 8)))
     out.append((grids.volume_3d(50, 30, 17, 9), (32, 16, 8)))
     out.append((grids.volume_3d(40, 25, 20, 10), (32, 8, 8)))
+    out.append((grids.volume_3d(45, 22, 18, 11), (32, 4, 4)))
+    out.append((grids.volume_3d(36, 24, 9, 12), (32, 8, 2)))
     out.append((grids.random_grid((5, 1, 1), 4, 9, cmax=10, tmax=20), (64, 64, 1)))
     return out
 

@@ -28,7 +28,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 WEIGHTS = os.path.join(ROOT, "paper_1109_1146_gb300", "weights", "warm_seg2d_1024_c4.npy")
 TILES2 = [(32, 32, 1), (64, 32, 1), (64, 64, 1)]
-TILES3 = [(32, 8, 4), (32, 8, 8), (32, 16, 8)]
+TILES3 = [(32, 8, 4), (32, 8, 8), (32, 16, 8), (32, 4, 4), (32, 8, 2)]
 
 
 def _batch_share():
@@ -62,7 +62,8 @@ def test_uneven_batch_share_cold_and_warm_vs_oracle():
         refs = list(ex.map(oracle.solve_instance, insts))
     handles = []
     for k, inst in enumerate(insts):
-        tile = (TILES2 if inst.conn == 4 else TILES3)[k % 3]
+        tiles = TILES2 if inst.conn == 4 else TILES3
+        tile = tiles[k % len(tiles)]
         g = Grid(inst.dims, inst.conn, tile=tile)
         g.set_caps(inst.cs, inst.ct, inst.nlink)
         handles.append(g)

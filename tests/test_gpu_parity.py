@@ -41,6 +41,8 @@ CASES = [
     ((45, 30, 19), 6, (32, 8, 8)),
     ((96, 48, 24), 6, (32, 16, 8)),
     ((70, 30, 22), 6, (32, 8, 4)),
+    ((75, 27, 22), 6, (32, 4, 4)),
+    ((66, 33, 13), 6, (32, 8, 2)),
 ]
 
 
@@ -61,7 +63,8 @@ def test_ragged_multi_region(dims, conn, tile, kind):
                                             ((64, 64, 1), 8, (64, 64, 1)), ((16, 16, 16), 6, (16, 16, 16)),
                                             ((1, 300, 1), 4, (32, 32, 1)), ((3, 3, 40), 6, (8, 8, 8)),
                                             ((1, 1, 1), 6, (32, 16, 8)), ((33, 1, 9), 6, (32, 8, 8)),
-                                            ((32, 16, 8), 6, (32, 16, 8))])
+                                            ((32, 16, 8), 6, (32, 16, 8)), ((1, 1, 1), 6, (32, 4, 4)),
+                                            ((33, 5, 3), 6, (32, 8, 2)), ((32, 4, 4), 6, (32, 4, 4))])
 def test_degenerate_shapes(dims, conn, tile):
     inst = grids.random_grid(dims, conn, 5, cmax=25, tmax=40)
     got = gpu_solve(inst, tile=tile)
