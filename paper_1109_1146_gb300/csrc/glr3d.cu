@@ -31,23 +31,32 @@ namespace cg = cooperative_groups;
 typedef unsigned int u32;
 
 // masks M[d][word] bit b = [c_f(v -> v + D(d)) > 0] and T[word] bit b = [c_f(v,t) > 0]
+// (a warp per grid row z * Y + y, lanes over x: coalesced plane reads, no
+// 64-bit index division)
 __global__ void glr3d_masks_kernel(const Geom g, const DevState st, int W32, u32 *M, u32 *T) {
     const size_t n = (size_t)g.n;
-    const size_t words = (size_t)g.Z * g.Y * W32;
-    const size_t nw = words;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < words * 32; t += (size_t)gridDim.x * blockDim.x) {
-        const size_t w = t >> 5;
-        const int xw = (int)(w % W32), y = (int)((w / W32) % g.Y), z = (int)(w / ((size_t)W32 * g.Y));
-        const int x = xw * 32 + (int)(t & 31);
-        const bool in = x < g.X;
-        const size_t v = ((size_t)z * g.Y + y) * g.X + x;
+    const size_t nw = (size_t)g.Z * g.Y * W32;
+    const int lane = threadIdx.x & 31;
+    const int rows = g.Z * g.Y;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps) {
+        const size_t v0 = (size_t)row * g.X, w0 = (size_t)row * W32;
+        for (int xw = 0; xw < W32; ++xw) {
+            const int x = xw * 32 + lane;
+            const bool in = x < g.X;
+            const size_t v = v0 + x;
+            int c[6];
 #pragma unroll
-        for (int d = 0; d < 6; ++d) {
-            const unsigned m = __ballot_sync(0xffffffffu, in && st.cap[d * n + v] > 0);
-            if ((threadIdx.x & 31) == 0) M[d * nw + w] = m;
+            for (int d = 0; d < 6; ++d) c[d] = in ? __ldg(&st.cap[d * n + v]) : 0;
+            const int tc = in ? __ldg(&st.tcap[v]) : 0;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                const unsigned m = __ballot_sync(0xffffffffu, c[d] > 0);
+                if (lane == 0) M[d * nw + w0 + xw] = m;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, tc > 0);
+            if (lane == 0) T[w0 + xw] = m;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, in && st.tcap[v] > 0);
-        if ((threadIdx.x & 31) == 0) T[w] = m;
     }
 }
 
@@ -162,6 +171,30 @@ __device__ bool glr3d_region(const Geom &g, int W32, int r, const u32 *__restric
     return __any_sync(FULL, grew);
 }
 
+// Per-region "grew at level l" flags (two bytes per region, by level parity):
+// S_l(r) depends only on S_{l-1} of r and of its six neighbour regions, so a
+// region none of which grew at level l-1 keeps its set at level l and is
+// skipped.  Its level-l buffer then still holds S_{l-2}(r) = S_{l-1}(r) = S_l(r)
+// (it did not grow at l-1 either); level 1 processes every region.
+__device__ __forceinline__ bool region_or_nbr_grew(const Geom &g, const unsigned char *f, int r) {
+    const int lane = threadIdx.x & 31;
+    bool b = false;
+    if (lane < 6) {
+        const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+        const int qx = rx + arc_dx(6, lane), qy = ry + arc_dy(6, lane), qz = rz + arc_dz(6, lane);
+        if (qx >= 0 && qx < g.RX && qy >= 0 && qy < g.RY && qz >= 0 && qz < g.RZ)
+            b = f[(qz * g.RY + qy) * g.RX + qx] != 0;
+    } else if (lane == 6) {
+        b = f[r] != 0;
+    }
+    return __any_sync(0xffffffffu, b);
+}
+
+// the region flags follow the level sets in the relabel scratch
+__host__ __device__ __forceinline__ unsigned char *glr3d_region_flags(u32 *B, size_t words) {
+    return (unsigned char *)(B + words);
+}
+
 // all levels in one cooperative launch; flags[3] triple-buffered "grew" words
 template <int TY, int TZ>
 __global__ void glr3d_levels_kernel(const Geom g, int W32, const u32 *__restrict__ M, const u32 *__restrict__ T,
@@ -176,18 +209,68 @@ __global__ void glr3d_levels_kernel(const Geom g, int W32, const u32 *__restrict
         flags[2] = 0;
     }
     grid.sync();
+    unsigned char *chg = glr3d_region_flags(B, (size_t)g.Z * g.Y * W32);
     int level = 1;
     for (; level < max_levels; ++level) {
         const u32 *in = (level & 1) ? B : A;
         u32 *out = (level & 1) ? A : B;
+        const unsigned char *cin = chg + (size_t)((level - 1) & 1) * g.nreg;
+        unsigned char *cout = chg + (size_t)(level & 1) * g.nreg;
         bool grew = false;
-        for (int r = wid; r < g.nreg; r += nwarps) grew |= glr3d_region<TY, TZ>(g, W32, r, M, T, in, out, level, lab);
+        for (int r = wid; r < g.nreg; r += nwarps) {
+            bool gr = false;
+            if (level == 1 || region_or_nbr_grew(g, cin, r)) gr = glr3d_region<TY, TZ>(g, W32, r, M, T, in, out, level, lab);
+            if (lane == 0) cout[r] = gr;
+            grew |= gr;
+        }
         if (grew && lane == 0) atomicOr(&flags[level % 3], 1);
         if (blockIdx.x == 0 && threadIdx.x == 0) flags[(level + 1) % 3] = 0;
         grid.sync();
         if (!*(volatile int *)&flags[level % 3]) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *levels_out = level + 1;
+}
+
+// The finish over grid rows [row0, row1) (row = z * Y + y) of the set S, a
+// warp per row and lanes over x (tiles are 32 voxels wide: the 32 voxels of
+// a word lie in one region): unreached vertices get d_inf, a region holding
+// excess below d_inf becomes active, and the labels of boundary vertices (an
+// in-grid neighbour in another region) go to the histogram, bins below SB
+// into the block's shared copy sh, equal labels of a warp as one update.
+__device__ __forceinline__ void glr3d_finish_rows(const Geom &g, const DevState &st, int W32, const u32 *S, int row0,
+                                                  int row1, int *sh, int SB) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int row = row0 + (int)(threadIdx.x >> 5); row < row1; row += nw) {
+        const int z = row / g.Y, y = row - z * g.Y;
+        const int ly = y & (g.ty - 1), lz = z & (g.tz - 1);
+        const bool yzb = (ly == 0 && y > 0) || (ly == g.ty - 1 && y + 1 < g.Y) || (lz == 0 && z > 0) ||
+                         (lz == g.tz - 1 && z + 1 < g.Z);
+        const int rbase = ((z >> g.sz) * g.RY + (y >> g.sy)) * g.RX;
+        const size_t v0 = (size_t)row * g.X;
+        for (int xw = 0; xw < W32; ++xw) {
+            const int x = xw * 32 + lane;
+            const u32 sw = S[(size_t)row * W32 + xw];
+            int l = g.dinf, e = 0;
+            if (x < g.X) {
+                l = st.lab[v0 + x];
+                e = st.exc[v0 + x];
+                if (!((sw >> lane) & 1u) && l != g.dinf) {
+                    l = g.dinf;
+                    st.lab[v0 + x] = l;
+                }
+            }
+            const bool live = l < g.dinf;
+            if (__any_sync(0xffffffffu, live && e > 0) && lane == 0) st.active[rbase + xw] = 1;
+            const bool xb = (lane == 0 && x > 0) || (lane == 31 && x + 1 < g.X);
+            const int key = live && (xb || yzb) ? l : -1;
+            const unsigned mm = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && lane == __ffs(mm) - 1) {
+                const int c = __popc(mm);
+                if (key < SB) atomicAdd(&sh[key], c);
+                else atomicAdd(&st.hist[key < kHistBins ? key : kHistBins], c);
+            }
+        }
+    }
 }
 
 // unreached vertices get d_inf; boundary-label histogram and region activity
@@ -200,27 +283,10 @@ __global__ void glr3d_finish_kernel(const Geom g, const DevState st, int W32, co
     __shared__ int sh[SB];
     for (int b = threadIdx.x; b < SB; b += blockDim.x) sh[b] = 0;
     __syncthreads();
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < (size_t)g.n; v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
-        int l = st.lab[v];
-        if (!((S[((size_t)z * g.Y + y) * W32 + (x >> 5)] >> (x & 31)) & 1u)) {
-            l = g.dinf;
-            st.lab[v] = l;
-        }
-        if (l >= g.dinf) continue;
-        const int r = ((z >> g.sz) * g.RY + (y >> g.sy)) * g.RX + (x >> g.sx);
-        if (st.exc[v] > 0) st.active[r] = 1;
-        bool inB = false;
-#pragma unroll
-        for (int d = 0; d < 6; ++d) {
-            const int wx = x + arc_dx(6, d), wy = y + arc_dy(6, d), wz = z + arc_dz(6, d);
-            if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y || wz < 0 || wz >= g.Z) continue;
-            if (((wz >> g.sz) * g.RY + (wy >> g.sy)) * g.RX + (wx >> g.sx) != r) inB = true;
-        }
-        if (!inB) continue;
-        if (l < SB) atomicAdd(&sh[l], 1);
-        else atomicAdd(&st.hist[l < kHistBins ? l : kHistBins], 1);
-    }
+    const int rows = g.Z * g.Y;
+    const int per = (rows + gridDim.x - 1) / gridDim.x;  // a block takes a run of rows
+    const int r0 = blockIdx.x * per;
+    glr3d_finish_rows(g, st, W32, S, r0, min(rows, r0 + per), sh, SB);
     __syncthreads();
     for (int b = threadIdx.x; b < SB; b += blockDim.x)
         if (sh[b]) atomicAdd(&st.hist[b], sh[b]);
@@ -298,11 +364,17 @@ __global__ void closure3d_kernel(const Geom g, int W32, const u32 *__restrict__ 
 
 __global__ void cut3d_bytes_kernel(const Geom g, int W32, const u32 *Smin, const u32 *Tset, unsigned char *smin,
                                    unsigned char *smax) {
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < (size_t)g.n; v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
-        const size_t w = ((size_t)z * g.Y + y) * W32 + (x >> 5);
-        smin[v] = (unsigned char)((Smin[w] >> (x & 31)) & 1u);
-        smax[v] = (unsigned char)(1u - ((Tset[w] >> (x & 31)) & 1u));
+    const int lane = threadIdx.x & 31;
+    const int rows = g.Z * g.Y;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps) {
+        const size_t v0 = (size_t)row * g.X, w0 = (size_t)row * W32;
+        for (int xw = 0; xw < W32; ++xw) {
+            const int x = xw * 32 + lane;
+            if (x >= g.X) continue;
+            smin[v0 + x] = (unsigned char)((Smin[w0 + xw] >> lane) & 1u);
+            smax[v0 + x] = (unsigned char)(1u - ((Tset[w0 + xw] >> lane) & 1u));
+        }
     }
 }
 
@@ -399,7 +471,12 @@ __global__ void glr3d_batch_levels_kernel(const GlrJob2 *__restrict__ jobs, int 
             if (level > 1 && !*(volatile int *)&J.st.ctr[kGlrFlags + fp]) continue;  // stopped growing
             const u32 *in = (const u32 *)((level & 1) ? J.B : J.A);
             u32 *out = (u32 *)((level & 1) ? J.A : J.B);
-            const bool grew = glr3d_unit_any(J, u - J.unit0, in, out, level);
+            const int r = u - J.unit0;
+            unsigned char *chg = glr3d_region_flags((u32 *)J.B, (size_t)J.g.Z * J.g.Y * J.W64);
+            bool grew = false;
+            if (level == 1 || region_or_nbr_grew(J.g, chg + (size_t)((level - 1) & 1) * J.g.nreg, r))
+                grew = glr3d_unit_any(J, r, in, out, level);
+            if (lane == 0) chg[(size_t)(level & 1) * J.g.nreg + r] = grew;
             if (grew && lane == 0) atomicOr(&J.st.ctr[kGlrFlags + f], 1);
             grew_any |= grew;
         }
@@ -433,7 +510,8 @@ __global__ void glr3d_batch_reset_kernel(const GlrJob2 *__restrict__ jobs) {
     if (threadIdx.x == 0) st.ctr[kActiveRegions] = 0;
 }
 
-constexpr int kFinishChunk3 = 16384;
+constexpr int kFinishChunk3 = 16384;  // voxels per unit of the batched cut bytes
+constexpr int kFinishRows3 = 64;      // grid rows per unit of the batched finish
 __global__ void glr3d_batch_finish_kernel(const GlrJob2 *__restrict__ jobs, const int2 *__restrict__ chunks, int nchunks) {
     constexpr int SB = 2048;
     __shared__ int sh[SB];
@@ -446,28 +524,8 @@ __global__ void glr3d_batch_finish_kernel(const GlrJob2 *__restrict__ jobs, cons
         __syncthreads();
         const int last = st.ctr[kGlrLevels] - 1;
         const u32 *S = (const u32 *)((last % 2 == 1) ? J.A : J.B);
-        const size_t v0 = (size_t)w.y * kFinishChunk3, v1 = min((size_t)g.n, v0 + kFinishChunk3);
-        for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-            const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
-            int l = st.lab[v];
-            if (!((S[((size_t)z * g.Y + y) * J.W64 + (x >> 5)] >> (x & 31)) & 1u)) {
-                l = g.dinf;
-                st.lab[v] = l;
-            }
-            if (l >= g.dinf) continue;
-            const int r = ((z >> g.sz) * g.RY + (y >> g.sy)) * g.RX + (x >> g.sx);
-            if (st.exc[v] > 0) st.active[r] = 1;
-            bool inB = false;
-#pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                const int wx = x + arc_dx(6, d), wy = y + arc_dy(6, d), wz = z + arc_dz(6, d);
-                if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y || wz < 0 || wz >= g.Z) continue;
-                if (((wz >> g.sz) * g.RY + (wy >> g.sy)) * g.RX + (wx >> g.sx) != r) inB = true;
-            }
-            if (!inB) continue;
-            if (l < SB) atomicAdd(&sh[l], 1);
-            else atomicAdd(&st.hist[l < kHistBins ? l : kHistBins], 1);
-        }
+        const int r0 = w.y * kFinishRows3;
+        glr3d_finish_rows(g, st, J.W64, S, r0, min(g.Z * g.Y, r0 + kFinishRows3), sh, SB);
         __syncthreads();
         for (int b = threadIdx.x; b < SB; b += blockDim.x)
             if (sh[b]) atomicAdd(&st.hist[b], sh[b]);
@@ -501,7 +559,7 @@ cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
         J.B = (unsigned long long *)(M + 8 * words);
         J.unit0 = (int)unit_job.size();
         for (int r = 0; r < J.g.nreg; ++r) unit_job.push_back(j);
-        const int nc = (int)((J.g.n + kFinishChunk3 - 1) / kFinishChunk3);
+        const int nc = (int)((J.g.Z * J.g.Y + kFinishRows3 - 1) / kFinishRows3);
         for (int c = 0; c < nc; ++c) chunks.push_back(make_int2(j, c));
     }
     cudaError_t e = bb.reserve(njobs * sizeof(GlrJob2), unit_job.size() * sizeof(int), chunks.size() * sizeof(int2));
@@ -514,7 +572,7 @@ cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
     if (e != cudaSuccess) return e;
     for (const GlrJob2 &J : jobs) {
         const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
-        const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, (size_t)device_sms() * 32);
+        const int mb = (int)std::min<size_t>(((size_t)J.g.Z * J.g.Y + 7) / 8, (size_t)device_sms() * 32);
         u32 *M = (u32 *)J.M;
         glr3d_masks_kernel<<<mb, 256, 0, s>>>(J.g, J.st, J.W64, M, M + 6 * words);
     }
@@ -674,7 +732,7 @@ bool glr3d_supported(const Geom &g) {
 
 size_t glr3d_scratch_bytes(const Geom &g) {
     const size_t words = (size_t)g.Z * g.Y * ((g.X + 31) / 32);
-    return words * 4 * (6 + 1 + 2);  // masks, T, two level sets
+    return words * 4 * (6 + 1 + 2) + 2 * (size_t)g.nreg;  // masks, T, two level sets, region flags
 }
 
 template <int TY, int TZ>
@@ -685,7 +743,7 @@ static cudaError_t glr3d_impl(const Geom &g, const DevState &st, void *scratch, 
     u32 *T = M + 6 * words;
     u32 *A = T + words;
     u32 *B = A + words;
-    const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, device_sms() * 32);
+    const int mb = (int)std::min<size_t>(((size_t)g.Z * g.Y + 7) / 8, device_sms() * 32);
     glr3d_masks_kernel<<<mb, 256, 0, s>>>(g, st, W32, M, T);
     int max_blocks = 0;
     {
@@ -709,7 +767,7 @@ static cudaError_t glr3d_impl(const Geom &g, const DevState &st, void *scratch, 
     if (e == cudaSuccess) e = cudaMemsetAsync(st.active, 0, (size_t)g.nreg, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&st.ctr[kActiveRegions], 0, 4, s);
     if (e != cudaSuccess) return e;
-    const int nb = (int)std::min<size_t>(((size_t)g.n + 255) / 256, device_sms() * 32);
+    const int nb = (int)std::min<size_t>(((size_t)g.Z * g.Y + 7) / 8, device_sms() * 32);
     glr3d_finish_kernel<<<nb, 256, 0, s>>>(g, st, W32, A, B);
     glr3d_count_kernel<<<(g.nreg + 255) / 256, 256, 0, s>>>(st, g.nreg);
     return cudaGetLastError();

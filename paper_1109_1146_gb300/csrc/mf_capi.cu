@@ -412,51 +412,22 @@ template <int CONN>
 __global__ void fuse2d_kernel(const Geom g, const DevState st) {
     const int P = perimeter_slots(g);
     const long long items = (long long)g.nreg * P;
-    const size_t n = (size_t)g.n;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < items; k += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(k / P), p = (int)(k % P);
-        if (!region_touched<CONN>(g, st, r)) continue;
-        if (p == 0) st.active[r] = st.left_active[r];
-        int lx, ly;
-        perimeter_xy(p, g.tx, g.ty, lx, ly);
-        const int x = (r % g.RX) * g.tx + lx, y = (r / g.RX) * g.ty + ly;
-        if (x >= g.X || y >= g.Y) continue;
-        const size_t u = (size_t)y * g.X + x;
-        const bool discr = st.disc[r];
-        bool boundary = false;
-        int back_total = 0, du = -1;
-#pragma unroll
-        for (int d = 0; d < CONN; ++d) {
-            const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d);
-            if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y) continue;
-            const int rw = (wy >> g.sy) * g.RX + (wx >> g.sx);
-            if (rw == r) continue;
-            if (!boundary) {
-                boundary = true;
-                du = discr ? st.lab_next[u] : st.lab[u];
-            }
-            const size_t w = (size_t)wy * g.X + wx;
-            const bool discw = st.disc[rw];
-            const int pu = discr ? st.bout[(size_t)d * n + u] : 0;
-            const int pw = discw ? st.bout[(size_t)(d ^ 1) * n + w] : 0;
-            if (!(pu | pw)) continue;  // no flow crossed this arc: nothing to accept or return
-            const int dw = discw ? st.lab_next[w] : st.lab[w];
-            const int back = (dw <= du + 1 ? 0 : pu) + (du <= dw + 1 ? pw : 0);
-            if (back) {
-                st.cap[(size_t)d * n + u] += back;
-                back_total += back;
+    const int lane = threadIdx.x & 31;
+    // warp-uniform steps (the histogram update is a warp operation)
+    for (long long k0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); k0 < items;
+         k0 += (long long)gridDim.x * blockDim.x) {
+        const long long k = k0 + lane;
+        int bo = -1, bn = -1;
+        if (k < items) {
+            const int r = (int)(k / P), p = (int)(k % P);
+            if (region_touched<CONN>(g, st, r)) {
+                if (p == 0) st.active[r] = st.left_active[r];
+                int lx, ly;
+                perimeter_xy(p, g.tx, g.ty, lx, ly);
+                fuse_cell<CONN>(g, st, r, lx, ly, 0, st.disc[r] != 0, bo, bn);
             }
         }
-        if (!boundary) continue;
-        if (back_total) st.exc[u] += back_total;
-        if (discr) {
-            const int old = st.lab[u];
-            if (old != du) {
-                if (old < g.dinf) atomicSub(&st.hist[hist_bin(old)], 1);
-                if (du < g.dinf) atomicAdd(&st.hist[hist_bin(du)], 1);
-                st.lab[u] = du;
-            }
-        }
+        hist_update_warp(st.hist, bo, bn);
     }
 }
 
