@@ -732,22 +732,27 @@ def run_batch_warm(args):
 
 def run_prd(args):
     """P-ARD against P-PRD (Discharge = PRD, kernel_variant 2) on the paper's
-    synthetic family (Sec. 7.1: 4-connected, excess U[-500, 500], constant
-    strength): sweeps and device ms of both on the same instances and
-    schedule (global relabel every 4 sweeps), over strength, size and region
-    size; every pair must reach the same flow value."""
+    synthetic family (Sec. 7.1: displacements from the paper's list, excess
+    U[-500, 500], constant strength): sweeps and device ms of both on the same
+    instances and schedule (global relabel every 4 sweeps), over strength,
+    size and connectivity (at connectivity c the strength is 150 * 8 / c, as
+    in the paper's connectivity series), and for connectivity 4 over the
+    region size; every pair must reach the same flow value."""
     from gen import grids
     from paper_1109_1146_gb300 import Grid, default_opts
 
-    cases = [(1000, s, (32, 32, 1)) for s in (20, 50, 150, 400, 1000)]
-    cases += [(n, 150, (32, 32, 1)) for n in (250, 500, 2000)]
-    cases += [(1000, 150, t) for t in ((64, 64, 1), (64, 32, 1))]
-    for side, strength, tile in cases:
+    t32 = (32, 32, 1)
+    cases = [(1000, s, 8, t32) for s in (20, 50, 150, 400, 1000)]        # strength, connectivity 8
+    cases += [(n, 150, 8, t32) for n in (250, 500, 2000)]                 # size
+    cases += [(1000, 1200 // c, c, t32) for c in (4, 12, 16, 20, 24, 28)]  # connectivity
+    cases += [(1000, s, 4, t32) for s in (20, 150, 400, 1000)]
+    cases += [(1000, 150, 4, t) for t in ((64, 64, 1), (64, 32, 1))]      # region size (4-connected)
+    for side, strength, conn, tile in cases:
         rows = {}
         for seed in range(args.prd_seeds):
-            inst = grids.paper_synthetic(side, side, seed, strength=strength)
+            inst = grids.paper_synthetic(side, side, seed, strength=strength, connectivity=conn)
             flows = set()
-            with Grid(inst.dims, 4, tile=tile) as g:
+            with Grid(inst.dims, inst.conn, tile=tile) as g:
                 g.set_caps(inst.cs, inst.ct, inst.nlink)
                 for name, variant in (("ard", 0), ("prd", 2)):
                     opts = default_opts(kernel_variant=variant)
@@ -758,9 +763,9 @@ def run_prd(args):
                     r["sweeps"].append(st.sweeps)
                     r["ms"].append(st.ms_total)
                     r["rounds"].append(st.rounds / max(1, st.discharges))
-            assert len(flows) == 1, (side, strength, seed, flows)
-        print(json.dumps({"workload": "prd", "instance": f"paper synthetic {side}x{side} 4-connected",
-                          "strength": strength, "tile": list(tile), "seeds": args.prd_seeds,
+            assert len(flows) == 1, (side, strength, conn, seed, flows)
+        print(json.dumps({"workload": "prd", "instance": f"paper synthetic {side}x{side} connectivity {conn}",
+                          "connectivity": conn, "strength": strength, "tile": list(tile), "seeds": args.prd_seeds,
                           **{f"{k}_{m}_mean": round(statistics.mean(v[m]), 3) for k, v in rows.items() for m in v}}),
               flush=True)
 

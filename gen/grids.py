@@ -299,33 +299,41 @@ def random_grid(dims, conn: int, seed: int, cmax: int = 20, tmax: int = 40,
 
 
 # displacements of the paper's synthetic networks (Sec. 7.1), in the order in
-# which they are added: the first pair gives connectivity 4, each further
-# pair adds 4 (only the first pair is a stencil of this package's grids)
+# which they are listed (each pair adds 4 to the connectivity), read as (dx, dy)
 PAPER_DISPLACEMENTS = ((0, 1), (1, 0), (1, 2), (2, 1), (1, 3), (3, 1), (2, 3), (3, 2), (0, 2), (2, 0), (2, 2),
                        (3, 3), (3, 4), (4, 2))
+
+
+def paper_connectivity_code(connectivity: int) -> int:
+    """Connectivity code of the synthetic stencil of the given connectivity:
+    4 is the 4-connected grid, c = 8, 12, ..., 28 the code 100 + c."""
+    if connectivity not in (4, 8, 12, 16, 20, 24, 28):
+        raise ValueError("the synthetic family has connectivity 4, 8, ..., 28")
+    return 4 if connectivity == 4 else 100 + connectivity
 
 
 def paper_synthetic(X: int, Y: int, seed: int, strength: int = 150, connectivity: int = 4,
                     name: str = "") -> GridInstance:
     """The synthetic family of Sec. 7.1: a 2D grid whose edges join the nodes
-    at the listed relative displacements, every edge with the same capacity
-    (the strength), and every node given an integer excess or deficit drawn
-    uniformly from [-500, 500] (PCG64 of the seed): a positive value is a
-    source link, a negative one a sink link.  Connectivity 4 (displacements
-    (0,1) and (1,0)) is this package's 4-connected grid; the higher
-    connectivities of the paper use knight-type displacements, which are not
-    among its stencils."""
-    if connectivity != 4:
-        raise ValueError("only connectivity 4 of the paper's synthetic family maps onto a supported stencil")
+    at the first connectivity/2 listed displacements (connectivity 4, 8, ...,
+    28), every edge with the same capacity (the strength), and every node
+    given an integer excess or deficit drawn uniformly from [-500, 500] (PCG64
+    of the seed): a positive value is a source link, a negative one a sink
+    link.  Plane h holds the edges of the h-th forward displacement; the
+    list's first pair, (0,1), (1,0), goes to planes 1, 0, so connectivity 4
+    is this package's 4-connected grid, and higher connectivities carry the
+    code 100 + connectivity."""
+    code = paper_connectivity_code(connectivity)
+    disp = ((1, 0), (0, 1)) + PAPER_DISPLACEMENTS[2:connectivity // 2]
     rng = np.random.Generator(np.random.PCG64(seed))
     e = rng.integers(-500, 501, X * Y)
     cs = np.where(e > 0, e, 0).astype(np.int32)
     ct = np.where(e < 0, -e, 0).astype(np.int32)
-    nl = np.zeros((2, Y, X), dtype=np.int32)
-    nl[0, :, : X - 1] = strength   # (1, 0)
-    nl[1, : Y - 1, :] = strength   # (0, 1)
-    return GridInstance((X, Y, 1), 4, cs, ct, nl.reshape(2, -1),
-                        name or f"paper_synth_{X}x{Y}_c4_str{strength}_s{seed}")
+    nl = np.zeros((len(disp), Y, X), dtype=np.int32)
+    for h, (dx, dy) in enumerate(disp):  # the edge exists where its head lies in the grid
+        nl[h, : max(0, Y - dy), : max(0, X - dx)] = strength
+    return GridInstance((X, Y, 1), code, cs, ct, nl.reshape(len(disp), -1),
+                        name or f"paper_synth_{X}x{Y}_c{connectivity}_str{strength}_s{seed}")
 
 
 # --- the five named workloads ------------------------------------------------

@@ -23,6 +23,17 @@
  *       8: h0 = (+1,0)   h1 = (0,+1)   h2 = (+1,+1)   h3 = (-1,+1)
  *       6: h0 = (+1,0,0) h1 = (0,+1,0) h2 = (0,0,+1)
  *     and H = connectivity/2;
+ *   - the synthetic networks of Sec. 7.1 join each node to the nodes at the
+ *     displacements of the paper's list; MF_PAPER_STENCIL(c) (c = 8, 12, ...,
+ *     28; ndim 2) takes its first c/2 entries as forward half-stencil
+ *       h0 = (1,0) h1 = (0,1) h2 = (1,2) h3 = (2,1) h4 = (1,3) h5 = (3,1)
+ *       h6 = (2,3) h7 = (3,2) h8 = (0,2) h9 = (2,0) h10 = (2,2) h11 = (3,3)
+ *       h12 = (3,4) h13 = (4,2)
+ *     (the list's first pair swapped so that c = 4 would be the 4-connected
+ *     grid) with H = c/2; such grids are solved one by one on 32x32 tiles with
+ *     the generic region discharge (kernel_variant 0 or 1 = ARD, 2 = PRD),
+ *     without the global relabel, warm start, region reduction, boundary
+ *     relabel, batches or MF_STATE_HOST;
  *   - arc directions d = 0..2H-1: D(2h) = +h-th offset, D(2h+1) = -h-th
  *     offset; the reverse of d is d^1;
  *   - all arrays are dense int32 (or uint8) and row-major as above;
@@ -47,6 +58,9 @@ extern "C" {
 #endif
 
 typedef struct mf_grid mf_grid; /* opaque; owns all device memory of one instance */
+
+/* connectivity code of the Sec. 7.1 synthetic stencil of connectivity c (see above) */
+#define MF_PAPER_STENCIL(c) (100 + (c))
 
 typedef enum {
     MF_OK = 0,
@@ -120,12 +134,13 @@ void mf_default_opts(mf_opts *opts);
  * Create a grid instance on the current CUDA device.
  *   ndim          2 or 3;
  *   dims          {X, Y, Z} (Z ignored and taken as 1 when ndim = 2), each >= 1;
- *   connectivity  4 or 8 for ndim = 2, 6 for ndim = 3;
+ *   connectivity  4, 8 or MF_PAPER_STENCIL(c) for ndim = 2, 6 for ndim = 3;
  *   tile          region shape {tx, ty, tz}: the fixed partition of V into
  *                 regions R_k of Sec. 3 is the tiling of the grid by this
  *                 shape (edge tiles may be ragged).  Supported: 2D 64x64,
- *                 64x32 and 32x32, 3D 32x16x8, 32x8x8, 32x8x4 (bit-parallel
- *                 discharge), 16x16x16 and 8x8x8; NULL or {0,0,0} picks 32x32
+ *                 64x32 and 32x32, 3D 32x16x8, 32x8x8, 32x8x4, 32x4x4 and
+ *                 32x8x2 (bit-parallel discharge), 16x16x16 and 8x8x8; the
+ *                 Sec. 7.1 stencils 32x32 only; NULL or {0,0,0} picks 32x32
  *                 (2D) / 32x8x4 (3D);
  *   cuda_stream   cudaStream_t to order all work on, or NULL for a stream
  *                 owned by the handle (non-blocking: device buffers that

@@ -23,6 +23,8 @@ Augmentation and Push-Relabel"):
                       0-1 BFS over the residual graph;
   * ``boundary_relabel`` — the boundary-relabel heuristic of Sec. 6.1 on an
                       explicit auxiliary graph of (region, label) groups.
+  The stencils are the 4/8-connected 2D and 6-connected 3D grids and the
+  synthetic networks of Sec. 7.1 (connectivity code 100 + c).
   ``oracle.cnn`` and ``oracle.warm`` hold the float64 warm-start network and
   the projection of a prediction to a preflow; ``oracle.reduction`` the
   region reduction of Sec. 8 on explicit per-region networks.
@@ -168,6 +170,14 @@ def verify(dims, conn, cs, ct, nlink, res, tres, exc, flow, smin=None, smax=None
 _FWD = {4: ((1, 0, 0), (0, 1, 0)),
         8: ((1, 0, 0), (0, 1, 0), (1, 1, 0), (-1, 1, 0)),
         6: ((1, 0, 0), (0, 1, 0), (0, 0, 1))}
+# The synthetic networks of Sec. 7.1: edges at the listed relative
+# displacements, read as (dx, dy); connectivity c takes the first c/2 of them
+# (code 100 + c).  The list's first pair, (0,1), (1,0), is kept here as
+# (1,0), (0,1) so that its planes are those of the 4-connected grid.
+_PAPER_LIST = ((1, 0), (0, 1), (1, 2), (2, 1), (1, 3), (3, 1), (2, 3), (3, 2), (0, 2), (2, 0), (2, 2), (3, 3),
+               (3, 4), (4, 2))
+for _c in range(8, 29, 4):
+    _FWD[100 + _c] = tuple((dx, dy, 0) for dx, dy in _PAPER_LIST[:_c // 2])
 
 
 def edge_list(dims, conn, nlink):

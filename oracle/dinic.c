@@ -30,6 +30,11 @@
 static const int FWD4[2][3] = {{1, 0, 0}, {0, 1, 0}};
 static const int FWD8[4][3] = {{1, 0, 0}, {0, 1, 0}, {1, 1, 0}, {-1, 1, 0}};
 static const int FWD6[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+/* Sec. 7.1: the displacements of the synthetic networks in the order listed,
+ * read as (dx, dy), the first pair written (1,0), (0,1) as in FWD4;
+ * connectivity c (code 100 + c) uses the first c/2 */
+static const int FWDP[14][3] = {{1, 0, 0}, {0, 1, 0}, {1, 2, 0}, {2, 1, 0}, {1, 3, 0}, {3, 1, 0}, {2, 3, 0},
+                                {3, 2, 0}, {0, 2, 0}, {2, 0, 0}, {2, 2, 0}, {3, 3, 0}, {3, 4, 0}, {4, 2, 0}};
 
 /* forward half-stencil of a connectivity; returns H (number of half-dirs) */
 int orc_stencil(int conn, const int (**fwd)[3]) {
@@ -37,7 +42,10 @@ int orc_stencil(int conn, const int (**fwd)[3]) {
     case 4: *fwd = FWD4; return 2;
     case 8: *fwd = FWD8; return 4;
     case 6: *fwd = FWD6; return 3;
-    default: *fwd = 0; return 0;
+    default:
+        if (conn >= 108 && conn <= 128 && conn % 4 == 0) { *fwd = FWDP; return (conn - 100) / 2; }
+        *fwd = 0;
+        return 0;
     }
 }
 

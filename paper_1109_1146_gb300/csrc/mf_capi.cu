@@ -112,7 +112,7 @@ __global__ void init_kernel(const Geom g, const DevState st, const int *__restri
         st.tcap[v] = b - m;
         st.lab[v] = 0;
 #pragma unroll
-        for (int d = 0; d < CONN; ++d) {
+        for (int d = 0; d < arcs_of(CONN); ++d) {
             const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
             int c = 0;
             if (in_grid(g, x + dx, y + dy, z + dz)) {
@@ -138,7 +138,7 @@ __global__ void validate_kernel(const Geom g, const int *cs, const int *ct, cons
         if (cs[v] < 0 || ct[v] < 0) f |= 1;
         long long sum = cs[v];
 #pragma unroll
-        for (int d = 0; d < CONN; ++d) {
+        for (int d = 0; d < arcs_of(CONN); ++d) {
             const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
             const bool ing = in_grid(g, x + dx, y + dy, z + dz);
             int c;
@@ -165,13 +165,20 @@ template <int CONN>
 __device__ __forceinline__ bool region_touched(const Geom &g, const DevState &st, int r) {
     if (st.disc[r]) return true;
     const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+    if constexpr (is_paper(CONN)) {  // displacements up to 4 < tile width: the eight surrounding regions
+        for (int qy = ry - 1; qy <= ry + 1; ++qy)
+            for (int qx = rx - 1; qx <= rx + 1; ++qx)
+                if (qx >= 0 && qx < g.RX && qy >= 0 && qy < g.RY && st.disc[qy * g.RX + qx]) return true;
+        return false;
+    } else {
 #pragma unroll
-    for (int d = 0; d < CONN; ++d) {
-        const int qx = rx + arc_dx(CONN, d), qy = ry + arc_dy(CONN, d), qz = rz + arc_dz(CONN, d);
-        if (qx < 0 || qx >= g.RX || qy < 0 || qy >= g.RY || qz < 0 || qz >= g.RZ) continue;
-        if (st.disc[(qz * g.RY + qy) * g.RX + qx]) return true;
+        for (int d = 0; d < arcs_of(CONN); ++d) {
+            const int qx = rx + arc_dx(CONN, d), qy = ry + arc_dy(CONN, d), qz = rz + arc_dz(CONN, d);
+            if (qx < 0 || qx >= g.RX || qy < 0 || qy >= g.RY || qz < 0 || qz >= g.RZ) continue;
+            if (st.disc[(qz * g.RY + qy) * g.RX + qx]) return true;
+        }
+        return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ int hist_bin(int l) { return l < kHistBins ? l : kHistBins; }
@@ -199,7 +206,7 @@ __device__ __forceinline__ void fuse_cell(const Geom &g, const DevState &st, con
     int back_total = 0;
     int du = -1;
 #pragma unroll
-    for (int d = 0; d < CONN; ++d) {
+    for (int d = 0; d < arcs_of(CONN); ++d) {
         const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d), wz = z + arc_dz(CONN, d);
         if (!in_grid(g, wx, wy, wz)) continue;
         const int rw = region_of(g, wx, wy, wz);
@@ -291,13 +298,16 @@ template <int CONN>
 __device__ __forceinline__ void fuse_region_warp(const Geom &g, const DevState &st, const int r) {
     if (!region_touched<CONN>(g, st, r)) return;
     const bool discr = st.disc[r];
-    const int P = surface_cells(g, CONN == 6);
+    // boundary vertices lie on the tile surface, or (the longer displacements
+    // of Sec. 7.1) anywhere in a band of the stencil's width: all cells then
+    const int P = is_paper(CONN) ? g.tx * g.ty : surface_cells(g, CONN == 6);
     for (int p0 = 0; p0 < P; p0 += 32) {  // whole warp per step: the histogram update is a warp operation
         const int p = p0 + (threadIdx.x & 31);
         int bo = -1, bn = -1;
         if (p < P) {
             int lx, ly, lz;
-            surface_cell(g, CONN == 6, p, lx, ly, lz);
+            if (is_paper(CONN)) { lx = p & (g.tx - 1); ly = p >> g.sx; lz = 0; }
+            else surface_cell(g, CONN == 6, p, lx, ly, lz);
             fuse_cell<CONN>(g, st, r, lx, ly, lz, discr, bo, bn);
         }
         hist_update_warp(st.hist, bo, bn);
@@ -327,15 +337,17 @@ __device__ __forceinline__ void post_region_warp(const Geom &g, const DevState &
                 l = g.dinf;
                 st.lab[u] = l;
             }
-            const bool border = lx == 0 || lx == g.tx - 1 || ly == 0 || ly == g.ty - 1 ||
+            constexpr int R = radius_of(CONN);
+            const bool border = lx < R || lx >= g.tx - R || ly < R || ly >= g.ty - R ||
                                 (CONN == 6 && (lz == 0 || lz == g.tz - 1));
             if (touched && border && l < g.dinf && st.exc[u] > 0) act = 1;
         }
     } else {
-        const int P = surface_cells(g, CONN == 6);
+        const int P = is_paper(CONN) ? g.tx * g.ty : surface_cells(g, CONN == 6);
         for (int p = lane; p < P && !act; p += 32) {
             int lx, ly, lz;
-            surface_cell(g, CONN == 6, p, lx, ly, lz);
+            if (is_paper(CONN)) { lx = p & (g.tx - 1); ly = p >> g.sx; lz = 0; }
+            else surface_cell(g, CONN == 6, p, lx, ly, lz);
             const int x = rx * g.tx + lx, y = ry * g.ty + ly, z = rz * g.tz + lz;
             if (!in_grid(g, x, y, z)) continue;
             const size_t u = ((size_t)z * g.Y + y) * g.X + x;
@@ -638,7 +650,7 @@ __global__ void cut_pass_kernel(const Geom g, const DevState st, unsigned char *
             if (!in_grid(g, x, y, z)) continue;
             const size_t u = ((size_t)z * g.Y + y) * g.X + x;
 #pragma unroll
-            for (int d = 0; d < CONN; ++d) {
+            for (int d = 0; d < arcs_of(CONN); ++d) {
                 const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
                 const int wx = x + dx, wy = y + dy, wz = z + dz;
                 if (!in_grid(g, wx, wy, wz)) continue;
@@ -696,7 +708,7 @@ static cudaError_t launch_validate(mf_grid *h, int *flags) {
 }
 template <int CONN>
 static cudaError_t launch_fuse_post(mf_grid *h, bool gap_on, cudaStream_t st) {
-    if (CONN != 6) {
+    if (CONN != 6 && !is_paper(CONN)) {
         const long long items = (long long)h->g.nreg * (2 * h->g.tx + 2 * (h->g.ty - 2));
         const int fb = (int)std::min<long long>((items + 255) / 256, device_sms() * 8);
         fuse2d_kernel<CONN><<<fb, 256, 0, st>>>(h->g, h->st);
@@ -719,8 +731,11 @@ static cudaError_t launch_cut_pass(mf_grid *h, unsigned char *set, int fwd, cuda
     return cudaGetLastError();
 }
 
-#define DISPATCH(conn, fn, ...) \
-    ((conn) == 4 ? fn<4>(__VA_ARGS__) : (conn) == 8 ? fn<8>(__VA_ARGS__) : fn<6>(__VA_ARGS__))
+#define DISPATCH(conn, fn, ...)                                                                              \
+    ((conn) == 4 ? fn<4>(__VA_ARGS__) : (conn) == 8 ? fn<8>(__VA_ARGS__) : (conn) == 6 ? fn<6>(__VA_ARGS__)    \
+     : (conn) == 108 ? fn<108>(__VA_ARGS__) : (conn) == 112 ? fn<112>(__VA_ARGS__)                            \
+     : (conn) == 116 ? fn<116>(__VA_ARGS__) : (conn) == 120 ? fn<120>(__VA_ARGS__)                            \
+     : (conn) == 124 ? fn<124>(__VA_ARGS__) : fn<128>(__VA_ARGS__))
 
 // Optimality certificate of a finished solve, from the original capacities:
 // counts violations of the capacity constraints (r(v,w) >= 0 and
@@ -747,7 +762,7 @@ __global__ void certify_kernel(const Geom g, const DevState st, const int *__res
         tin += (unsigned long long)(b - tc);
         long long e = (long long)(a - m) - (long long)(b - m - tc);
 #pragma unroll
-        for (int d = 0; d < CONN; ++d) {
+        for (int d = 0; d < arcs_of(CONN); ++d) {
             const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d), wz = z + arc_dz(CONN, d);
             const int r = st.cap[(size_t)d * n + v];
             if (!in_grid(g, wx, wy, wz)) {
@@ -799,6 +814,34 @@ static long long boundary_count(const Geom &g) {
     return (long long)g.n - inner(g.X, g.tx) * inner(g.Y, g.ty) * inner(g.Z, g.tz);
 }
 
+// |B| for a stencil with longer displacements: the vertices with an in-grid
+// neighbour in another region, counted on one tile position per class of
+// tiles (interior tiles share one count, edge tiles are counted one by one)
+static long long boundary_count_stencil(const Geom &g, int conn) {
+    const int H = arcs_of(conn) / 2;
+    long long b = 0;
+    for (int ry = 0; ry < g.RY; ++ry)
+        for (int rx = 0; rx < g.RX; ++rx) {
+            const bool interior = rx > 0 && rx + 1 < g.RX && ry > 0 && ry + 1 < g.RY;
+            if (interior && !(rx == 1 && ry == 1)) continue;  // counted once below
+            long long c = 0;
+            for (int ly = 0; ly < g.ty; ++ly)
+                for (int lx = 0; lx < g.tx; ++lx) {
+                    const int x = rx * g.tx + lx, y = ry * g.ty + ly;
+                    if (x >= g.X || y >= g.Y) continue;
+                    bool inB = false;
+                    for (int d = 0; d < 2 * H && !inB; ++d) {
+                        const int wx = x + ((d & 1) ? -paper_dx(d >> 1) : paper_dx(d >> 1));
+                        const int wy = y + ((d & 1) ? -paper_dy(d >> 1) : paper_dy(d >> 1));
+                        if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y) continue;
+                        inB = (wx >> g.sx) != rx || (wy >> g.sy) != ry;
+                    }
+                    c += inB;
+                }
+            b += interior ? c * (long long)(g.RX - 2) * (g.RY - 2) : c;
+        }
+    return b;
+}
 
 extern "C" {
 
@@ -865,8 +908,10 @@ mf_status mf_create_grid_ex(mf_grid **out, int ndim, const int64_t dims[3], int 
     if (!out) return fail(nullptr, MF_EINVAL, "out is NULL");
     *out = nullptr;
     if (!dims) return fail(nullptr, MF_EINVAL, "dims is NULL");
-    if (!((ndim == 2 && (connectivity == 4 || connectivity == 8)) || (ndim == 3 && connectivity == 6)))
-        return fail(nullptr, MF_EINVAL, "connectivity must be 4 or 8 (ndim 2) or 6 (ndim 3)");
+    const bool paper = ndim == 2 && connectivity >= 108 && connectivity <= 128 && connectivity % 4 == 0;
+    if (!((ndim == 2 && (connectivity == 4 || connectivity == 8)) || paper || (ndim == 3 && connectivity == 6)))
+        return fail(nullptr, MF_EINVAL, "connectivity must be 4, 8 or MF_PAPER_STENCIL(8..28) (ndim 2) or 6 (ndim 3)");
+    if (paper && (flags & MF_STATE_HOST)) return fail(nullptr, MF_EINVAL, "MF_STATE_HOST is for the 4/8/6 stencils");
     long long X = dims[0], Y = dims[1], Z = ndim == 3 ? dims[2] : 1;
     if (X < 1 || Y < 1 || Z < 1 || X > INT_MAX || Y > INT_MAX || Z > INT_MAX)
         return fail(nullptr, MF_EINVAL, "dims must be >= 1");
@@ -887,15 +932,15 @@ mf_status mf_create_grid_ex(mf_grid **out, int ndim, const int64_t dims[3], int 
     g->host_state = (flags & MF_STATE_HOST) != 0;
     g->st.host = g->host_state ? 1 : 0;
     g->conn = connectivity;
-    g->H = connectivity / 2;
-    g->N = connectivity;
+    g->H = arcs_of(connectivity) / 2;
+    g->N = arcs_of(connectivity);
     Geom &G = g->g;
     G.X = (int)X; G.Y = (int)Y; G.Z = (int)Z; G.n = nll;
     G.tx = tx; G.ty = ty; G.tz = tz;
     G.sx = __builtin_ctz(tx); G.sy = __builtin_ctz(ty); G.sz = __builtin_ctz(tz);
     G.RX = (int)((X + tx - 1) / tx); G.RY = (int)((Y + ty - 1) / ty); G.RZ = (int)((Z + tz - 1) / tz);
     G.nreg = G.RX * G.RY * G.RZ;
-    g->boundary = boundary_count(G);
+    g->boundary = paper ? boundary_count_stencil(G, connectivity) : boundary_count(G);
     G.dinf = (int)std::max<long long>(g->boundary, 1);
     auto bail = [&](mf_status s) { free_all(g); std::string m = g->err; delete g; g_static_err = m; return s; };
     cudaError_t e = cudaGetDevice(&g->device);
@@ -907,7 +952,7 @@ mf_status mf_create_grid_ex(mf_grid **out, int ndim, const int64_t dims[3], int 
         if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MF_ECUDA); }
         g->own_stream = true;
     }
-    const size_t N = (size_t)connectivity;
+    const size_t N = (size_t)arcs_of(connectivity);
     const size_t n = (size_t)nll;
     // the planes and stored inputs: device memory, or with MF_STATE_HOST pinned
     // host memory that the kernels read and write over NVLink-C2C
@@ -927,8 +972,8 @@ mf_status mf_create_grid_ex(mf_grid **out, int ndim, const int64_t dims[3], int 
         {(void **)&g->st.left_active, (size_t)G.nreg}, {(void **)&g->st.flow_t, 8}, {(void **)&g->st.flow0, 8},
         {(void **)&g->st.hist, (kHistBins + 1) * 4}, {(void **)&g->st.ctr, kCtrWords * 4},
         {(void **)&g->smin, (size_t)n}, {(void **)&g->tset, (size_t)n}, {(void **)&g->c64, sizeof(Counters64)},
-        {(void **)&g->cut_scratch, ndim == 2 ? cut2d_scratch_bytes(G, connectivity)
-                                             : (glr3d_supported(G) ? glr3d_scratch_bytes(G) : 0)}};
+        {(void **)&g->cut_scratch, paper ? stencil_glr_scratch_bytes(G) : ndim == 2 ? cut2d_scratch_bytes(G, connectivity)
+                                                       : (glr3d_supported(G) ? glr3d_scratch_bytes(G) : 0)}};
     for (auto &a : allocs) {
         if (a.bytes == 0) continue;
         e = cudaMalloc(a.p, a.bytes);
@@ -1046,6 +1091,8 @@ static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer) {
     else mf_default_opts(&g->opts);
     if (g->opts.max_rounds <= 0) g->opts.max_rounds = 1 << 16;
     if (g->opts.kernel_variant < 0 || g->opts.kernel_variant > 2) return fail(g, MF_EINVAL, "kernel_variant must be 0, 1 or 2");
+    if (is_paper(g->conn) && (g->opts.warm_start || g->opts.region_reduction || g->opts.boundary_relabel_period > 0))
+        return fail(g, MF_EINVAL, "the Sec. 7.1 stencils run without warm start, region reduction and boundary relabel");
     // Discharge = PRD (kernel_variant 2): distance labels with unit arc lengths
     // reach up to n - 1, so d_inf = n; the global gap on boundary labels relies
     // on ARD's region distances (labels drop only between regions) and is off
@@ -1119,10 +1166,12 @@ static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer) {
 
 // the global relabel (exact region distance), 2D or 3D
 static bool glr_supported(const mf_grid *g) {
+    if (is_paper(g->conn)) return stencil_glr_supported(g->conn, g->g);  // the bit-mask relabels take unit steps only
     return g->ndim == 2 ? glr2d_supported(g->g) : glr3d_supported(g->g);
 }
 // (enqueued without waiting; the levels run are left in st.ctr[kGlrLevels])
 static cudaError_t glr_run(mf_grid *g, cudaStream_t s) {
+    if (is_paper(g->conn)) return stencil_glr(g->conn, g->g, g->st, g->cut_scratch, s);
     return g->ndim == 2 ? glr2d(g->conn, g->g, g->st, g->cut_scratch, s) : glr3d(g->g, g->st, g->cut_scratch, s);
 }
 
@@ -1259,7 +1308,7 @@ static mf_status finish_enqueue(mf_grid *g, cudaStream_t st, bool cut_done = fal
     if (!cut_done) g->h_fin->passes[0] = g->h_fin->passes[1] = 0;
     if (cut_done) {
         // the cut closures ran batched with other grids
-    } else if (g->ndim == 2) {
+    } else if (g->ndim == 2 && !is_paper(g->conn)) {
         CK(cut2d(g->conn, g->g, g->st, g->cut_scratch, g->smin, g->tset, g->h_fin->passes, st));
         g->launches += 5;
     } else if (glr3d_supported(g->g)) {
@@ -1548,6 +1597,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     for (int i = 0; i < count; ++i) {
         if (!grids[i]->caps_set) return fail(g, MF_ESTATE, "a grid of the batch has no capacities");
         if (grids[i]->device != g->device) return fail(g, MF_EINVAL, "all grids must be on one device");
+        if (is_paper(grids[i]->conn)) return fail(g, MF_EINVAL, "the Sec. 7.1 stencils are solved one by one (mf_solve)");
         for (int j = 0; j < i; ++j)
             if (grids[j] == grids[i]) return fail(g, MF_EINVAL, "a grid appears twice in the batch");
     }
@@ -1839,6 +1889,7 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
 mf_status mf_region_reduction(mf_grid *g, const int32_t tile[3], uint8_t *codes, int on_device, int64_t counts[4]) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!codes) return fail(g, MF_EINVAL, "codes is NULL");
+    if (is_paper(g->conn)) return fail(g, MF_EINVAL, "the region reduction is for the 4/8/6 stencils");
     if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
     const int saved = g->opts.max_rounds;
     g->opts.max_rounds = 0;
@@ -1858,7 +1909,7 @@ mf_status mf_region_reduction(mf_grid *g, const int32_t tile[3], uint8_t *codes,
 mf_status mf_warm_features(mf_grid *g, float *x) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!x) return fail(g, MF_EINVAL, "x is NULL");
-    if (g->ndim != 2) return fail(g, MF_EINVAL, "the warm start is for 2D grids");
+    if (g->ndim != 2 || is_paper(g->conn)) return fail(g, MF_EINVAL, "the warm start is for 2D 4/8-connected grids");
     if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
     CK(launch_warm_features(g->conn, g->g, g->cs, g->ct, g->nl, x, g->stream));
     return MF_OK;
@@ -1867,7 +1918,7 @@ mf_status mf_warm_features(mf_grid *g, float *x) {
 mf_status mf_warm_targets(mf_grid *g, float *t) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!t) return fail(g, MF_EINVAL, "t is NULL");
-    if (g->ndim != 2) return fail(g, MF_EINVAL, "the warm start is for 2D grids");
+    if (g->ndim != 2 || is_paper(g->conn)) return fail(g, MF_EINVAL, "the warm start is for 2D 4/8-connected grids");
     if (!g->finished) return fail(g, MF_ESTATE, "no finished solve");
     CK(launch_warm_targets(g->conn, g->g, g->st, g->cs, g->ct, g->nl, t, g->stream));
     return MF_OK;
@@ -1876,6 +1927,7 @@ mf_status mf_warm_targets(mf_grid *g, float *t) {
 // The projection of a prediction, enqueued on stream st; its flag words go to
 // the grid's pinned h_warm (warm_collect reads them after a wait).
 static mf_status warm_enqueue(mf_grid *g, const float *pred, int32_t max_rounds, cudaStream_t st) {
+    if (g->ndim != 2 || is_paper(g->conn)) return fail(g, MF_EINVAL, "the warm start is for 2D 4/8-connected grids");
     g->warm_ready = false;
     g->warm_pending = false;
     const size_t n = (size_t)g->g.n;
@@ -1908,7 +1960,7 @@ static int warm_collect(mf_grid *g) {
 mf_status mf_warm_start(mf_grid *g, const float *pred, int32_t max_rounds, int32_t *rounds) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!pred) return fail(g, MF_EINVAL, "pred is NULL");
-    if (g->ndim != 2) return fail(g, MF_EINVAL, "the warm start is for 2D grids");
+    if (g->ndim != 2 || is_paper(g->conn)) return fail(g, MF_EINVAL, "the warm start is for 2D 4/8-connected grids");
     if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
     mf_status s = warm_enqueue(g, pred, max_rounds, g->stream);
     if (s != MF_OK) return s;

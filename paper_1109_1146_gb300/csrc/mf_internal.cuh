@@ -23,12 +23,32 @@ namespace mf {
 constexpr int kInf = 0x7fffffff;   // "no distance" inside a discharge
 constexpr int kHistBins = 16384;   // exact gap histogram bins; labels >= this share one bin
 
+// The synthetic networks of Sec. 7.1 join every node to the nodes at the
+// displacements of a fixed list; connectivity c takes its first c/2 entries.
+// As forward half-stencil (dx, dy) in the list's order, except that the first
+// pair is swapped to (1,0), (0,1) so that c = 4 is the 4-connected grid.
+// Such a grid has the connectivity code 100 + c (c = 8, 12, ..., 28).
+__host__ __device__ constexpr bool is_paper(int conn) { return conn > 100; }
+__host__ __device__ constexpr int arcs_of(int conn) { return conn > 100 ? conn - 100 : conn; }
+__host__ __device__ constexpr int paper_dx(int h) {
+    return h == 0 ? 1 : h == 1 ? 0 : h == 2 ? 1 : h == 3 ? 2 : h == 4 ? 1 : h == 5 ? 3 : h == 6 ? 2 : h == 7 ? 3
+         : h == 8 ? 0 : h == 9 ? 2 : h == 10 ? 2 : h == 11 ? 3 : h == 12 ? 3 : 4;
+}
+__host__ __device__ constexpr int paper_dy(int h) {
+    return h == 0 ? 0 : h == 1 ? 1 : h == 2 ? 2 : h == 3 ? 1 : h == 4 ? 3 : h == 5 ? 1 : h == 6 ? 3 : h == 7 ? 2
+         : h == 8 ? 2 : h == 9 ? 0 : h == 10 ? 2 : h == 11 ? 3 : h == 12 ? 4 : 2;
+}
+// largest |dx|, |dy| of a stencil (the width of the band of boundary vertices)
+__host__ __device__ constexpr int radius_of(int conn) {
+    return !is_paper(conn) ? 1 : arcs_of(conn) <= 4 ? 1 : arcs_of(conn) <= 8 ? 2 : arcs_of(conn) <= 24 ? 3 : 4;
+}
+
 // forward half-stencil and arc directions (see include/mf.h)
 __host__ __device__ constexpr int fwd_dx(int conn, int h) {
-    return conn == 8 ? (h == 0 ? 1 : h == 1 ? 0 : h == 2 ? 1 : -1) : (h == 0 ? 1 : 0);
+    return is_paper(conn) ? paper_dx(h) : conn == 8 ? (h == 0 ? 1 : h == 1 ? 0 : h == 2 ? 1 : -1) : (h == 0 ? 1 : 0);
 }
 __host__ __device__ constexpr int fwd_dy(int conn, int h) {
-    return conn == 6 ? (h == 1 ? 1 : 0) : (h == 0 ? 0 : 1);
+    return is_paper(conn) ? paper_dy(h) : conn == 6 ? (h == 1 ? 1 : 0) : (h == 0 ? 0 : 1);
 }
 __host__ __device__ constexpr int fwd_dz(int conn, int h) { return (conn == 6 && h == 2) ? 1 : 0; }
 __host__ __device__ constexpr int arc_dx(int conn, int d) { return (d & 1) ? -fwd_dx(conn, d >> 1) : fwd_dx(conn, d >> 1); }
@@ -214,6 +234,15 @@ cudaError_t ensure_smem_attr(const void *kernel, int bytes);
 // launchers (ard_discharge.cu)
 size_t discharge_smem_bytes(int conn, int tx, int ty, int tz);
 bool discharge_supported(int conn, int tx, int ty, int tz);
+// the synthetic stencils of Sec. 7.1 (codes 100 + c), generic kernel, single solves;
+// their exact region-distance relabel (glr_stencil.cu, 32x32 tiles)
+bool stencil_glr_supported(int conn, const Geom &g);
+size_t stencil_glr_scratch_bytes(const Geom &g);
+cudaError_t stencil_glr(int conn, const Geom &g, const DevState &st, void *scratch, cudaStream_t s);
+bool discharge_paper_supported(int conn, int tx, int ty, int tz);
+size_t discharge_paper_smem_bytes(int conn, int tx, int ty, int tz);
+cudaError_t launch_discharge_paper(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
+                                   cudaStream_t stream);
 cudaError_t launch_discharge(int conn, const Geom &g, const DevState &st, const SweepArgs &sa,
                              cudaStream_t stream);
 // cut2d.cu: residual closures S_min / S_max of a 2D grid on bit masks

@@ -18,6 +18,17 @@ LIBPATH = os.path.join(_HERE, "_lib", "libmf.so")
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EOVERFLOW, MF_ESWEEPLIMIT, MF_EROUNDLIMIT, MF_ESTATE = range(8)
 MF_STATE_HOST = 1
+
+
+def paper_stencil(c: int) -> int:
+    """Connectivity code of the Sec. 7.1 synthetic stencil of connectivity c
+    (c = 8, 12, ..., 28; MF_PAPER_STENCIL in mf.h); c = 4 is the plain 4."""
+    return 4 if c == 4 else 100 + c
+
+
+def arcs_of(connectivity: int) -> int:
+    """Arcs per vertex of a connectivity code (2H)."""
+    return connectivity - 100 if connectivity > 100 else connectivity
 STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "MF_ESWEEPLIMIT",
                 "MF_EROUNDLIMIT", "MF_ESTATE"]
 
@@ -230,7 +241,7 @@ class Grid:
         self.dims = dims
         self.conn = connectivity
         self.n = dims[0] * dims[1] * dims[2]
-        self.H = connectivity // 2
+        self.H = arcs_of(connectivity) // 2
         d = (ctypes.c_int64 * 3)(*dims)
         t = None if tile is None else (ctypes.c_int32 * 3)(*(tuple(tile) + (1,) * (3 - len(tile))))
         s = _stream_arg(stream)

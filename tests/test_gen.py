@@ -95,5 +95,35 @@ def test_paper_synthetic_family():
     again = grids.paper_synthetic(60, 40, 3, strength=150)
     assert (again.cs == inst.cs).all() and (again.ct == inst.ct).all()
     import pytest
-    with pytest.raises(ValueError):
-        grids.paper_synthetic(10, 10, 0, connectivity=8)
+    for bad in (6, 10, 32):
+        with pytest.raises(ValueError):
+            grids.paper_synthetic(10, 10, 0, connectivity=bad)
+
+
+# Sec. 7.1, the displacement list as printed (each pair adds 4 to the connectivity)
+PRINTED_DISPLACEMENTS = [(0, 1), (1, 0), (1, 2), (2, 1), (1, 3), (3, 1), (2, 3), (3, 2), (0, 2), (2, 0), (2, 2),
+                         (3, 3), (3, 4), (4, 2)]
+
+
+def test_paper_synthetic_higher_connectivity():
+    assert list(grids.PAPER_DISPLACEMENTS) == PRINTED_DISPLACEMENTS
+    X, Y = 37, 29
+    for c in (8, 12, 16, 20, 24, 28):
+        inst = grids.paper_synthetic(X, Y, 5, strength=1200 // c, connectivity=c)
+        assert inst.conn == 100 + c and inst.nlink.shape == (c // 2, X * Y)
+        # the same terminal links as connectivity 4 with the same seed
+        base = grids.paper_synthetic(X, Y, 5, connectivity=4)
+        assert (inst.cs == base.cs).all() and (inst.ct == base.ct).all()
+        nl = inst.nlink.reshape(c // 2, Y, X)
+        disp = [(1, 0), (0, 1)] + PRINTED_DISPLACEMENTS[2:c // 2]
+        for h, (dx, dy) in enumerate(disp):
+            # an edge per node whose displaced partner lies in the grid, none otherwise
+            yy, xx = np.mgrid[0:Y, 0:X]
+            inside = (xx + dx < X) & (yy + dy < Y)
+            assert (nl[h][inside] == 1200 // c).all() and (nl[h][~inside] == 0).all()
+        # connectivity = the number of edges at a node far from the boundary
+        deg = np.zeros((Y, X), dtype=int)
+        for h, (dx, dy) in enumerate(disp):
+            deg += nl[h] > 0
+            deg[dy:, dx:] += nl[h][: Y - dy, : X - dx] > 0
+        assert deg[10, 10] == c

@@ -232,3 +232,96 @@ def test_boundary_size_of_named_workloads():
     assert oracle.boundary_size((256, 256, 1), 4, (64, 64, 1)) == 3036
     assert oracle.sweep_bound((256, 256, 1), 4, (64, 64, 1)) == 2 * 3036 ** 2 + 1
     assert _closed_form_B((512, 512, 384), (16, 16, 16)) == 512 * 512 * 384 - 450 * 450 * 338
+
+
+# ---- the synthetic stencils of Sec. 7.1 (connectivity code 100 + c) --------
+# the displacement list as printed in Sec. 7.1 (each pair adds 4 to the connectivity)
+PRINTED_DISPLACEMENTS = [(0, 1), (1, 0), (1, 2), (2, 1), (1, 3), (3, 1), (2, 3), (3, 2), (0, 2), (2, 0), (2, 2),
+                         (3, 3), (3, 4), (4, 2)]
+
+
+def _paper_fwd(c):
+    # the list read as (dx, dy), its first pair as (1,0), (0,1) (the 4-connected planes)
+    return [(1, 0), (0, 1)] + PRINTED_DISPLACEMENTS[2:c // 2]
+
+
+def _paper_random(dims, c, seed, cmax=5, tmax=7):
+    X, Y, _ = dims
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cs = rng.integers(0, tmax + 1, X * Y).astype(np.int32)
+    ct = rng.integers(0, tmax + 1, X * Y).astype(np.int32)
+    nl = rng.integers(0, cmax + 1, (c // 2, Y, X)).astype(np.int32)
+    for h, (dx, dy) in enumerate(_paper_fwd(c)):  # no edge whose partner leaves the grid
+        nl[h, max(0, Y - dy):, :] = 0
+        nl[h, :, max(0, X - dx):] = 0
+    return cs, ct, nl.reshape(c // 2, -1)
+
+
+def test_paper_stencil_tables_are_the_printed_list():
+    for c in range(8, 29, 4):
+        assert [(dx, dy) for dx, dy, dz in oracle._FWD[100 + c]] == _paper_fwd(c)
+        assert all(dz == 0 for _, _, dz in oracle._FWD[100 + c])
+
+
+@pytest.mark.parametrize("c", [8, 12, 20, 28])
+@pytest.mark.parametrize("seed", range(4))
+def test_paper_stencil_cut_cost_by_hand(c, seed):
+    # Eq. 1 from an edge list written here from the printed displacements:
+    # pins the C oracle's stencil table (cut_cost) independently of the Python one
+    dims = (9, 7, 1)
+    X, Y, _ = dims
+    cs, ct, nl = _paper_random(dims, c, seed)
+    rng = np.random.Generator(np.random.PCG64(100 + seed))
+    for _ in range(5):
+        S = rng.integers(0, 2, X * Y).astype(np.uint8)
+        cost = int(np.where(S == 1, ct, cs).astype(np.int64).sum())
+        for h, (dx, dy) in enumerate(_paper_fwd(c)):
+            for y in range(Y - dy):
+                for x in range(X - dx):
+                    u, w = y * X + x, (y + dy) * X + x + dx
+                    if S[u] != S[w]:
+                        cost += int(nl[h, u])
+        assert oracle.cut_cost(dims, 100 + c, cs, ct, nl, S) == cost
+
+
+@pytest.mark.parametrize("c", [8, 12, 20, 28])
+@pytest.mark.parametrize("seed", range(4))
+def test_paper_stencil_dinic_vs_brute_force(c, seed):
+    dims = (5, 4, 1)
+    cs, ct, nl = _paper_random(dims, c, seed)
+    r = oracle.maxflow(dims, 100 + c, cs, ct, nl)
+    b = oracle.brute_force(dims, 100 + c, cs, ct, nl)
+    assert r["flow"] == b["min_cost"]
+    np.testing.assert_array_equal(r["smin"], b["smin"])
+    np.testing.assert_array_equal(r["smax"], b["smax"])
+
+
+@pytest.mark.parametrize("c", [8, 28])
+def test_paper_stencil_verifier_accepts_optimum(c):
+    dims = (23, 19, 1)
+    cs, ct, nl = _paper_random(dims, c, 7, cmax=40, tmax=60)
+    st = oracle.maxflow_state(dims, 100 + c, cs, ct, nl)
+    r = oracle.maxflow(dims, 100 + c, cs, ct, nl)
+    assert st["flow"] == r["flow"]
+    ok, msg, info = oracle.verify(dims, 100 + c, cs, ct, nl, st["res"], st["tres"], st["exc"], st["flow"],
+                                  r["smin"], r["smax"])
+    assert ok, msg
+    assert info["cut_cost"] == r["flow"]
+
+
+def test_paper_stencil_boundary_size_by_definition():
+    # |B|: vertices with a stencil neighbour (either direction) in another tile
+    for c in (8, 16, 28):
+        for dims, tile in (((70, 45, 1), (32, 32, 1)), ((100, 96, 1), (32, 32, 1))):
+            X, Y, _ = dims
+            inB = 0
+            for y in range(Y):
+                for x in range(X):
+                    hit = False
+                    for dx, dy in _paper_fwd(c):
+                        for s in (1, -1):
+                            x2, y2 = x + s * dx, y + s * dy
+                            if 0 <= x2 < X and 0 <= y2 < Y and (x2 // 32, y2 // 32) != (x // 32, y // 32):
+                                hit = True
+                    inB += hit
+            assert oracle.boundary_size(dims, 100 + c, tile) == inB
