@@ -102,7 +102,7 @@ def workload_name(side=SIDE):
 def kernel_name(conn, tile, batch=False):
     tx, ty, tz = tile
     if conn == 6:
-        nt = 512 if ty * tz >= 128 else 256
+        nt = 512 if ty * tz >= 128 else 128 if ty * tz == 16 else 256
         return f"ard_discharge3d{'_batch' if batch else ''}_kernel<{ty},{tz},{nt}>"
     return f"ard_discharge2d{'_batch' if batch else ''}_kernel<{conn},{tx},{ty},{256 if tx * ty <= 2048 else 512}>"
 

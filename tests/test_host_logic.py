@@ -94,6 +94,7 @@ def test_batch_kinds_and_the_3d_traffic_figure():
     recorded = [ln.split("=", 1)[1].strip() for ln in open(p) if ln.startswith("bench: kernel_sha256_16=")]
     v = bench.committed_traffic(bench.kernel_name(6, (32, 8, 4), batch=True), (32, 8, 4))
     if recorded == [sha]:
-        assert v is not None and 72.0 <= v < 200.0
+        # rows that did not change are not written back: below the 72 B algorithmic count is possible
+        assert v is not None and 20.0 < v < 200.0
     else:
         assert v is None
