@@ -400,7 +400,6 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
         if (aug) ++stages;
         if (aug && reach) {
             any_aug = true;
-            bool fresh_end = false;  // warp 0: the stage ended on a fresh closure without excess
             for (int round = 0;; ++round) {
                 if (round >= sa.max_rounds) { err = true; break; }
                 if (++epoch >= 32767) {  // deep-layer tags wrap: clear them
@@ -412,26 +411,10 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                 DIAG_MARK();
                 if (warp == 0) {
                     DIAG_ADD(5, 1);
-                    // after a round's pushes the stage check's closure is stale: take
-                    // the closure of T_k afresh (run fills, fewer steps than BFS
-                    // layers); if it holds no excess the stage is done without a
-                    // BFS, else the BFS stops at the deepest excess that can still
-                    // reach T_k instead of exploring all layers for cut-off excess
-                    bool go = true;
-                    if (round > 0) {
-                        u32 sd[RPL];
-                        seed_rows(k, sd);
-#pragma unroll
-                        for (int j = 0; j < RPL; ++j) Cl[j] = 0u;
-                        flood(sd);
-                        go = closure_meets_excess();
-                        fresh_end = !go;
-                    }
-                    int lmax = 0, L = 0;
-                    if (go) {
                     u32 Rm[N][RPL], vis[RPL], fr[RPL], want[RPL];
                     load_masks(Rm);
                     seed_rows(k, fr);
+                    int lmax = 0;
                     bool pending = false;
 #pragma unroll
                     for (int j = 0; j < RPL; ++j) {
@@ -446,7 +429,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                         want[j] = ex & ~vis[j];
                         pending |= want[j] != 0u;
                     }
-                    L = 1;
+                    int L = 1;
                     while (__any_sync(FULL, pending)) {
                         u32 nf[RPL];
                         expand(Rm, fr, nf);
@@ -474,7 +457,6 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                             want[j] &= ~nf[j];
                             pending |= want[j] != 0u;
                         }
-                    }
                     }
                     lmax = __reduce_max_sync(FULL, lmax);
                     if (lane == 0) s_ctl[2] = lmax;
@@ -580,9 +562,7 @@ __device__ __forceinline__ void discharge3d_region(const Geom &g, const DevState
                 DIAG_LAP(3);
                 DIAG_ADD(8, Lmax);
             }
-            // the residual graph changed; Cl is its closure of T_k only if the
-            // stage ended on a fresh flood
-            if (warp == 0) cl_valid = fresh_end;
+            if (warp == 0) cl_valid = false;  // the residual graph changed
         }
         if (kn == INT_MAX) break;
         if (any_aug && (kn > klimit || err)) break;
