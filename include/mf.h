@@ -138,7 +138,7 @@ void mf_default_opts(mf_opts *opts);
  *   tile          region shape {tx, ty, tz}: the fixed partition of V into
  *                 regions R_k of Sec. 3 is the tiling of the grid by this
  *                 shape (edge tiles may be ragged).  Supported: 2D 64x64,
- *                 64x32 and 32x32, 3D 32x16x8, 32x8x8, 32x8x4, 32x4x4 and
+ *                 64x32, 32x32 and 32x16, 3D 32x16x8, 32x8x8, 32x8x4, 32x4x4 and
  *                 32x8x2 (bit-parallel discharge), 16x16x16 and 8x8x8; the
  *                 Sec. 7.1 stencils 32x32 only; NULL or {0,0,0} picks 32x32
  *                 (2D) / 32x8x4 (3D);

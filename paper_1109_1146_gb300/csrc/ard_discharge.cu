@@ -13,6 +13,8 @@ namespace mf {
     X(8, 32, 32, 1, 256)            \
     X(4, 64, 32, 1, 256)            \
     X(8, 64, 32, 1, 256)            \
+    X(4, 32, 16, 1, 128)            \
+    X(8, 32, 16, 1, 128)            \
     X(6, 16, 16, 16, 1024)          \
     X(6, 8, 8, 8, 256)              \
     X(6, 32, 16, 8, 1024)           \

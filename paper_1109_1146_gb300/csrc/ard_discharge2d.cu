@@ -49,23 +49,27 @@ struct Cfg2D {
     static constexpr int N = CONN;
     static constexpr int V = TX * TY;
     static constexpr int NW = NT / 32;                  // warps
-    static constexpr int RPL = TY / 32;                 // rows per lane of the graph warp
+    static constexpr bool PART = TY < 32;               // 32x16 tiles: lanes 16..31 of the graph warp hold no row
+    static constexpr int RPL = PART ? 1 : TY / 32;      // rows per lane of the graph warp
     static constexpr int HW = TX / 32;                  // 32-bit halves per row
     static constexpr int HL = 2 * (TX + 2) + 2 * TY;    // halo cells (B^R plus unused corners)
     static constexpr int PER = 2 * TX + 2 * TY;         // perimeter slots: top, bottom, left, right
     // 8-connected 32x32 tiles: four blocks per SM (64 registers, 24 layers kept
     // as masks so that four fit in shared memory; deeper layers use label tags)
     static constexpr bool DENSE = CONN == 8 && TX == 32;
-    static constexpr int LCAP = DENSE ? 24 : 64;       // BFS layers kept as masks
+    // 32x16 tiles (128 threads): eight blocks per SM, 16 layers kept as masks
+    // at 8-connectivity so that eight fit in shared memory
+    static constexpr int LCAP = (DENSE && PART) ? 16 : DENSE ? 24 : 64;  // BFS layers kept as masks
     // resident blocks per SM the registers must allow (64x32 tiles: two, as
     // their shared memory would allow three)
-    static constexpr int MINB = DENSE ? 4 : (CONN == 4 && TX == 32) ? 4 : (TX * TY == 2048) ? 2 : 1;
+    static constexpr int MINB = PART ? 8 : DENSE ? 4 : (CONN == 4 && TX == 32) ? 4 : (TX * TY == 2048) ? 2 : 1;
     static constexpr size_t smem = (size_t)(N + 3) * V * 4                  // cap, tcap, exc, lab
                                    + (size_t)(N + 4) * TY * 8               // R[N], T, E, inc, vis
                                    + (size_t)(LCAP + 1) * TY * 8            // BFS layers 1..LCAP
                                    + (size_t)(HL + PER) * 4 + TY + 64;      // halo labels, hmin, dirty rows
     static_assert(TX == 32 || TX == 64, "row width must be 32 or 64");
-    static_assert(TY % 32 == 0 && TY <= 64 && V % NT == 0 && NT % 32 == 0, "tile/threads mismatch");
+    static_assert((TY % 32 == 0 || (TY == 16 && TX == 32)) && TY <= 64 && V % NT == 0 && NT % 32 == 0,
+                  "tile/threads mismatch");
 };
 
 // halo cell index of (hx, hy), a cell just outside the tile
@@ -124,6 +128,8 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
     __shared__ unsigned long long s_flow;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // does this lane of the graph warp hold tile rows (all do unless the tile has 16 rows)
+    const bool lrow = !C::PART || lane < TY;
     DIAG_DECL
     const long long diag_t0 = clock64();
     (void)diag_t0;
@@ -264,17 +270,20 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
 #pragma unroll
         for (int h = 0; h < RPL; ++h) {
             const int y = lane + 32 * h;
-            lft[h] = __ballot_sync(0xffffffffu, s_hmin[2 * TX + y] < k);
-            rgt[h] = __ballot_sync(0xffffffffu, s_hmin[2 * TX + TY + y] < k);
+            lft[h] = __ballot_sync(0xffffffffu, y < TY && s_hmin[2 * TX + y] < k);
+            rgt[h] = __ballot_sync(0xffffffffu, y < TY && s_hmin[2 * TX + TY + y] < k);
         }
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
             const int y = lane * RPL + j;
-            u64 s = s_T[y];
-            s |= (u64)((lft[y >> 5] >> (y & 31)) & 1u);
-            s |= (u64)((rgt[y >> 5] >> (y & 31)) & 1u) << (TX - 1);
-            if (y == 0) s |= top;
-            if (y == TY - 1) s |= bot;
+            u64 s = 0;
+            if (lrow) {
+                s = s_T[y];
+                s |= (u64)((lft[y >> 5] >> (y & 31)) & 1u);
+                s |= (u64)((rgt[y >> 5] >> (y & 31)) & 1u) << (TX - 1);
+                if (y == 0) s |= top;
+                if (y == TY - 1) s |= bot;
+            }
             sd[j] = s;
         }
     };
@@ -282,7 +291,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
 #pragma unroll
         for (int j = 0; j < RPL; ++j)
 #pragma unroll
-            for (int d = 0; d < N; ++d) Rm[d][j] = s_R[d * TY + lane * RPL + j];
+            for (int d = 0; d < N; ++d) Rm[d][j] = lrow ? s_R[d * TY + lane * RPL + j] : 0ull;
     };
     // one backward BFS step on the masks: vertices with a residual arc into f
     auto expand = [&](const u64 (&Rm)[N][RPL], const u64 (&f)[RPL], u64 (&out)[RPL]) {
@@ -328,13 +337,15 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
                 any |= f != 0ull;
             }
         }
+        if (lrow) {
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) s_inc[lane * RPL + j] = inc[j];
+            for (int j = 0; j < RPL; ++j) s_inc[lane * RPL + j] = inc[j];
+        }
     };
     auto closure_meets_excess = [&]() -> bool {
         bool m = false;
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) m |= (Cl[j] & s_E[lane * RPL + j]) != 0ull;
+        for (int j = 0; j < RPL; ++j) m |= lrow && (Cl[j] & s_E[lane * RPL + j]) != 0ull;
         return __any_sync(0xffffffffu, m);
     };
     // all threads: label the vertices of s_inc with k
@@ -405,10 +416,12 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
                     for (int j = 0; j < RPL; ++j) {
                         const int y = lane * RPL + j;
                         // excess that can reach T_k lies inside the (older) closure
-                        const u64 ex = s_E[y] & Cl[j];
+                        const u64 ex = lrow ? s_E[y] & Cl[j] : 0ull;
                         vis[j] = fr[j];
-                        s_layer[1 * TY + y] = fr[j];
-                        s_vis[y] = 0ull;  // vertices that receive excess in this round's push
+                        if (lrow) {
+                            s_layer[1 * TY + y] = fr[j];
+                            s_vis[y] = 0ull;  // vertices that receive excess in this round's push
+                        }
                         if (fr[j] & ex) lmax = 1;
                         want[j] = ex & ~vis[j];
                         pending |= want[j] != 0ull;
@@ -432,7 +445,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
                             vis[j] |= nf[j];
                             fr[j] = nf[j];
                             if (L <= LCAP) {
-                                s_layer[L * TY + y] = nf[j];
+                                if (lrow) s_layer[L * TY + y] = nf[j];
                             } else {
                                 const int tg = deep_tag(epoch, L);
                                 for (u64 m = nf[j]; m; m &= m - 1) s_lab[y * TX + __ffsll((long long)m) - 1] = tg;
@@ -584,7 +597,7 @@ __device__ __forceinline__ void discharge2d_region(const Geom &g, const DevState
         }
         DIAG_LAP(9);
     }
-    if (warp == 0) {
+    if (warp == 0 && lrow) {
 #pragma unroll
         for (int j = 0; j < RPL; ++j) s_vis[lane * RPL + j] = Cl[j];
     }
@@ -694,7 +707,8 @@ static cudaError_t launch2d_batch(const Inst *insts, const int2 *items, const in
         const cudaError_t e_at = ensure_smem_attr((const void *)k, (int)C::smem);
         if (e_at != cudaSuccess) return e_at;
     }
-    k<<<blocks, NT, C::smem, s>>>(insts, items, count, head, sa);
+    const int resident = device_sms() * C::MINB;  // persistent blocks: at least as many as can be resident
+    k<<<blocks > resident ? blocks : resident, NT, C::smem, s>>>(insts, items, count, head, sa);
     return cudaGetLastError();
 }
 
@@ -711,7 +725,8 @@ static cudaError_t launch2d(const Geom &g, const DevState &st, const SweepArgs &
 }
 
 bool discharge2d_supported(int conn, int tx, int ty) {
-    return (conn == 4 || conn == 8) && ((tx == 64 && ty == 64) || (tx == 32 && ty == 32) || (tx == 64 && ty == 32));
+    return (conn == 4 || conn == 8) &&
+           ((tx == 64 && ty == 64) || (tx == 32 && ty == 32) || (tx == 64 && ty == 32) || (tx == 32 && ty == 16));
 }
 
 cudaError_t launch_discharge2d_batch(int conn, int tx, int ty, const Inst *insts, const int2 *items,
@@ -723,6 +738,8 @@ cudaError_t launch_discharge2d_batch(int conn, int tx, int ty, const Inst *insts
     if (conn == 8 && tx == 32 && ty == 32) return launch2d_batch<8, 32, 32, 256>(insts, items, count, head, sa, blocks, stream);
     if (conn == 4 && tx == 64 && ty == 32) return launch2d_batch<4, 64, 32, 256>(insts, items, count, head, sa, blocks, stream);
     if (conn == 8 && tx == 64 && ty == 32) return launch2d_batch<8, 64, 32, 256>(insts, items, count, head, sa, blocks, stream);
+    if (conn == 4 && tx == 32 && ty == 16) return launch2d_batch<4, 32, 16, 128>(insts, items, count, head, sa, blocks, stream);
+    if (conn == 8 && tx == 32 && ty == 16) return launch2d_batch<8, 32, 16, 128>(insts, items, count, head, sa, blocks, stream);
     return cudaErrorInvalidValue;
 }
 
@@ -734,6 +751,8 @@ cudaError_t launch_discharge2d(int conn, const Geom &g, const DevState &st, cons
     if (conn == 8 && g.tx == 32 && g.ty == 32) return launch2d<8, 32, 32, 256>(g, st, sa, stream);
     if (conn == 4 && g.tx == 64 && g.ty == 32) return launch2d<4, 64, 32, 256>(g, st, sa, stream);
     if (conn == 8 && g.tx == 64 && g.ty == 32) return launch2d<8, 64, 32, 256>(g, st, sa, stream);
+    if (conn == 4 && g.tx == 32 && g.ty == 16) return launch2d<4, 32, 16, 128>(g, st, sa, stream);
+    if (conn == 8 && g.tx == 32 && g.ty == 16) return launch2d<8, 32, 16, 128>(g, st, sa, stream);
     return cudaErrorInvalidValue;
 }
 

@@ -19,6 +19,8 @@ def _batch_instances():
     out.append((grids.segmentation_2d(64, 64, 2, conn=4), (64, 64, 1)))
     out.append((grids.segmentation_2d(213, 150, 3, conn=4, hard_seed_frac=0.05), (64, 64, 1)))
     out.append((grids.segmentation_2d(97, 61, 4, conn=4), (32, 32, 1)))
+    out.append((grids.segmentation_2d(120, 75, 13, conn=4), (32, 16, 1)))
+    out.append((grids.segmentation_2d(90, 66, 14, conn=8), (32, 16, 1)))
     out.append((grids.segmentation_2d(130, 170, 5, conn=8, hard_seed_frac=0.05), (64, 64, 1)))
     out.append((grids.random_grid((77, 55, 1), 8, 6, cmax=30, tmax=60, p_zero=0.3), (32, 32, 1)))
     out.append((grids.volume_3d(30, 28, 26, 7), (16, 16, 16)))

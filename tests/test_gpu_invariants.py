@@ -70,6 +70,7 @@ def check_state(inst, res, tres, exc, lab, dinf, inB, targets):
 @pytest.mark.parametrize("conn,dims,tile,partial", [
     (4, (192, 160, 1), (64, 64, 1), 0), (8, (150, 130, 1), (64, 64, 1), 0),
     (8, (100, 90, 1), (32, 32, 1), 0), (4, (120, 96, 1), (32, 32, 1), 1), (8, (140, 70, 1), (64, 32, 1), 0),
+    (8, (90, 70, 1), (32, 16, 1), 0), (4, (100, 60, 1), (32, 16, 1), 1),
     (6, (40, 36, 30), (16, 16, 16), 0), (6, (24, 20, 18), (8, 8, 8), 1),
     (6, (70, 36, 20), (32, 16, 8), 0), (6, (40, 20, 18), (32, 8, 8), 1), (6, (50, 20, 14), (32, 8, 4), 0),
     (6, (45, 18, 14), (32, 4, 4), 0), (6, (40, 20, 9), (32, 8, 2), 1)])
@@ -132,7 +133,8 @@ def test_certify_needs_a_finished_solve():
 
 
 @pytest.mark.parametrize("conn,dims,tile", [(4, (96, 80, 1), (32, 32, 1)), (8, (100, 70, 1), (64, 64, 1)),
-                                            (8, (90, 66, 1), (64, 32, 1)), (6, (64, 24, 20), (32, 8, 4)),
+                                            (8, (90, 66, 1), (64, 32, 1)), (8, (80, 70, 1), (32, 16, 1)),
+                                            (6, (64, 24, 20), (32, 8, 4)),
                                             (6, (40, 30, 20), (32, 8, 8)), (6, (50, 22, 18), (32, 4, 4)),
                                             (6, (40, 20, 11), (32, 8, 2))])
 def test_global_relabel_labels_are_region_distances(conn, dims, tile):

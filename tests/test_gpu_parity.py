@@ -35,6 +35,8 @@ CASES = [
     ((75, 90, 1), 8, (32, 32, 1)),
     ((150, 77, 1), 8, (64, 32, 1)),
     ((131, 100, 1), 4, (64, 32, 1)),
+    ((97, 61, 1), 4, (32, 16, 1)),
+    ((75, 90, 1), 8, (32, 16, 1)),
     ((40, 35, 20), 6, (16, 16, 16)),
     ((21, 19, 13), 6, (8, 8, 8)),
     ((70, 37, 21), 6, (32, 16, 8)),
@@ -64,7 +66,8 @@ def test_ragged_multi_region(dims, conn, tile, kind):
                                             ((1, 300, 1), 4, (32, 32, 1)), ((3, 3, 40), 6, (8, 8, 8)),
                                             ((1, 1, 1), 6, (32, 16, 8)), ((33, 1, 9), 6, (32, 8, 8)),
                                             ((32, 16, 8), 6, (32, 16, 8)), ((1, 1, 1), 6, (32, 4, 4)),
-                                            ((33, 5, 3), 6, (32, 8, 2)), ((32, 4, 4), 6, (32, 4, 4))])
+                                            ((33, 5, 3), 6, (32, 8, 2)), ((32, 4, 4), 6, (32, 4, 4)),
+                                            ((1, 40, 1), 8, (32, 16, 1)), ((32, 16, 1), 4, (32, 16, 1))])
 def test_degenerate_shapes(dims, conn, tile):
     inst = grids.random_grid(dims, conn, 5, cmax=25, tmax=40)
     got = gpu_solve(inst, tile=tile)
