@@ -366,8 +366,11 @@ def run_config4(args):
     p_ms, p_stats = timed(plain, kw, 1)
     assert [g.flow_value() for g in hp] == flow_b, "batched and plain solves disagree on a flow value"
     assert all(np.array_equal(g.get_cut(0), s) for g, s in zip(hp, smin_b)), "batched and plain S_min differ"
-    # host-driven batch loop: the same solve with per-kernel-type event timing (roofline)
+    # host-driven batch loop: the same solve with per-kernel-type event timing
+    # (roofline); an NVTX range names it for profilers (ncu --nvtx-include)
+    torch.cuda.nvtx.range_push("batched_host_loop")
     _, h_stats = timed(lambda: mf.solve_batch(hb, default_opts(**sched)), 1, 1)
+    torch.cuda.nvtx.range_pop()
     # end to end through the C ABI from pinned host buffers: H2D of every
     # instance's capacities, the batched solve, D2H of every S_min and flow value
     pin = [(torch.from_numpy(x.cs).pin_memory(), torch.from_numpy(x.ct).pin_memory(),

@@ -292,11 +292,36 @@ __device__ __forceinline__ void surface_cell(const Geom &g, bool is3d, int p, in
     lz = 1 + q / (g.ty - 2);
 }
 
+// region_touched for a whole warp in one round of loads: lane d reads the
+// flag of the neighbour region across arc d (the 3 x 3 block of regions for
+// the Sec. 7.1 stencils), the next lane the region's own
+template <int CONN>
+__device__ __forceinline__ bool region_touched_warp(const Geom &g, const DevState &st, int r) {
+    const int lane = threadIdx.x & 31;
+    const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
+    bool f = false;
+    if constexpr (is_paper(CONN)) {
+        if (lane < 9) {
+            const int qx = rx + lane % 3 - 1, qy = ry + lane / 3 - 1;
+            if (qx >= 0 && qx < g.RX && qy >= 0 && qy < g.RY) f = st.disc[qy * g.RX + qx] != 0;
+        }
+    } else {
+        if (lane < CONN) {
+            const int qx = rx + arc_dx(CONN, lane), qy = ry + arc_dy(CONN, lane), qz = rz + arc_dz(CONN, lane);
+            if (qx >= 0 && qx < g.RX && qy >= 0 && qy < g.RY && qz >= 0 && qz < g.RZ)
+                f = st.disc[(qz * g.RY + qy) * g.RX + qx] != 0;
+        } else if (lane == CONN) {
+            f = st.disc[r] != 0;
+        }
+    }
+    return __any_sync(0xffffffffu, f);
+}
+
 // Fusion of one touched region by one warp over the tile surface (only
 // surface cells can be boundary vertices).
 template <int CONN>
 __device__ __forceinline__ void fuse_region_warp(const Geom &g, const DevState &st, const int r) {
-    if (!region_touched<CONN>(g, st, r)) return;
+    if (!region_touched_warp<CONN>(g, st, r)) return;
     const bool discr = st.disc[r];
     // boundary vertices lie on the tile surface, or (the longer displacements
     // of Sec. 7.1) anywhere in a band of the stencil's width: all cells then
@@ -321,7 +346,7 @@ __device__ __forceinline__ void fuse_region_warp(const Geom &g, const DevState &
 template <int CONN>
 __device__ __forceinline__ void post_region_warp(const Geom &g, const DevState &st, const int r, const int gap) {
     const int lane = threadIdx.x & 31;
-    const bool touched = region_touched<CONN>(g, st, r);
+    const bool touched = region_touched_warp<CONN>(g, st, r);
     if (!touched && gap == 0) return;
     const int rx = r % g.RX, ry = (r / g.RX) % g.RY, rz = r / (g.RX * g.RY);
     int act = touched ? st.left_active[r] : 0;
@@ -537,14 +562,26 @@ __global__ void batch_reset_kernel(const Inst *insts, const unsigned char *done,
 }
 
 // work lists of the active regions, one list per kernel type
+// (warp-uniform steps: the lanes that queue items of one kernel type take
+// their slots with one atomic; neighbouring regions share an instance and so
+// a type, and one atomic per item on the few counters serialised)
 __global__ void batch_items_kernel(const Inst *insts, const int2 *regs, int nregs, const unsigned char *done,
                                    const int *type_of, int cap_per_type, int2 *items, int *cnt) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nregs; i += gridDim.x * blockDim.x) {
-        const int2 w = regs[i];
-        if (done[w.x] || !insts[w.x].st.active[w.y]) continue;
-        const int t = type_of[w.x];
-        const int pos = atomicAdd(&cnt[t], 1);
-        items[(size_t)t * cap_per_type + pos] = w;
+    const int lane = threadIdx.x & 31;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x - lane); i0 < nregs; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + lane;
+        int t = -1;
+        int2 w = make_int2(0, 0);
+        if (i < nregs) {
+            w = regs[i];
+            if (!done[w.x] && insts[w.x].st.active[w.y]) t = type_of[w.x];
+        }
+        const unsigned m = __match_any_sync(0xffffffffu, t);
+        const int leader = __ffs(m) - 1;
+        int base = 0;
+        if (t >= 0 && lane == leader) base = atomicAdd(&cnt[t], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (t >= 0) items[(size_t)t * cap_per_type + base + __popc(m & ((1u << lane) - 1u))] = w;
     }
 }
 
