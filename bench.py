@@ -372,7 +372,8 @@ def run_config4(args):
     _, h_stats = timed(lambda: mf.solve_batch(hb, default_opts(**sched)), 1, 1)
     torch.cuda.nvtx.range_pop()
     # end to end through the C ABI from pinned host buffers: H2D of every
-    # instance's capacities, the batched solve, D2H of every S_min and flow value
+    # instance's capacities (mf_set_caps_batch), the batched solve, D2H of
+    # every S_min and flow value (mf_get_cuts_batch)
     pin = [(torch.from_numpy(x.cs).pin_memory(), torch.from_numpy(x.ct).pin_memory(),
             torch.from_numpy(x.nlink).pin_memory(), torch.empty(x.n, dtype=torch.uint8).pin_memory())
            for x in insts]
@@ -381,13 +382,9 @@ def run_config4(args):
     for k in range(ke + 1):
         barrier()
         t0 = time.perf_counter()
-        for g, (a, b, c, _) in zip(hb, pin):
-            g.set_caps(a, b, c)
+        mf.set_caps_batch(hb, [(a, b, c) for a, b, c, _ in pin])
         mf.solve_batch(hb, bopts)
-        fl = []
-        for g, (_, _, _, out) in zip(hb, pin):
-            g.get_cut(0, out=out)
-            fl.append(g.flow_value())
+        _, fl = mf.get_cuts_batch(hb, 0, [p[3] for p in pin])
         t1 = time.perf_counter()
         if k > 0:
             e2e_ms.append((t1 - t0) * 1e3)

@@ -184,6 +184,15 @@ mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const in
                       int on_device);
 
 /*
+ * mf_set_caps for count grids: the copies and validations of all grids are
+ * enqueued first, then one wait per distinct stream; cs[i], ct[i], nlink[i]
+ * as in mf_set_caps for grid i.  The first grid that fails decides the
+ * status (its message is also left on grids[0]); grids before it are set.
+ */
+mf_status mf_set_caps_batch(mf_grid *const *grids, int count, const int32_t *const *cs, const int32_t *const *ct,
+                            const int32_t *const *nlink, int on_device);
+
+/*
  * Solve: Init (Sec. 2: saturate every s-link; the part min(cs, ct) of each
  * vertex is sent s -> v -> t at once and counted in the flow value), then
  * sweeps of Algorithm 2 with Discharge = ARD until no vertex is active, then
@@ -287,6 +296,15 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
  * out is uint8[n] (host, or device when on_device = 1).
  */
 mf_status mf_get_cut(mf_grid *g, uint8_t *out, int which, int on_device);
+
+/*
+ * mf_get_cut for count grids with one wait per distinct stream: out[i] is
+ * uint8[n_i] for grid i; flows, if not NULL, int64[count] receives every
+ * grid's flow value.  MF_ESTATE if a grid has no finished solve (nothing is
+ * copied from that grid on); MF_EINVAL for NULL arrays or entries.
+ */
+mf_status mf_get_cuts_batch(mf_grid *const *grids, int count, int which, uint8_t *const *out, int on_device,
+                            int64_t *flows);
 
 /* |f| = sum of min(cs, ct) plus all flow the sweeps sent into t (int64). */
 mf_status mf_flow_value(mf_grid *g, int64_t *out);

@@ -53,6 +53,7 @@ struct mf_grid {
     int graph_key[5] = {-1, -1, -1, -1, -1};          // options baked into the graph
     Counters64 *c64 = nullptr;
     int *h_ctr = nullptr;                             // pinned mirror of st.ctr
+    bool flow_cached = false;                         // stats.flow_value is that of the current state
     struct FinishHost {                               // pinned: results of the cut extraction, read after a sync
         int passes[2];
         long long f0;
@@ -1044,27 +1045,78 @@ mf_status mf_destroy(mf_grid *g) {
     return MF_OK;
 }
 
-mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const int32_t *nlink, int on_device) {
-    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+// mf_set_caps in two halves: the copies and the validation kernel enqueued
+// on the grid's stream, then (after a wait) the verdict from the flags
+static mf_status set_caps_enqueue(mf_grid *g, const int32_t *cs, const int32_t *ct, const int32_t *nlink) {
     if (!cs || !ct || !nlink) return fail(g, MF_EINVAL, "cs, ct and nlink must be non-NULL");
     const size_t n = (size_t)g->g.n, H = (size_t)g->H;
     g->caps_set = false;
     g->begun = g->finished = false;
+    g->flow_cached = false;
     g->warm_ready = false;
-    (void)on_device;  // unified addressing: the copy direction follows from the pointers
-    const cudaMemcpyKind kind = cudaMemcpyDefault;
+    const cudaMemcpyKind kind = cudaMemcpyDefault;  // unified addressing: the direction follows from the pointers
     CK(cudaMemcpyAsync(g->cs, cs, n * 4, kind, g->stream));
     CK(cudaMemcpyAsync(g->ct, ct, n * 4, kind, g->stream));
     CK(cudaMemcpyAsync(g->nl, nlink, H * n * 4, kind, g->stream));
     CK(cudaMemsetAsync(g->st.ctr, 0, kCtrWords * 4, g->stream));
     CK(DISPATCH(g->conn, launch_validate, g, &g->st.ctr[kError]));
     CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
+    return MF_OK;
+}
+static mf_status set_caps_verdict(mf_grid *g) {
     const int f = g->h_ctr[kError];
     if (f & 1) return fail(g, MF_EINVAL, "negative capacity");
     if (f & 2) return fail(g, MF_EINVAL, "nonzero neighbour capacity leaving the grid");
     if (f & 4) return fail(g, MF_EOVERFLOW, "capacities could overflow int32");
     g->caps_set = true;
+    return MF_OK;
+}
+
+mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const int32_t *nlink, int on_device) {
+    if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
+    (void)on_device;
+    mf_status st = set_caps_enqueue(g, cs, ct, nlink);
+    if (st != MF_OK) return st;
+    CK(cudaStreamSynchronize(g->stream));
+    return set_caps_verdict(g);
+}
+
+// one wait per distinct stream of the grids
+static cudaError_t sync_streams(mf_grid *const *grids, int count) {
+    std::vector<cudaStream_t> done;
+    for (int i = 0; i < count; ++i) {
+        const cudaStream_t s = grids[i]->stream;
+        if (std::find(done.begin(), done.end(), s) != done.end()) continue;
+        done.push_back(s);
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+mf_status mf_set_caps_batch(mf_grid *const *grids, int count, const int32_t *const *cs, const int32_t *const *ct,
+                            const int32_t *const *nlink, int on_device) {
+    mf_grid *g = nullptr;
+    (void)on_device;
+    if (!grids || count < 1 || !cs || !ct || !nlink) return fail(nullptr, MF_EINVAL, "bad batch arguments");
+    for (int i = 0; i < count; ++i)
+        if (!grids[i]) return fail(nullptr, MF_EINVAL, "null grid in the batch");
+    g = grids[0];
+    for (int i = 0; i < count; ++i) {
+        mf_status st = set_caps_enqueue(grids[i], cs[i], ct[i], nlink[i]);
+        if (st != MF_OK) {
+            if (grids[i] != g) fail(g, st, std::string("grid ") + std::to_string(i) + ": " + grids[i]->err);
+            return st;
+        }
+    }
+    CK(sync_streams(grids, count));
+    for (int i = 0; i < count; ++i) {
+        mf_status st = set_caps_verdict(grids[i]);
+        if (st != MF_OK) {
+            if (grids[i] != g) fail(g, st, std::string("grid ") + std::to_string(i) + ": " + grids[i]->err);
+            return st;
+        }
+    }
     return MF_OK;
 }
 
@@ -1255,6 +1307,7 @@ static mf_status br_step(mf_grid *g, cudaStream_t s, int *active, BrResult *r) {
 }
 
 static mf_status run_sweep(mf_grid *g, int32_t *active_out) {
+    g->flow_cached = false;
     SweepArgs sa{};
     sa.sweep = g->sweep;
     sa.partial = g->opts.partial_discharge;
@@ -1393,6 +1446,7 @@ static void finish_collect(mf_grid *g) {
     g->stats.launches = g->launches;
     g->red_konst = g->reduced ? (long long)g->h_red[4] : 0;
     g->finished = true;
+    g->flow_cached = true;
 }
 
 mf_status mf_finish(mf_grid *g) {
@@ -2046,10 +2100,31 @@ mf_status mf_get_cut(mf_grid *g, uint8_t *out, int which, int on_device) {
     return MF_OK;
 }
 
+mf_status mf_get_cuts_batch(mf_grid *const *grids, int count, int which, uint8_t *const *out, int on_device,
+                            int64_t *flows) {
+    if (!grids || count < 1 || !out || (which != 0 && which != 1)) return fail(nullptr, MF_EINVAL, "bad batch arguments");
+    for (int i = 0; i < count; ++i)
+        if (!grids[i] || !out[i]) return fail(nullptr, MF_EINVAL, "null grid or output in the batch");
+    mf_grid *g = grids[0];
+    for (int i = 0; i < count; ++i) {
+        mf_grid *h = grids[i];
+        if (!h->finished) return fail(g, MF_ESTATE, std::string("grid ") + std::to_string(i) + " has no finished solve");
+        CK(cudaMemcpyAsync(out[i], which == 0 ? h->smin : h->tset, (size_t)h->g.n,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+        if (flows) flows[i] = h->stats.flow_value;
+    }
+    if (!on_device) CK(sync_streams(grids, count));
+    return MF_OK;
+}
+
 mf_status mf_flow_value(mf_grid *g, int64_t *out) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!out) return fail(g, MF_EINVAL, "out is NULL");
     if (!g->begun) return fail(g, MF_ESTATE, "no solve");
+    if (g->flow_cached) {  // read back with the finished solve's results
+        *out = g->stats.flow_value;
+        return MF_OK;
+    }
     long long f0 = 0;
     unsigned long long ft = 0;
     CK(cudaMemcpyAsync(&f0, g->st.flow0, 8, cudaMemcpyDeviceToHost, g->stream));

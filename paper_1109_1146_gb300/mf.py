@@ -33,8 +33,8 @@ STATUS_NAMES = ["MF_OK", "MF_EINVAL", "MF_ENOMEM", "MF_ECUDA", "MF_EOVERFLOW", "
                 "MF_EROUNDLIMIT", "MF_ESTATE"]
 
 # every symbol include/mf.h declares
-EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_create_grid_ex", "mf_set_caps", "mf_solve", "mf_begin", "mf_sweep",
-           "mf_finish", "mf_boundary_relabel", "mf_region_reduction", "mf_get_cut", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
+EXPORTS = ["mf_default_opts", "mf_create_grid", "mf_create_grid_ex", "mf_set_caps", "mf_set_caps_batch", "mf_solve", "mf_begin", "mf_sweep",
+           "mf_finish", "mf_boundary_relabel", "mf_region_reduction", "mf_get_cut", "mf_get_cuts_batch", "mf_flow_value", "mf_get_residual", "mf_get_labels", "mf_destroy",
            "mf_last_error", "mf_min_cut_2d_noalloc", "mf_solve_batch", "mf_warm_features", "mf_warm_targets",
            "mf_warm_start", "mf_warm_start_batch", "mf_certify", "mf_get_flow", "mf_load_model", "mf_cnn_create", "mf_cnn_destroy", "mf_cnn_last_error", "mf_cnn_num_params",
            "mf_cnn_get_params", "mf_cnn_set_params", "mf_cnn_get_grads", "mf_cnn_forward", "mf_cnn_infer",
@@ -82,6 +82,8 @@ SIGNATURES = {
     "mf_create_grid": (_I, [ctypes.POINTER(_P), _I, _P, _I, _P, _P]),
     "mf_create_grid_ex": (_I, [ctypes.POINTER(_P), _I, _P, _I, _P, _P, _I]),
     "mf_set_caps": (_I, [_P, _P, _P, _P, _I]),
+    "mf_set_caps_batch": (_I, [_P, _I, _P, _P, _P, _I]),
+    "mf_get_cuts_batch": (_I, [_P, _I, _I, _P, _I, _P]),
     "mf_solve": (_I, [_P, ctypes.POINTER(mf_opts), ctypes.POINTER(mf_stats)]),
     "mf_begin": (_I, [_P, ctypes.POINTER(mf_opts)]),
     "mf_sweep": (_I, [_P, ctypes.POINTER(ctypes.c_int32)]),
@@ -216,6 +218,49 @@ def warm_start_batch(grids, preds, max_rounds=0):
     if st != MF_OK:
         raise MFError(st, lib.mf_last_error(grids[0]._h).decode())
     return list(rounds)
+
+
+def set_caps_batch(grids, caps):
+    """mf_set_caps_batch: caps[i] = (cs, ct, nlink) for grids[i] (all host or
+    all device buffers); one wait for all grids."""
+    lib = load()
+    n = len(grids)
+    arr = (ctypes.c_void_p * n)(*[g._h.value for g in grids])
+    pcs, pct, pnl, devs = [], [], [], set()
+    for cs, ct, nl in caps:
+        for buf, out in ((cs, pcs), (ct, pct), (nl, pnl)):
+            p, dev = _ptr(buf)
+            out.append(p)
+            devs.add(dev)
+    if len(devs) != 1:
+        raise ValueError("the capacities must all be host or all be device buffers")
+    st = lib.mf_set_caps_batch(arr, n, (ctypes.c_void_p * n)(*pcs), (ctypes.c_void_p * n)(*pct),
+                               (ctypes.c_void_p * n)(*pnl), devs.pop())
+    if st != MF_OK:
+        raise MFError(st, lib.mf_last_error(grids[0]._h).decode())
+
+
+def get_cuts_batch(grids, which=0, outs=None):
+    """mf_get_cuts_batch: the cut `which` of every grid into outs (uint8
+    buffers, all host or all device; allocated on the host if None) and every
+    flow value; one wait for all grids.  Returns (outs, flows)."""
+    lib = load()
+    n = len(grids)
+    if outs is None:
+        outs = [np.empty(g.n, dtype=np.uint8) for g in grids]
+    arr = (ctypes.c_void_p * n)(*[g._h.value for g in grids])
+    ptrs, devs = [], set()
+    for o in outs:
+        p, dev = _ptr(o)
+        ptrs.append(p)
+        devs.add(dev)
+    if len(devs) != 1:
+        raise ValueError("the outputs must all be host or all be device buffers")
+    flows = (ctypes.c_int64 * n)()
+    st = lib.mf_get_cuts_batch(arr, n, int(which), (ctypes.c_void_p * n)(*ptrs), devs.pop(), flows)
+    if st != MF_OK:
+        raise MFError(st, lib.mf_last_error(grids[0]._h).decode())
+    return outs, list(flows)
 
 
 def solve_batch(grids, opts: mf_opts | None = None):

@@ -83,3 +83,56 @@ def test_batch_rejects_bad_input():
     with pytest.raises(mf.MFError):
         mf.solve_batch([a, a])  # the same grid twice
     a.close()
+
+
+def test_batched_set_caps_and_cut_reads():
+    # mf_set_caps_batch / mf_get_cuts_batch: the same state and results as the
+    # per-grid calls, host and device buffers, errors reported for the batch
+    import torch
+    insts = [grids.segmentation_2d(90, 70, 21, conn=4), grids.volume_3d(40, 30, 20, 22),
+             grids.random_grid((70, 50, 1), 8, 23, cmax=20, tmax=40, p_zero=0.3)]
+    refs = [oracle.solve_instance(x) for x in insts]
+    handles = [Grid(x.dims, x.conn) for x in insts]
+    for device in (False, True):
+        caps = [(x.cs, x.ct, x.nlink) for x in insts]
+        if device:
+            caps = [tuple(torch.from_numpy(a).cuda() for a in c) for c in caps]
+        mf.set_caps_batch(handles, caps)
+        mf.solve_batch(handles, default_opts(graph_loop=1))
+        outs = None if not device else [torch.empty(x.n, dtype=torch.uint8, device="cuda") for x in insts]
+        outs, flows = mf.get_cuts_batch(handles, 0, outs)
+        smax, _ = mf.get_cuts_batch(handles, 1)
+        for x, ref, o, f, sm, g in zip(insts, refs, outs, flows, smax, handles):
+            o = o.cpu().numpy() if device else o
+            assert f == ref["flow"] == g.flow_value()
+            np.testing.assert_array_equal(o, ref["smin"])
+            np.testing.assert_array_equal(sm, ref["smax"])
+    # a negative capacity in the second grid: the batch fails with MF_EINVAL
+    bad = insts[1].cs.copy()
+    bad[5] = -1
+    with pytest.raises(mf.MFError) as ei:
+        mf.set_caps_batch(handles, [(insts[0].cs, insts[0].ct, insts[0].nlink), (bad, insts[1].ct, insts[1].nlink),
+                                    (insts[2].cs, insts[2].ct, insts[2].nlink)])
+    assert ei.value.status == mf.MF_EINVAL
+    # a grid without a finished solve: MF_ESTATE
+    with pytest.raises(mf.MFError) as ei:
+        mf.get_cuts_batch(handles, 0)
+    assert ei.value.status == mf.MF_ESTATE
+    for g in handles:
+        g.close()
+
+
+def test_flow_value_follows_extra_sweeps():
+    # the flow value read back with a finished solve is returned without a
+    # device read; a later sweep invalidates it
+    inst = grids.segmentation_2d(120, 90, 24, conn=4)
+    ref = oracle.solve_instance(inst)
+    with Grid(inst.dims, 4) as g:
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        g.begin(default_opts())
+        g.sweep()
+        partial = g.flow_value()
+        while g.sweep():
+            pass
+        g.finish()
+        assert g.flow_value() == ref["flow"] >= partial
