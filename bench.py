@@ -736,8 +736,9 @@ def run_prd(args):
     U[-500, 500], constant strength): sweeps and device ms of both on the same
     instances and schedule (global relabel every 4 sweeps), over strength,
     size and connectivity (at connectivity c the strength is 150 * 8 / c, as
-    in the paper's connectivity series), and for connectivity 4 over the
-    region size; every pair must reach the same flow value."""
+    in the paper's connectivity series), and over the region size (the
+    number of regions) at connectivity 8 and 4; every pair must reach the
+    same flow value."""
     from gen import grids
     from paper_1109_1146_gb300 import Grid, default_opts
 
@@ -746,7 +747,8 @@ def run_prd(args):
     cases += [(n, 150, 8, t32) for n in (250, 500, 2000)]                 # size
     cases += [(1000, 1200 // c, c, t32) for c in (4, 12, 16, 20, 24, 28)]  # connectivity
     cases += [(1000, s, 4, t32) for s in (20, 150, 400, 1000)]
-    cases += [(1000, 150, 4, t) for t in ((64, 64, 1), (64, 32, 1))]      # region size (4-connected)
+    cases += [(1000, 150, 8, t) for t in ((64, 32, 1), (64, 64, 1))]      # number of regions, connectivity 8
+    cases += [(1000, 150, 4, t) for t in ((64, 64, 1), (64, 32, 1))]      # and 4
     for side, strength, conn, tile in cases:
         rows = {}
         for seed in range(args.prd_seeds):

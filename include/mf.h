@@ -30,7 +30,8 @@
  *       h6 = (2,3) h7 = (3,2) h8 = (0,2) h9 = (2,0) h10 = (2,2) h11 = (3,3)
  *       h12 = (3,4) h13 = (4,2)
  *     (the list's first pair swapped so that c = 4 would be the 4-connected
- *     grid) with H = c/2; such grids are solved one by one on 32x32 tiles with
+ *     grid) with H = c/2; such grids are solved one by one on 32x32 tiles (or
+ *     64x32 / 64x64 at c = 8) with
  *     the generic region discharge (kernel_variant 0 or 1 = ARD, 2 = PRD),
  *     without the global relabel, warm start, region reduction, boundary
  *     relabel, batches or MF_STATE_HOST;
@@ -140,7 +141,8 @@ void mf_default_opts(mf_opts *opts);
  *                 shape (edge tiles may be ragged).  Supported: 2D 64x64,
  *                 64x32, 32x32 and 32x16, 3D 32x16x8, 32x8x8, 32x8x4, 32x4x4 and
  *                 32x8x2 (bit-parallel discharge), 16x16x16 and 8x8x8; the
- *                 Sec. 7.1 stencils 32x32 only; NULL or {0,0,0} picks 32x32
+ *                 Sec. 7.1 stencils 32x32 (and 64x32, 64x64 at connectivity
+ *                 8); NULL or {0,0,0} picks 32x32
  *                 (2D) / 32x8x4 (3D);
  *   cuda_stream   cudaStream_t to order all work on, or NULL for a stream
  *                 owned by the handle (non-blocking: device buffers that

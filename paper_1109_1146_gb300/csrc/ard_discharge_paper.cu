@@ -1,6 +1,7 @@
 // The generic region discharge (ard_generic.cuh) for the synthetic networks
 // of Sec. 7.1 (connectivity codes 100 + c, c = 8 .. 28; displacements up to
-// 4): 32x32 tiles, single solves.  A translation unit of its own, since the
+// 4): 32x32 tiles, and 64x32 / 64x64 at connectivity 8 (the paper's default,
+// for the dependence on the number of regions); single solves.  A translation unit of its own, since the
 // 28-arc instantiations are the slowest code of the library to compile.
 #include "ard_generic.cuh"
 
@@ -14,7 +15,9 @@ namespace mf {
     X(116, 32, 32, 1, 256)          \
     X(120, 32, 32, 1, 256)          \
     X(124, 32, 32, 1, 256)          \
-    X(128, 32, 32, 1, 256)
+    X(128, 32, 32, 1, 256)          \
+    X(108, 64, 32, 1, 256)          \
+    X(108, 64, 64, 1, 1024)
 
 bool discharge_paper_supported(int conn, int tx, int ty, int tz) {
 #define X(c, a, b, z, t) if (conn == c && tx == a && ty == b && tz == z) return true;

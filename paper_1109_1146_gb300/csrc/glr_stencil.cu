@@ -9,7 +9,7 @@
 // closes each region under its inner residual arcs.  A vertex first reached
 // at level l gets d := max(d, l); vertices never reached get d_inf (as the 2D
 // and 3D relabels).  One thread block per region and level, the region's set
-// in shared memory (32x32 tiles: one byte per vertex); all levels in one
+// in shared memory (one byte per vertex of the tile); all levels in one
 // cooperative launch with a grid barrier per level.
 #include <algorithm>
 #include <climits>
@@ -22,19 +22,17 @@ namespace mf {
 
 namespace cg = cooperative_groups;
 
-constexpr int kStTile = 32;                       // the stencil grids' tile side
-constexpr int kStV = kStTile * kStTile;
-
 // level `level` of region r: S_l(r) from S_{l-1} (in; unused at level 0) into
 // out; raises the labels of the vertices it adds; returns whether it added any
-template <int CONN>
+template <int CONN, int TX, int TY>
 __device__ bool stencil_region_level(const Geom &g, const DevState &st, int r, const unsigned char *in,
                                      unsigned char *out, int level, unsigned char *m) {
-    constexpr int N = arcs_of(CONN);
+    constexpr int N = arcs_of(CONN), V = TX * TY;
+    constexpr int SX = TX == 64 ? 6 : 5;  // log2 TX
     const int rx = r % g.RX, ry = r / g.RX;
     const size_t n = (size_t)g.n;
-    for (int i = threadIdx.x; i < kStV; i += blockDim.x) {
-        const int x = rx * kStTile + (i & (kStTile - 1)), y = ry * kStTile + (i >> 5);
+    for (int i = threadIdx.x; i < V; i += blockDim.x) {
+        const int x = rx * TX + (i & (TX - 1)), y = ry * TY + (i >> SX);
         unsigned char s = 0;
         if (x < g.X && y < g.Y) {
             const size_t v = (size_t)y * g.X + x;
@@ -46,7 +44,7 @@ __device__ bool stencil_region_level(const Geom &g, const DevState &st, int r, c
                 for (int d = 0; d < N && !s; ++d) {  // a residual arc into S_{l-1} of another region
                     const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d);
                     if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y) continue;
-                    if ((wx >> 5) == rx && (wy >> 5) == ry) continue;
+                    if (wx / TX == rx && wy / TY == ry) continue;
                     s = in[(size_t)wy * g.X + wx] && st.cap[(size_t)d * n + v] > 0;
                 }
             }
@@ -57,18 +55,18 @@ __device__ bool stencil_region_level(const Geom &g, const DevState &st, int r, c
     // closure inside the region (monotone: a stale read only delays)
     for (;;) {
         int ch = 0;
-        for (int i = threadIdx.x; i < kStV; i += blockDim.x) {
+        for (int i = threadIdx.x; i < V; i += blockDim.x) {
             if (m[i]) continue;
-            const int lx = i & (kStTile - 1), ly = i >> 5;
-            const int x = rx * kStTile + lx, y = ry * kStTile + ly;
+            const int lx = i & (TX - 1), ly = i >> SX;
+            const int x = rx * TX + lx, y = ry * TY + ly;
             if (x >= g.X || y >= g.Y) continue;
             const size_t v = (size_t)y * g.X + x;
 #pragma unroll
             for (int d = 0; d < N; ++d) {
                 const int nx = lx + arc_dx(CONN, d), ny = ly + arc_dy(CONN, d);
-                if (nx < 0 || nx >= kStTile || ny < 0 || ny >= kStTile) continue;
+                if (nx < 0 || nx >= TX || ny < 0 || ny >= TY) continue;
                 if (x + arc_dx(CONN, d) >= g.X || y + arc_dy(CONN, d) >= g.Y) continue;
-                if (m[ny * kStTile + nx] && st.cap[(size_t)d * n + v] > 0) {
+                if (m[ny * TX + nx] && st.cap[(size_t)d * n + v] > 0) {
                     m[i] = 1;
                     ch = 1;
                     break;
@@ -78,8 +76,8 @@ __device__ bool stencil_region_level(const Geom &g, const DevState &st, int r, c
         if (!__syncthreads_or(ch)) break;
     }
     int grew = 0;
-    for (int i = threadIdx.x; i < kStV; i += blockDim.x) {
-        const int x = rx * kStTile + (i & (kStTile - 1)), y = ry * kStTile + (i >> 5);
+    for (int i = threadIdx.x; i < V; i += blockDim.x) {
+        const int x = rx * TX + (i & (TX - 1)), y = ry * TY + (i >> SX);
         if (x >= g.X || y >= g.Y) continue;
         const size_t v = (size_t)y * g.X + x;
         out[v] = m[i];
@@ -92,12 +90,12 @@ __device__ bool stencil_region_level(const Geom &g, const DevState &st, int r, c
 }
 
 // all levels in one cooperative launch; flags[3] triple-buffered "grew" words
-template <int CONN>
+template <int CONN, int TX, int TY>
 __global__ void stencil_glr_levels_kernel(const Geom g, const DevState st, unsigned char *A, unsigned char *B,
                                           int *flags, int *levels_out, int max_levels) {
     cg::grid_group grid = cg::this_grid();
-    __shared__ unsigned char m[kStV];
-    for (int r = blockIdx.x; r < g.nreg; r += gridDim.x) stencil_region_level<CONN>(g, st, r, nullptr, B, 0, m);
+    __shared__ unsigned char m[TX * TY];
+    for (int r = blockIdx.x; r < g.nreg; r += gridDim.x) stencil_region_level<CONN, TX, TY>(g, st, r, nullptr, B, 0, m);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         flags[1] = 0;
         flags[2] = 0;
@@ -108,7 +106,8 @@ __global__ void stencil_glr_levels_kernel(const Geom g, const DevState st, unsig
         const unsigned char *in = (level & 1) ? B : A;
         unsigned char *out = (level & 1) ? A : B;
         bool grew = false;
-        for (int r = blockIdx.x; r < g.nreg; r += gridDim.x) grew |= stencil_region_level<CONN>(g, st, r, in, out, level, m);
+        for (int r = blockIdx.x; r < g.nreg; r += gridDim.x)
+            grew |= stencil_region_level<CONN, TX, TY>(g, st, r, in, out, level, m);
         if (grew && threadIdx.x == 0) atomicOr(&flags[level % 3], 1);
         if (blockIdx.x == 0 && threadIdx.x == 0) flags[(level + 1) % 3] = 0;
         grid.sync();
@@ -135,14 +134,14 @@ __global__ void stencil_glr_finish_kernel(const Geom g, const DevState st, const
             st.lab[v] = l;
         }
         if (l >= g.dinf) continue;
-        const int r = (y >> 5) * g.RX + (x >> 5);
+        const int r = (y >> g.sy) * g.RX + (x >> g.sx);
         if (st.exc[v] > 0) st.active[r] = 1;
         bool inB = false;
 #pragma unroll
         for (int d = 0; d < arcs_of(CONN); ++d) {
             const int wx = x + arc_dx(CONN, d), wy = y + arc_dy(CONN, d);
             if (wx < 0 || wx >= g.X || wy < 0 || wy >= g.Y) continue;
-            inB |= (wy >> 5) * g.RX + (wx >> 5) != r;
+            inB |= (wy >> g.sy) * g.RX + (wx >> g.sx) != r;
         }
         if (!inB) continue;
         if (l < SB) atomicAdd(&sh[l], 1);
@@ -160,12 +159,12 @@ __global__ void stencil_glr_count_kernel(const DevState st, int nreg) {
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
 }
 
-template <int CONN>
+template <int CONN, int TX, int TY>
 static cudaError_t stencil_glr_impl(const Geom &g, const DevState &st, void *scratch, cudaStream_t s) {
     unsigned char *A = (unsigned char *)scratch, *B = A + g.n;
     int max_blocks = 0;
     {
-        const cudaError_t e_mb = coop_max_blocks((const void *)stencil_glr_levels_kernel<CONN>, 256, 0, &max_blocks);
+        const cudaError_t e_mb = coop_max_blocks((const void *)stencil_glr_levels_kernel<CONN, TX, TY>, 256, 0, &max_blocks);
         if (e_mb != cudaSuccess) return e_mb;
     }
     const int nblocks = std::max(1, std::min(g.nreg, max_blocks));
@@ -175,7 +174,7 @@ static cudaError_t stencil_glr_impl(const Geom &g, const DevState &st, void *scr
     Geom gg = g;
     DevState ss = st;
     void *args[] = {&gg, &ss, &A, &B, &flags, &lvl, &max_levels};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)stencil_glr_levels_kernel<CONN>, dim3(nblocks),
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)stencil_glr_levels_kernel<CONN, TX, TY>, dim3(nblocks),
                                                 dim3(256), args, 0, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(st.hist, 0, (kHistBins + 1) * 4, s);
@@ -189,19 +188,24 @@ static cudaError_t stencil_glr_impl(const Geom &g, const DevState &st, void *scr
 }
 
 bool stencil_glr_supported(int conn, const Geom &g) {
-    return is_paper(conn) && g.tx == kStTile && g.ty == kStTile && g.tz == 1;
+    return is_paper(conn) && g.tz == 1 &&
+           ((g.tx == 32 && g.ty == 32) || (conn == 108 && g.tx == 64 && (g.ty == 32 || g.ty == 64)));
 }
 
 size_t stencil_glr_scratch_bytes(const Geom &g) { return 2 * (size_t)g.n; }
 
 cudaError_t stencil_glr(int conn, const Geom &g, const DevState &st, void *scratch, cudaStream_t s) {
+    if (g.tx == 64) {  // connectivity 8 only
+        if (conn != 108) return cudaErrorInvalidValue;
+        return g.ty == 64 ? stencil_glr_impl<108, 64, 64>(g, st, scratch, s) : stencil_glr_impl<108, 64, 32>(g, st, scratch, s);
+    }
     switch (conn) {
-        case 108: return stencil_glr_impl<108>(g, st, scratch, s);
-        case 112: return stencil_glr_impl<112>(g, st, scratch, s);
-        case 116: return stencil_glr_impl<116>(g, st, scratch, s);
-        case 120: return stencil_glr_impl<120>(g, st, scratch, s);
-        case 124: return stencil_glr_impl<124>(g, st, scratch, s);
-        case 128: return stencil_glr_impl<128>(g, st, scratch, s);
+        case 108: return stencil_glr_impl<108, 32, 32>(g, st, scratch, s);
+        case 112: return stencil_glr_impl<112, 32, 32>(g, st, scratch, s);
+        case 116: return stencil_glr_impl<116, 32, 32>(g, st, scratch, s);
+        case 120: return stencil_glr_impl<120, 32, 32>(g, st, scratch, s);
+        case 124: return stencil_glr_impl<124, 32, 32>(g, st, scratch, s);
+        case 128: return stencil_glr_impl<128, 32, 32>(g, st, scratch, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -84,10 +84,25 @@ def test_strength_sweep_matches_the_oracle():
             assert_parity(inst, got, verify=False)
 
 
+@pytest.mark.parametrize("tile", [(64, 32, 1), (64, 64, 1)])
+@pytest.mark.parametrize("variant", [0, 2])
+def test_larger_tiles_at_connectivity_8(tile, variant):
+    # the paper's dependence on the number of regions at its default connectivity
+    inst = grids.paper_synthetic(150, 140, 9, strength=150, connectivity=8)
+    got = gpu_solve(inst, tile=tile, opts=default_opts(kernel_variant=variant))
+    assert_parity(inst, got)
+    assert got["stats"].boundary_size == oracle.boundary_size(inst.dims, inst.conn, tile)
+    assert got["stats"].global_relabels > 0
+    inst = _random((130, 70), 8, 10)
+    got = gpu_solve(inst, tile=tile, opts=default_opts(kernel_variant=variant, graph_loop=1))
+    assert_parity(inst, got)
+
+
 def test_unsupported_uses_are_rejected():
     inst = grids.paper_synthetic(64, 64, 1, connectivity=8)
+    big = grids.paper_synthetic(64, 64, 1, connectivity=12)
     with pytest.raises(mf.MFError) as ei:
-        Grid(inst.dims, inst.conn, tile=(64, 64, 1))
+        Grid(big.dims, big.conn, tile=(64, 64, 1))  # 15 planes of 64x64 do not fit in shared memory
     assert ei.value.status == mf.MF_EINVAL
     with pytest.raises(mf.MFError) as ei:
         Grid(inst.dims, inst.conn, host_state=True)
@@ -109,13 +124,14 @@ def test_unsupported_uses_are_rejected():
         assert g.flow_value() == oracle.solve_instance(inst)["flow"]
 
 
-@pytest.mark.parametrize("c", [8, 16, 28])
-def test_global_relabel_gives_region_distances(c):
+@pytest.mark.parametrize("c,tile", [(8, (32, 32, 1)), (16, (32, 32, 1)), (28, (32, 32, 1)), (8, (64, 32, 1)),
+                                    (8, (64, 64, 1))])
+def test_global_relabel_gives_region_distances(c, tile):
     # with the relabel after every sweep the labels equal the oracle's 0-1 BFS
     # region distances (d_inf where t is unreachable), as for the unit stencils
-    inst = _random((75, 70), c, 6)
+    inst = _random((140, 70), c, 6)
     checked = 0
-    with Grid(inst.dims, inst.conn, tile=(32, 32, 1)) as g:
+    with Grid(inst.dims, inst.conn, tile=tile) as g:
         g.set_caps(inst.cs, inst.ct, inst.nlink)
         g.begin(default_opts(global_relabel_period=1))
         for _ in range(500):
@@ -123,7 +139,7 @@ def test_global_relabel_gives_region_distances(c):
                 break
             lab, dinf = g.get_labels()
             res, tres, _ = g.get_residual()
-            d = oracle.region_distance(inst.dims, inst.conn, (32, 32, 1), res, tres)
+            d = oracle.region_distance(inst.dims, inst.conn, tile, res, tres)
             np.testing.assert_array_equal(lab, np.where(d >= 0, d, dinf))
             checked += 1
         g.finish()
