@@ -32,9 +32,10 @@
  *     (the list's first pair swapped so that c = 4 would be the 4-connected
  *     grid) with H = c/2; such grids are solved one by one on 32x32 tiles (or
  *     64x32 / 64x64 at c = 8) with
- *     the generic region discharge (kernel_variant 0 or 1 = ARD, 2 = PRD),
- *     without the global relabel, warm start, region reduction, boundary
- *     relabel, batches or MF_STATE_HOST;
+ *     the generic region discharge (kernel_variant 0 or 1 = ARD, 2 = PRD)
+ *     and a global relabel of their own (opts.global_relabel_period), without
+ *     warm start, region reduction, boundary relabel, batches or
+ *     MF_STATE_HOST;
  *   - arc directions d = 0..2H-1: D(2h) = +h-th offset, D(2h+1) = -h-th
  *     offset; the reverse of d is d^1;
  *   - all arrays are dense int32 (or uint8) and row-major as above;
