@@ -189,7 +189,10 @@ mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const in
 /*
  * mf_set_caps for count grids: the copies and validations of all grids are
  * enqueued first, then one wait per distinct stream; cs[i], ct[i], nlink[i]
- * as in mf_set_caps for grid i.  The first grid that fails decides the
+ * as in mf_set_caps for grid i.  When every buffer is device, managed or
+ * pinned host memory and the grids share one stream, a single kernel copies
+ * all arrays (pinned host memory is read over the C2C link) and a single
+ * kernel validates all grids.  The first grid that fails decides the
  * status (its message is also left on grids[0]); grids before it are set.
  */
 mf_status mf_set_caps_batch(mf_grid *const *grids, int count, const int32_t *const *cs, const int32_t *const *ct,

@@ -6,6 +6,7 @@
 //   cut       residual closures giving S_min and S_max.
 #include <algorithm>
 #include <climits>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -128,35 +129,68 @@ __global__ void init_kernel(const Geom g, const DevState st, const int *__restri
     if ((threadIdx.x & 31) == 0 && part) atomicAdd((unsigned long long *)st.flow0, (unsigned long long)part);
 }
 
-// Input validation for device-resident capacities: bit 0 negative value,
+// Input validation of the capacities of vertex v: bit 0 negative value,
 // bit 1 nonzero link leaving the grid, bit 2 possible int32 overflow.
 template <int CONN>
-__global__ void validate_kernel(const Geom g, const int *cs, const int *ct, const int *nl, int *flags) {
+__device__ __forceinline__ int validate_vertex(const Geom &g, const int *cs, const int *ct, const int *nl, size_t v) {
     const size_t n = (size_t)g.n;
+    const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
     int f = 0;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
-        if (cs[v] < 0 || ct[v] < 0) f |= 1;
-        long long sum = cs[v];
+    if (cs[v] < 0 || ct[v] < 0) f |= 1;
+    long long sum = cs[v];
 #pragma unroll
-        for (int d = 0; d < arcs_of(CONN); ++d) {
-            const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
-            const bool ing = in_grid(g, x + dx, y + dy, z + dz);
-            int c;
-            if (d & 1) {
-                if (!ing) continue;
-                c = nl[(size_t)(d >> 1) * n + ((size_t)(z + dz) * g.Y + (y + dy)) * g.X + (x + dx)];
-            } else {
-                c = nl[(size_t)(d >> 1) * n + v];
-                if (!ing && c != 0) f |= 2;
-            }
-            if (c < 0) f |= 1;
-            if (c > INT_MAX / 2) f |= 4;
-            sum += c;
+    for (int d = 0; d < arcs_of(CONN); ++d) {
+        const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
+        const bool ing = in_grid(g, x + dx, y + dy, z + dz);
+        int c;
+        if (d & 1) {
+            if (!ing) continue;
+            c = nl[(size_t)(d >> 1) * n + ((size_t)(z + dz) * g.Y + (y + dy)) * g.X + (x + dx)];
+        } else {
+            c = nl[(size_t)(d >> 1) * n + v];
+            if (!ing && c != 0) f |= 2;
         }
-        if (sum > INT_MAX) f |= 4;
+        if (c < 0) f |= 1;
+        if (c > INT_MAX / 2) f |= 4;
+        sum += c;
     }
+    if (sum > INT_MAX) f |= 4;
+    return f;
+}
+
+template <int CONN>
+__global__ void validate_kernel(const Geom g, const int *cs, const int *ct, const int *nl, int *flags) {
+    int f = 0;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < (size_t)g.n; v += (size_t)gridDim.x * blockDim.x)
+        f |= validate_vertex<CONN>(g, cs, ct, nl, v);
     if (f) atomicOr(flags, f);
+}
+
+// the validation of many grids in one launch: units (grid, 64K vertices)
+struct ValJob {
+    Geom g;
+    const int *cs, *ct, *nl;
+    int conn;
+};
+constexpr int kValChunk = 65536;
+__global__ void validate_batch_kernel(const ValJob *__restrict__ jobs, const int2 *__restrict__ units, int nunits,
+                                      int *flags) {
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int2 w = units[u];
+        const ValJob &J = jobs[w.x];
+        const size_t v0 = (size_t)w.y * kValChunk, v1 = min((size_t)J.g.n, v0 + kValChunk);
+        int f = 0;
+        for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            switch (J.conn) {
+                case 4: f |= validate_vertex<4>(J.g, J.cs, J.ct, J.nl, v); break;
+                case 8: f |= validate_vertex<8>(J.g, J.cs, J.ct, J.nl, v); break;
+                case 6: f |= validate_vertex<6>(J.g, J.cs, J.ct, J.nl, v); break;
+                default: f |= 8;  // not a connectivity of the batched path
+            }
+        }
+        f = __reduce_or_sync(0xffffffffu, f);
+        if ((threadIdx.x & 31) == 0 && f) atomicOr(&flags[w.x], f);
+    }
 }
 
 // A region is "touched" in a sweep when it or one of its neighbour regions
@@ -1045,9 +1079,12 @@ mf_status mf_destroy(mf_grid *g) {
     return MF_OK;
 }
 
-// mf_set_caps in two halves: the copies and the validation kernel enqueued
-// on the grid's stream, then (after a wait) the verdict from the flags
-static mf_status set_caps_enqueue(mf_grid *g, const int32_t *cs, const int32_t *ct, const int32_t *nlink) {
+// mf_set_caps in phases: the copies, the validation kernel, the read-back of
+// its flags (each enqueued on the grid's stream), then (after a wait) the
+// verdict.  A batch runs each phase for all grids before the next, so that
+// the copies follow one another on the copy engine instead of alternating
+// with the validation kernels.
+static mf_status set_caps_copies(mf_grid *g, const int32_t *cs, const int32_t *ct, const int32_t *nlink) {
     if (!cs || !ct || !nlink) return fail(g, MF_EINVAL, "cs, ct and nlink must be non-NULL");
     const size_t n = (size_t)g->g.n, H = (size_t)g->H;
     g->caps_set = false;
@@ -1058,10 +1095,22 @@ static mf_status set_caps_enqueue(mf_grid *g, const int32_t *cs, const int32_t *
     CK(cudaMemcpyAsync(g->cs, cs, n * 4, kind, g->stream));
     CK(cudaMemcpyAsync(g->ct, ct, n * 4, kind, g->stream));
     CK(cudaMemcpyAsync(g->nl, nlink, H * n * 4, kind, g->stream));
+    return MF_OK;
+}
+static mf_status set_caps_validate(mf_grid *g) {
     CK(cudaMemsetAsync(g->st.ctr, 0, kCtrWords * 4, g->stream));
     CK(DISPATCH(g->conn, launch_validate, g, &g->st.ctr[kError]));
+    return MF_OK;
+}
+static mf_status set_caps_readback(mf_grid *g) {
     CK(cudaMemcpyAsync(g->h_ctr, g->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, g->stream));
     return MF_OK;
+}
+static mf_status set_caps_enqueue(mf_grid *g, const int32_t *cs, const int32_t *ct, const int32_t *nlink) {
+    mf_status st = set_caps_copies(g, cs, ct, nlink);
+    if (st == MF_OK) st = set_caps_validate(g);
+    if (st == MF_OK) st = set_caps_readback(g);
+    return st;
 }
 static mf_status set_caps_verdict(mf_grid *g) {
     const int f = g->h_ctr[kError];
@@ -1094,6 +1143,45 @@ static cudaError_t sync_streams(mf_grid *const *grids, int count) {
     return cudaSuccess;
 }
 
+// one launch copies many segments (src and dst device-accessible: device or
+// pinned host memory, read over NVLink-C2C); 16-byte words where both ends
+// and the length allow, 4-byte words otherwise
+struct CopySeg {
+    const void *src;
+    void *dst;
+    unsigned long long bytes;
+};
+__global__ void gather_copy_kernel(const CopySeg *__restrict__ segs, int nseg) {
+    for (int k = blockIdx.y; k < nseg; k += gridDim.y) {
+        const CopySeg sg = segs[k];
+        const bool v16 = ((reinterpret_cast<uintptr_t>(sg.src) | reinterpret_cast<uintptr_t>(sg.dst) | sg.bytes) & 15) == 0;
+        const size_t stride = (size_t)gridDim.x * blockDim.x;
+        if (v16) {
+            const int4 *a = (const int4 *)sg.src;
+            int4 *b = (int4 *)sg.dst;
+            for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sg.bytes / 16; i += stride) b[i] = a[i];
+        } else {
+            const int *a = (const int *)sg.src;
+            int *b = (int *)sg.dst;
+            for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sg.bytes / 4; i += stride) b[i] = a[i];
+        }
+    }
+}
+
+// the address a kernel reads p through (device memory, managed memory or
+// pinned host memory), or nullptr if it cannot (pageable host memory)
+static const void *device_view(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // an unknown pointer: clear the (non-sticky) error
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged && a.type != cudaMemoryTypeHost) return nullptr;
+    if (!a.devicePointer) return nullptr;
+    // the offset of p inside its allocation carries over to the device view
+    return (const char *)a.devicePointer + ((const char *)p - (const char *)(a.hostPointer ? a.hostPointer : a.devicePointer));
+}
+
 mf_status mf_set_caps_batch(mf_grid *const *grids, int count, const int32_t *const *cs, const int32_t *const *ct,
                             const int32_t *const *nlink, int on_device) {
     mf_grid *g = nullptr;
@@ -1102,13 +1190,90 @@ mf_status mf_set_caps_batch(mf_grid *const *grids, int count, const int32_t *con
     for (int i = 0; i < count; ++i)
         if (!grids[i]) return fail(nullptr, MF_EINVAL, "null grid in the batch");
     g = grids[0];
-    for (int i = 0; i < count; ++i) {
-        mf_status st = set_caps_enqueue(grids[i], cs[i], ct[i], nlink[i]);
-        if (st != MF_OK) {
-            if (grids[i] != g) fail(g, st, std::string("grid ") + std::to_string(i) + ": " + grids[i]->err);
-            return st;
+    for (int i = 0; i < count; ++i)
+        if (!cs[i] || !ct[i] || !nlink[i]) return fail(g, MF_EINVAL, std::string("grid ") + std::to_string(i) +
+                                                                  ": cs, ct and nlink must be non-NULL");
+    // on one stream, with sources a kernel can read: one gather launch for all
+    // copies (a copy per array costs more than its bytes on small grids)
+    bool gather = true;
+    std::vector<const void *> views((size_t)count * 3, nullptr);
+    for (int i = 0; i < count && gather; ++i) {
+        views[3 * i] = device_view(cs[i]);
+        views[3 * i + 1] = device_view(ct[i]);
+        views[3 * i + 2] = device_view(nlink[i]);
+        gather = grids[i]->stream == g->stream && views[3 * i] && views[3 * i + 1] && views[3 * i + 2];
+    }
+    if (gather) {
+        std::vector<CopySeg> segs;
+        segs.reserve((size_t)count * 3);
+        for (int i = 0; i < count; ++i) {
+            mf_grid *h = grids[i];
+            const unsigned long long n4 = (unsigned long long)h->g.n * 4;
+            segs.push_back({views[3 * i], h->cs, n4});
+            segs.push_back({views[3 * i + 1], h->ct, n4});
+            segs.push_back({views[3 * i + 2], h->nl, (unsigned long long)h->H * n4});
+            h->caps_set = false;
+            h->begun = h->finished = false;
+            h->flow_cached = false;
+            h->warm_ready = false;
+        }
+        CopySeg *dsegs = nullptr;
+        CK(cudaMallocAsync((void **)&dsegs, segs.size() * sizeof(CopySeg), g->stream));
+        CK(cudaMemcpyAsync(dsegs, segs.data(), segs.size() * sizeof(CopySeg), cudaMemcpyHostToDevice, g->stream));
+        const int ns = (int)segs.size();
+        gather_copy_kernel<<<dim3(64, std::min(ns, 65535)), 256, 0, g->stream>>>(dsegs, ns);
+        CK(cudaGetLastError());
+        CK(cudaFreeAsync(dsegs, g->stream));
+        bool unit_stencils = true;  // the batched validation covers the 4/8/6 stencils
+        for (int i = 0; i < count; ++i) unit_stencils &= !is_paper(grids[i]->conn);
+        if (unit_stencils) {
+            // every grid's validation in one launch, one read-back of the flags
+            std::vector<ValJob> jobs((size_t)count);
+            std::vector<int2> units;
+            for (int i = 0; i < count; ++i) {
+                mf_grid *h = grids[i];
+                jobs[i] = ValJob{h->g, h->cs, h->ct, h->nl, h->conn};
+                const long long nc = (h->g.n + kValChunk - 1) / kValChunk;
+                for (long long c = 0; c < nc; ++c) units.push_back(make_int2(i, (int)c));
+            }
+            ValJob *djobs = nullptr;
+            int2 *dunits = nullptr;
+            int *dflags = nullptr;
+            std::vector<int> hflags((size_t)count, 0);
+            CK(cudaMallocAsync((void **)&djobs, jobs.size() * sizeof(ValJob), g->stream));
+            CK(cudaMallocAsync((void **)&dunits, units.size() * sizeof(int2), g->stream));
+            CK(cudaMallocAsync((void **)&dflags, (size_t)count * sizeof(int), g->stream));
+            CK(cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(ValJob), cudaMemcpyHostToDevice, g->stream));
+            CK(cudaMemcpyAsync(dunits, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice, g->stream));
+            CK(cudaMemsetAsync(dflags, 0, (size_t)count * sizeof(int), g->stream));
+            const int nu = (int)units.size();
+            validate_batch_kernel<<<std::min(nu, device_sms() * 16), 256, 0, g->stream>>>(djobs, dunits, nu, dflags);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(hflags.data(), dflags, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaFreeAsync(djobs, g->stream));
+            CK(cudaFreeAsync(dunits, g->stream));
+            CK(cudaFreeAsync(dflags, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            for (int i = 0; i < count; ++i) {
+                grids[i]->h_ctr[kError] = hflags[i];
+                mf_status st = set_caps_verdict(grids[i]);
+                if (st != MF_OK) {
+                    if (grids[i] != g) fail(g, st, std::string("grid ") + std::to_string(i) + ": " + grids[i]->err);
+                    return st;
+                }
+            }
+            return MF_OK;
         }
     }
+    for (int phase = gather ? 1 : 0; phase < 3; ++phase)
+        for (int i = 0; i < count; ++i) {
+            mf_status st = phase == 0 ? set_caps_copies(grids[i], cs[i], ct[i], nlink[i])
+                           : phase == 1 ? set_caps_validate(grids[i]) : set_caps_readback(grids[i]);
+            if (st != MF_OK) {
+                if (grids[i] != g) fail(g, st, std::string("grid ") + std::to_string(i) + ": " + grids[i]->err);
+                return st;
+            }
+        }
     CK(sync_streams(grids, count));
     for (int i = 0; i < count; ++i) {
         mf_status st = set_caps_verdict(grids[i]);

@@ -107,13 +107,37 @@ def test_batched_set_caps_and_cut_reads():
             assert f == ref["flow"] == g.flow_value()
             np.testing.assert_array_equal(o, ref["smin"])
             np.testing.assert_array_equal(sm, ref["smax"])
-    # a negative capacity in the second grid: the batch fails with MF_EINVAL
-    bad = insts[1].cs.copy()
-    bad[5] = -1
-    with pytest.raises(mf.MFError) as ei:
-        mf.set_caps_batch(handles, [(insts[0].cs, insts[0].ct, insts[0].nlink), (bad, insts[1].ct, insts[1].nlink),
-                                    (insts[2].cs, insts[2].ct, insts[2].nlink)])
-    assert ei.value.status == mf.MF_EINVAL
+    # pinned host buffers (the gathered copy and the batched validation)
+    pinned = [tuple(torch.from_numpy(a).pin_memory() for a in (x.cs, x.ct, x.nlink)) for x in insts]
+    mf.set_caps_batch(handles, pinned)
+    mf.solve_batch(handles, default_opts())
+    outs, flows = mf.get_cuts_batch(handles, 0)
+    for ref, o, f in zip(refs, outs, flows):
+        assert f == ref["flow"]
+        np.testing.assert_array_equal(o, ref["smin"])
+    # a negative capacity, a link leaving the grid or an overflow in one grid:
+    # the batch fails with that grid's status (pageable, pinned and device buffers)
+    for kind, status in (("negative", mf.MF_EINVAL), ("leaving", mf.MF_EINVAL), ("overflow", mf.MF_EOVERFLOW)):
+        cs, nl = insts[1].cs.copy(), insts[1].nlink.copy()
+        if kind == "negative":
+            cs[5] = -1
+        elif kind == "leaving":
+            X = insts[1].dims[0]
+            nl[0, X - 1] = 3  # the +x link of the last column
+        else:
+            cs[7] = 2 ** 31 - 2
+        caps = [(insts[0].cs, insts[0].ct, insts[0].nlink), (cs, insts[1].ct, nl),
+                (insts[2].cs, insts[2].ct, insts[2].nlink)]
+        for mode in ("pageable", "pinned", "device"):
+            if mode == "pinned":
+                cc = [tuple(torch.from_numpy(a).pin_memory() for a in c) for c in caps]
+            elif mode == "device":
+                cc = [tuple(torch.from_numpy(a).cuda() for a in c) for c in caps]
+            else:
+                cc = caps
+            with pytest.raises(mf.MFError) as ei:
+                mf.set_caps_batch(handles, cc)
+            assert ei.value.status == status, (kind, mode)
     # a grid without a finished solve: MF_ESTATE
     with pytest.raises(mf.MFError) as ei:
         mf.get_cuts_batch(handles, 0)
