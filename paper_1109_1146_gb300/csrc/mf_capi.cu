@@ -101,32 +101,85 @@ __device__ __forceinline__ int region_of(const Geom &g, int x, int y, int z) {
 // Init (Sec. 2): every s-link saturated, f := 0 on the rest, d := 0.  The part
 // min(cs, ct) of a vertex is sent s -> v -> t at once (counted in flow0):
 // exc = cs - min, tcap = ct - min.  cap[d] gets the edge capacity of arc d.
+// Init of vertex v; returns min(cs, ct), its share of flow0
+template <int CONN>
+__device__ __forceinline__ int init_vertex(const Geom &g, const DevState &st, const int *__restrict__ cs,
+                                           const int *__restrict__ ct, const int *__restrict__ nl, size_t v) {
+    const size_t n = (size_t)g.n;
+    const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
+    const int a = cs[v], b = ct[v], m = min(a, b);
+    st.exc[v] = a - m;
+    st.tcap[v] = b - m;
+    st.lab[v] = 0;
+#pragma unroll
+    for (int d = 0; d < arcs_of(CONN); ++d) {
+        const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
+        int c = 0;
+        if (in_grid(g, x + dx, y + dy, z + dz)) {
+            const size_t w = ((size_t)(z + dz) * g.Y + (y + dy)) * g.X + (x + dx);
+            c = (d & 1) ? nl[(size_t)(d >> 1) * n + w] : nl[(size_t)(d >> 1) * n + v];
+        }
+        st.cap[(size_t)d * n + v] = c;
+    }
+    if (a - m > 0) st.active[region_of(g, x, y, z)] = 1;
+    return m;
+}
+
 template <int CONN>
 __global__ void init_kernel(const Geom g, const DevState st, const int *__restrict__ cs,
                             const int *__restrict__ ct, const int *__restrict__ nl) {
-    const size_t n = (size_t)g.n;
     long long part = 0;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % g.X), y = (int)((v / g.X) % g.Y), z = (int)(v / ((size_t)g.X * g.Y));
-        const int a = cs[v], b = ct[v], m = min(a, b);
-        part += m;
-        st.exc[v] = a - m;
-        st.tcap[v] = b - m;
-        st.lab[v] = 0;
-#pragma unroll
-        for (int d = 0; d < arcs_of(CONN); ++d) {
-            const int dx = arc_dx(CONN, d), dy = arc_dy(CONN, d), dz = arc_dz(CONN, d);
-            int c = 0;
-            if (in_grid(g, x + dx, y + dy, z + dz)) {
-                const size_t w = ((size_t)(z + dz) * g.Y + (y + dy)) * g.X + (x + dx);
-                c = (d & 1) ? nl[(size_t)(d >> 1) * n + w] : nl[(size_t)(d >> 1) * n + v];
-            }
-            st.cap[(size_t)d * n + v] = c;
-        }
-        if (a - m > 0) st.active[region_of(g, x, y, z)] = 1;
-    }
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < (size_t)g.n; v += (size_t)gridDim.x * blockDim.x)
+        part += init_vertex<CONN>(g, st, cs, ct, nl, v);
     for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
     if ((threadIdx.x & 31) == 0 && part) atomicAdd((unsigned long long *)st.flow0, (unsigned long long)part);
+}
+
+// Init of many grids (a batch whose grids start cold): one launch resets the
+// per-grid state (a block per grid: region flags, flow, counters, the label
+// histogram with every boundary vertex at label 0), one runs Init over
+// (grid, 64K vertices) units
+struct InitJob {
+    Geom g;
+    DevState st;
+    Counters64 *c64;
+    const int *cs, *ct, *nl;
+    int conn;
+    int boundary;
+};
+constexpr int kInitChunk = 65536;
+__global__ void batch_begin_reset_kernel(const InitJob *__restrict__ jobs) {
+    const InitJob &J = jobs[blockIdx.x];
+    const DevState &st = J.st;
+    for (int r = threadIdx.x; r < J.g.nreg; r += blockDim.x) {
+        st.active[r] = 0;
+        st.disc[r] = 0;
+        st.left_active[r] = 0;
+    }
+    for (int b = threadIdx.x; b <= kHistBins; b += blockDim.x) st.hist[b] = b == 0 ? J.boundary : 0;
+    for (int w = threadIdx.x; w < kCtrWords; w += blockDim.x) st.ctr[w] = 0;
+    if (threadIdx.x == 0) {
+        *st.flow_t = 0;
+        *st.flow0 = 0;
+        *J.c64 = Counters64{};
+    }
+}
+__global__ void batch_init_kernel(const InitJob *__restrict__ jobs, const int2 *__restrict__ units, int nunits) {
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int2 w = units[u];
+        const InitJob &J = jobs[w.x];
+        const size_t v0 = (size_t)w.y * kInitChunk, v1 = min((size_t)J.g.n, v0 + kInitChunk);
+        long long part = 0;
+        for (size_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+            switch (J.conn) {
+                case 4: part += init_vertex<4>(J.g, J.st, J.cs, J.ct, J.nl, v); break;
+                case 8: part += init_vertex<8>(J.g, J.st, J.cs, J.ct, J.nl, v); break;
+                default: part += init_vertex<6>(J.g, J.st, J.cs, J.ct, J.nl, v); break;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0 && part) atomicAdd((unsigned long long *)J.st.flow0, (unsigned long long)part);
+    }
 }
 
 // Input validation of the capacities of vertex v: bit 0 negative value,
@@ -1334,11 +1387,14 @@ static void begin_collect(mf_grid *g) {
 
 // defer: leave the relabel of a warm start in flight (a batch waits once for
 // all its grids and then calls begin_collect)
-static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer);
+static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer, bool *batched_init = nullptr);
 
 mf_status mf_begin(mf_grid *g, const mf_opts *opts) { return begin_impl(g, opts, false); }
 
-static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer) {
+// batched_init: a cold start without region reduction leaves its device
+// reset and Init to the caller (set to true then), who runs them for many
+// grids at once
+static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer, bool *batched_init) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (!g->caps_set) return fail(g, MF_ESTATE, "mf_set_caps has not succeeded");
     if (opts) g->opts = *opts;
@@ -1359,6 +1415,20 @@ static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer) {
         g->g.dinf = (int)std::max<long long>(g->boundary, 1);
     }
     const size_t nreg = (size_t)g->g.nreg;
+    const bool defer_init = batched_init && !g->opts.warm_start && !g->opts.region_reduction;
+    if (batched_init) *batched_init = defer_init;
+    if (defer_init) {  // the caller resets the state and runs Init
+        g->reduced = false;
+        g->launches = 0;
+        g->sweep = 0;
+        g->begun = true;
+        g->finished = false;
+        g->flow_cached = false;
+        memset(&g->stats, 0, sizeof(g->stats));
+        g->stats.boundary_size = (int32_t)g->boundary;
+        g->begin_active = -1;
+        return MF_OK;
+    }
     CK(cudaMemsetAsync(g->st.active, 0, nreg, g->stream));
     CK(cudaMemsetAsync(g->st.disc, 0, nreg, g->stream));
     CK(cudaMemsetAsync(g->st.left_active, 0, nreg, g->stream));
@@ -1395,6 +1465,7 @@ static mf_status begin_impl(mf_grid *g, const mf_opts *opts, bool defer) {
     g->sweep = 0;
     g->begun = true;
     g->finished = false;
+    g->flow_cached = false;
     memset(&g->stats, 0, sizeof(g->stats));
     g->stats.boundary_size = (int32_t)g->boundary;
     g->stats.projection_rounds = g->opts.warm_start ? g->warm_rounds : 0;
@@ -1859,8 +1930,11 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     }
     cudaStream_t s = g->stream;
     CK(cudaEventRecord(g->ev[0], s));
-    // Init of every instance on its own stream, then everything on the batch stream
+    // Init of every instance on its own stream, then everything on the batch
+    // stream; the cold starts on the batch stream are reset and initialised
+    // by two launches for all of them
     long long cap = 0;
+    std::vector<int> to_init;
     for (int i = 0; i < count; ++i) {
         // with opts.warm_start, each grid starts from its projected preflow if
         // mf_warm_start succeeded on it, and cold otherwise
@@ -1868,8 +1942,10 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         if (opts) oi = *opts;
         else mf_default_opts(&oi);
         if (oi.warm_start && !grids[i]->warm_ready) oi.warm_start = 0;
-        mf_status st = begin_impl(grids[i], &oi, grids[i]->stream == s);
+        bool bi = false;
+        mf_status st = begin_impl(grids[i], &oi, grids[i]->stream == s, grids[i]->stream == s ? &bi : nullptr);
         if (st != MF_OK) return st;
+        if (bi) to_init.push_back(i);
         if (grids[i]->stream != s) {
             cudaError_t e = cudaStreamSynchronize(grids[i]->stream);
             if (e != cudaSuccess) return fail(g, MF_ECUDA, cudaGetErrorString(e));
@@ -1877,6 +1953,30 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         const long long b = grids[i]->opts.kernel_variant == 2 ? (long long)grids[i]->g.n : grids[i]->boundary;
         cap = std::max(cap, g->opts.max_sweeps > 0 ? (long long)g->opts.max_sweeps
                                                     : std::min<long long>(2 * b * b + 1, 1ll << 30));
+    }
+    if (!to_init.empty()) {
+        std::vector<InitJob> jobs;
+        std::vector<int2> units;
+        for (int i : to_init) {
+            mf_grid *h = grids[i];
+            const int j = (int)jobs.size();
+            jobs.push_back(InitJob{h->g, h->st, h->c64, h->cs, h->ct, h->nl, h->conn, (int)h->boundary});
+            const long long nc = (h->g.n + kInitChunk - 1) / kInitChunk;
+            for (long long c = 0; c < nc; ++c) units.push_back(make_int2(j, (int)c));
+            h->launches = 2;  // its share: the reset and Init launches
+        }
+        InitJob *djobs = nullptr;
+        int2 *dunits = nullptr;
+        CK(cudaMallocAsync((void **)&djobs, jobs.size() * sizeof(InitJob), s));
+        CK(cudaMallocAsync((void **)&dunits, units.size() * sizeof(int2), s));
+        CK(cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(InitJob), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dunits, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        batch_begin_reset_kernel<<<(int)jobs.size(), 256, 0, s>>>(djobs);
+        const int nu = (int)units.size();
+        batch_init_kernel<<<std::min(nu, device_sms() * 16), 256, 0, s>>>(djobs, dunits, nu);
+        CK(cudaGetLastError());
+        CK(cudaFreeAsync(djobs, s));
+        CK(cudaFreeAsync(dunits, s));
     }
     // the relabels of warm starts were left in flight: one wait for all; a grid
     // whose initial labels already show a maximum preflow makes no sweep

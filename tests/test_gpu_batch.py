@@ -153,7 +153,10 @@ def test_flow_value_follows_extra_sweeps():
     ref = oracle.solve_instance(inst)
     with Grid(inst.dims, 4) as g:
         g.set_caps(inst.cs, inst.ct, inst.nlink)
-        g.begin(default_opts())
+        g.solve(default_opts())
+        assert g.flow_value() == ref["flow"]
+        g.begin(default_opts())  # a new solve: the finished one's value no longer holds
+        assert g.flow_value() <= ref["flow"]
         g.sweep()
         partial = g.flow_value()
         while g.sweep():
