@@ -31,13 +31,13 @@ typedef unsigned long long u64;
 // which = 0: forward masks (arc into v) and seeds e > 0; which = 1: arc out of
 // v and seeds c_f(v,t) > 0.
 template <int CONN>
-__global__ void cut_masks_kernel(const Geom g, const DevState st, int W64, int which, unsigned *M,
-                                 unsigned *S) {
+__device__ __forceinline__ void cut_masks_range(const Geom &g, const DevState &st, int W64, int which, unsigned *M,
+                                                unsigned *S, size_t t, size_t end, size_t step) {
     const size_t n = (size_t)g.n;
     const size_t rowbits = (size_t)W64 * 64;
-    const size_t total = rowbits * g.Y;
     const size_t plane32 = (size_t)g.Y * W64 * 2;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    // t and end differ from a multiple of 32 by the lane only, so a warp stays converged
+    for (; t < end; t += step) {
         const int y = (int)(t / rowbits), x = (int)(t % rowbits);
         const bool in = x < g.X;
         const size_t v = (size_t)y * g.X + x;
@@ -61,6 +61,13 @@ __global__ void cut_masks_kernel(const Geom g, const DevState st, int W64, int w
         const unsigned m = __ballot_sync(0xffffffffu, s);
         if ((threadIdx.x & 31) == 0) S[word32] = m;
     }
+}
+
+template <int CONN>
+__global__ void cut_masks_kernel(const Geom g, const DevState st, int W64, int which, unsigned *M,
+                                 unsigned *S) {
+    cut_masks_range<CONN>(g, st, W64, which, M, S, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                          (size_t)W64 * 64 * g.Y, (size_t)gridDim.x * blockDim.x);
 }
 
 __device__ __forceinline__ u64 fill_row(u64 g, u64 pl, u64 pr) {
@@ -465,9 +472,9 @@ static cudaError_t glr2d_impl(const Geom &g, const DevState &st, void *scratch, 
 // for a relabel: a work unit is (grid, 64x64 block), a warp takes units in
 // turn, the grid barrier separates levels.  A grid whose set did not grow at
 // a level has its final set and is skipped from then on; its level count is
-// recorded when it stops.  The finish (d_inf for unreached vertices, the
-// boundary-label histogram, region activity) and the count of active regions
-// are one launch each over all grids.
+// recorded when it stops.  The masks before the levels, the finish (d_inf for
+// unreached vertices, the boundary-label histogram, region activity) and the
+// count of active regions after them are one launch each over all grids.
 template <int CONN>
 __device__ __forceinline__ bool glr2d_unit(const GlrJob2 &J, int blk, const u64 *in, u64 *out, int level) {
     GlrBlock<CONN> B;
@@ -604,12 +611,33 @@ __global__ void glr_batch_count_kernel(const GlrJob2 *__restrict__ jobs) {
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
 }
 
+// The masks and seeds of many grids in one launch: a block per unit (grid,
+// kMaskRows rows); which as in cut_masks_kernel, the seeds go to the grid's
+// set A (set_b = 0) or B (set_b = 1).
+__global__ void cut_masks_batch_kernel(const GlrJob2 *__restrict__ jobs, const int2 *__restrict__ rows, int nrows,
+                                       int which, int set_b) {
+    for (int u = blockIdx.x; u < nrows; u += gridDim.x) {
+        const int2 r = rows[u];
+        const GlrJob2 &J = jobs[r.x];
+        const size_t rowbits = (size_t)J.W64 * 64;
+        const int y0 = r.y * kMaskRows, y1 = min(J.g.Y, y0 + kMaskRows);
+        unsigned *S = (unsigned *)(set_b ? J.B : J.A);
+        const size_t t0 = (size_t)y0 * rowbits + threadIdx.x, end = (size_t)y1 * rowbits;
+        if (J.conn == 4) cut_masks_range<4>(J.g, J.st, J.W64, which, (unsigned *)J.M, S, t0, end, blockDim.x);
+        else cut_masks_range<8>(J.g, J.st, J.W64, which, (unsigned *)J.M, S, t0, end, blockDim.x);
+    }
+}
+
+static void push_mask_rows(std::vector<int2> &rows, int job, int nrow) {
+    for (int c = 0; c < (nrow + kMaskRows - 1) / kMaskRows; ++c) rows.push_back(make_int2(job, c));
+}
+
 cudaError_t glr2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, cudaStream_t s) {
     const int njobs = (int)jobs_in.size();
     if (njobs == 0) return cudaSuccess;
     std::vector<GlrJob2> jobs(jobs_in);
     std::vector<int> unit_job;
-    std::vector<int2> chunks;
+    std::vector<int2> chunks, rows;
     for (int j = 0; j < njobs; ++j) {
         GlrJob2 &J = jobs[j];
         J.W64 = (J.g.X + 63) / 64;
@@ -622,6 +650,7 @@ cudaError_t glr2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
         for (int b = 0; b < J.W64 * J.BY; ++b) unit_job.push_back(j);
         const int nc = (int)((J.g.n + kFinishChunk - 1) / kFinishChunk);
         for (int c = 0; c < nc; ++c) chunks.push_back(make_int2(j, c));
+        push_mask_rows(rows, j, J.g.Y);
     }
     cudaError_t e = bb.reserve(njobs * sizeof(GlrJob2), unit_job.size() * sizeof(int), chunks.size() * sizeof(int2));
     if (e != cudaSuccess) return e;
@@ -630,13 +659,12 @@ cudaError_t glr2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
         e = cudaMemcpyAsync(bb.units, unit_job.data(), unit_job.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(bb.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = bb.upload_rows(rows, s);
     if (e != cudaSuccess) return e;
-    for (const GlrJob2 &J : jobs) {  // residual masks and the level-0 seeds of every grid
-        const size_t total = (size_t)J.W64 * 64 * J.g.Y;
-        const int mb = (int)std::min<size_t>((total + 255) / 256, (size_t)device_sms() * 32);
-        if (J.conn == 4) cut_masks_kernel<4><<<mb, 256, 0, s>>>(J.g, J.st, J.W64, 1, (unsigned *)J.M, (unsigned *)J.A);
-        else cut_masks_kernel<8><<<mb, 256, 0, s>>>(J.g, J.st, J.W64, 1, (unsigned *)J.M, (unsigned *)J.A);
-    }
+    // residual masks and the level-0 seeds of every grid
+    const int nrows = (int)rows.size();
+    cut_masks_batch_kernel<<<std::min(nrows, device_sms() * 8), 256, 0, s>>>((const GlrJob2 *)bb.jobs,
+                                                                             (const int2 *)bb.rows, nrows, 1, 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int max_blocks = 0;
@@ -655,11 +683,12 @@ cudaError_t glr2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
     const int nch = (int)chunks.size();
     glr2d_batch_finish_kernel<<<std::min(nch, device_sms() * 8), 256, 0, s>>>(pj, (const int2 *)bb.chunks, nch);
     glr_batch_count_kernel<<<njobs, 256, 0, s>>>(pj);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    return e == cudaSuccess ? glr_batch_out(pj, njobs, 0, s) : e;
 }
 
 // ---- both cut closures of many 2D grids at once (batched solves) --------------
-// Per closure: the masks of every grid (one launch each), then one cooperative
+// Per closure: the masks of every grid (one launch), then one cooperative
 // launch of block passes over the units (grid, 64x64 block) of all grids, a
 // grid leaving the passes once a pass adds nothing to its set; then the bytes
 // of S_min and S_max of every grid in one launch.  The pass count of each
@@ -722,12 +751,12 @@ __global__ void cut2d_batch_bytes_kernel(const GlrJob2 *__restrict__ jobs, const
     }
 }
 
-cudaError_t cut2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, int *const *h_passes, cudaStream_t s) {
+cudaError_t cut2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, cudaStream_t s) {
     const int njobs = (int)jobs_in.size();
     if (njobs == 0) return cudaSuccess;
     std::vector<GlrJob2> jobs(jobs_in);
     std::vector<int> unit_job;
-    std::vector<int2> chunks;
+    std::vector<int2> chunks, rows;
     for (int j = 0; j < njobs; ++j) {
         GlrJob2 &J = jobs[j];
         J.W64 = (J.g.X + 63) / 64;
@@ -740,6 +769,7 @@ cudaError_t cut2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, i
         for (int b = 0; b < J.W64 * J.BY; ++b) unit_job.push_back(j);
         const int nc = (int)((J.g.n + kFinishChunk - 1) / kFinishChunk);
         for (int c = 0; c < nc; ++c) chunks.push_back(make_int2(j, c));
+        push_mask_rows(rows, j, J.g.Y);
     }
     cudaError_t e = bb.reserve(njobs * sizeof(GlrJob2), unit_job.size() * sizeof(int), chunks.size() * sizeof(int2));
     if (e != cudaSuccess) return e;
@@ -748,20 +778,17 @@ cudaError_t cut2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, i
         e = cudaMemcpyAsync(bb.units, unit_job.data(), unit_job.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(bb.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = bb.upload_rows(rows, s);
     if (e != cudaSuccess) return e;
+    const int nrows = (int)rows.size();
     int max_blocks = 0;
     e = coop_max_blocks((const void *)cut2d_batch_closure_kernel, 256, 0, &max_blocks);
     if (e != cudaSuccess) return e;
     const int nunits = (int)unit_job.size();
     const int nblocks = std::max(1, std::min((nunits + 7) / 8, max_blocks));
     for (int which = 0; which < 2; ++which) {
-        for (const GlrJob2 &J : jobs) {
-            const size_t total = (size_t)J.W64 * 64 * J.g.Y;
-            const int mb = (int)std::min<size_t>((total + 255) / 256, (size_t)device_sms() * 32);
-            unsigned *S = (unsigned *)(which == 0 ? J.A : J.B);
-            if (J.conn == 4) cut_masks_kernel<4><<<mb, 256, 0, s>>>(J.g, J.st, J.W64, which, (unsigned *)J.M, S);
-            else cut_masks_kernel<8><<<mb, 256, 0, s>>>(J.g, J.st, J.W64, which, (unsigned *)J.M, S);
-        }
+        cut_masks_batch_kernel<<<std::min(nrows, device_sms() * 8), 256, 0, s>>>(
+            (const GlrJob2 *)bb.jobs, (const int2 *)bb.rows, nrows, which, which);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const GlrJob2 *pj = (const GlrJob2 *)bb.jobs;
@@ -770,12 +797,8 @@ cudaError_t cut2d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, i
         int nj = njobs, nu = nunits, mp = 1 << 20, wh = which;
         void *args[] = {(void *)&pj, &nj, (void *)&pu, &nu, &pany, &mp, &wh};
         e = cudaLaunchCooperativeKernel((const void *)cut2d_batch_closure_kernel, dim3(nblocks), dim3(256), args, 0, s);
+        if (e == cudaSuccess) e = glr_batch_out(pj, njobs, which, s);
         if (e != cudaSuccess) return e;
-        if (h_passes)
-            for (int j = 0; j < njobs; ++j) {
-                e = cudaMemcpyAsync(h_passes[j] + which, &jobs[j].st.ctr[kGlrLevels], 4, cudaMemcpyDeviceToHost, s);
-                if (e != cudaSuccess) return e;
-            }
     }
     const int nch = (int)chunks.size();
     cut2d_batch_bytes_kernel<<<std::min(nch, device_sms() * 8), 256, 0, s>>>((const GlrJob2 *)bb.jobs,
@@ -800,8 +823,33 @@ cudaError_t GlrBatchBufs::reserve(size_t jobs_bytes, size_t units_bytes, size_t 
     return e;
 }
 
+__global__ void glr_batch_out_kernel(const GlrJob2 *__restrict__ jobs, int njobs, int slot) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < njobs && jobs[j].hout) jobs[j].hout[slot] = jobs[j].st.ctr[kGlrLevels];
+}
+
+cudaError_t glr_batch_out(const GlrJob2 *jobs_dev, int njobs, int slot, cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    glr_batch_out_kernel<<<(njobs + 255) / 256, 256, 0, s>>>(jobs_dev, njobs, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t GlrBatchBufs::upload_rows(const std::vector<int2> &units_in, cudaStream_t s) {
+    const size_t want = std::max<size_t>(1, units_in.size()) * sizeof(int2);
+    if (want > rows_cap) {
+        if (rows) cudaFree(rows);
+        rows = nullptr;
+        rows_cap = 0;
+        const cudaError_t e = cudaMalloc(&rows, want);
+        if (e != cudaSuccess) return e;
+        rows_cap = want;
+    }
+    if (units_in.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(rows, units_in.data(), units_in.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+}
+
 GlrBatchBufs::~GlrBatchBufs() {
-    for (void *p : {jobs, units, chunks, (void *)any})
+    for (void *p : {jobs, units, chunks, rows, (void *)any})
         if (p) cudaFree(p);
 }
 

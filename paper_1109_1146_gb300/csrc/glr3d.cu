@@ -33,31 +33,34 @@ typedef unsigned int u32;
 // masks M[d][word] bit b = [c_f(v -> v + D(d)) > 0] and T[word] bit b = [c_f(v,t) > 0]
 // (a warp per grid row z * Y + y, lanes over x: coalesced plane reads, no
 // 64-bit index division)
-__global__ void glr3d_masks_kernel(const Geom g, const DevState st, int W32, u32 *M, u32 *T) {
+__device__ __forceinline__ void glr3d_mask_row(const Geom &g, const DevState &st, int W32, u32 *M, u32 *T, int row,
+                                               int lane) {
     const size_t n = (size_t)g.n;
     const size_t nw = (size_t)g.Z * g.Y * W32;
-    const int lane = threadIdx.x & 31;
+    const size_t v0 = (size_t)row * g.X, w0 = (size_t)row * W32;
+    for (int xw = 0; xw < W32; ++xw) {
+        const int x = xw * 32 + lane;
+        const bool in = x < g.X;
+        const size_t v = v0 + x;
+        int c[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) c[d] = in ? __ldg(&st.cap[d * n + v]) : 0;
+        const int tc = in ? __ldg(&st.tcap[v]) : 0;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            const unsigned m = __ballot_sync(0xffffffffu, c[d] > 0);
+            if (lane == 0) M[d * nw + w0 + xw] = m;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, tc > 0);
+        if (lane == 0) T[w0 + xw] = m;
+    }
+}
+
+__global__ void glr3d_masks_kernel(const Geom g, const DevState st, int W32, u32 *M, u32 *T) {
     const int rows = g.Z * g.Y;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps) {
-        const size_t v0 = (size_t)row * g.X, w0 = (size_t)row * W32;
-        for (int xw = 0; xw < W32; ++xw) {
-            const int x = xw * 32 + lane;
-            const bool in = x < g.X;
-            const size_t v = v0 + x;
-            int c[6];
-#pragma unroll
-            for (int d = 0; d < 6; ++d) c[d] = in ? __ldg(&st.cap[d * n + v]) : 0;
-            const int tc = in ? __ldg(&st.tcap[v]) : 0;
-#pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                const unsigned m = __ballot_sync(0xffffffffu, c[d] > 0);
-                if (lane == 0) M[d * nw + w0 + xw] = m;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, tc > 0);
-            if (lane == 0) T[w0 + xw] = m;
-        }
-    }
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps)
+        glr3d_mask_row(g, st, W32, M, T, row, threadIdx.x & 31);
 }
 
 template <int TY, int TZ>
@@ -305,10 +308,12 @@ __global__ void glr3d_count_kernel(const DevState st, int nreg) {
 // leads to a member.  which = 0 (S_min): the bit of d at v is [c_f(v + D(d)
 // -> v) > 0] (the arc into v), seeds e > 0; which = 1 ({v -> t}): the bit is
 // [c_f(v -> v + D(d)) > 0], seeds c_f(v,t) > 0.
-__global__ void cut3d_masks_kernel(const Geom g, const DevState st, int W32, int which, u32 *M, u32 *S) {
+__device__ __forceinline__ void cut3d_masks_range(const Geom &g, const DevState &st, int W32, int which, u32 *M,
+                                                  u32 *S, size_t t, size_t end, size_t step) {
     const size_t n = (size_t)g.n;
     const size_t words = (size_t)g.Z * g.Y * W32;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < words * 32; t += (size_t)gridDim.x * blockDim.x) {
+    // t and end differ from a multiple of 32 by the lane only, so a warp stays converged
+    for (; t < end; t += step) {
         const size_t w = t >> 5;
         const int xw = (int)(w % W32), y = (int)((w / W32) % g.Y), z = (int)(w / ((size_t)W32 * g.Y));
         const int x = xw * 32 + (int)(t & 31);
@@ -332,6 +337,12 @@ __global__ void cut3d_masks_kernel(const Geom g, const DevState st, int W32, int
         const unsigned m = __ballot_sync(0xffffffffu, in && (which == 1 ? st.tcap[v] > 0 : st.exc[v] > 0));
         if ((threadIdx.x & 31) == 0) S[w] = m;
     }
+}
+
+__global__ void cut3d_masks_kernel(const Geom g, const DevState st, int W32, int which, u32 *M, u32 *S) {
+    const size_t words = (size_t)g.Z * g.Y * W32;
+    cut3d_masks_range(g, st, W32, which, M, S, blockIdx.x * (size_t)blockDim.x + threadIdx.x, words * 32,
+                      (size_t)gridDim.x * blockDim.x);
 }
 
 // passes over all regions (a warp each: seeds across the faces from the
@@ -424,10 +435,11 @@ cudaError_t cut3d(const Geom &g, const DevState &st, void *scratch, unsigned cha
 }
 
 // ---- the same relabel for many 3D grids at once (batched solves) -------------
-// As glr2d_batch: one cooperative launch runs the levels of every due grid, a
-// work unit is (grid, region), a warp per unit; then one finish launch over
-// (grid, chunk) units and one count.  The masks keep the layout above; the
-// job's A/B fields hold the grid's level sets (u32 words here).
+// As glr2d_batch: one launch builds the masks of every due grid, one
+// cooperative launch runs their levels, a work unit is (grid, region), a warp
+// per unit; then one finish launch over (grid, chunk) units and one count.
+// The masks keep the layout above; the job's A/B fields hold the grid's level
+// sets (u32 words here).
 template <int TY, int TZ>
 __device__ __forceinline__ bool glr3d_unit(const GlrJob2 &J, int r, const u32 *in, u32 *out, int level) {
     const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
@@ -542,12 +554,46 @@ __global__ void glr3d_batch_count_kernel(const GlrJob2 *__restrict__ jobs) {
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st.ctr[kActiveRegions], c);
 }
 
+// The relabel masks of many grids in one launch: a block per unit (grid,
+// kMaskRows rows z * Y + y), a warp per row.
+__global__ void glr3d_masks_batch_kernel(const GlrJob2 *__restrict__ jobs, const int2 *__restrict__ rows, int nrows) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int u = blockIdx.x; u < nrows; u += gridDim.x) {
+        const int2 r = rows[u];
+        const GlrJob2 &J = jobs[r.x];
+        const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
+        u32 *M = (u32 *)J.M;
+        const int y0 = r.y * kMaskRows, y1 = min(J.g.Z * J.g.Y, y0 + kMaskRows);
+        for (int row = y0 + warp; row < y1; row += nw)
+            glr3d_mask_row(J.g, J.st, J.W64, M, M + 6 * words, row, threadIdx.x & 31);
+    }
+}
+
+// The cut masks and seeds of many grids in one launch, a block per unit (grid,
+// kMaskRows rows); which as in cut3d_masks_kernel, the seeds go to set A
+// (which = 0) or B (which = 1).
+__global__ void cut3d_masks_batch_kernel(const GlrJob2 *__restrict__ jobs, const int2 *__restrict__ rows, int nrows,
+                                         int which) {
+    for (int u = blockIdx.x; u < nrows; u += gridDim.x) {
+        const int2 r = rows[u];
+        const GlrJob2 &J = jobs[r.x];
+        const int y0 = r.y * kMaskRows, y1 = min(J.g.Z * J.g.Y, y0 + kMaskRows);
+        const size_t t0 = (size_t)y0 * J.W64 * 32 + threadIdx.x, end = (size_t)y1 * J.W64 * 32;
+        cut3d_masks_range(J.g, J.st, J.W64, which, (u32 *)J.M, (u32 *)(which == 0 ? J.A : J.B), t0, end,
+                          blockDim.x);
+    }
+}
+
+static void push_mask_rows3(std::vector<int2> &rows, int job, int nrow) {
+    for (int c = 0; c < (nrow + kMaskRows - 1) / kMaskRows; ++c) rows.push_back(make_int2(job, c));
+}
+
 cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, cudaStream_t s) {
     const int njobs = (int)jobs_in.size();
     if (njobs == 0) return cudaSuccess;
     std::vector<GlrJob2> jobs(jobs_in);
     std::vector<int> unit_job;
-    std::vector<int2> chunks;
+    std::vector<int2> chunks, rows;
     for (int j = 0; j < njobs; ++j) {
         GlrJob2 &J = jobs[j];
         J.W64 = (J.g.X + 31) / 32;  // here: 32-voxel words per row
@@ -561,6 +607,7 @@ cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
         for (int r = 0; r < J.g.nreg; ++r) unit_job.push_back(j);
         const int nc = (int)((J.g.Z * J.g.Y + kFinishRows3 - 1) / kFinishRows3);
         for (int c = 0; c < nc; ++c) chunks.push_back(make_int2(j, c));
+        push_mask_rows3(rows, j, J.g.Z * J.g.Y);
     }
     cudaError_t e = bb.reserve(njobs * sizeof(GlrJob2), unit_job.size() * sizeof(int), chunks.size() * sizeof(int2));
     if (e != cudaSuccess) return e;
@@ -569,13 +616,11 @@ cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
         e = cudaMemcpyAsync(bb.units, unit_job.data(), unit_job.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(bb.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = bb.upload_rows(rows, s);
     if (e != cudaSuccess) return e;
-    for (const GlrJob2 &J : jobs) {
-        const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
-        const int mb = (int)std::min<size_t>(((size_t)J.g.Z * J.g.Y + 7) / 8, (size_t)device_sms() * 32);
-        u32 *M = (u32 *)J.M;
-        glr3d_masks_kernel<<<mb, 256, 0, s>>>(J.g, J.st, J.W64, M, M + 6 * words);
-    }
+    const int nrows = (int)rows.size();
+    glr3d_masks_batch_kernel<<<std::min(nrows, device_sms() * 8), 256, 0, s>>>((const GlrJob2 *)bb.jobs,
+                                                                               (const int2 *)bb.rows, nrows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int max_blocks = 0;
@@ -594,7 +639,8 @@ cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, c
     const int nch = (int)chunks.size();
     glr3d_batch_finish_kernel<<<std::min(nch, device_sms() * 8), 256, 0, s>>>(pj, (const int2 *)bb.chunks, nch);
     glr3d_batch_count_kernel<<<njobs, 256, 0, s>>>(pj);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    return e == cudaSuccess ? glr_batch_out(pj, njobs, 0, s) : e;
 }
 
 // ---- both cut closures of many 3D grids at once (batched solves) --------------
@@ -664,12 +710,12 @@ __global__ void cut3d_batch_bytes_kernel(const GlrJob2 *__restrict__ jobs, const
     }
 }
 
-cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, int *const *h_passes, cudaStream_t s) {
+cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, cudaStream_t s) {
     const int njobs = (int)jobs_in.size();
     if (njobs == 0) return cudaSuccess;
     std::vector<GlrJob2> jobs(jobs_in);
     std::vector<int> unit_job;
-    std::vector<int2> chunks;
+    std::vector<int2> chunks, rows;
     for (int j = 0; j < njobs; ++j) {
         GlrJob2 &J = jobs[j];
         J.W64 = (J.g.X + 31) / 32;
@@ -683,6 +729,7 @@ cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, i
         for (int r = 0; r < J.g.nreg; ++r) unit_job.push_back(j);
         const int nc = (int)((J.g.n + kFinishChunk3 - 1) / kFinishChunk3);
         for (int c = 0; c < nc; ++c) chunks.push_back(make_int2(j, c));
+        push_mask_rows3(rows, j, J.g.Z * J.g.Y);
     }
     cudaError_t e = bb.reserve(njobs * sizeof(GlrJob2), unit_job.size() * sizeof(int), chunks.size() * sizeof(int2));
     if (e != cudaSuccess) return e;
@@ -691,19 +738,17 @@ cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, i
         e = cudaMemcpyAsync(bb.units, unit_job.data(), unit_job.size() * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(bb.chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = bb.upload_rows(rows, s);
     if (e != cudaSuccess) return e;
+    const int nrows = (int)rows.size();
     int max_blocks = 0;
     e = coop_max_blocks((const void *)cut3d_batch_closure_kernel, 256, 0, &max_blocks);
     if (e != cudaSuccess) return e;
     const int nunits = (int)unit_job.size();
     const int nblocks = std::max(1, std::min((nunits + 7) / 8, max_blocks));
     for (int which = 0; which < 2; ++which) {
-        for (const GlrJob2 &J : jobs) {
-            const size_t words = (size_t)J.g.Z * J.g.Y * J.W64;
-            const int mb = (int)std::min<size_t>((words * 32 + 255) / 256, (size_t)device_sms() * 32);
-            cut3d_masks_kernel<<<mb, 256, 0, s>>>(J.g, J.st, J.W64, which, (u32 *)J.M,
-                                                  (u32 *)(which == 0 ? J.A : J.B));
-        }
+        cut3d_masks_batch_kernel<<<std::min(nrows, device_sms() * 8), 256, 0, s>>>(
+            (const GlrJob2 *)bb.jobs, (const int2 *)bb.rows, nrows, which);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const GlrJob2 *pj = (const GlrJob2 *)bb.jobs;
@@ -712,12 +757,8 @@ cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs_in, GlrBatchBufs &bb, i
         int nj = njobs, nu = nunits, mp = 1 << 20, wh = which;
         void *args[] = {(void *)&pj, &nj, (void *)&pu, &nu, &pany, &mp, &wh};
         e = cudaLaunchCooperativeKernel((const void *)cut3d_batch_closure_kernel, dim3(nblocks), dim3(256), args, 0, s);
+        if (e == cudaSuccess) e = glr_batch_out(pj, njobs, which, s);
         if (e != cudaSuccess) return e;
-        if (h_passes)
-            for (int j = 0; j < njobs; ++j) {
-                e = cudaMemcpyAsync(h_passes[j] + which, &jobs[j].st.ctr[kGlrLevels], 4, cudaMemcpyDeviceToHost, s);
-                if (e != cudaSuccess) return e;
-            }
     }
     const int nch = (int)chunks.size();
     cut3d_batch_bytes_kernel<<<std::min(nch, device_sms() * 8), 256, 0, s>>>((const GlrJob2 *)bb.jobs,

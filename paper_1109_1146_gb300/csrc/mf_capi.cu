@@ -61,6 +61,8 @@ struct mf_grid {
         unsigned long long ft;
         Counters64 c;
     } *h_fin = nullptr;
+    int *h_ctr_dv = nullptr;                          // device views of h_ctr and h_fin (kernels write them)
+    FinishHost *h_fin_dv = nullptr;
     long long boundary = 0;
     bool caps_set = false, begun = false, finished = false;
     int sweep = 0;
@@ -72,6 +74,20 @@ struct mf_grid {
 };
 
 static thread_local std::string g_static_err;
+
+// the address a kernel reads p through (device memory, managed memory or
+// pinned host memory), or nullptr if it cannot (pageable host memory)
+static const void *device_view(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // an unknown pointer: clear the (non-sticky) error
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged && a.type != cudaMemoryTypeHost) return nullptr;
+    if (!a.devicePointer) return nullptr;
+    // the offset of p inside its allocation carries over to the device view
+    return (const char *)a.devicePointer + ((const char *)p - (const char *)(a.hostPointer ? a.hostPointer : a.devicePointer));
+}
 
 void mf::set_static_error(const std::string &m) { g_static_err = m; }
 
@@ -1110,6 +1126,9 @@ mf_status mf_create_grid_ex(mf_grid **out, int ndim, const int64_t dims[3], int 
     e = cudaMallocHost((void **)&g->h_ctr, kCtrWords * 4);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_fin, sizeof(mf_grid::FinishHost));
     if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MF_ENOMEM); }
+    g->h_ctr_dv = (int *)device_view(g->h_ctr);
+    g->h_fin_dv = (mf_grid::FinishHost *)device_view(g->h_fin);
+    if (!g->h_ctr_dv || !g->h_fin_dv) { g->err = "pinned host memory without a device view"; return bail(MF_ECUDA); }
     for (auto &ev : g->ev) {
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MF_ECUDA); }
@@ -1219,20 +1238,6 @@ __global__ void gather_copy_kernel(const CopySeg *__restrict__ segs, int nseg) {
             for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sg.bytes / 4; i += stride) b[i] = a[i];
         }
     }
-}
-
-// the address a kernel reads p through (device memory, managed memory or
-// pinned host memory), or nullptr if it cannot (pageable host memory)
-static const void *device_view(const void *p) {
-    cudaPointerAttributes a{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();  // an unknown pointer: clear the (non-sticky) error
-        return nullptr;
-    }
-    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged && a.type != cudaMemoryTypeHost) return nullptr;
-    if (!a.devicePointer) return nullptr;
-    // the offset of p inside its allocation carries over to the device view
-    return (const char *)a.devicePointer + ((const char *)p - (const char *)(a.hostPointer ? a.hostPointer : a.devicePointer));
 }
 
 mf_status mf_set_caps_batch(mf_grid *const *grids, int count, const int32_t *const *cs, const int32_t *const *ct,
@@ -1630,7 +1635,8 @@ mf_status mf_boundary_relabel(mf_grid *g, int32_t *info) {
 // enqueued on stream st without waiting (results land in g->h_fin); the
 // closures of 2D grids and of 3D grids with 32-wide tiles run on the device
 // to their fixed point, other 3D tiles loop on the host.
-static mf_status finish_enqueue(mf_grid *g, cudaStream_t st, bool cut_done = false) {
+// copies = false: the caller has the flow parts and stage counts read back
+static mf_status finish_enqueue(mf_grid *g, cudaStream_t st, bool cut_done = false, bool copies = true) {
     if (!cut_done) g->h_fin->passes[0] = g->h_fin->passes[1] = 0;
     if (cut_done) {
         // the cut closures ran batched with other grids
@@ -1664,6 +1670,7 @@ static mf_status finish_enqueue(mf_grid *g, cudaStream_t st, bool cut_done = fal
         CK(launch_reduction_cut((size_t)g->g.n, g->red_codes, g->smin, g->tset, st));
         ++g->launches;
     }
+    if (!copies) return MF_OK;
     CK(cudaMemcpyAsync(&g->h_fin->f0, g->st.flow0, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&g->h_fin->ft, g->st.flow_t, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&g->h_fin->c, g->c64, sizeof(Counters64), cudaMemcpyDeviceToHost, st));
@@ -1834,6 +1841,19 @@ mf_status mf_solve(mf_grid *g, const mf_opts *opts, mf_stats *stats) {
 }
 
 // ---- batched solve --------------------------------------------------------------
+// A warp per instance of a batch: st.ctr into the pinned mirror, the flow
+// parts and the stage counts into the pinned record of the finished solve.
+__global__ void batch_readback_kernel(const Inst *__restrict__ insts, int count) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= count) return;
+    const Inst &I = insts[i];
+    if (lane < kCtrWords) I.h_ctr[lane] = I.st.ctr[lane];
+    mf_grid::FinishHost *f = (mf_grid::FinishHost *)I.h_fin;
+    if (lane == kCtrWords) f->f0 = *I.st.flow0;
+    if (lane == kCtrWords + 1) f->ft = *I.st.flow_t;
+    if (lane == kCtrWords + 2) f->c = *I.c64;
+}
+
 struct BatchBufs {
     int *loop = nullptr;                   // graph loop state (kLoop* words)
     cudaStream_t cap_stream = nullptr;     // private capture stream of the graph loop
@@ -1886,14 +1906,13 @@ static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *ins
         J.st = h->st;
         J.conn = h->conn;
         J.scratch = h->cut_scratch;
+        J.hout = h->h_ctr_dv + kGlrLevels;  // the level count lands in the pinned mirror
         (h->ndim == 2 ? jobs2 : jobs3).push_back(J);
         glr.push_back(i);
     }
     cudaError_t eg = glr2d_batch(jobs2, glr2, s);
     if (eg == cudaSuccess) eg = glr3d_batch(jobs3, glr3, s);
     if (eg != cudaSuccess) return fail(g, MF_ECUDA, std::string("batched global relabel: ") + cudaGetErrorString(eg));
-    for (int i : glr)
-        CK(cudaMemcpyAsync(&grids[i]->h_ctr[kGlrLevels], &grids[i]->st.ctr[kGlrLevels], 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemsetAsync(any_dev, 0, sizeof(int), s));
     batch_relabel_end_kernel<<<(count + 255) / 256, 256, 0, s>>>(insts, done_dev, any_dev, count);
     CK(cudaGetLastError());
@@ -1908,10 +1927,10 @@ static mf_status batch_relabel(mf_grid *const *grids, int count, const Inst *ins
         const int levels = h->h_ctr[kGlrLevels];
         h->stats.global_relabels++;
         h->stats.relabel_levels += levels;
-        h->launches += 1;  // its masks; the batched levels, reset, finish and count launches are counted once below
     }
-    if (!jobs2.empty()) g->launches += 4;
-    if (!jobs3.empty()) g->launches += 4;
+    // per dimension: masks, levels, reset, finish, count and the level counts
+    if (!jobs2.empty()) g->launches += 6;
+    if (!jobs3.empty()) g->launches += 6;
     return MF_OK;
 }
 
@@ -2008,6 +2027,8 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
         hinst[i].st = h->st;
         hinst[i].c64 = h->c64;
         hinst[i].conn = h->conn;
+        hinst[i].h_ctr = h->h_ctr_dv;
+        hinst[i].h_fin = h->h_fin_dv;
         for (int r = 0; r < h->g.nreg; ++r) hregs.push_back(make_int2(i, r));
     }
     const int nregs = (int)hregs.size();
@@ -2177,14 +2198,15 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
     CK(cudaMemcpyAsync(hsweeps.data(), B.sweeps, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
     // error words of every instance, then (if the loop ended normally) the cut
     // extraction of every instance, all enqueued on the batch stream with one
-    // wait at the end
-    for (int i = 0; i < count; ++i)
-        CK(cudaMemcpyAsync(grids[i]->h_ctr, grids[i]->st.ctr, kCtrWords * 4, cudaMemcpyDeviceToHost, s));
+    // wait at the end; one launch writes every instance's counters, flow parts
+    // and stage counts into its pinned records
+    batch_readback_kernel<<<(count + 7) / 8, 256, 0, s>>>(B.insts, count);
+    CK(cudaGetLastError());
+    ++launches;
     if (rs == MF_OK) {
         // the cut closures of all grids with bit-mask cuts in one cooperative
         // launch per closure and dimension, then each grid's read-back
         std::vector<GlrJob2> j2, j3;
-        std::vector<int *> p2, p3;
         std::vector<char> batched(count, 0);
         for (int i = 0; i < count; ++i) {
             mf_grid *h = grids[i];
@@ -2196,19 +2218,18 @@ mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, 
             J.scratch = h->cut_scratch;
             J.smin = h->smin;
             J.smax = h->tset;
+            J.hout = h->h_fin_dv->passes;
             h->h_fin->passes[0] = h->h_fin->passes[1] = 0;
             (h->ndim == 2 ? j2 : j3).push_back(J);
-            (h->ndim == 2 ? p2 : p3).push_back(h->h_fin->passes);
-            h->launches += 2;  // its masks
             batched[i] = 1;
         }
-        cudaError_t ec = cut2d_batch(j2, B.glr2, p2.data(), s);
-        if (ec == cudaSuccess) ec = cut3d_batch(j3, B.glr3, p3.data(), s);
+        cudaError_t ec = cut2d_batch(j2, B.glr2, s);
+        if (ec == cudaSuccess) ec = cut3d_batch(j3, B.glr3, s);
         if (ec != cudaSuccess) return fail(g, MF_ECUDA, std::string("batched cut: ") + cudaGetErrorString(ec));
-        if (!j2.empty()) launches += 3;  // two closures and the bytes
-        if (!j3.empty()) launches += 3;
+        if (!j2.empty()) launches += 7;  // per closure: masks, passes, pass counts; then the bytes
+        if (!j3.empty()) launches += 7;
         for (int i = 0; i < count; ++i) {
-            mf_status st = finish_enqueue(grids[i], s, batched[i] != 0);
+            mf_status st = finish_enqueue(grids[i], s, batched[i] != 0, false);
             if (st != MF_OK) return fail(g, st, grids[i]->err);
         }
     }

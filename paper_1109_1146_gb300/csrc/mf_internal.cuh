@@ -171,6 +171,8 @@ struct Inst {
     DevState st;
     Counters64 *c64;
     int conn;   // stencil of the instance (batched fusion kernels are per connectivity)
+    int *h_ctr;      // device view of the pinned mirror of st.ctr
+    void *h_fin;     // device view of the pinned record of the finished solve
 };
 
 // reduction.cu: region reduction of Sec. 8 (class codes per vertex)
@@ -205,24 +207,31 @@ struct GlrJob2 {
     int W64, BY, unit0;              // derived: row words, 64-row blocks, first work unit
     unsigned long long *M, *A, *B;   // derived: masks, level sets / closure sets
     unsigned char *smin, *smax;      // batched cut: the byte outputs
+    int *hout;                       // device view of pinned host ints that receive the level
+                                     // count (relabel: [0]) or the closure passes (cut: [0], [1]); or NULL
 };
 // device tables of a batched relabel, grown as needed and reused
 struct GlrBatchBufs {
-    void *jobs = nullptr, *units = nullptr, *chunks = nullptr;
-    size_t jobs_cap = 0, units_cap = 0, chunks_cap = 0;
+    void *jobs = nullptr, *units = nullptr, *chunks = nullptr, *rows = nullptr;
+    size_t jobs_cap = 0, units_cap = 0, chunks_cap = 0, rows_cap = 0;
     int *any = nullptr;
     cudaError_t reserve(size_t jobs_bytes, size_t units_bytes, size_t chunks_bytes);
+    // (job, row chunk) units of the batched mask builds, uploaded on stream s
+    cudaError_t upload_rows(const std::vector<int2> &units, cudaStream_t s);
     ~GlrBatchBufs();
 };
+constexpr int kMaskRows = 16;  // grid rows per unit of a batched mask build
 // the relabel of every listed 2D grid (tiles 32 or 64 wide), enqueued without
 // waiting; each grid's levels land in its st.ctr[kGlrLevels]
 cudaError_t glr2d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, cudaStream_t s);
 cudaError_t glr3d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, cudaStream_t s);
 // both cut closures of every listed grid (2D; 3D with 32-wide tiles) and the
-// S_min / S_max bytes; h_passes[j] (pinned int[2] or NULL) receives the
-// passes of each closure asynchronously
-cudaError_t cut2d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, int *const *h_passes, cudaStream_t s);
-cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, int *const *h_passes, cudaStream_t s);
+// S_min / S_max bytes; the passes of each closure land in the job's hout
+cudaError_t cut2d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, cudaStream_t s);
+cudaError_t cut3d_batch(const std::vector<GlrJob2> &jobs, GlrBatchBufs &bb, cudaStream_t s);
+// one launch: hout[slot] = st.ctr[kGlrLevels] for every job of the uploaded
+// table that has an hout
+cudaError_t glr_batch_out(const GlrJob2 *jobs_dev, int njobs, int slot, cudaStream_t s);
 
 // devinfo.cu: per-device launch facts, cached per (kernel, device)
 int device_sms();  // SMs of the current device (1 if it cannot be queried)
