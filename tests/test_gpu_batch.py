@@ -59,6 +59,11 @@ def test_batch_matches_oracle_and_single_solves(kw):
             s1 = h.solve(opts)
             assert s1.sweeps == st.sweeps
             assert s1.discharges == st.discharges
+            # counters and level counts reach the host through the batch's
+            # own read-back launches: the same values as the single solve's
+            assert (s1.stages, s1.rounds, s1.discharged_vertices) == (st.stages, st.rounds, st.discharged_vertices)
+            assert (s1.global_relabels, s1.relabel_levels) == (st.global_relabels, st.relabel_levels)
+            assert st.cut_passes >= 2  # each of the two closures makes at least one pass
     for g in handles:
         g.close()
 
