@@ -1153,7 +1153,7 @@ mf_status mf_destroy(mf_grid *g) {
 
 // mf_set_caps in phases: the copies, the validation kernel, the read-back of
 // its flags (each enqueued on the grid's stream), then (after a wait) the
-// verdict.  A batch runs each phase for all grids before the next, so that
+// status.  A batch runs each phase for all grids before the next, so that
 // the copies follow one another on the copy engine instead of alternating
 // with the validation kernels.
 static mf_status set_caps_copies(mf_grid *g, const int32_t *cs, const int32_t *ct, const int32_t *nlink) {
@@ -1184,7 +1184,7 @@ static mf_status set_caps_enqueue(mf_grid *g, const int32_t *cs, const int32_t *
     if (st == MF_OK) st = set_caps_readback(g);
     return st;
 }
-static mf_status set_caps_verdict(mf_grid *g) {
+static mf_status set_caps_status(mf_grid *g) {
     const int f = g->h_ctr[kError];
     if (f & 1) return fail(g, MF_EINVAL, "negative capacity");
     if (f & 2) return fail(g, MF_EINVAL, "nonzero neighbour capacity leaving the grid");
@@ -1199,7 +1199,7 @@ mf_status mf_set_caps(mf_grid *g, const int32_t *cs, const int32_t *ct, const in
     mf_status st = set_caps_enqueue(g, cs, ct, nlink);
     if (st != MF_OK) return st;
     CK(cudaStreamSynchronize(g->stream));
-    return set_caps_verdict(g);
+    return set_caps_status(g);
 }
 
 // one wait per distinct stream of the grids
@@ -1314,7 +1314,7 @@ mf_status mf_set_caps_batch(mf_grid *const *grids, int count, const int32_t *con
             CK(cudaStreamSynchronize(g->stream));
             for (int i = 0; i < count; ++i) {
                 grids[i]->h_ctr[kError] = hflags[i];
-                mf_status st = set_caps_verdict(grids[i]);
+                mf_status st = set_caps_status(grids[i]);
                 if (st != MF_OK) {
                     if (grids[i] != g) fail(g, st, std::string("grid ") + std::to_string(i) + ": " + grids[i]->err);
                     return st;
@@ -1334,7 +1334,7 @@ mf_status mf_set_caps_batch(mf_grid *const *grids, int count, const int32_t *con
         }
     CK(sync_streams(grids, count));
     for (int i = 0; i < count; ++i) {
-        mf_status st = set_caps_verdict(grids[i]);
+        mf_status st = set_caps_status(grids[i]);
         if (st != MF_OK) {
             if (grids[i] != g) fail(g, st, std::string("grid ") + std::to_string(i) + ": " + grids[i]->err);
             return st;
