@@ -68,6 +68,38 @@ def test_batch_matches_oracle_and_single_solves(kw):
         g.close()
 
 
+@pytest.mark.parametrize("kw", [dict(global_relabel_period=2), dict(global_relabel_period=2, graph_loop=1)])
+def test_batch_with_instances_done_at_init(kw):
+    # grids with nothing to do (all capacities zero) or only terminal links
+    # (what Init leaves cannot move) finish before the first sweep; they must
+    # keep exact results while the others sweep, relabel and cut beside them
+    insts = [(grids.random_grid((70, 40, 1), 4, 1, cmax=0, tmax=0), (32, 32, 1)),
+             (grids.random_grid((66, 50, 1), 8, 2, cmax=0, tmax=50), (64, 64, 1)),
+             (grids.segmentation_2d(150, 120, 3, conn=4), (32, 32, 1)),
+             (grids.random_grid((40, 30, 20), 6, 4, cmax=0, tmax=0), (32, 8, 4)),
+             (grids.volume_3d(45, 30, 21, 5), (32, 8, 4)),
+             (grids.random_grid((33, 17, 9), 6, 6, cmax=0, tmax=40), (32, 4, 4))]
+    opts = default_opts(**kw)
+    handles = []
+    for inst, tile in insts:
+        g = Grid(inst.dims, inst.conn, tile=tile)
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        handles.append(g)
+    stats = mf.solve_batch(handles, opts)
+    for (inst, tile), g, st in zip(insts, handles, stats):
+        got = {"flow": g.flow_value(), "smin": g.get_cut(0), "smax": g.get_cut(1)}
+        got["res"], got["tres"], got["exc"] = g.get_residual()
+        assert_parity(inst, got)
+        assert st.flow_value == got["flow"]
+        with Grid(inst.dims, inst.conn, tile=tile) as h:
+            h.set_caps(inst.cs, inst.ct, inst.nlink)
+            s1 = h.solve(opts)
+            assert (s1.sweeps, s1.discharges, s1.stages) == (st.sweeps, st.discharges, st.stages)
+    assert stats[0].flow_value == 0 and stats[3].flow_value == 0
+    for g in handles:
+        g.close()
+
+
 def test_batch_of_one_and_repeat():
     inst = grids.config0(3)
     ref = oracle.solve_instance(inst)
