@@ -290,7 +290,9 @@ mf_status mf_region_reduction(mf_grid *g, const int32_t tile[3], uint8_t *codes,
  * sweeps as alone.  With opts->warm_start = 1 each grid starts from its
  * projected preflow if mf_warm_start succeeded on it, and from Init
  * otherwise.  With opts->graph_loop = 1 the sweep loop of the batch is one
- * CUDA graph.
+ * CUDA graph.  MF_ESWEEPLIMIT if instances are still active after
+ * opts->max_sweeps sweeps (no cut is extracted; the grids stay usable and the
+ * next solve starts again from Init).
  */
 mf_status mf_solve_batch(mf_grid *const *grids, int count, const mf_opts *opts, mf_stats *stats);
 

@@ -100,6 +100,27 @@ def test_batch_with_instances_done_at_init(kw):
         g.close()
 
 
+@pytest.mark.parametrize("graph_loop", [0, 1])
+def test_batch_sweep_cap_then_exact_solve(graph_loop):
+    # a sweep cap below what the instances need ends the batch with
+    # MF_ESWEEPLIMIT; the grids stay usable and a full batched solve is exact
+    insts = [(grids.segmentation_2d(150, 120, 7, conn=4), (32, 32, 1)),
+             (grids.volume_3d(45, 30, 21, 8), (32, 8, 4))]
+    handles = []
+    for inst, tile in insts:
+        g = Grid(inst.dims, inst.conn, tile=tile)
+        g.set_caps(inst.cs, inst.ct, inst.nlink)
+        handles.append(g)
+    with pytest.raises(mf.MFError) as err:
+        mf.solve_batch(handles, default_opts(max_sweeps=1, graph_loop=graph_loop))
+    assert err.value.status == mf.MF_ESWEEPLIMIT
+    mf.solve_batch(handles, default_opts(graph_loop=graph_loop))
+    for (inst, tile), g in zip(insts, handles):
+        got = {"flow": g.flow_value(), "smin": g.get_cut(0), "smax": g.get_cut(1)}
+        assert_parity(inst, got)
+        g.close()
+
+
 def test_batch_of_one_and_repeat():
     inst = grids.config0(3)
     ref = oracle.solve_instance(inst)
