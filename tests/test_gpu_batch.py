@@ -114,6 +114,9 @@ def test_batch_sweep_cap_then_exact_solve(graph_loop):
     with pytest.raises(mf.MFError) as err:
         mf.solve_batch(handles, default_opts(max_sweeps=1, graph_loop=graph_loop))
     assert err.value.status == mf.MF_ESWEEPLIMIT
+    with pytest.raises(mf.MFError) as err:  # no finished solve, so no cut to read
+        mf.get_cuts_batch(handles, 0)
+    assert err.value.status == mf.MF_ESTATE
     mf.solve_batch(handles, default_opts(graph_loop=graph_loop))
     for (inst, tile), g in zip(insts, handles):
         got = {"flow": g.flow_value(), "smin": g.get_cut(0), "smax": g.get_cut(1)}
