@@ -2463,6 +2463,7 @@ mf_status mf_get_flow(mf_grid *g, int32_t *residual_out) {
 mf_status mf_get_labels(mf_grid *g, int32_t *lab, int32_t *d_inf, int on_device) {
     if (!g) return fail(nullptr, MF_EINVAL, "grid is NULL");
     if (d_inf) *d_inf = g->g.dinf;
+    (void)on_device;  // cudaMemcpyDefault tells host from device buffers itself
     if (lab) {
         if (!g->begun) return fail(g, MF_ESTATE, "no solve");
         CK(cudaMemcpyAsync(lab, g->st.lab, (size_t)g->g.n * 4, cudaMemcpyDefault, g->stream));

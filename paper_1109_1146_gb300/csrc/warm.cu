@@ -283,8 +283,8 @@ __global__ void warm_init_kernel(const Geom g, const DevState st, const int *cs,
 }
 
 static int nblk(const Geom &g) {
-    const size_t b = ((size_t)g.n + 255) / 256;
-    return (int)(b < device_sms() * 16 ? (b ? b : 1) : device_sms() * 16);
+    const size_t b = ((size_t)g.n + 255) / 256, cap = (size_t)device_sms() * 16;
+    return (int)(b < cap ? (b ? b : 1) : cap);
 }
 
 #define WARM_DISPATCH(conn, kern, ...)                                            \
