@@ -94,7 +94,6 @@ def test_paper_synthetic_family():
     assert (nl[1, :39, :] == 150).all() and (nl[1, 39, :] == 0).all()
     again = grids.paper_synthetic(60, 40, 3, strength=150)
     assert (again.cs == inst.cs).all() and (again.ct == inst.ct).all()
-    import pytest
     for bad in (6, 10, 32):
         with pytest.raises(ValueError):
             grids.paper_synthetic(10, 10, 0, connectivity=bad)
