@@ -73,7 +73,7 @@ def batch_instances(batch_seed=0, count=0, threads=None, only=None, kind="all"):
     """The uneven batch, generated on host threads (numpy releases the GIL);
     kind "2d" / "3d" keeps only those members."""
     from gen import grids
-    shapes = grids.config4_shapes(batch_seed)
+    shapes = grids.uneven_batch_shapes(batch_seed)
     idx = list(range(len(shapes))) if only is None else list(only)
     if kind != "all":
         idx = [i for i in idx if (shapes[i][2] == 1) == (kind == "2d")]
@@ -109,7 +109,7 @@ def kernel_name(conn, tile, batch=False):
 
 def make_instance(seed, side=SIDE):
     from gen import grids
-    return grids.config1(seed=seed, side=side)
+    return grids.seg2d_2048_c8_hard(seed=seed, side=side)
 
 
 def directed_arcs(dims, conn):
@@ -266,7 +266,7 @@ def roofline_of(stats, insts, tiles, batch):
             "discharge_ms_by_kernel": share}
 
 
-def run_config4(args):
+def run_uneven_batch(args):
     """The batched-solve workload: batched (value), batched with the learned
     warm start, and plain one-by-one solves of the same 512 instances."""
     import numpy as np
@@ -407,13 +407,14 @@ def run_config4(args):
     del dcs, dct, dnl
 
     extras = {}
-    if rank == 0 and "c1" in args.extras.split(","):
+    extra_keys = args.extras.split(",")
+    if rank == 0 and "seg2048" in extra_keys:
         extras["seg2d_2048_c8"] = run_single_extra(args, make_instance(0), stream, dev)
-    if rank == 0 and "c1h" in args.extras.split(","):
+    if rank == 0 and "seg2048_host" in extra_keys:
         extras["seg2d_2048_c8_grace_state"] = run_single_extra(args, make_instance(0), stream, dev, host_state=True)
-    if rank == 0 and "c2" in args.extras:
+    if rank == 0 and "vol512" in extra_keys:
         from gen import grids
-        extras["vol3d_512x512x384"] = run_single_extra(args, grids.config2(0), stream, dev)
+        extras["vol3d_512x512x384"] = run_single_extra(args, grids.vol3d_512x512x384(0), stream, dev)
 
     if rank != 0:
         if ws > 1:
@@ -670,7 +671,7 @@ def run_batch_warm(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     count = args.batch_count or 64
-    insts = [grids.config3(warmstart.EVAL_SEED0 + i) for i in range(count)]
+    insts = [grids.seg2d_1024_c4_mu(warmstart.EVAL_SEED0 + i) for i in range(count)]
     stream = torch.cuda.current_stream()
     weights = os.path.join(ROOT, "paper_1109_1146_gb300", "weights", "warm_seg2d_1024_c4.npy")
     net = warmstart.load_network(weights)
@@ -800,14 +801,14 @@ def run_relabel(args):
 
     glr = ["none", "glr2", "glr4", "glr8", "br1", "br2", "pd", "pd+br1", "br1+glr8"]
     no_glr = ["none", "br1", "br2", "pd", "pd+br1"]
-    cases = [("seg2d 2048x2048 8-connected (config of the headline)", lambda: grids.config1(0), (32, 32, 1), glr),
+    cases = [("seg2d 2048x2048 8-connected (config of the headline)", lambda: grids.seg2d_2048_c8_hard(0), (32, 32, 1), glr),
              ("seg2d 1024x1024 4-connected, held-out seed of the warm-start set",
-              lambda: grids.config3(warmstart.EVAL_SEED0), (32, 32, 1), glr),
-             ("seg2d 256x256 4-connected", lambda: grids.config0(0), (32, 32, 1), glr),
-             ("volume 256x256x128 6-connected", lambda: grids.config2(0, dims=(256, 256, 128)), (32, 8, 4), glr),
+              lambda: grids.seg2d_1024_c4_mu(warmstart.EVAL_SEED0), (32, 32, 1), glr),
+             ("seg2d 256x256 4-connected", lambda: grids.seg2d_256_c4(0), (32, 32, 1), glr),
+             ("volume 256x256x128 6-connected", lambda: grids.vol3d_512x512x384(0, dims=(256, 256, 128)), (32, 8, 4), glr),
              ("volume 256x256x128 6-connected, 16^3 tiles (no global relabel)",
-              lambda: grids.config2(0, dims=(256, 256, 128)), (16, 16, 16), no_glr),
-             ("volume 512x512x384 6-connected", lambda: grids.config2(0), (32, 8, 4),
+              lambda: grids.vol3d_512x512x384(0, dims=(256, 256, 128)), (16, 16, 16), no_glr),
+             ("volume 512x512x384 6-connected", lambda: grids.vol3d_512x512x384(0), (32, 8, 4),
               ["glr4", "br1", "br2", "br1+glr8"])]
     if args.relabel_case >= 0:
         cases = [cases[args.relabel_case]]
@@ -850,7 +851,7 @@ def run_reference(args):
     if rank != 0:
         return
     from gen import grids
-    shapes = grids.config4_shapes(0)
+    shapes = grids.uneven_batch_shapes(0)
     count = args.batch_count or len(shapes)
     thr = host_threads()
     steps = max(1, args.steps)
@@ -888,16 +889,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="config4", choices=["config4", "seg2048", "batch_warm", "relabel", "prd"])
+    ap.add_argument("--workload", default="batch512", choices=["batch512", "seg2048", "batch_warm", "relabel", "prd"])
     ap.add_argument("--prd-seeds", type=int, default=3, help="prd workload: instances per point")
     ap.add_argument("--batch-count", type=int, default=0, help="first N instances of the batch (0 = all 512)")
     ap.add_argument("--batch-kind", default="all", choices=["all", "2d", "3d"],
                     help="batched line: all members, or only the 2D / 3D ones")
     ap.add_argument("--aux-steps", type=int, default=3,
                     help="timed steps of the warm, plain and end-to-end modes of the batched line (<= --steps)")
-    ap.add_argument("--extras", default="c1,c1h,c2",
-                    help="extra keys of the batched line: c1 = 2048^2 8-connected grid, c1h = the same with its "
-                         "state in Grace memory, c2 = 512x512x384 volume")
+    ap.add_argument("--extras", default="seg2048,seg2048_host,vol512",
+                    help="extra keys of the batched line: seg2048 = 2048^2 8-connected grid, seg2048_host = the same "
+                         "with its state in Grace memory, vol512 = 512x512x384 volume; none = no extra")
     ap.add_argument("--relabel-case", type=int, default=-1, help="relabel workload: only this instance (index)")
     ap.add_argument("--relabel-schedule", default="", help="relabel workload: only this schedule")
     args = ap.parse_args()
@@ -905,8 +906,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "config4":
-        run_config4(args)
+    elif args.workload == "batch512":
+        run_uneven_batch(args)
     elif args.workload == "batch_warm":
         run_batch_warm(args)
     elif args.workload == "relabel":

@@ -338,24 +338,24 @@ def paper_synthetic(X: int, Y: int, seed: int, strength: int = 150, connectivity
 
 # --- the five named workloads ------------------------------------------------
 
-def config0(seed: int = 0) -> GridInstance:
+def seg2d_256_c4(seed: int = 0) -> GridInstance:
     """256x256 4-connected segmentation grid (65,536 vertices; 64x64 regions)."""
     return segmentation_2d(256, 256, seed, conn=4, name=f"seg2d_256x256_c4_s{seed}")
 
 
-def config1(seed: int = 0, side: int = 2048) -> GridInstance:
+def seg2d_2048_c8_hard(seed: int = 0, side: int = 2048) -> GridInstance:
     """2048x2048 8-connected segmentation grid, 5% hard seeds at 10^6."""
     return segmentation_2d(side, side, seed, conn=8, hard_seed_frac=0.05,
                            name=f"seg2d_{side}x{side}_c8_hard_s{seed}")
 
 
-def config2(seed: int = 0, dims=(512, 512, 384)) -> GridInstance:
+def vol3d_512x512x384(seed: int = 0, dims=(512, 512, 384)) -> GridInstance:
     """512x512x384 6-connected Perlin volume (1.0e8 vertices; 16^3 regions)."""
     X, Y, Z = dims
     return volume_3d(X, Y, Z, seed, name=f"vol3d_{X}x{Y}x{Z}_s{seed}")
 
 
-def config3(seed: int, side: int = 1024) -> GridInstance:
+def seg2d_1024_c4_mu(seed: int, side: int = 1024) -> GridInstance:
     """1024x1024 4-connected segmentation grid, mu_fg and mu_bg ~ U[60, 200]
     per instance (drawn from SplitMix64(seed)); t-links round(|I - mu|)."""
     h = _hash(seed, 4242, np.arange(2))
@@ -364,7 +364,7 @@ def config3(seed: int, side: int = 1024) -> GridInstance:
                            name=f"seg2d_{side}x{side}_c4_mu_s{seed}")
 
 
-def config4_shapes(seed: int = 0, n2d: int = 384, n3d: int = 128):
+def uneven_batch_shapes(seed: int = 0, n2d: int = 384, n3d: int = 128):
     """Shapes of the uneven batch: 2D sides ~ U{64..1024}, 3D sides ~ U{48..128}."""
     rng = np.random.Generator(np.random.PCG64(seed))
     s2 = rng.integers(64, 1025, n2d)

@@ -130,7 +130,7 @@ def load_network(path: str, conn: int = 4) -> CNN:
 def _make(seed_side):
     from gen import grids
     seed, side = seed_side
-    return grids.config3(seed, side=side)
+    return grids.seg2d_1024_c4_mu(seed, side=side)
 
 
 def _instances(pool, seeds, side):

@@ -17,13 +17,13 @@ def test_splitmix64_reference_values():
 
 
 def test_deterministic():
-    a, b = grids.config0(3), grids.config0(3)
+    a, b = grids.seg2d_256_c4(3), grids.seg2d_256_c4(3)
     assert grids.instance_digest(a) == grids.instance_digest(b)
-    assert grids.instance_digest(a) != grids.instance_digest(grids.config0(4))
+    assert grids.instance_digest(a) != grids.instance_digest(grids.seg2d_256_c4(4))
 
 
-def test_config0_recipe():
-    g = grids.config0(0)
+def test_seg2d_256_recipe():
+    g = grids.seg2d_256_c4(0)
     assert g.dims == (256, 256, 1) and g.conn == 4 and g.nlink.shape == (2, 65536)
     I = grids.value_noise_2d(256, 256, 0).ravel()
     assert I.min() == 0 and I.max() == 255
@@ -38,7 +38,7 @@ def test_config0_recipe():
     assert (g.nlink[1].reshape(256, 256)[-1, :] == 0).all()
 
 
-def test_config1_hard_seeds_small():
+def test_hard_seeds_small():
     g = grids.segmentation_2d(256, 256, 1, conn=8, hard_seed_frac=0.05)
     hard = (g.cs == 10 ** 6) | (g.ct == 10 ** 6)
     assert 0.04 < hard.mean() < 0.06
@@ -66,14 +66,14 @@ def test_volume_small():
     assert (nl[0, :, :, -1] == 0).all() and (nl[1, :, -1, :] == 0).all() and (nl[2, -1] == 0).all()
 
 
-def test_config3_mu_range():
+def test_seg2d_1024_mu_range():
     for s in range(5):
-        g = grids.config3(s, side=64)
+        g = grids.seg2d_1024_c4_mu(s, side=64)
         assert g.cs.max() <= 200 and g.ct.max() <= 200
 
 
-def test_config4_shapes():
-    sh = grids.config4_shapes(0)
+def test_uneven_batch_shapes():
+    sh = grids.uneven_batch_shapes(0)
     assert len(sh) == 512
     assert all(64 <= s[0] <= 1024 and s[2] == 1 for s in sh[:384])
     assert all(48 <= s[0] <= 128 and s[0] == s[2] for s in sh[384:])

@@ -125,7 +125,7 @@ def test_batch_sweep_cap_then_exact_solve(graph_loop):
 
 
 def test_batch_of_one_and_repeat():
-    inst = grids.config0(3)
+    inst = grids.seg2d_256_c4(3)
     ref = oracle.solve_instance(inst)
     with Grid(inst.dims, 4) as g:
         g.set_caps(inst.cs, inst.ct, inst.nlink)
@@ -136,7 +136,7 @@ def test_batch_of_one_and_repeat():
 
 
 def test_batch_rejects_bad_input():
-    inst = grids.config0(0)
+    inst = grids.seg2d_256_c4(0)
     a = Grid(inst.dims, 4)
     with pytest.raises(mf.MFError):
         mf.solve_batch([a])  # no capacities yet

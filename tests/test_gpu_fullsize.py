@@ -22,7 +22,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
 def test_bench_workload_full_size():
-    inst = grids.config1(0)
+    inst = grids.seg2d_2048_c8_hard(0)
     ref = oracle.solve_instance(inst)
     got = gpu_solve(inst, tile=(32, 32, 1), opts=opts(global_relabel_period=8))
     assert_parity(inst, got, ref=ref)
@@ -35,7 +35,7 @@ def test_bench_workload_full_size():
 
 
 def test_volume_full_size_certified():
-    inst = grids.config2(0)
+    inst = grids.vol3d_512x512x384(0)
     got = gpu_solve(inst)  # default 3D tile (32x8x8, bit-parallel discharge)
     ok, msg, info = oracle.verify(inst.dims, 6, inst.cs, inst.ct, inst.nlink, got["res"], got["tres"], got["exc"],
                                   got["flow"], got["smin"], got["smax"])

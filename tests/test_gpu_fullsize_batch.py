@@ -32,7 +32,7 @@ TILES3 = [(32, 8, 4), (32, 8, 8), (32, 16, 8), (32, 4, 4), (32, 8, 2)]
 
 
 def _batch_share():
-    shapes = grids.config4_shapes(0)
+    shapes = grids.uneven_batch_shapes(0)
     n2 = [i for i, s in enumerate(shapes) if s[2] == 1]
     n3 = [i for i, s in enumerate(shapes) if s[2] > 1]
     big2 = max(n2, key=lambda i: shapes[i][0])
@@ -92,7 +92,7 @@ def test_uneven_batch_share_cold_and_warm_vs_oracle():
 
 
 def test_warm_start_1024_vs_dinic():
-    inst = grids.config3(warmstart.EVAL_SEED0 + 5)
+    inst = grids.seg2d_1024_c4_mu(warmstart.EVAL_SEED0 + 5)
     ref = oracle.solve_instance(inst)
     net = warmstart.load_network(WEIGHTS)
     with Grid(inst.dims, 4) as g:

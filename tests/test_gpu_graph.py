@@ -35,7 +35,7 @@ def test_graph_loop_equals_host_loop(make, tile, kw):
 
 
 def test_graph_loop_sweep_cap_and_reuse():
-    inst = grids.config0(3)
+    inst = grids.seg2d_256_c4(3)
     with Grid(inst.dims, inst.conn, tile=(64, 64, 1)) as g:
         g.set_caps(inst.cs, inst.ct, inst.nlink)
         with pytest.raises(MFError, match="SWEEPLIMIT"):

@@ -20,8 +20,8 @@ def _bound_ok(inst, got, tile):
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_config0_workload(seed):
-    inst = grids.config0(seed)
+def test_seg2d_256_workload(seed):
+    inst = grids.seg2d_256_c4(seed)
     got = gpu_solve(inst, tile=(64, 64, 1))
     assert_parity(inst, got)
     _bound_ok(inst, got, (64, 64, 1))
@@ -137,7 +137,7 @@ def test_options_keep_exact_results(kw, conn, tile):
 
 def test_repeat_solve_same_handle():
     from paper_1109_1146_gb300 import Grid
-    inst = grids.config0(5)
+    inst = grids.seg2d_256_c4(5)
     ref = oracle.solve_instance(inst)
     with Grid(inst.dims, 4) as g:
         g.set_caps(inst.cs, inst.ct, inst.nlink)

@@ -97,7 +97,7 @@ def test_prd_in_a_batch_and_against_ard():
 
 
 def test_prd_rejects_warm_start_and_reduction():
-    inst = grids.config0(0)
+    inst = grids.seg2d_256_c4(0)
     with Grid(inst.dims, 4) as g:
         g.set_caps(inst.cs, inst.ct, inst.nlink)
         for kw in (dict(region_reduction=1), dict(kernel_variant=3)):

@@ -86,7 +86,7 @@ def test_reduction_in_a_batch_is_exact():
 
 
 def test_reduction_rejects_warm_start_and_oversized_tiles():
-    inst = grids.config0(0)
+    inst = grids.seg2d_256_c4(0)
     with Grid(inst.dims, 4, tile=(64, 64, 1)) as g:
         with pytest.raises(mf.MFError) as ei:
             g.region_reduction()  # before set_caps

@@ -104,7 +104,7 @@ def test_projection_of_the_exact_flows_is_immediate(conn):
 
 @pytest.mark.parametrize("noise", [0.0, 0.3, 3.0])
 def test_noisy_predictions_project_and_solve_exactly(noise):
-    inst = grids.config3(7, side=128)
+    inst = grids.seg2d_1024_c4_mu(7, side=128)
     t, _ = _solved_targets(inst)
     gen = torch.Generator(device=DEV).manual_seed(1)
     pred = t + noise * torch.randn(t.shape, generator=gen, device=DEV)
@@ -153,7 +153,7 @@ def test_trained_network_saves_sweeps():
     net = warmstart.load_network(WEIGHTS)
     cold_sw, warm_sw = [], []
     for seed in range(warmstart.EVAL_SEED0, warmstart.EVAL_SEED0 + 32):
-        inst = grids.config3(seed)
+        inst = grids.seg2d_1024_c4_mu(seed)
         with Grid(inst.dims, 4) as g:
             g.set_caps(inst.cs, inst.ct, inst.nlink)
             cold = g.solve()
@@ -170,7 +170,7 @@ def test_trained_network_saves_sweeps():
 
 
 def test_untrained_network_gives_exact_results():
-    inst = grids.config3(warmstart.EVAL_SEED0 + 77, side=512)
+    inst = grids.seg2d_1024_c4_mu(warmstart.EVAL_SEED0 + 77, side=512)
     ref = oracle.solve_instance(inst)
     net = mf.CNN(channels=6, seed=99)
     with Grid(inst.dims, 4) as g:
@@ -184,7 +184,7 @@ def test_batched_warm_start_is_exact():
     # a batch of 2D 4-connected grids, half of them warm-started from noisy
     # solution flows, plus one 3D grid that stays cold: exact results for all
     from paper_1109_1146_gb300 import mf as mfmod
-    insts = [grids.config3(30 + i, side=96 + 32 * i) for i in range(4)] + [grids.volume_3d(40, 30, 20, 3)]
+    insts = [grids.seg2d_1024_c4_mu(30 + i, side=96 + 32 * i) for i in range(4)] + [grids.volume_3d(40, 30, 20, 3)]
     handles = []
     for k, inst in enumerate(insts):
         g = Grid(inst.dims, inst.conn)
@@ -249,7 +249,7 @@ def test_projection_round_cap_falls_back_to_cold():
     # a prediction whose trims need many rounds, with a cap of one round:
     # mf_warm_start reports MF_EROUNDLIMIT, the warm solve starts cold, and the
     # result is exact
-    inst = grids.config3(11, side=128)
+    inst = grids.seg2d_1024_c4_mu(11, side=128)
     t, _ = _solved_targets(inst)
     pred = t * 3.0  # large over-predictions cascade through many trim rounds
     net = mf.CNN(channels=6, seed=1)
@@ -270,7 +270,7 @@ def test_batched_projection_matches_single_projections():
     # mf_warm_start_batch enqueues every projection and waits once: the same
     # preflows (hence the same warm solves) as mf_warm_start one grid at a time,
     # a grid with no prediction stays cold, results exact against the oracle
-    insts = [grids.config3(60 + i, side=80 + 24 * i) for i in range(3)]
+    insts = [grids.seg2d_1024_c4_mu(60 + i, side=80 + 24 * i) for i in range(3)]
     preds = []
     for k, inst in enumerate(insts):
         t, _ = _solved_targets(inst)

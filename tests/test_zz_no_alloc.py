@@ -35,7 +35,7 @@ def _solve_and_residual(inst, torch, dev):
 
 @pytest.mark.parametrize("make", [
     lambda: grids.segmentation_2d(300, 170, 3, conn=8, hard_seed_frac=0.05),
-    lambda: grids.config0(1),
+    lambda: grids.seg2d_256_c4(1),
     lambda: grids.random_grid((129, 65, 1), 4, 7, cmax=20, tmax=40),
 ])
 def test_noalloc_cut_matches_solver_cut(make):
