@@ -801,7 +801,7 @@ def run_relabel(args):
 
     glr = ["none", "glr2", "glr4", "glr8", "br1", "br2", "pd", "pd+br1", "br1+glr8"]
     no_glr = ["none", "br1", "br2", "pd", "pd+br1"]
-    cases = [("seg2d 2048x2048 8-connected (config of the headline)", lambda: grids.seg2d_2048_c8_hard(0), (32, 32, 1), glr),
+    cases = [("seg2d 2048x2048 8-connected, 5% hard seeds", lambda: grids.seg2d_2048_c8_hard(0), (32, 32, 1), glr),
              ("seg2d 1024x1024 4-connected, held-out seed of the warm-start set",
               lambda: grids.seg2d_1024_c4_mu(warmstart.EVAL_SEED0), (32, 32, 1), glr),
              ("seg2d 256x256 4-connected", lambda: grids.seg2d_256_c4(0), (32, 32, 1), glr),
